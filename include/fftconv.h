@@ -1,0 +1,168 @@
+/*
+ * fftconv.h -- C ABI of the B300 (sm_103a) FFT-convolution CG solver.
+ *
+ * The library solves the fibre-bundle system of Gjerden, "Making the case of
+ * GPUs in courses on computational physics" (arXiv:1305.3625):
+ *
+ *   Eq. 1a-1b give f_i = -k_i (u_i - D) and u_i = sum_j G_ij f_j; Eq. 2 is
+ *   (I + K G) f = K D.  Multiplied by K^-1 it becomes the symmetric positive
+ *   definite system (C + S) x = b with S = diag(s_i), s_i = 1/k_i, b = D, and
+ *   C the coupling operator (C x)_i = sum_j G(r_i - r_j) x_j over the open
+ *   L x L grid, G(r) = 1/(pi r) for r > 0 and G(0) = 4 ln(1 + sqrt 2)/pi
+ *   (Eq. 1c with a = 1 and (1 - nu^2)/E = 1).
+ *
+ *   C is applied as in Section 3 (Eq. 3, Listing 3): zero-pad x to the M x M
+ *   grid (M = smallest power of two >= 2L), forward 2D FFT, multiply by the
+ *   precomputed kernel spectrum, inverse 2D FFT, keep the [0, L)^2 corner.
+ *   The solve is unpreconditioned conjugate gradients (Listing 2).
+ *
+ * Conventions for every entry point:
+ *   - Fields are row-major L x L arrays, flat index i = iy*L + ix.
+ *   - "device pointer" means memory of the current CUDA device (cudaMalloc,
+ *     or a torch CUDA tensor).  The library never frees caller memory.
+ *   - Plans and servers own their device workspaces and free them on
+ *     destroy.  A plan may be used by one host thread at a time.
+ *   - Every call returns an int status: FC_OK (0) or a negative FC_E* code.
+ *     No call aborts the process or throws across the ABI.
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).
+ */
+#ifndef FFTCONV_H
+#define FFTCONV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fc_stream_t; /* identical to cudaStream_t */
+
+/* status codes */
+#define FC_OK 0
+#define FC_EINVAL (-1)   /* bad argument: size, null pointer, precision, mode  */
+#define FC_ENOMEM (-2)   /* a device or pinned-host allocation failed          */
+#define FC_EBUDGET (-3)  /* a request can never fit the server's memory budget */
+#define FC_ENOCONV (-4)  /* CG stopped at max_iter above the tolerance         */
+#define FC_ENANINF (-5)  /* NaN or Inf met in the data or the iteration        */
+#define FC_ETIMEOUT (-6) /* a bounded wait ran out                              */
+#define FC_ECUDA (-7)    /* a CUDA runtime call failed (see fc_last_error)     */
+#define FC_ENOTFOUND (-8)/* unknown server ticket                               */
+
+/* precision flags (bit set) */
+#define FC_F32 1
+#define FC_F64 2
+
+/* solve modes */
+#define FC_MODE_F64 0   /* plain FP64: FFTs, vectors and reductions in FP64   */
+#define FC_MODE_MIXED 1 /* FP32 FFTs and vectors, FP64 reductions, FP64 true
+                           residual driving iterative refinement             */
+
+typedef struct fftconv_plan fftconv_plan;
+typedef struct cg_server cg_server;
+
+/* Launch-shape overrides; all zero = built-in choices. Reserved for tuning. */
+typedef struct cg_tune {
+    int reserved[8];
+} cg_tune;
+
+typedef struct cg_opts {
+    double rtol;       /* stop when ||P(b - A x)||_2 <= rtol ||P b||_2, judged on the
+                          FP64 recomputed residual                              */
+    int max_iter;      /* cap on CG iterations (matrix-vector products), all cycles */
+    int mode;          /* FC_MODE_F64 or FC_MODE_MIXED                           */
+    int refine_every;  /* cap on inner iterations between two true residuals
+                          (0: 100000)                                           */
+    int max_refine;    /* cap on true-residual evaluations (0: 60)              */
+    double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 1e-4)    */
+    int x0_zero;       /* 1: start from x = 0 and ignore the input x            */
+    int reserved;
+} cg_opts;
+
+typedef struct cg_result {
+    int status;            /* FC_OK, FC_ENOCONV or FC_ENANINF                    */
+    int iters;             /* CG iterations (products in the inner loops)        */
+    int refinements;       /* true-residual evaluations (FP64 products)          */
+    int reserved;
+    double true_rel_resid; /* ||P(b - A x)|| / ||P b|| from the last FP64 residual */
+    double bnorm;          /* ||P b||                                           */
+} cg_result;
+
+/* Library version string and the last CUDA error text of this thread. */
+const char *fc_version(void);
+const char *fc_last_error(void);
+
+/*
+ * fftconv_plan_create -- set up C for an L x L grid (Section 3: the transform
+ * of G is static and computed at initialisation, Listing 3).
+ *   p     out: new plan (host pointer to a handle).
+ *   L     1 <= L <= 4096.  M = smallest power of two >= 2L.
+ *   prec  FC_F32, FC_F64 or FC_F32|FC_F64 (the mixed solve needs both).
+ *   tune  NULL or overrides.
+ * Builds, on the current device: the twiddle tables, the circulant kernel
+ * table, its 2D FFT in FP64 scaled by 1/M^2 (real, since G is even), kept as
+ * the (M/2+1)^2 quarter in each requested precision, and all workspaces.
+ * Synchronous.  Errors: FC_EINVAL (L, prec), FC_ENOMEM, FC_ECUDA, FC_ENANINF
+ * (spectrum not real to 1e-12).
+ */
+int fftconv_plan_create(fftconv_plan **p, int L, int prec, const cg_tune *tune);
+
+/* Free a plan and its device memory (synchronises the device first). */
+int fftconv_plan_destroy(fftconv_plan *p);
+
+/* Query a plan: side L, padded side M, precision flags, device bytes held. */
+int fftconv_plan_info(const fftconv_plan *p, int *L, int *M, int *prec, size_t *device_bytes);
+
+/*
+ * fftconv_apply -- y = C x (Listing 3: cpyComplex, FFT, elementMult, inverse
+ * FFT, cpyReal), three kernel passes on stream.
+ *   x, y  device pointers to L*L values (float for an FC_F32 apply, double
+ *         for FC_F64); x and y must not overlap.
+ * A plan created with FC_F32 only applies in FP32, one with FC_F64 only in
+ * FP64; a plan with both applies in FP32 here (use fftconv_apply_prec).
+ * Asynchronous.  Errors: FC_EINVAL, FC_ECUDA.
+ */
+int fftconv_apply(fftconv_plan *p, const void *x, void *y, fc_stream_t stream);
+
+/* As fftconv_apply with the precision given explicitly (FC_F32 or FC_F64). */
+int fftconv_apply_prec(fftconv_plan *p, int prec, const void *x, void *y, fc_stream_t stream);
+
+/*
+ * cg_solve -- solve P (C + S) P x = P b by CG (Listing 2), P the projection
+ * on active fibres (mask), x = 0 off the active set.
+ *   s     device, L*L doubles: diagonal s_i > 0 (compliance 1/k_i, Eq. 1a).
+ *   b     device, L*L doubles: right-hand side (the displacement D, Eq. 2).
+ *   x     device, L*L doubles: in = warm start (unless o->x0_zero), out = solution.
+ *   mask  device, L*L bytes, 1 = active, or NULL (all active).
+ *   o     host pointer to options (NULL: rtol 1e-10, FC_MODE_F64).
+ *   r     host pointer receiving the result (may be NULL).
+ * FC_MODE_F64 needs an FC_F64 plan; FC_MODE_MIXED needs FC_F32|FC_F64.
+ * The whole solve is one CUDA graph launch on stream (device-side while
+ * loops; no host round trip per iteration).  The call blocks the host
+ * thread until the solve ends, then returns the status also stored in r.
+ * Errors: FC_EINVAL, FC_ECUDA; FC_ENOCONV / FC_ENANINF from the iteration
+ * (x then holds the last iterate).
+ */
+int cg_solve(fftconv_plan *p, const double *s, const double *b, double *x, const uint8_t *mask,
+             const cg_opts *o, cg_result *r, fc_stream_t stream);
+
+/*
+ * fc_masked_step -- one quasi-static breaking step (Section 2: for each step
+ * the displacement is set, the forces computed, and over-strained bonds
+ * break).  The load is linear in D, so the first fibre to fail as D grows is
+ * i* = argmax over active i of |x_i| / t_i (ties to the lowest index); it is
+ * removed: mask[i*] = 0, x[i*] = 0.
+ *   t        device, L*L doubles, thresholds > 0.
+ *   mask     device, L*L bytes, updated in place.
+ *   x        device, L*L doubles (the last solution), updated in place.
+ *   removed  device pointer to one int64: receives i* (-1 if no active site).
+ * Asynchronous.  Errors: FC_EINVAL, FC_ECUDA.
+ */
+int fc_masked_step(fftconv_plan *p, const double *t, uint8_t *mask, double *x, int64_t *removed,
+                   fc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTCONV_H */

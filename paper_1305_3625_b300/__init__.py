@@ -1,0 +1,205 @@
+"""Python binding of the fftconv C ABI (include/fftconv.h).
+
+Argument marshalling only: every step of the FFT convolution and of the CG
+solve runs in the CUDA kernels of libfftconv.so.  Tensors are torch CUDA
+tensors (torch provides device memory and streams); their data pointers and
+the current stream are passed straight to the C entry points of the same
+names.  If the shared library is missing this module raises at import: there
+is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+FC_OK = 0
+FC_EINVAL = -1
+FC_ENOMEM = -2
+FC_EBUDGET = -3
+FC_ENOCONV = -4
+FC_ENANINF = -5
+FC_ETIMEOUT = -6
+FC_ECUDA = -7
+FC_ENOTFOUND = -8
+FC_F32 = 1
+FC_F64 = 2
+FC_MODE_F64 = 0
+FC_MODE_MIXED = 1
+
+STATUS_NAMES = {0: "FC_OK", -1: "FC_EINVAL", -2: "FC_ENOMEM", -3: "FC_EBUDGET", -4: "FC_ENOCONV",
+                -5: "FC_ENANINF", -6: "FC_ETIMEOUT", -7: "FC_ECUDA", -8: "FC_ENOTFOUND"}
+
+
+class FcError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = f"{what}: {STATUS_NAMES.get(code, code)}"
+        err = _lib.fc_last_error().decode() if _lib is not None else ""
+        if err:
+            msg += f" ({err})"
+        super().__init__(msg)
+
+
+class cg_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
+                ("refine_every", ctypes.c_int), ("max_refine", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("x0_zero", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class cg_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("bnorm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"status": self.status, "iters": self.iters, "refinements": self.refinements,
+                "true_rel_resid": self.true_rel_resid, "bnorm": self.bnorm}
+
+
+LIB_PATH = _build.LIB
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_1305_3625_b300.build` "
+                          "(or __graft_entry__.build()) first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    lib.fc_version.restype = ctypes.c_char_p
+    lib.fc_last_error.restype = ctypes.c_char_p
+    lib.fftconv_plan_create.argtypes = [ctypes.POINTER(vp), i, i, vp]
+    lib.fftconv_plan_destroy.argtypes = [vp]
+    lib.fftconv_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
+                                      ctypes.POINTER(sz)]
+    lib.fftconv_apply.argtypes = [vp, vp, vp, vp]
+    lib.fftconv_apply_prec.argtypes = [vp, i, vp, vp, vp]
+    lib.cg_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
+    lib.fc_masked_step.argtypes = [vp, vp, vp, vp, vp, vp]
+    return lib
+
+
+_lib = _load()
+
+
+def fc_version() -> str:
+    return _lib.fc_version().decode()
+
+
+def fc_last_error() -> str:
+    return _lib.fc_last_error().decode()
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t, dtype, n, name):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{name} must be contiguous with {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owning handle of an fftconv_plan (destroyed with the object)."""
+
+    def __init__(self, handle, L, prec):
+        self._h = handle
+        self.L = L
+        self.prec = prec
+        Li, Mi, pi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nb = ctypes.c_size_t()
+        _lib.fftconv_plan_info(self._h, ctypes.byref(Li), ctypes.byref(Mi), ctypes.byref(pi),
+                               ctypes.byref(nb))
+        self.M = Mi.value
+        self.device_bytes = nb.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.fftconv_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fftconv_plan_create(L: int, prec: int = FC_F32 | FC_F64) -> Plan:
+    h = ctypes.c_void_p()
+    rc = _lib.fftconv_plan_create(ctypes.byref(h), int(L), int(prec), None)
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_plan_create")
+    return Plan(h, int(L), int(prec))
+
+
+def fftconv_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def fftconv_apply_prec(plan: Plan, prec: int, x, y, stream=None) -> None:
+    dt = torch.float32 if prec == FC_F32 else torch.float64
+    n = plan.L * plan.L
+    rc = _lib.fftconv_apply_prec(plan.handle, int(prec), _ptr(x, dt, n, "x"), _ptr(y, dt, n, "y"),
+                                 _stream(stream))
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_apply_prec")
+
+
+def fftconv_apply(plan: Plan, x, y, stream=None) -> None:
+    prec = FC_F32 if x.dtype == torch.float32 else FC_F64
+    fftconv_apply_prec(plan, prec, x, y, stream)
+
+
+def cg_solve(plan: Plan, s, b, x, mask=None, rtol: float = 1e-10, mode: int = FC_MODE_F64,
+             max_iter: int = 0, refine_every: int = 0, max_refine: int = 0,
+             inner_rtol: float = 0.0, x0_zero: bool = False, stream=None, check: bool = False) -> dict:
+    """Solve P (C + S) P x = P b in place in x; returns the cg_result fields."""
+    n = plan.L * plan.L
+    o = cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode),
+                refine_every=int(refine_every), max_refine=int(max_refine),
+                inner_rtol=float(inner_rtol), x0_zero=int(bool(x0_zero)), reserved=0)
+    r = cg_result()
+    rc = _lib.cg_solve(plan.handle, _ptr(s, torch.float64, n, "s"), _ptr(b, torch.float64, n, "b"),
+                       _ptr(x, torch.float64, n, "x"), _ptr(mask, torch.uint8, n, "mask"),
+                       ctypes.byref(o), ctypes.byref(r), _stream(stream))
+    if rc in (FC_EINVAL, FC_ECUDA, FC_ENOMEM) or (check and rc != FC_OK):
+        raise FcError(rc, "cg_solve")
+    out = r.as_dict()
+    out["rc"] = rc
+    return out
+
+
+def fc_masked_step(plan: Plan, t, mask, x, removed, stream=None) -> None:
+    n = plan.L * plan.L
+    rc = _lib.fc_masked_step(plan.handle, _ptr(t, torch.float64, n, "t"),
+                             _ptr(mask, torch.uint8, n, "mask"), _ptr(x, torch.float64, n, "x"),
+                             _ptr(removed, torch.int64, 1, "removed"), _stream(stream))
+    if rc != FC_OK:
+        raise FcError(rc, "fc_masked_step")
+
+
+def fftconv_plan_info(plan: Plan) -> dict:
+    Li, Mi, pi = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nb = ctypes.c_size_t()
+    rc = _lib.fftconv_plan_info(plan.handle, ctypes.byref(Li), ctypes.byref(Mi), ctypes.byref(pi),
+                                ctypes.byref(nb))
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_plan_info")
+    return {"L": Li.value, "M": Mi.value, "prec": pi.value, "device_bytes": nb.value}

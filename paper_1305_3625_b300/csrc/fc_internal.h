@@ -1,0 +1,146 @@
+// Internal device-side state and kernel argument blocks of the fftconv
+// library.  Not part of the C ABI (include/fftconv.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fftconv.h"
+
+namespace fc {
+
+template <typename T>
+struct cpx;
+
+// Scalars of one solve, resident in device memory.  Each field is written by
+// exactly one pass and read by later passes only, so no kernel reads a field
+// that another block of the same kernel may be writing.
+struct CgState {
+    double rr;           // r.r of the current inner residual (pass A, direct sum)
+    double alpha, beta;  // CG step length and direction update of the last product
+    double tol2;         // inner stop: recursive r.r <= tol2
+    double sigma;        // norm of the true residual the inner run started from
+    double rr64, bb;     // last true residual r.r and masked b.b (FP64)
+    double rtol2;        // target: rr64 <= rtol2 * bb
+    double inner_rtol2;  // mixed: inner target relative to the unit right-hand side
+    int iter;            // products spent in inner loops (all cycles)
+    int max_iter;
+    int cycle_iter, cycle_max;
+    int cycles, max_cycles;  // true-residual evaluations
+    int first;               // 1: the next pass A starts a new inner run (p = r)
+    int inner_done;          // 0 running, 1 converged, 2 cap reached, 3 breakdown
+    int status;              // FC_OK, FC_ENOCONV or FC_ENANINF once finished
+    int mixed;               // 1: inner runs in FP32 on the scaled residual
+    int finished;
+    int pad_;
+    unsigned cntA, cntC;  // last-block counters of passes A and C
+};
+
+enum { RF_PLAIN = 0, RF_CG = 1, RF_XUPD = 2 };
+enum { RI_PLAIN = 0, RI_CG = 1, RI_RESID = 2 };
+
+template <typename T>
+struct RowFwdArgs {
+    int L, mode;
+    const T* x;                  // RF_PLAIN: input field
+    T *cx, *cr, *cp;             // RF_CG: CG vectors updated in place
+    const T* cq;                 // RF_CG: last product
+    const double* r64;           // RF_CG, mixed: first pass starts from r64/sigma
+    double* x64;                 // RF_XUPD: FP64 iterate (updated, then transformed)
+    const float* d32;            // RF_XUPD: correction from the last inner run (or null)
+    const uint8_t* mask;         // RF_XUPD: x is zeroed off the active set (null: all active)
+    CgState* st;
+    double* part;                // per-block partial sums
+    cpx<T>* Z;                   // L x M intermediate
+    const cpx<T>* tw;            // exp(-2 pi i m/M), m < M
+};
+
+template <typename T>
+struct ColArgs {
+    int L;
+    cpx<T>* Z;
+    const T* Gq;                 // (M/2+1)^2 real spectrum quarter, 1/M^2 folded in
+    const cpx<T>* tw;
+};
+
+template <typename T>
+struct RowInvArgs {
+    int L, mode;
+    T* y;                        // RI_PLAIN output
+    const T* s;                  // RI_CG: diagonal
+    const T* cp;
+    const T* cr;
+    T* cq;                       // RI_CG: product q = P (C p + s p)
+    const uint8_t* mask;         // 1 = active fibre (null: all active)
+    const double *x64, *b64, *s64;
+    double* r64;                 // RI_RESID: r = P (b - C x - s x)
+    CgState* st;
+    double* part;
+    unsigned long long h_outer, h_inner;  // graph conditional handles (0: none)
+    const cpx<T>* Z;
+    const cpx<T>* tw;
+};
+
+// Decide the CG step after the product q = A p of one iteration of Listing 2.
+// With pq = p.q, rq = r.q, qq = q.q: alpha = rr/pq and the new residual norm
+// |r - alpha q|^2 = rr - 2 alpha rq + alpha^2 qq, which gives beta without a
+// second pass over the vectors.
+__device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq, double qq,
+                                               unsigned long long h_inner) {
+    const double rr = st->rr;
+    double alpha = rr / pq;
+    double rrn = rr - 2.0 * alpha * rq + alpha * alpha * qq;
+    if (rrn < 0.0) rrn = 0.0;
+    int d = 0;
+    if (!(pq > 0.0) || !isfinite(alpha) || !isfinite(rrn)) {
+        d = 3;
+        alpha = 0.0;
+    } else if (rrn <= st->tol2) {
+        d = 1;
+    }
+    st->iter += 1;
+    st->cycle_iter += 1;
+    if (d == 0 && (st->iter >= st->max_iter || st->cycle_iter >= st->cycle_max)) d = 2;
+    st->alpha = alpha;
+    st->beta = rr > 0.0 ? rrn / rr : 0.0;
+    st->first = 0;
+    st->inner_done = d;
+    if (h_inner) cudaGraphSetConditional(h_inner, d == 0 ? 1u : 0u);
+}
+
+// Decide the outer loop after a true residual r = P (b - A x): stop when
+// |r| <= rtol |P b|, otherwise start a new inner run from it.
+__device__ __forceinline__ void refine_decide(CgState* st, double rr64, double bb,
+                                              unsigned long long h_outer, unsigned long long h_inner) {
+    st->rr64 = rr64;
+    st->bb = bb;
+    st->cycles += 1;
+    int go = 0;
+    if (!isfinite(rr64) || !isfinite(bb)) {
+        st->status = FC_ENANINF;
+    } else if (bb == 0.0 || rr64 <= st->rtol2 * bb) {
+        st->status = FC_OK;
+    } else if (st->iter >= st->max_iter || st->cycles > st->max_cycles) {
+        st->status = FC_ENOCONV;
+    } else {
+        go = 1;
+    }
+    if (go) {
+        st->first = 1;
+        st->cycle_iter = 0;
+        st->inner_done = 0;
+        if (st->mixed) {
+            st->sigma = sqrt(rr64);
+            st->tol2 = st->inner_rtol2;
+        } else {
+            st->sigma = 1.0;
+            st->tol2 = st->rtol2 * bb;
+        }
+    }
+    if (!go) st->first = 1;  // no inner run follows: the final update is a no-op
+    st->finished = go ? 0 : 1;
+    if (h_outer) cudaGraphSetConditional(h_outer, (unsigned)go);
+    if (h_inner) cudaGraphSetConditional(h_inner, (unsigned)go);
+}
+
+}  // namespace fc

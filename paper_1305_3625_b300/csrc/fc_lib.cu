@@ -1,0 +1,807 @@
+// fftconv library: plans, the FFT-convolution operator and the CG solve
+// behind the C ABI of include/fftconv.h.
+//
+// One plan holds, for one grid side L, everything the hot path touches:
+// twiddle tables, the (M/2+1)^2 quarter of the kernel spectrum, the L x M
+// intermediate, the CG vectors and the device-resident solve state.  A solve
+// is one CUDA graph with two nested device-side while loops (outer: FP64 true
+// residual and refinement; inner: CG iterations), so the host launches once
+// per solve and reads one status block at the end.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <mutex>
+#include <new>
+
+#include "fc_passes.cuh"
+
+using namespace fc;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int set_cuda_err(cudaError_t e, const char* what) {
+    snprintf(g_err, sizeof(g_err), "%s: %s", what, cudaGetErrorString(e));
+    return FC_ECUDA;
+}
+
+#define FC_CK(call)                                        \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return set_cuda_err(e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------- utility kernels --
+
+// exp(-2 pi i m / M) in FP64 (CUDA's sincospi) and rounded to FP32.
+__global__ void k_twiddles(int M, cpx<double>* tw64, cpx<float>* tw32) {
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double s, c;
+    sincospi(2.0 * (double)m / (double)M, &s, &c);
+    if (tw64) tw64[m] = cpx<double>{c, -s};
+    if (tw32) tw32[m] = cpx<float>{(float)c, (float)-s};
+}
+
+// Green's function of Eq. 1c (a = 1, (1-nu^2)/E = 1): point form 1/(pi r) and
+// the exact self term 4 ln(1 + sqrt 2)/pi.
+__device__ double green(long dx, long dy) {
+    if (dx == 0 && dy == 0) return 4.0 * log1p(sqrt(2.0)) / 3.14159265358979323846;
+    return 1.0 / (3.14159265358979323846 * sqrt((double)(dx * dx + dy * dy)));
+}
+
+// Circulant embedding on the M x M grid: index j < L is offset j, index
+// j > M - L is offset j - M; indices in between are reached by no pair of
+// sites and hold 0.
+__global__ void k_kernel_table(int L, int M, cpx<double>* K) {
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)M * M) return;
+    int jy = (int)(idx / M), jx = (int)(idx % M);
+    bool okx = jx < L || jx > M - L, oky = jy < L || jy > M - L;
+    long dx = jx < L ? jx : (long)jx - M, dy = jy < L ? jy : (long)jy - M;
+    K[idx] = cpx<double>{(okx && oky) ? green(dx, dy) : 0.0, 0.0};
+}
+
+// Unpruned forward FFT of every row of an M x M grid (spectrum set-up only).
+template <int M>
+__global__ void __launch_bounds__(Cfg<double, M>::ROW_THREADS) k_rows_full(cpx<double>* K, const cpx<double>* tw) {
+    using C = cpx<double>;
+    constexpr int E = Cfg<double, M>::E, G = Cfg<double, M>::G, RB = Cfg<double, M>::RB;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int j = threadIdx.x % G, c = threadIdx.x / G, row = blockIdx.x * RB + c;
+    const bool ok = row < M;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = ok ? K[(size_t)row * M + j + e * G] : C{0, 0};
+    fft_stages<double, M, false>(v, j, sm + c * seg_len(M), tw);
+    if (ok)
+#pragma unroll
+        for (int e = 0; e < E; ++e) K[(size_t)row * M + j + e * G] = v[e];
+}
+
+// Unpruned forward FFT of every column of an M x M grid.
+template <int M>
+__global__ void __launch_bounds__(Cfg<double, M>::COL_THREADS) k_cols_full(cpx<double>* K, const cpx<double>* tw) {
+    using C = cpx<double>;
+    constexpr int E = Cfg<double, M>::E, G = Cfg<double, M>::G, CB = Cfg<double, M>::CB;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int c = threadIdx.x % CB, j = threadIdx.x / CB, col = blockIdx.x * CB + c;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = K[(size_t)(j + e * G) * M + col];
+    fft_stages<double, M, false>(v, j, sm + c * seg_len(M), tw);
+#pragma unroll
+    for (int e = 0; e < E; ++e) K[(size_t)(j + e * G) * M + col] = v[e];
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
+    // non-negative doubles order like their bit patterns
+    atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// Keep the (M/2+1)^2 quarter of Re(FFT2(k))/M^2; track max |Im| and max |Re|.
+__global__ void k_spectrum_quarter(int M, const cpx<double>* K, double* gq64, float* gq32, double* maxes) {
+    const int Q = M / 2 + 1;
+    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double mi = 0.0, mr = 0.0;
+    if (idx < (size_t)M * M) {
+        const double scale = 1.0 / ((double)M * (double)M);
+        cpx<double> z = K[idx];
+        mi = fabs(z.y) * scale;
+        mr = fabs(z.x) * scale;
+        int fy = (int)(idx / M), fx = (int)(idx % M);
+        if (fy < Q && fx < Q) {
+            double g = z.x * scale;
+            if (gq64) gq64[(size_t)fy * Q + fx] = g;
+            if (gq32) gq32[(size_t)fy * Q + fx] = (float)g;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        mi = fmax(mi, __shfl_down_sync(0xffffffffu, mi, off));
+        mr = fmax(mr, __shfl_down_sync(0xffffffffu, mr, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(maxes + 0, mi);
+        atomic_max_nonneg(maxes + 1, mr);
+    }
+}
+
+// Last step of an inner CG run: x += alpha p (the residual is recomputed).
+template <typename T>
+__global__ void k_cg_final(long N, const CgState* st, T* x, const T* p) {
+    if (st->first) return;
+    const T alpha = (T)st->alpha;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+        x[i] += alpha * p[i];
+}
+
+__global__ void k_f64_to_f32(long N, const double* a, float* b) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+__global__ void k_fill_u8(long N, uint8_t* m, uint8_t v) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) m[i] = v;
+}
+
+struct ArgmaxCtl {
+    unsigned cnt;
+    int pad;
+};
+
+// One quasi-static breaking step: i* = argmax over active i of |x_i|/t_i (ties
+// to the lowest index), then mask[i*] = 0 and x[i*] = 0.  The last block to
+// finish reduces the per-block winners in block order.
+__global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, uint8_t* mask, double* x,
+                                                       int64_t* removed, double* pv, long long* pi,
+                                                       ArgmaxCtl* ctl) {
+    __shared__ double sv[256];
+    __shared__ long long si[256];
+    __shared__ bool is_last;
+    double bv = -1.0;
+    long long bi = -1;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        if (!mask[i]) continue;
+        double v = fabs(x[i]) / t[i];
+        if (v > bv || (v == bv && (bi < 0 || i < bi))) {
+            bv = v;
+            bi = i;
+        }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            double ov = sv[threadIdx.x + s];
+            long long oi = si[threadIdx.x + s];
+            double mv = sv[threadIdx.x];
+            long long mi = si[threadIdx.x];
+            if (oi >= 0 && (mi < 0 || ov > mv || (ov == mv && oi < mi))) {
+                sv[threadIdx.x] = ov;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = sv[0];
+        pi[blockIdx.x] = si[0];
+        __threadfence();
+        is_last = atomicAdd(&ctl->cnt, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double gv = -1.0;
+        long long gi = -1;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            double ov = __ldcg(pv + b);
+            long long oi = __ldcg(pi + b);
+            if (oi >= 0 && (gi < 0 || ov > gv || (ov == gv && oi < gi))) {
+                gv = ov;
+                gi = oi;
+            }
+        }
+        *removed = gi;
+        if (gi >= 0) {
+            mask[gi] = 0;
+            x[gi] = 0.0;
+        }
+        ctl->cnt = 0u;
+    }
+}
+
+// ------------------------------------------------------- dispatch tables --
+
+struct KernSet {
+    const void* row_fwd = nullptr;
+    const void* col_conv = nullptr;
+    const void* row_inv = nullptr;
+    const void* rows_full = nullptr;
+    const void* cols_full = nullptr;
+    int rb = 0, cb = 0, row_threads = 0, col_threads = 0;
+    size_t row_smem = 0, col_smem = 0;
+};
+
+template <typename T, int M>
+KernSet make_set() {
+    using Cf = Cfg<T, M>;
+    KernSet s;
+    s.row_fwd = (const void*)k_row_fwd<T, M>;
+    s.col_conv = (const void*)k_col_conv<T, M>;
+    s.row_inv = (const void*)k_row_inv<T, M>;
+    if constexpr (sizeof(T) == 8) {
+        s.rows_full = (const void*)k_rows_full<M>;
+        s.cols_full = (const void*)k_cols_full<M>;
+    }
+    s.rb = Cf::RB;
+    s.cb = Cf::CB;
+    s.row_threads = Cf::ROW_THREADS;
+    s.col_threads = Cf::COL_THREADS;
+    s.row_smem = Cf::ROW_SMEM;
+    s.col_smem = Cf::COL_SMEM;
+    return s;
+}
+
+template <typename T>
+bool get_set(int M, KernSet* s) {
+    switch (M) {
+        case 2: *s = make_set<T, 2>(); return true;
+        case 4: *s = make_set<T, 4>(); return true;
+        case 8: *s = make_set<T, 8>(); return true;
+        case 16: *s = make_set<T, 16>(); return true;
+        case 32: *s = make_set<T, 32>(); return true;
+        case 64: *s = make_set<T, 64>(); return true;
+        case 128: *s = make_set<T, 128>(); return true;
+        case 256: *s = make_set<T, 256>(); return true;
+        case 512: *s = make_set<T, 512>(); return true;
+        case 1024: *s = make_set<T, 1024>(); return true;
+        case 2048: *s = make_set<T, 2048>(); return true;
+        case 4096: *s = make_set<T, 4096>(); return true;
+        case 8192: *s = make_set<T, 8192>(); return true;
+        default: return false;
+    }
+}
+
+int set_smem_attrs(const KernSet& k) {
+    const void* fr[3] = {k.row_fwd, k.row_inv, k.rows_full};
+    for (const void* f : fr)
+        if (f && k.row_smem > 48 * 1024)
+            FC_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.row_smem));
+    const void* fc_[2] = {k.col_conv, k.cols_full};
+    for (const void* f : fc_)
+        if (f && k.col_smem > 48 * 1024)
+            FC_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.col_smem));
+    return FC_OK;
+}
+
+int grid_1d(long n, int threads) {
+    long g = (n + threads - 1) / threads;
+    if (g > 148L * 16) g = 148L * 16;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan --
+
+struct PrecRes {
+    bool on = false;
+    KernSet k;
+    void* Z = nullptr;   // cpx<T>[L*M]
+    void* tw = nullptr;  // cpx<T>[M]
+    void* Gq = nullptr;  // T[(M/2+1)^2]
+};
+
+struct fftconv_plan {
+    int L = 0, M = 0, prec = 0, dev = 0;
+    long N = 0;
+    size_t bytes = 0;
+    PrecRes p32, p64;
+    // solve workspace (FP64 side)
+    double *x64 = nullptr, *r64 = nullptr, *p64v = nullptr, *q64 = nullptr, *b64 = nullptr, *s64 = nullptr;
+    uint8_t* mask = nullptr;
+    // solve workspace (FP32 side, mixed mode)
+    float *d32 = nullptr, *r32 = nullptr, *p32v = nullptr, *q32 = nullptr, *s32 = nullptr;
+    CgState* st = nullptr;
+    CgState* st_host = nullptr;  // pinned
+    double* part = nullptr;
+    double* am_v = nullptr;
+    long long* am_i = nullptr;
+    ArgmaxCtl* am_ctl = nullptr;
+    int am_grid = 0;
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+};
+
+namespace {
+
+int dalloc(fftconv_plan* p, void** ptr, size_t bytes) {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        set_cuda_err(e, "cudaMalloc");
+        return FC_ENOMEM;
+    }
+    p->bytes += bytes;
+    return FC_OK;
+}
+
+void plan_free(fftconv_plan* p) {
+    if (!p) return;
+    for (int m = 0; m < 2; ++m) {
+        if (p->gexec[m]) cudaGraphExecDestroy(p->gexec[m]);
+        if (p->graph[m]) cudaGraphDestroy(p->graph[m]);
+    }
+    void* ptrs[] = {p->p32.Z, p->p32.tw, p->p32.Gq, p->p64.Z, p->p64.tw, p->p64.Gq, p->x64, p->r64,
+                    p->p64v, p->q64, p->b64, p->s64, p->mask, p->d32, p->r32, p->p32v, p->q32, p->s32,
+                    p->st, p->part, p->am_v, p->am_i, p->am_ctl};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (p->st_host) cudaFreeHost(p->st_host);
+    delete p;
+}
+
+template <typename T>
+int launch(const void* f, int grid, int threads, size_t smem, cudaStream_t s, T& args) {
+    void* kp[1] = {(void*)&args};
+    FC_CK(cudaLaunchKernel(f, dim3(grid), dim3(threads), kp, smem, s));
+    return FC_OK;
+}
+
+int row_grid(const fftconv_plan* p, const KernSet& k) { return (p->L + k.rb - 1) / k.rb; }
+
+}  // namespace
+
+extern "C" const char* fc_version(void) { return "fftconv-b300 0.1 (sm_103a)"; }
+extern "C" const char* fc_last_error(void) { return g_err; }
+
+extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg_tune* tune) {
+    (void)tune;
+    if (!out) return FC_EINVAL;
+    *out = nullptr;
+    if (L < 1 || L > 4096 || prec < 1 || prec > 3) return FC_EINVAL;
+    fftconv_plan* p = new (std::nothrow) fftconv_plan();
+    if (!p) return FC_ENOMEM;
+    p->L = L;
+    p->prec = prec;
+    p->M = 2;
+    while (p->M < 2 * L) p->M *= 2;
+    p->N = (long)L * L;
+    const int M = p->M;
+    const long N = p->N;
+    const int Q = M / 2 + 1;
+    int rc = FC_OK;
+    cpx<double>* K = nullptr;
+    double* maxes = nullptr;
+    double hmax[2] = {0, 0};
+    cudaError_t e;
+#define FC_TRY(x)                     \
+    do {                              \
+        rc = (x);                     \
+        if (rc != FC_OK) goto fail;   \
+    } while (0)
+#define FC_TRYC(x)                                       \
+    do {                                                 \
+        e = (x);                                         \
+        if (e != cudaSuccess) {                          \
+            rc = set_cuda_err(e, #x);                    \
+            goto fail;                                   \
+        }                                                \
+    } while (0)
+    FC_TRYC(cudaGetDevice(&p->dev));
+    // both precisions need FP64 set-up: the spectrum is built in FP64
+    p->p64.on = true;
+    p->p32.on = (prec & FC_F32) != 0;
+    if (!get_set<double>(M, &p->p64.k) || !get_set<float>(M, &p->p32.k)) {
+        rc = FC_EINVAL;
+        goto fail;
+    }
+    FC_TRY(set_smem_attrs(p->p64.k));
+    if (p->p32.on) FC_TRY(set_smem_attrs(p->p32.k));
+    FC_TRY(dalloc(p, &p->p64.tw, sizeof(cpx<double>) * M));
+    FC_TRY(dalloc(p, &p->p64.Gq, sizeof(double) * (size_t)Q * Q));
+    if (p->p32.on) {
+        FC_TRY(dalloc(p, &p->p32.tw, sizeof(cpx<float>) * M));
+        FC_TRY(dalloc(p, &p->p32.Gq, sizeof(float) * (size_t)Q * Q));
+    }
+    // spectrum: kernel table -> unpruned FP64 2D FFT -> quarter / M^2
+    e = cudaMalloc(&K, sizeof(cpx<double>) * (size_t)M * M);
+    if (e != cudaSuccess) {
+        rc = FC_ENOMEM;
+        set_cuda_err(e, "cudaMalloc(spectrum grid)");
+        goto fail;
+    }
+    FC_TRYC(cudaMalloc(&maxes, 2 * sizeof(double)));
+    FC_TRYC(cudaMemset(maxes, 0, 2 * sizeof(double)));
+    k_twiddles<<<(M + 255) / 256, 256>>>(M, (cpx<double>*)p->p64.tw, (cpx<float>*)p->p32.tw);
+    FC_TRYC(cudaGetLastError());
+    {
+        size_t MM = (size_t)M * M;
+        k_kernel_table<<<(unsigned)((MM + 255) / 256), 256>>>(L, M, K);
+        FC_TRYC(cudaGetLastError());
+        const KernSet& k = p->p64.k;
+        void* a1[2] = {(void*)&K, (void*)&p->p64.tw};
+        FC_TRYC(cudaLaunchKernel(k.rows_full, dim3((M + k.rb - 1) / k.rb), dim3(k.row_threads), a1, k.row_smem, 0));
+        FC_TRYC(cudaLaunchKernel(k.cols_full, dim3(M / k.cb), dim3(k.col_threads), a1, k.col_smem, 0));
+        k_spectrum_quarter<<<(unsigned)((MM + 255) / 256), 256>>>(M, K, (double*)p->p64.Gq, (float*)p->p32.Gq,
+                                                                   maxes);
+        FC_TRYC(cudaGetLastError());
+        FC_TRYC(cudaMemcpy(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost));
+    }
+    cudaFree(K);
+    K = nullptr;
+    cudaFree(maxes);
+    maxes = nullptr;
+    if (!(hmax[0] <= 1e-12 * hmax[1])) {
+        snprintf(g_err, sizeof(g_err), "kernel spectrum not real: max|Im| %.3e, max|Re| %.3e", hmax[0], hmax[1]);
+        rc = FC_ENANINF;
+        goto fail;
+    }
+    if (!(prec & FC_F64)) {
+        // an FP32-only plan keeps no FP64 spectrum or intermediate
+    }
+    // intermediates and solve workspace
+    if (prec & FC_F64) FC_TRY(dalloc(p, &p->p64.Z, sizeof(cpx<double>) * (size_t)L * M));
+    if (p->p32.on) FC_TRY(dalloc(p, &p->p32.Z, sizeof(cpx<float>) * (size_t)L * M));
+    if (prec & FC_F64) {
+        FC_TRY(dalloc(p, (void**)&p->x64, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->r64, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->p64v, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->q64, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->b64, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->s64, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->mask, N));
+        if (p->p32.on) {
+            FC_TRY(dalloc(p, (void**)&p->d32, sizeof(float) * N));
+            FC_TRY(dalloc(p, (void**)&p->r32, sizeof(float) * N));
+            FC_TRY(dalloc(p, (void**)&p->p32v, sizeof(float) * N));
+            FC_TRY(dalloc(p, (void**)&p->q32, sizeof(float) * N));
+            FC_TRY(dalloc(p, (void**)&p->s32, sizeof(float) * N));
+        }
+    }
+    FC_TRY(dalloc(p, (void**)&p->st, sizeof(CgState)));
+    FC_TRYC(cudaMemset(p->st, 0, sizeof(CgState)));
+    {
+        int g = L;  // row passes never use more blocks than rows
+        FC_TRY(dalloc(p, (void**)&p->part, sizeof(double) * 3 * (size_t)(g + 1)));
+        p->am_grid = grid_1d(N, 256);
+        FC_TRY(dalloc(p, (void**)&p->am_v, sizeof(double) * p->am_grid));
+        FC_TRY(dalloc(p, (void**)&p->am_i, sizeof(long long) * p->am_grid));
+        FC_TRY(dalloc(p, (void**)&p->am_ctl, sizeof(ArgmaxCtl)));
+        FC_TRYC(cudaMemset(p->am_ctl, 0, sizeof(ArgmaxCtl)));
+    }
+    if (!(prec & FC_F64)) {
+        // FP32-only plan: drop the FP64 tables once the FP32 ones exist
+        cudaFree(p->p64.tw);
+        cudaFree(p->p64.Gq);
+        p->bytes -= sizeof(cpx<double>) * M + sizeof(double) * (size_t)Q * Q;
+        p->p64.tw = p->p64.Gq = nullptr;
+        p->p64.on = false;
+    }
+    FC_TRYC(cudaMallocHost(&p->st_host, sizeof(CgState)));
+    FC_TRYC(cudaDeviceSynchronize());
+    *out = p;
+    return FC_OK;
+fail:
+    if (K) cudaFree(K);
+    if (maxes) cudaFree(maxes);
+    plan_free(p);
+    return rc;
+#undef FC_TRY
+#undef FC_TRYC
+}
+
+extern "C" int fftconv_plan_destroy(fftconv_plan* p) {
+    if (!p) return FC_EINVAL;
+    cudaDeviceSynchronize();
+    plan_free(p);
+    return FC_OK;
+}
+
+extern "C" int fftconv_plan_info(const fftconv_plan* p, int* L, int* M, int* prec, size_t* bytes) {
+    if (!p) return FC_EINVAL;
+    if (L) *L = p->L;
+    if (M) *M = p->M;
+    if (prec) *prec = p->prec;
+    if (bytes) *bytes = p->bytes;
+    return FC_OK;
+}
+
+namespace {
+
+template <typename T>
+int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
+    const KernSet& k = R.k;
+    RowFwdArgs<T> a{};
+    a.L = p->L;
+    a.mode = RF_PLAIN;
+    a.x = x;
+    a.st = p->st;
+    a.part = p->part;
+    a.Z = (cpx<T>*)R.Z;
+    a.tw = (const cpx<T>*)R.tw;
+    int rc = launch(k.row_fwd, row_grid(p, k), k.row_threads, k.row_smem, s, a);
+    if (rc) return rc;
+    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
+    rc = launch(k.col_conv, p->M / k.cb, k.col_threads, k.col_smem, s, b);
+    if (rc) return rc;
+    RowInvArgs<T> c{};
+    c.L = p->L;
+    c.mode = RI_PLAIN;
+    c.y = y;
+    c.st = p->st;
+    c.part = p->part;
+    c.Z = (const cpx<T>*)R.Z;
+    c.tw = (const cpx<T>*)R.tw;
+    return launch(k.row_inv, row_grid(p, k), k.row_threads, k.row_smem, s, c);
+}
+
+}  // namespace
+
+extern "C" int fftconv_apply_prec(fftconv_plan* p, int prec, const void* x, void* y, fc_stream_t stream) {
+    if (!p || !x || !y) return FC_EINVAL;
+    if (prec == FC_F32 && p->p32.on && p->p32.Z)
+        return apply_t<float>(p, p->p32, (const float*)x, (float*)y, (cudaStream_t)stream);
+    if (prec == FC_F64 && (p->prec & FC_F64))
+        return apply_t<double>(p, p->p64, (const double*)x, (double*)y, (cudaStream_t)stream);
+    return FC_EINVAL;
+}
+
+extern "C" int fftconv_apply(fftconv_plan* p, const void* x, void* y, fc_stream_t stream) {
+    if (!p) return FC_EINVAL;
+    return fftconv_apply_prec(p, (p->prec & FC_F32) ? FC_F32 : FC_F64, x, y, stream);
+}
+
+// ------------------------------------------------------------- CG graph --
+
+namespace {
+
+struct GraphBuilder {
+    int rc = FC_OK;
+    template <typename... A>
+    cudaGraphNode_t kernel(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const void* f, int grid, int threads,
+                           size_t smem, const A&... args) {
+        cudaGraphNode_t n = nullptr;
+        if (rc) return n;
+        cudaKernelNodeParams kp{};
+        kp.func = (void*)f;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(threads);
+        kp.sharedMemBytes = (unsigned)smem;
+        void* args_[] = {(void*)&args...};
+        kp.kernelParams = args_;
+        cudaError_t e = cudaGraphAddKernelNode(&n, g, deps, ndeps, &kp);
+        if (e != cudaSuccess) rc = set_cuda_err(e, "cudaGraphAddKernelNode");
+        return n;
+    }
+    cudaGraph_t while_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, cudaGraphConditionalHandle h,
+                           cudaGraphNode_t* node) {
+        if (rc) return nullptr;
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaError_t e = cudaGraphAddNode(node, g, deps, nullptr, ndeps, &np);
+        if (e != cudaSuccess) {
+            rc = set_cuda_err(e, "cudaGraphAddNode(while)");
+            return nullptr;
+        }
+        return np.conditional.phGraph_out[0];
+    }
+};
+
+// Inner CG loop body (Listing 2): pass A (update + row FFT), B, C (product,
+// dot products, step decision).
+template <typename T>
+void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp, T* cq,
+                    const T* s, const double* r64_start, cudaGraphConditionalHandle h_inner) {
+    const KernSet& k = R.k;
+    RowFwdArgs<T> a{};
+    a.L = p->L;
+    a.mode = RF_CG;
+    a.cx = cx;
+    a.cr = cr;
+    a.cp = cp;
+    a.cq = cq;
+    a.r64 = r64_start;
+    a.st = p->st;
+    a.part = p->part;
+    a.Z = (cpx<T>*)R.Z;
+    a.tw = (const cpx<T>*)R.tw;
+    cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, k.row_fwd, row_grid(p, k), k.row_threads, k.row_smem, a);
+    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
+    cudaGraphNode_t nB = gb.kernel(body, &nA, 1, k.col_conv, p->M / k.cb, k.col_threads, k.col_smem, b);
+    RowInvArgs<T> c{};
+    c.L = p->L;
+    c.mode = RI_CG;
+    c.s = s;
+    c.cp = cp;
+    c.cr = cr;
+    c.cq = cq;
+    c.mask = p->mask;
+    c.st = p->st;
+    c.part = p->part;
+    c.h_inner = h_inner;
+    c.Z = (const cpx<T>*)R.Z;
+    c.tw = (const cpx<T>*)R.tw;
+    gb.kernel(body, &nB, 1, k.row_inv, row_grid(p, k), k.row_threads, k.row_smem, c);
+}
+
+// Build the solve graph for one mode:
+//   [prologue] -> while(outer) { A64 (fold correction, mask, FFT x) -> B64 ->
+//                                C64 (true residual, decide) ->
+//                                while(inner) { A -> B -> C } -> final }
+int build_graph(fftconv_plan* p, int mode) {
+    GraphBuilder gb;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
+    cudaGraphNode_t nPro = nullptr, nOuter = nullptr;
+    const long N = p->N;
+    const bool mixed = mode == FC_MODE_MIXED;
+    FC_CK(cudaGraphCreate(&g, 0));
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h_outer, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_cuda_err(e, "cudaGraphConditionalHandleCreate");
+    }
+    int ndeps = 0;
+    if (mixed) {
+        // FP32 copy of the diagonal for the inner products
+        const double* sa = p->s64;
+        float* sb = p->s32;
+        nPro = gb.kernel(g, nullptr, 0, (const void*)k_f64_to_f32, grid_1d(N, 256), 256, 0, N, sa, sb);
+        ndeps = 1;
+    }
+    cudaGraph_t outer = gb.while_node(g, ndeps ? &nPro : nullptr, ndeps, h_outer, &nOuter);
+    if (!gb.rc) {
+        e = cudaGraphConditionalHandleCreate(&h_inner, outer, 0, 0);
+        if (e != cudaSuccess) gb.rc = set_cuda_err(e, "cudaGraphConditionalHandleCreate(inner)");
+    }
+    if (!gb.rc) {
+        const KernSet& k = p->p64.k;
+        RowFwdArgs<double> a{};
+        a.L = p->L;
+        a.mode = RF_XUPD;
+        a.x64 = p->x64;
+        a.d32 = mixed ? p->d32 : nullptr;
+        a.mask = p->mask;
+        a.st = p->st;
+        a.part = p->part;
+        a.Z = (cpx<double>*)p->p64.Z;
+        a.tw = (const cpx<double>*)p->p64.tw;
+        // the mask is applied to x in the same pass (x = 0 off the active set)
+        a.cq = nullptr;
+        a.cp = nullptr;
+        a.cr = nullptr;
+        a.cx = nullptr;
+        a.r64 = nullptr;
+        a.x = nullptr;
+        cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, k.row_fwd, row_grid(p, k), k.row_threads, k.row_smem, a);
+        ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tw};
+        cudaGraphNode_t nB = gb.kernel(outer, &nA, 1, k.col_conv, p->M / k.cb, k.col_threads, k.col_smem, b);
+        RowInvArgs<double> c{};
+        c.L = p->L;
+        c.mode = RI_RESID;
+        c.mask = p->mask;
+        c.x64 = p->x64;
+        c.b64 = p->b64;
+        c.s64 = p->s64;
+        c.r64 = p->r64;
+        c.st = p->st;
+        c.part = p->part;
+        c.h_outer = h_outer;
+        c.h_inner = h_inner;
+        c.Z = (const cpx<double>*)p->p64.Z;
+        c.tw = (const cpx<double>*)p->p64.tw;
+        cudaGraphNode_t nC = gb.kernel(outer, &nB, 1, k.row_inv, row_grid(p, k), k.row_threads, k.row_smem, c);
+        cudaGraphNode_t nInner = nullptr;
+        cudaGraph_t inner = gb.while_node(outer, &nC, 1, h_inner, &nInner);
+        if (!gb.rc) {
+            if (mixed)
+                add_inner_body<float>(gb, inner, p, p->p32, p->d32, p->r32, p->p32v, p->q32, p->s32, p->r64, h_inner);
+            else
+                add_inner_body<double>(gb, inner, p, p->p64, p->x64, p->r64, p->p64v, p->q64, p->s64, nullptr,
+                                       h_inner);
+        }
+        const CgState* cst = p->st;
+        if (mixed) {
+            float* fx = p->d32;
+            const float* fp = p->p32v;
+            gb.kernel(outer, &nInner, 1, (const void*)k_cg_final<float>, grid_1d(N, 256), 256, 0, N, cst, fx, fp);
+        } else {
+            double* fx = p->x64;
+            const double* fp = p->p64v;
+            gb.kernel(outer, &nInner, 1, (const void*)k_cg_final<double>, grid_1d(N, 256), 256, 0, N, cst, fx, fp);
+        }
+    }
+    if (gb.rc) {
+        cudaGraphDestroy(g);
+        return gb.rc;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return set_cuda_err(e, "cudaGraphInstantiate");
+    }
+    p->graph[mode] = g;
+    p->gexec[mode] = ex;
+    return FC_OK;
+}
+
+}  // namespace
+
+extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, double* x, const uint8_t* mask,
+                        const cg_opts* o, cg_result* r, fc_stream_t stream) {
+    if (!p || !s || !b || !x) return FC_EINVAL;
+    cg_opts def{};
+    def.rtol = 1e-10;
+    def.mode = FC_MODE_F64;
+    if (!o) o = &def;
+    const int mode = o->mode;
+    if (mode != FC_MODE_F64 && mode != FC_MODE_MIXED) return FC_EINVAL;
+    if (!(p->prec & FC_F64)) return FC_EINVAL;
+    if (mode == FC_MODE_MIXED && !(p->prec & FC_F32)) return FC_EINVAL;
+    if (!(o->rtol >= 0.0)) return FC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const long N = p->N;
+    if (!p->gexec[mode]) {
+        int rc = build_graph(p, mode);
+        if (rc) return rc;
+    }
+    // inputs into the plan's buffers (the graph is built on them)
+    FC_CK(cudaMemcpyAsync(p->s64, s, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(p->b64, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    if (o->x0_zero)
+        FC_CK(cudaMemsetAsync(p->x64, 0, sizeof(double) * N, st));
+    else
+        FC_CK(cudaMemcpyAsync(p->x64, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    if (mask) {
+        FC_CK(cudaMemcpyAsync(p->mask, mask, N, cudaMemcpyDeviceToDevice, st));
+    } else {
+        k_fill_u8<<<grid_1d(N, 256), 256, 0, st>>>(N, p->mask, 1);
+        FC_CK(cudaGetLastError());
+    }
+    CgState h{};
+    h.rtol2 = o->rtol * o->rtol;
+    const double irt = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+    h.inner_rtol2 = irt * irt;
+    h.max_iter = o->max_iter > 0 ? o->max_iter : 1000000;
+    h.cycle_max = o->refine_every > 0 ? o->refine_every : 100000;
+    h.max_cycles = o->max_refine > 0 ? o->max_refine : 60;
+    h.mixed = mode == FC_MODE_MIXED;
+    h.sigma = 0.0;
+    h.first = 1;
+    *p->st_host = h;
+    FC_CK(cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st));
+    FC_CK(cudaGraphLaunch(p->gexec[mode], st));
+    FC_CK(cudaMemcpyAsync(x, p->x64, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+    FC_CK(cudaStreamSynchronize(st));
+    const CgState& f = *p->st_host;
+    if (r) {
+        r->status = f.status;
+        r->iters = f.iter;
+        r->refinements = f.cycles;
+        r->true_rel_resid = f.bb > 0 ? sqrt(f.rr64 / f.bb) : 0.0;
+        r->bnorm = sqrt(f.bb);
+    }
+    return f.status;
+}
+
+extern "C" int fc_masked_step(fftconv_plan* p, const double* t, uint8_t* mask, double* x, int64_t* removed,
+                              fc_stream_t stream) {
+    if (!p || !t || !mask || !x || !removed) return FC_EINVAL;
+    k_masked_argmax<<<p->am_grid, 256, 0, (cudaStream_t)stream>>>(p->N, t, mask, x, removed, p->am_v, p->am_i,
+                                                                   p->am_ctl);
+    FC_CK(cudaGetLastError());
+    return FC_OK;
+}
