@@ -1,0 +1,406 @@
+"""Benchmark of the fibre-bundle FFT-convolution CG solve on B300.
+
+Workload (one "step"): one step of the quasi-static breaking loop on an
+L = 1024 grid (padded 2048 x 2048 FFT): a CG solve of P (C + S) P x = P b,
+warm-started from the previous solution, to a relative residual of 1e-10
+(certified on the FP64 recomputed residual), followed by the removal of the
+fibre with the largest |x_i| / t_i.  s ~ U[0.5, 1.5] (seed 0), b = 1,
+t ~ U(0, 1).  The timed solves use the mixed path (FP32 FFTs and vectors,
+FP64 reductions and FP64 true residuals driving refinement); the same steps
+are then re-run from the same state with the plain FP64 path for the
+comparison, and the FFT-convolution matvec is timed on its own for the
+roofline.
+
+`python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]`
+prints one JSON line.  Under torchrun each rank runs its own replica (seed =
+rank): independent problems, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+L_BENCH = 1024
+RTOL = 1e-10
+METRIC = "CG matvec GB/s vs HBM peak; solves/sec + p50/p99 latency, mixed vs FP64 plain"
+WORKLOAD = ("quasi-static breaking loop, L=1024 (padded 2048^2 FFT): warm-started CG to "
+            "rtol 1e-10 + argmax |x|/t removal per step; s~U[0.5,1.5] seed 0, b=1, t~U(0,1)")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clk", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        os.unlink(self.path)
+        busy = [v for v in sm if v > 0.5 * (max(smax) if smax else 1)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+# ---------------------------------------------------------------- oracle --
+
+def oracle_iteration_time(L, budget_s):
+    """Seconds per CG iteration of the plain FP64 oracle at size L, from a
+    bounded run of its CG (cold start, capped iterations)."""
+    import fc_inputs
+    import oracle
+    p = fc_inputs.problem(L, seed=0, with_t=True)
+    oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=1)  # compile / page in
+    t0 = time.perf_counter()
+    _, _, it1, _ = oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=1)
+    one = time.perf_counter() - t0
+    k = max(2, min(200, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    _, _, itk, _ = oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=k)
+    tk = time.perf_counter() - t0
+    # a solve = setup + iterations; separate the two from the 1- and k-iteration runs
+    per_it = max((tk - one) / max(itk - it1, 1), 1e-9)
+    setup = max(one - per_it * it1, 0.0)
+    return per_it, setup, itk, tk + one
+
+
+# ------------------------------------------------------------------ ours --
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+
+    import fc_inputs
+    import paper_1305_3625_b300 as fc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    L = L_BENCH
+    N = L * L
+    p = fc_inputs.problem(L, seed=rank, with_t=True)
+    plan = fc.fftconv_plan_create(L, fc.FC_F32 | fc.FC_F64)
+    s = torch.tensor(p["s"], device=dev)
+    b = torch.tensor(p["b"], device=dev)
+    t = torch.tensor(p["t"], device=dev)
+    mask = torch.ones(N, device=dev, dtype=torch.uint8)
+    x = torch.zeros(N, device=dev, dtype=torch.float64)
+    removed = torch.empty(1, device=dev, dtype=torch.int64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)  # > 126 MB L2
+
+    def step(mode, x_, mask_):
+        r = fc.cg_solve(plan, s, b, x_, mask=mask_, rtol=RTOL, mode=mode)
+        if r["status"] != fc.FC_OK:
+            raise RuntimeError(f"solve failed: {r}")
+        fc.fc_masked_step(plan, t, mask_, x_, removed)
+        return r
+
+    def launches(r, mode):
+        # prologue (mixed) + per true residual 3 passes + final update, 3 passes
+        # per CG iteration, 1 removal kernel
+        return (1 if mode == fc.FC_MODE_MIXED else 0) + 4 * r["refinements"] + 3 * r["iters"] + 1
+
+    # warm-up: the cold first solve plus W-1 warm steps
+    for _ in range(max(args.warmup, 3)):
+        step(fc.FC_MODE_MIXED, x, mask)
+    torch.cuda.synchronize()
+    x_start, mask_start = x.clone(), mask.clone()
+
+    def timed_loop(mode, K):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        res = []
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            res.append(step(mode, x, mask))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(bb) for a, bb in ev]
+        return ms, res
+
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    ms_mixed, res_mixed = timed_loop(fc.FC_MODE_MIXED, args.steps)
+    wall_mixed = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+
+    # the same K steps from the same state with the plain FP64 path
+    x.copy_(x_start)
+    mask.copy_(mask_start)
+    k64 = max(1, min(args.steps, args.f64_steps))
+    ms_f64, res_f64 = timed_loop(fc.FC_MODE_F64, k64)
+
+    # matvec roofline: FP32 fftconv_apply (3 passes), L2 flushed before each
+    xin = torch.rand(N, device=dev, dtype=torch.float32)
+    yout = torch.empty_like(xin)
+
+    def time_apply(pl, xi, yo, reps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for _ in range(3):
+            fc.fftconv_apply_prec(pl, fc.FC_F32, xi, yo)
+        for a, bb in evs:
+            flush.zero_()
+            a.record(stream)
+            fc.fftconv_apply_prec(pl, fc.FC_F32, xi, yo)
+            bb.record(stream)
+        torch.cuda.synchronize()
+        return statistics.median(a.elapsed_time(bb) for a, bb in evs)
+
+    mv_ms = time_apply(plan, xin, yout, 50)
+    clk = clocks.stop()
+    M = plan.M
+    Q = M // 2 + 1
+    mv_bytes = 72 * N + 4 * Q * Q  # x, y (4N each), 4 passes over the L x M intermediate (16N each), spectrum quarter
+    peak, peak_kind = load_peaks()
+    mv_gbs = mv_bytes / (mv_ms * 1e-3) / 1e9
+
+    big = None
+    if args.big:
+        L4 = 4096
+        plan4 = fc.fftconv_plan_create(L4, fc.FC_F32)
+        x4 = torch.rand(L4 * L4, device=dev, dtype=torch.float32)
+        y4 = torch.empty_like(x4)
+        ms4 = time_apply(plan4, x4, y4, 20)
+        Q4 = plan4.M // 2 + 1
+        b4 = 72 * L4 * L4 + 4 * Q4 * Q4
+        big = {"L": L4, "ms": round(ms4, 4), "bytes": b4, "GB_s": round(b4 / (ms4 * 1e-3) / 1e9, 1),
+               "frac_of_hbm": round(b4 / (ms4 * 1e-3) / 1e9 / peak, 3)}
+        del plan4, x4, y4
+
+    # end-to-end through the C ABI with host buffers: inputs up, result down
+    e2e = None
+    if args.e2e_steps > 0:
+        hs = torch.tensor(p["s"]).pin_memory()
+        hb = torch.tensor(p["b"]).pin_memory()
+        ht = torch.tensor(p["t"]).pin_memory()
+        hx = x_start.cpu().pin_memory()
+        hm = mask_start.cpu().pin_memory()
+        hrem = torch.empty(1, dtype=torch.int64).pin_memory()
+        ds, db, dt_ = torch.empty_like(s), torch.empty_like(b), torch.empty_like(t)
+        torch.cuda.synchronize()
+        e0 = time.perf_counter()
+        ke = args.e2e_steps
+        for _ in range(ke):
+            ds.copy_(hs, non_blocking=True)
+            db.copy_(hb, non_blocking=True)
+            dt_.copy_(ht, non_blocking=True)
+            x.copy_(hx, non_blocking=True)
+            mask.copy_(hm, non_blocking=True)
+            r = fc.cg_solve(plan, ds, db, x, mask=mask, rtol=RTOL, mode=fc.FC_MODE_MIXED)
+            fc.fc_masked_step(plan, dt_, mask, x, removed)
+            hx.copy_(x, non_blocking=True)
+            hm.copy_(mask, non_blocking=True)
+            hrem.copy_(removed, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - e0
+        h2d = 3 * 8 * N + 8 * N + N
+        d2h = 8 * N + N + 8
+        e2e = {"value": round(ke / e2e_s, 3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke}
+
+    # aggregate over ranks (max time)
+    tot_ms = sum(ms_mixed)
+    if pg:
+        import torch.distributed as dist
+        tt = torch.tensor([tot_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    value = world * args.steps / (tot_ms * 1e-3)
+
+    out = None
+    if rank == 0:
+        srt = sorted(ms_mixed)
+
+        def pct(v, q):
+            return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
+
+        iters = [r["iters"] for r in res_mixed]
+        iters64 = [r["iters"] for r in res_f64]
+        f64_rate = k64 / (sum(ms_f64) * 1e-3)
+        per_it_cpu, setup_cpu, it_cpu, cpu_s = oracle_iteration_time(L, args.cpu_budget)
+        cpu_solve_s = setup_cpu + per_it_cpu * statistics.mean(iters64)
+        out = {
+            "metric": METRIC,
+            "value": round(value, 3),
+            "unit": "solves/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": max(args.warmup, 3),
+            "ms_per_step": round(tot_ms / args.steps, 4),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64 (mixed: FP32 FFT/vectors, FP64 reductions and true residuals)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": L, "M": M, "rtol": RTOL, "mode": "mixed",
+                       "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+            "p50_ms": round(pct(srt, 0.5), 4),
+            "p99_ms": round(pct(srt, 0.99), 4),
+            "iters_per_solve": round(statistics.mean(iters), 2),
+            "true_residuals_per_solve": round(statistics.mean(r["refinements"] for r in res_mixed), 2),
+            "f64_plain": {"value": round(f64_rate, 3), "unit": "solves/s", "steps": k64,
+                          "p50_ms": round(statistics.median(ms_f64), 3),
+                          "p99_ms": round(max(ms_f64), 3),
+                          "iters_per_solve": round(statistics.mean(iters64), 2)},
+            "mixed_over_f64": round(value / world / f64_rate, 2),
+            "matvec": {"L": L, "ms": round(mv_ms, 4), "bytes": mv_bytes, "GB_s": round(mv_gbs, 1),
+                       "frac_of_hbm": round(mv_gbs / peak, 3)},
+            "matvec_L4096": big,
+            "roofline": {"bound": "hbm", "kernel": "fftconv_apply FP32 (3 passes), L=1024",
+                         "achieved": round(mv_gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(mv_gbs / peak, 3), "traffic": args.traffic,
+                         "peak_kind": peak_kind},
+            "cpu_baseline": {"value": round(1.0 / cpu_solve_s, 5), "unit": "solves/s",
+                             "cores": int(os.environ.get("OMP_NUM_THREADS", "1")), "kind": "oracle",
+                             "sample": (f"oracle FP64 CG at L={L}: {it_cpu} iterations timed "
+                                        f"({cpu_s:.1f} s), scaled by the FP64 path's "
+                                        f"{statistics.mean(iters64):.1f} iterations per solve")},
+            "e2e": e2e,
+            "gpu_launches": sum(launches(r, fc.FC_MODE_MIXED) for r in res_mixed),
+            "clocks": clk,
+            "wall_s_timed_region": round(wall_mixed, 3),
+        }
+    return out
+
+
+def run_reference(args, world, rank):
+    """The oracle, as it stands, on the host cores: each step is a bounded
+    sample (a few CG iterations of the L = 1024 solve) scaled to solves/s."""
+    if rank != 0:
+        return None
+    import fc_inputs
+    import oracle
+    L = L_BENCH
+    p = fc_inputs.problem(L, seed=0, with_t=True)
+    iters_per_solve = args.ref_iters
+    ms = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, _, it, _ = oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=args.ref_sample_iters)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            ms.append(dt * 1e3 * iters_per_solve / max(it, 1))
+    value = len(ms) / (sum(ms) * 1e-3)
+    cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
+    sample = (f"per step: oracle FP64 CG at L={L}, {args.ref_sample_iters} iterations from x=0, "
+              f"scaled to {iters_per_solve} iterations per solve")
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(statistics.mean(ms), 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": L, "rtol": RTOL, "mode": "oracle FP64 CG (CPU)"},
+            "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--f64-steps", type=int, default=6, dest="f64_steps")
+    ap.add_argument("--e2e-steps", type=int, default=5, dest="e2e_steps")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget")
+    ap.add_argument("--big", type=int, default=1)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per matvec from a capture of the current kernels")
+    ap.add_argument("--ref-sample-iters", type=int, default=3, dest="ref_sample_iters")
+    ap.add_argument("--ref-iters", type=int, default=60, dest="ref_iters",
+                    help="CG iterations per warm-started solve used to scale the reference")
+    args = ap.parse_args()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_ours(args, world, rank, local, pg)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

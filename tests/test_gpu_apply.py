@@ -5,7 +5,7 @@ import torch
 
 import fc_inputs
 import oracle
-from gpu_util import U32, U64, conv_bound, dev, host
+from gpu_util import U32, U64, conv_err, conv_rel_bound, dev, host
 
 pytestmark = pytest.mark.gpu
 
@@ -31,10 +31,11 @@ def run_apply(L, x64):
     return host(x32).astype(np.float64), host(y32).astype(np.float64), host(y64)
 
 
-def ghat_max(L):
-    """max |Ghat| = Ghat(0) = sum of the (non-negative) kernel table / M^2."""
-    M = fc_inputs.padded_side(L)
-    return float(oracle.kernel_table(L).sum()) / M**2
+def check(y, ref, u, M, what):
+    e = conv_err(y, ref)
+    bound = conv_rel_bound(u, M)
+    print(f"{what}: rel err {e:.3e}, bound {bound:.3e}, ratio {e / bound:.3f}")
+    assert e <= bound, (what, e, bound)
 
 
 @pytest.mark.parametrize("L", SMALL)
@@ -43,11 +44,8 @@ def test_apply_matches_direct_sum(L):
     x = rng.standard_normal(L * L)
     x32, y32, y64 = run_apply(L, x)
     M = fc_inputs.padded_side(L)
-    gm = ghat_max(L)
-    ref64 = oracle.conv_direct(L, x)
-    ref32 = oracle.conv_direct(L, x32)  # the FP32 path sees the rounded input
-    assert np.linalg.norm(y64 - ref64) <= conv_bound(U64, M, gm, x)
-    assert np.linalg.norm(y32 - ref32) <= conv_bound(U32, M, gm, x32)
+    check(y64, oracle.conv_direct(L, x), U64, M, f"L={L} f64")
+    check(y32, oracle.conv_direct(L, x32), U32, M, f"L={L} f32")  # FP32 sees the rounded input
 
 
 @pytest.mark.parametrize("L", [64, 100, 128, 256])
@@ -56,9 +54,8 @@ def test_apply_matches_oracle_fft_route(L):
     x = rng.uniform(-1, 1, L * L)
     x32, y32, y64 = run_apply(L, x)
     M = fc_inputs.padded_side(L)
-    gm = ghat_max(L)
-    assert np.linalg.norm(y64 - oracle.conv_fft(L, x)) <= conv_bound(U64, M, gm, x)
-    assert np.linalg.norm(y32 - oracle.conv_fft(L, x32)) <= conv_bound(U32, M, gm, x32)
+    check(y64, oracle.conv_fft(L, x), U64, M, f"L={L} f64")
+    check(y32, oracle.conv_fft(L, x32), U32, M, f"L={L} f32")
 
 
 @pytest.mark.parametrize("L", [1024, 2048])
@@ -69,16 +66,17 @@ def test_apply_full_size(L):
     x = p["s"] - 1.0  # values in (-0.5, 0.5)
     x32, y32, y64 = run_apply(L, x)
     M = fc_inputs.padded_side(L)
-    gm = ghat_max(L)
-    assert np.linalg.norm(y64 - oracle.conv_fft(L, x)) <= conv_bound(U64, M, gm, x)
-    assert np.linalg.norm(y32 - oracle.conv_fft(L, x32)) <= conv_bound(U32, M, gm, x32)
+    ref64 = oracle.conv_fft(L, x)
+    check(y64, ref64, U64, M, f"L={L} f64")
+    check(y32, oracle.conv_fft(L, x32), U32, M, f"L={L} f32")
+    ynorm = float(np.linalg.norm(ref64))
     rng = np.random.default_rng(7)
     pts = [(0, 0), (L - 1, L - 1), (0, L - 1), (L // 2, L // 3)] + \
           [tuple(v) for v in rng.integers(0, L, size=(12, 2))]
     for iy, ix in pts:
         # one entry may carry at most the whole l2 error
-        assert abs(y64[iy * L + ix] - oracle.conv_direct_at(L, x, iy, ix)) <= conv_bound(U64, M, gm, x)
-        assert abs(y32[iy * L + ix] - oracle.conv_direct_at(L, x32, iy, ix)) <= conv_bound(U32, M, gm, x32)
+        assert abs(y64[iy * L + ix] - oracle.conv_direct_at(L, x, iy, ix)) <= conv_rel_bound(U64, M) * ynorm
+        assert abs(y32[iy * L + ix] - oracle.conv_direct_at(L, x32, iy, ix)) <= conv_rel_bound(U32, M) * ynorm
 
 
 def test_delta_reproduces_green_row():
@@ -118,7 +116,7 @@ def test_f32_only_plan_applies():
     fc.fftconv_apply(p, x32, y32)
     xr = host(x32).astype(np.float64)
     M = fc_inputs.padded_side(L)
-    assert np.linalg.norm(host(y32) - oracle.conv_direct(L, xr)) <= conv_bound(U32, M, ghat_max(L), xr)
+    check(host(y32).astype(np.float64), oracle.conv_direct(L, xr), U32, M, "f32-only plan")
     # an FP32-only plan has no FP64 operator
     with pytest.raises(fc.FcError):
         fc.fftconv_apply_prec(p, fc.FC_F64, dev(x), torch.empty(L * L, device="cuda", dtype=torch.float64))
