@@ -25,8 +25,8 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol():
-    from paper_1305_3625_b300 import build
-    lib_path = build.build()
+    import __graft_entry__
+    lib_path = __graft_entry__._build_module().build()
     lib = ctypes.CDLL(lib_path)
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, f"not exported: {missing}"
