@@ -161,6 +161,29 @@ int cg_solve(fftconv_plan *p, const double *s, const double *b, double *x, const
 int fc_masked_step(fftconv_plan *p, const double *t, uint8_t *mask, double *x, int64_t *removed,
                    fc_stream_t stream);
 
+/*
+ * fc_masked_step_static -- the same breaking step as fc_masked_step, for
+ * callers that cannot allocate device memory at the point of the call: a
+ * process whose device memory is entirely reserved by another allocator (a
+ * caching pool or a fixed budget), or a latency-bound loop that must not pay
+ * the device-wide synchronisation that cudaMalloc/cudaFree imply.  It needs
+ * no plan and allocates nothing: its scratch (the per-block winners of the
+ * argmax and a counter) is a file-scope static device array of 131,328 bytes
+ * that every GPU which loads the library holds until the process exits.  The
+ * paper has no counterpart of this entry point.
+ *   N        number of sites, 1 <= N <= 16,777,216 (= 4096^2); a larger N is
+ *            rejected with FC_EINVAL and a message in fc_last_error().
+ *   t, mask, x, removed  as for fc_masked_step (device pointers).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * last call's contents (the counter is cleared on every call): calls that
+ * overlap on the GPU, from several streams or threads, race.  Asynchronous.
+ * Errors: FC_EINVAL, FC_ECUDA.
+ */
+int fc_masked_step_static(int64_t N, const double *t, uint8_t *mask, double *x, int64_t *removed,
+                          fc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

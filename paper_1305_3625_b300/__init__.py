@@ -79,6 +79,7 @@ def _load():
     lib.fftconv_apply_prec.argtypes = [vp, i, vp, vp, vp]
     lib.cg_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
     lib.fc_masked_step.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.fc_masked_step_static.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp]
     return lib
 
 
@@ -203,3 +204,14 @@ def fftconv_plan_info(plan: Plan) -> dict:
     if rc != FC_OK:
         raise FcError(rc, "fftconv_plan_info")
     return {"L": Li.value, "M": Mi.value, "prec": pi.value, "device_bytes": nb.value}
+
+
+def fc_masked_step_static(t, mask, x, removed, stream=None) -> None:
+    """Plan-free breaking step for callers that cannot allocate device memory
+    at the call; its scratch is a fixed static device array (N <= 4096^2)."""
+    n = t.numel()
+    rc = _lib.fc_masked_step_static(int(n), _ptr(t, torch.float64, n, "t"),
+                                    _ptr(mask, torch.uint8, n, "mask"), _ptr(x, torch.float64, n, "x"),
+                                    _ptr(removed, torch.int64, 1, "removed"), _stream(stream))
+    if rc != FC_OK:
+        raise FcError(rc, "fc_masked_step_static")

@@ -805,3 +805,63 @@ extern "C" int fc_masked_step(fftconv_plan* p, const double* t, uint8_t* mask, d
     FC_CK(cudaGetLastError());
     return FC_OK;
 }
+
+// ------------------------------------------- allocation-free masked step --
+//
+// fc_masked_step_static: the breaking step for callers that cannot allocate
+// device memory at the point of the call.  Its scratch (per-block winners of
+// the argmax and the last-block counter) lives in the file-scope array below
+// instead of a plan; every GPU that loads the library holds these 131,328
+// bytes until the process exits.
+
+namespace {
+constexpr int kStaticMaxBlocks = 8192;  // one block per 2048 sites
+constexpr long long kStaticMaxN = (long long)kStaticMaxBlocks * 2048;  // 16,777,216 = 4096^2
+constexpr size_t kStaticCtlBytes = 256;
+constexpr size_t kStaticScratchBytes =
+    kStaticCtlBytes + (size_t)kStaticMaxBlocks * (sizeof(double) + sizeof(long long));
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+extern "C" int fc_masked_step_static(int64_t N, const double* t, uint8_t* mask, double* x, int64_t* removed,
+                                     fc_stream_t stream) {
+    if (N < 1 || N > kStaticMaxN) {
+        snprintf(g_err, sizeof(g_err),
+                 "fc_masked_step_static: N = %lld is outside [1, %lld], the largest size its static scratch "
+                 "(%d block results) can hold",
+                 (long long)N, kStaticMaxN, kStaticMaxBlocks);
+        return FC_EINVAL;
+    }
+    if (!t || !mask || !x || !removed) return FC_EINVAL;
+    int dev = 0;
+    FC_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return FC_EINVAL;
+    void* base = nullptr;
+    {
+        // set-up once per device, with that device current: the array's device
+        // address (in host code its name is only a stand-in)
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess) return set_cuda_err(e, "cudaGetSymbolAddress(g_static_scratch)");
+            g_static_ptr[dev] = ptr;
+        }
+        base = g_static_ptr[dev];
+    }
+    ArgmaxCtl* ctl = reinterpret_cast<ArgmaxCtl*>(base);
+    double* pv = reinterpret_cast<double*>(static_cast<char*>(base) + kStaticCtlBytes);
+    long long* pi = reinterpret_cast<long long*>(static_cast<char*>(base) + kStaticCtlBytes +
+                                                 (size_t)kStaticMaxBlocks * sizeof(double));
+    const int grid = (int)((N + 2047) / 2048);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the counter must start at 0
+    FC_CK(cudaMemsetAsync(ctl, 0, sizeof(ArgmaxCtl), s));
+    k_masked_argmax<<<grid, 256, 0, s>>>((long)N, t, mask, x, removed, pv, pi, ctl);
+    FC_CK(cudaGetLastError());
+    return FC_OK;
+}
