@@ -61,9 +61,17 @@ typedef struct CUstream_st *fc_stream_t; /* identical to cudaStream_t */
 typedef struct fftconv_plan fftconv_plan;
 typedef struct cg_server cg_server;
 
-/* Launch-shape overrides; all zero = built-in choices. Reserved for tuning. */
+/* Launch-shape choice for the three FFT passes.  Each pass has a few compiled
+ * shapes (values per thread, rows or columns per block); by default the plan
+ * times them on its own size and keeps the fastest (cached in the file named
+ * by FC_TUNE_CACHE, default $HOME/.cache/fftconv/tune_sm103.txt; FC_AUTOTUNE=0
+ * disables the timing).  All zero = that default. */
 typedef struct cg_tune {
-    int reserved[8];
+    int shape_rfwd;  /* 0: tuned; k > 0: compiled shape k-1 of the row pass A */
+    int shape_col;   /* 0: tuned; k > 0: shape k-1 of the column pass B      */
+    int shape_rinv;  /* 0: tuned; k > 0: shape k-1 of the row pass C         */
+    int no_autotune; /* 1: no timing (cached choice or shape 0)             */
+    int reserved[4];
 } cg_tune;
 
 typedef struct cg_opts {
@@ -112,6 +120,12 @@ int fftconv_plan_destroy(fftconv_plan *p);
 
 /* Query a plan: side L, padded side M, precision flags, device bytes held. */
 int fftconv_plan_info(const fftconv_plan *p, int *L, int *M, int *prec, size_t *device_bytes);
+
+/* Launch shapes of a plan for one precision (FC_F32 or FC_F64): for passes
+ * A, B, C (index 0, 1, 2) the number of compiled shapes, the chosen one, and
+ * its values per thread and rows-pairs / columns per block.  Host only. */
+int fftconv_plan_shapes(const fftconv_plan *p, int prec, int n_shapes[3], int chosen[3], int radix[3],
+                        int per_block[3]);
 
 /*
  * fftconv_apply -- y = C x (Listing 3: cpyComplex, FFT, elementMult, inverse

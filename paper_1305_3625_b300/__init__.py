@@ -50,6 +50,11 @@ class cg_opts(ctypes.Structure):
                 ("inner_rtol", ctypes.c_double), ("x0_zero", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
+class cg_tune(ctypes.Structure):
+    _fields_ = [("shape_rfwd", ctypes.c_int), ("shape_col", ctypes.c_int), ("shape_rinv", ctypes.c_int),
+                ("no_autotune", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
 class cg_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("reserved", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
@@ -71,7 +76,9 @@ def _load():
     vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
     lib.fc_version.restype = ctypes.c_char_p
     lib.fc_last_error.restype = ctypes.c_char_p
-    lib.fftconv_plan_create.argtypes = [ctypes.POINTER(vp), i, i, vp]
+    lib.fftconv_plan_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(cg_tune)]
+    ip3 = ctypes.c_int * 3
+    lib.fftconv_plan_shapes.argtypes = [vp, i, ip3, ip3, ip3, ip3]
     lib.fftconv_plan_destroy.argtypes = [vp]
     lib.fftconv_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(sz)]
@@ -142,9 +149,18 @@ class Plan:
             pass
 
 
-def fftconv_plan_create(L: int, prec: int = FC_F32 | FC_F64) -> Plan:
+def fftconv_plan_create(L: int, prec: int = FC_F32 | FC_F64, shapes=None, no_autotune: bool = False) -> Plan:
+    """shapes: optional (pass A, pass B, pass C) compiled-shape indices (0-based)
+    to force instead of the tuned choice."""
     h = ctypes.c_void_p()
-    rc = _lib.fftconv_plan_create(ctypes.byref(h), int(L), int(prec), None)
+    tune = None
+    if shapes is not None or no_autotune:
+        tune = cg_tune()
+        if shapes is not None:
+            tune.shape_rfwd, tune.shape_col, tune.shape_rinv = (int(k) + 1 for k in shapes)
+        tune.no_autotune = int(bool(no_autotune))
+    rc = _lib.fftconv_plan_create(ctypes.byref(h), int(L), int(prec),
+                                  ctypes.byref(tune) if tune is not None else None)
     if rc != FC_OK:
         raise FcError(rc, "fftconv_plan_create")
     return Plan(h, int(L), int(prec))
@@ -215,3 +231,13 @@ def fc_masked_step_static(t, mask, x, removed, stream=None) -> None:
                                     _ptr(removed, torch.int64, 1, "removed"), _stream(stream))
     if rc != FC_OK:
         raise FcError(rc, "fc_masked_step_static")
+
+
+def fftconv_plan_shapes(plan: Plan, prec: int) -> dict:
+    """Compiled and chosen launch shapes of the three passes (A, B, C)."""
+    ip3 = ctypes.c_int * 3
+    n, ch, rad, per = ip3(), ip3(), ip3(), ip3()
+    rc = _lib.fftconv_plan_shapes(plan.handle, int(prec), n, ch, rad, per)
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_plan_shapes")
+    return {"n_shapes": list(n), "chosen": list(ch), "radix": list(rad), "per_block": list(per)}

@@ -137,24 +137,14 @@ __host__ __device__ constexpr int seg_len(int M) { return M + (M >> 4) + 2; }
 
 constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
 
-// Per-size launch shape: elements per thread E (the stage radix).
-template <typename T, int M>
-struct Shape {
-    // FP64 keeps half as many values in registers up to M = 2048
-    static constexpr int EMAX = (sizeof(T) == 4 || M >= 4096) ? 16 : 8;
-    static constexpr int E = M < EMAX ? M : EMAX;
-    static constexpr int G = M / E;  // threads per transform
-};
-
-// Stockham transform of one length-M sequence held as v[e] = x[j + e*G] by
-// thread j of its group; on return v[e] = X[j + e*G].  sm is this group's
-// shared segment (seg_len(M) elements); tw[m] = exp(-2 pi i m / M).
-// All threads of the block must call this together (it uses __syncthreads).
-template <typename T, int M, bool INV, int NS = 1>
-__device__ __forceinline__ void fft_stages(cpx<T> (&v)[Shape<T, M>::E], int j, cpx<T>* sm,
-                                           const cpx<T>* __restrict__ tw) {
-    constexpr int E = Shape<T, M>::E;
-    constexpr int G = Shape<T, M>::G;
+// Stockham transform of one length-M sequence held by G = M/E threads as
+// v[e] = x[j + e*G] (thread j of its group); on return v[e] = X[j + e*G].
+// sm is this group's shared segment (seg_len(M) elements); tw[m] =
+// exp(-2 pi i m / M).  All threads of the block call this together (it uses
+// __syncthreads between the exchanges).
+template <typename T, int M, int E, bool INV, int NS = 1>
+__device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm, const cpx<T>* __restrict__ tw) {
+    constexpr int G = M / E;
     if constexpr (NS * E <= M) {
         const int k = j & (NS - 1);
         if constexpr (NS > 1) {
@@ -174,7 +164,7 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[Shape<T, M>::E], int j, c
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = sm[spad(j + e * G)];
             __syncthreads();
-            fft_stages<T, M, INV, NS * E>(v, j, sm, tw);
+            fft_stages<T, M, E, INV, NS * E>(v, j, sm, tw);
         }
     } else {
         constexpr int R = M / NS;  // 2 <= R < E, last stage

@@ -12,6 +12,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <sys/stat.h>
+
 #include <mutex>
 #include <new>
 
@@ -66,10 +68,10 @@ __global__ void k_kernel_table(int L, int M, cpx<double>* K) {
 }
 
 // Unpruned forward FFT of every row of an M x M grid (spectrum set-up only).
-template <int M>
-__global__ void __launch_bounds__(Cfg<double, M>::ROW_THREADS) k_rows_full(cpx<double>* K, const cpx<double>* tw) {
+template <int M, int E, int RB>
+__global__ void __launch_bounds__(RB*(M / E)) k_rows_full(cpx<double>* K, const cpx<double>* tw) {
     using C = cpx<double>;
-    constexpr int E = Cfg<double, M>::E, G = Cfg<double, M>::G, RB = Cfg<double, M>::RB;
+    constexpr int G = M / E;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
     const int j = threadIdx.x % G, c = threadIdx.x / G, row = blockIdx.x * RB + c;
@@ -77,24 +79,24 @@ __global__ void __launch_bounds__(Cfg<double, M>::ROW_THREADS) k_rows_full(cpx<d
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = ok ? K[(size_t)row * M + j + e * G] : C{0, 0};
-    fft_stages<double, M, false>(v, j, sm + c * seg_len(M), tw);
+    fft_stages<double, M, E, false>(v, j, sm + c * seg_len(M), tw);
     if (ok)
 #pragma unroll
         for (int e = 0; e < E; ++e) K[(size_t)row * M + j + e * G] = v[e];
 }
 
 // Unpruned forward FFT of every column of an M x M grid.
-template <int M>
-__global__ void __launch_bounds__(Cfg<double, M>::COL_THREADS) k_cols_full(cpx<double>* K, const cpx<double>* tw) {
+template <int M, int E, int CB>
+__global__ void __launch_bounds__(CB*(M / E)) k_cols_full(cpx<double>* K, const cpx<double>* tw) {
     using C = cpx<double>;
-    constexpr int E = Cfg<double, M>::E, G = Cfg<double, M>::G, CB = Cfg<double, M>::CB;
+    constexpr int G = M / E;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
     const int c = threadIdx.x % CB, j = threadIdx.x / CB, col = blockIdx.x * CB + c;
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = K[(size_t)(j + e * G) * M + col];
-    fft_stages<double, M, false>(v, j, sm + c * seg_len(M), tw);
+    fft_stages<double, M, E, false>(v, j, sm + c * seg_len(M), tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) K[(size_t)(j + e * G) * M + col] = v[e];
 }
@@ -104,16 +106,19 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
     atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// Keep the (M/2+1)^2 quarter of Re(FFT2(k))/M^2; track max |Im| and max |Re|.
-__global__ void k_spectrum_quarter(int M, const cpx<double>* K, double* gq64, float* gq32, double* maxes) {
+// Keep the (M/2+1)^2 quarter of Re(FFT2(k))/M^2; track max |Im| and max |Re|
+// (block maxima, one atomic per block).
+__global__ void __launch_bounds__(256) k_spectrum_quarter(int M, const cpx<double>* K, double* gq64, float* gq32,
+                                                          double* maxes) {
+    __shared__ double smi[8], smr[8];
     const int Q = M / 2 + 1;
-    size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double scale = 1.0 / ((double)M * (double)M);
     double mi = 0.0, mr = 0.0;
-    if (idx < (size_t)M * M) {
-        const double scale = 1.0 / ((double)M * (double)M);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < (size_t)M * M;
+         idx += (size_t)gridDim.x * blockDim.x) {
         cpx<double> z = K[idx];
-        mi = fabs(z.y) * scale;
-        mr = fabs(z.x) * scale;
+        mi = fmax(mi, fabs(z.y) * scale);
+        mr = fmax(mr, fabs(z.x) * scale);
         int fy = (int)(idx / M), fx = (int)(idx % M);
         if (fy < Q && fx < Q) {
             double g = z.x * scale;
@@ -126,6 +131,15 @@ __global__ void k_spectrum_quarter(int M, const cpx<double>* K, double* gq64, fl
         mr = fmax(mr, __shfl_down_sync(0xffffffffu, mr, off));
     }
     if ((threadIdx.x & 31) == 0) {
+        smi[threadIdx.x >> 5] = mi;
+        smr[threadIdx.x >> 5] = mr;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            mi = fmax(mi, smi[w]);
+            mr = fmax(mr, smr[w]);
+        }
         atomic_max_nonneg(maxes + 0, mi);
         atomic_max_nonneg(maxes + 1, mr);
     }
@@ -157,6 +171,27 @@ struct ArgmaxCtl {
 // One quasi-static breaking step: i* = argmax over active i of |x_i|/t_i (ties
 // to the lowest index), then mask[i*] = 0 and x[i*] = 0.  The last block to
 // finish reduces the per-block winners in block order.
+// (value, index) order of the breaking rule: larger |x|/t first, then the
+// lower index; an index of -1 marks "no active site".
+__device__ __forceinline__ bool am_better(double ov, long long oi, double mv, long long mi) {
+    return oi >= 0 && (mi < 0 || ov > mv || (ov == mv && oi < mi));
+}
+
+__device__ __forceinline__ void am_block_reduce(double* sv, long long* si) {
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s && am_better(sv[threadIdx.x + s], si[threadIdx.x + s], sv[threadIdx.x], si[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + s];
+            si[threadIdx.x] = si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+}
+
+// One quasi-static breaking step: i* = argmax over active i of |x_i|/t_i (ties
+// to the lowest index), then mask[i*] = 0 and x[i*] = 0.  Each block reduces
+// its sites; the last block to finish reduces the per-block winners.  The
+// order is total, so the result does not depend on the reduction order.
 __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, uint8_t* mask, double* x,
                                                        int64_t* removed, double* pv, long long* pi,
                                                        ArgmaxCtl* ctl) {
@@ -168,27 +203,14 @@ __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, 
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
         if (!mask[i]) continue;
         double v = fabs(x[i]) / t[i];
-        if (v > bv || (v == bv && (bi < 0 || i < bi))) {
+        if (am_better(v, i, bv, bi)) {
             bv = v;
             bi = i;
         }
     }
     sv[threadIdx.x] = bv;
     si[threadIdx.x] = bi;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            double ov = sv[threadIdx.x + s];
-            long long oi = si[threadIdx.x + s];
-            double mv = sv[threadIdx.x];
-            long long mi = si[threadIdx.x];
-            if (oi >= 0 && (mi < 0 || ov > mv || (ov == mv && oi < mi))) {
-                sv[threadIdx.x] = ov;
-                si[threadIdx.x] = oi;
-            }
-        }
-        __syncthreads();
-    }
+    am_block_reduce(sv, si);
     if (threadIdx.x == 0) {
         pv[blockIdx.x] = sv[0];
         pi[blockIdx.x] = si[0];
@@ -198,17 +220,21 @@ __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, 
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    if (threadIdx.x == 0) {
-        double gv = -1.0;
-        long long gi = -1;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            double ov = __ldcg(pv + b);
-            long long oi = __ldcg(pi + b);
-            if (oi >= 0 && (gi < 0 || ov > gv || (ov == gv && oi < gi))) {
-                gv = ov;
-                gi = oi;
-            }
+    bv = -1.0;
+    bi = -1;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+        double ov = __ldcg(pv + b);
+        long long oi = __ldcg(pi + b);
+        if (am_better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
         }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    am_block_reduce(sv, si);
+    if (threadIdx.x == 0) {
+        const long long gi = si[0];
         *removed = gi;
         if (gi >= 0) {
             mask[gi] = 0;
@@ -220,66 +246,111 @@ __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, 
 
 // ------------------------------------------------------- dispatch tables --
 
-struct KernSet {
-    const void* row_fwd = nullptr;
-    const void* col_conv = nullptr;
-    const void* row_inv = nullptr;
-    const void* rows_full = nullptr;
-    const void* cols_full = nullptr;
-    int rb = 0, cb = 0, row_threads = 0, col_threads = 0;
-    size_t row_smem = 0, col_smem = 0;
+// One compiled launch shape of a pass: E values per thread (stage radix) and
+// `per` row pairs (passes A, C) or columns (pass B) per block.
+struct KV {
+    const void* f = nullptr;
+    int threads = 0, per = 0, E = 0;
+    size_t smem = 0;
 };
 
+struct Variants {
+    KV rfwd[4], colc[4], rinv[4];
+    int n_rfwd = 0, n_colc = 0, n_rinv = 0;
+    KV rows_full, cols_full;  // FP64 only: spectrum set-up
+};
+
+constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+template <typename T, int M, int E, int RB>
+void add_row(Variants& v) {
+    KV f{(const void*)k_rfwd<T, M, E, RB>, RB * (M / E), RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<T>)};
+    KV i{(const void*)k_rinv<T, M, E, RB>, RB * (M / E), RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<T>)};
+    for (int k = 0; k < v.n_rfwd; ++k)
+        if (v.rfwd[k].f == f.f) return;
+    v.rfwd[v.n_rfwd++] = f;
+    v.rinv[v.n_rinv++] = i;
+}
+
+template <typename T, int M, int E, int CB>
+void add_col(Variants& v) {
+    KV c{(const void*)k_colc<T, M, E, CB>, CB * (M / E), CB, E, (size_t)CB * seg_len(M) * sizeof(cpx<T>)};
+    for (int k = 0; k < v.n_colc; ++k)
+        if (v.colc[k].f == c.f) return;
+    v.colc[v.n_colc++] = c;
+}
+
+// Launch shapes compiled for each (precision, M).  FP32 sizes from 256 up
+// carry three shapes per pass for the autotuner; FP64 (ALU-bound on this
+// part) carries one.
 template <typename T, int M>
-KernSet make_set() {
-    using Cf = Cfg<T, M>;
-    KernSet s;
-    s.row_fwd = (const void*)k_row_fwd<T, M>;
-    s.col_conv = (const void*)k_col_conv<T, M>;
-    s.row_inv = (const void*)k_row_inv<T, M>;
-    if constexpr (sizeof(T) == 8) {
-        s.rows_full = (const void*)k_rows_full<M>;
-        s.cols_full = (const void*)k_cols_full<M>;
+void make_variants(Variants& v) {
+    constexpr int H = M / 2;
+    if constexpr (sizeof(T) == 4) {
+        if constexpr (M <= 16) {
+            add_row<T, M, M, 64>(v);
+            add_col<T, M, M, clampi(64, 1, H)>(v);
+        } else if constexpr (M <= 128) {
+            constexpr int G = M / 16;
+            add_row<T, M, 16, clampi(128 / G, 1, 128)>(v);
+            add_col<T, M, 16, clampi(256 / G, 1, H)>(v);
+        } else {
+            constexpr int G16 = M / 16, G8 = M / 8;
+            add_row<T, M, 16, clampi(256 / G16, 1, 64)>(v);
+            add_row<T, M, 8, clampi(256 / G8, 1, 64)>(v);
+            add_row<T, M, 16, clampi(512 / G16, 1, 64)>(v);
+            add_col<T, M, 16, clampi(256 / G16, 1, H)>(v);
+            add_col<T, M, 8, clampi(256 / G8, 1, H)>(v);
+            add_col<T, M, 16, clampi(512 / G16, 1, H)>(v);
+        }
+    } else {
+        constexpr int E = M <= 8 ? M : (M <= 2048 ? 8 : 16);
+        constexpr int G = M / E;
+        constexpr int RB = M <= 8 ? 64 : clampi(256 / G, 1, 128);
+        constexpr int CB = clampi(256 / G, 1, H);
+        add_row<T, M, E, RB>(v);
+        add_col<T, M, E, CB>(v);
+        constexpr int CBF = clampi(256 / G, 1, M);
+        v.rows_full = KV{(const void*)k_rows_full<M, E, RB>, RB * G, RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<double>)};
+        v.cols_full = KV{(const void*)k_cols_full<M, E, CBF>, CBF * G, CBF, E, (size_t)CBF * seg_len(M) * sizeof(cpx<double>)};
     }
-    s.rb = Cf::RB;
-    s.cb = Cf::CB;
-    s.row_threads = Cf::ROW_THREADS;
-    s.col_threads = Cf::COL_THREADS;
-    s.row_smem = Cf::ROW_SMEM;
-    s.col_smem = Cf::COL_SMEM;
-    return s;
 }
 
 template <typename T>
-bool get_set(int M, KernSet* s) {
+bool get_variants(int M, Variants* v) {
+    *v = Variants{};
     switch (M) {
-        case 2: *s = make_set<T, 2>(); return true;
-        case 4: *s = make_set<T, 4>(); return true;
-        case 8: *s = make_set<T, 8>(); return true;
-        case 16: *s = make_set<T, 16>(); return true;
-        case 32: *s = make_set<T, 32>(); return true;
-        case 64: *s = make_set<T, 64>(); return true;
-        case 128: *s = make_set<T, 128>(); return true;
-        case 256: *s = make_set<T, 256>(); return true;
-        case 512: *s = make_set<T, 512>(); return true;
-        case 1024: *s = make_set<T, 1024>(); return true;
-        case 2048: *s = make_set<T, 2048>(); return true;
-        case 4096: *s = make_set<T, 4096>(); return true;
-        case 8192: *s = make_set<T, 8192>(); return true;
+        case 2: make_variants<T, 2>(*v); return true;
+        case 4: make_variants<T, 4>(*v); return true;
+        case 8: make_variants<T, 8>(*v); return true;
+        case 16: make_variants<T, 16>(*v); return true;
+        case 32: make_variants<T, 32>(*v); return true;
+        case 64: make_variants<T, 64>(*v); return true;
+        case 128: make_variants<T, 128>(*v); return true;
+        case 256: make_variants<T, 256>(*v); return true;
+        case 512: make_variants<T, 512>(*v); return true;
+        case 1024: make_variants<T, 1024>(*v); return true;
+        case 2048: make_variants<T, 2048>(*v); return true;
+        case 4096: make_variants<T, 4096>(*v); return true;
+        case 8192: make_variants<T, 8192>(*v); return true;
         default: return false;
     }
 }
 
-int set_smem_attrs(const KernSet& k) {
-    const void* fr[3] = {k.row_fwd, k.row_inv, k.rows_full};
-    for (const void* f : fr)
-        if (f && k.row_smem > 48 * 1024)
-            FC_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.row_smem));
-    const void* fc_[2] = {k.col_conv, k.cols_full};
-    for (const void* f : fc_)
-        if (f && k.col_smem > 48 * 1024)
-            FC_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.col_smem));
+int set_smem_attr(const KV& k) {
+    if (k.f && k.smem > 48 * 1024)
+        FC_CK(cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
     return FC_OK;
+}
+
+int set_smem_attrs(const Variants& v) {
+    int rc = FC_OK;
+    for (int k = 0; k < v.n_rfwd && !rc; ++k) rc = set_smem_attr(v.rfwd[k]);
+    for (int k = 0; k < v.n_rinv && !rc; ++k) rc = set_smem_attr(v.rinv[k]);
+    for (int k = 0; k < v.n_colc && !rc; ++k) rc = set_smem_attr(v.colc[k]);
+    if (!rc) rc = set_smem_attr(v.rows_full);
+    if (!rc) rc = set_smem_attr(v.cols_full);
+    return rc;
 }
 
 int grid_1d(long n, int threads) {
@@ -294,10 +365,14 @@ int grid_1d(long n, int threads) {
 
 struct PrecRes {
     bool on = false;
-    KernSet k;
-    void* Z = nullptr;   // cpx<T>[L*M]
-    void* tw = nullptr;  // cpx<T>[M]
-    void* Gq = nullptr;  // T[(M/2+1)^2]
+    Variants v;
+    int sel[3] = {0, 0, 0};  // chosen shape of pass A, B, C
+    void* Z = nullptr;       // cpx<T>[(M/2) * L], column-major half spectra
+    void* tw = nullptr;      // cpx<T>[M]
+    void* Gq = nullptr;      // T[(M/2+1)^2]
+    const KV& rfwd() const { return v.rfwd[sel[0]]; }
+    const KV& colc() const { return v.colc[sel[1]]; }
+    const KV& rinv() const { return v.rinv[sel[2]]; }
 };
 
 struct fftconv_plan {
@@ -355,7 +430,208 @@ int launch(const void* f, int grid, int threads, size_t smem, cudaStream_t s, T&
     return FC_OK;
 }
 
-int row_grid(const fftconv_plan* p, const KernSet& k) { return (p->L + k.rb - 1) / k.rb; }
+int row_grid(const fftconv_plan* p, const KV& k) { return ((p->L + 1) / 2 + k.per - 1) / k.per; }
+int col_grid(const fftconv_plan* p, const KV& k) { return (p->M / 2) / k.per; }
+
+}  // namespace
+
+// ------------------------------------------------------------- autotuner --
+//
+// Each pass has a few compiled launch shapes (values per thread E, rows or
+// columns per block).  At plan creation the tuner times every shape of each
+// pass on the plan's own size (median-free: the mean of 5 launches after 2
+// warm-ups, on a private stream) and keeps the fastest; choices are cached
+// per (precision, M, L, pass) in a text file (FC_TUNE_CACHE, default
+// $HOME/.cache/fftconv/tune_sm103.txt).  FC_AUTOTUNE=0 skips the timing.
+
+namespace {
+
+std::mutex g_tune_mu;
+bool g_tune_loaded = false;
+struct TuneEntry {
+    char key[96];
+    int idx;
+};
+TuneEntry g_tune[512];
+int g_ntune = 0;
+
+void tune_path(char* out, size_t n) {
+    const char* e = getenv("FC_TUNE_CACHE");
+    if (e && *e) {
+        snprintf(out, n, "%s", e);
+        return;
+    }
+    const char* h = getenv("HOME");
+    snprintf(out, n, "%s/.cache/fftconv/tune_sm103.txt", h ? h : "/tmp");
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    char path[512];
+    tune_path(path, sizeof(path));
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char line[160];
+    while (g_ntune < 512 && fgets(line, sizeof(line), f)) {
+        // "<key>| <index>"; keys contain no '|'
+        char* bar = strrchr(line, '|');
+        if (!bar) continue;
+        *bar = 0;
+        int idx = -1;
+        if (sscanf(bar + 1, "%d", &idx) == 1) {
+            snprintf(g_tune[g_ntune].key, sizeof(g_tune[g_ntune].key), "%s", line);
+            g_tune[g_ntune].idx = idx;
+            ++g_ntune;
+        }
+    }
+    fclose(f);
+}
+
+bool tune_lookup(const char* key, int* idx) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    for (int k = g_ntune - 1; k >= 0; --k)
+        if (!strcmp(g_tune[k].key, key)) {
+            *idx = g_tune[k].idx;
+            return true;
+        }
+    return false;
+}
+
+void tune_store(const char* key, int idx) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    if (g_ntune < 512) {
+        snprintf(g_tune[g_ntune].key, sizeof(g_tune[g_ntune].key), "%s", key);
+        g_tune[g_ntune].idx = idx;
+        ++g_ntune;
+    }
+    char path[512];
+    tune_path(path, sizeof(path));
+    char dir[512];
+    snprintf(dir, sizeof(dir), "%s", path);
+    char* slash = strrchr(dir, '/');
+    if (slash) {
+        *slash = 0;
+        char cmd[600];
+        // best effort: the cache is an optimisation only
+        snprintf(cmd, sizeof(cmd), "%s", dir);
+        for (char* q = cmd + 1; *q; ++q)
+            if (*q == '/') {
+                *q = 0;
+                mkdir(cmd, 0755);
+                *q = '/';
+            }
+        mkdir(cmd, 0755);
+    }
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%s| %d\n", key, idx);
+    fclose(f);
+}
+
+// time one launch shape of one pass (kind 0: A, 1: B, 2: C), PLAIN mode
+template <typename T>
+int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStream_t s, cudaEvent_t e0,
+               cudaEvent_t e1, float* ms) {
+    RowFwdArgs<T> a{};
+    a.L = p->L;
+    a.mode = RF_PLAIN;
+    a.x = x;
+    a.Z = (cpx<T>*)R.Z;
+    a.tw = (const cpx<T>*)R.tw;
+    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
+    RowInvArgs<T> c{};
+    c.L = p->L;
+    c.mode = RI_PLAIN;
+    c.y = y;
+    c.Z = (const cpx<T>*)R.Z;
+    c.tw = (const cpx<T>*)R.tw;
+    const KV& kv = kind == 0 ? R.v.rfwd[k] : (kind == 1 ? R.v.colc[k] : R.v.rinv[k]);
+    const int grid = kind == 1 ? col_grid(p, kv) : row_grid(p, kv);
+    auto go = [&]() -> int {
+        if (kind == 0) return launch(kv.f, grid, kv.threads, kv.smem, s, a);
+        if (kind == 1) return launch(kv.f, grid, kv.threads, kv.smem, s, b);
+        return launch(kv.f, grid, kv.threads, kv.smem, s, c);
+    };
+    int rc = FC_OK;
+    for (int w = 0; w < 2 && !rc; ++w) rc = go();
+    if (rc) return rc;
+    FC_CK(cudaEventRecord(e0, s));
+    for (int w = 0; w < 5 && !rc; ++w) rc = go();
+    if (rc) return rc;
+    FC_CK(cudaEventRecord(e1, s));
+    FC_CK(cudaEventSynchronize(e1));
+    FC_CK(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= 5.0f;
+    return FC_OK;
+}
+
+template <typename T>
+int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
+    const int n[3] = {R.v.n_rfwd, R.v.n_colc, R.v.n_rinv};
+    const int forced[3] = {tune ? tune->shape_rfwd : 0, tune ? tune->shape_col : 0, tune ? tune->shape_rinv : 0};
+    const char* env = getenv("FC_AUTOTUNE");
+    const bool timing = !(tune && tune->no_autotune) && !(env && !strcmp(env, "0"));
+    const char* names[3] = {"rfwd", "colc", "rinv"};
+    bool need[3] = {false, false, false};
+    char keys[3][96];
+    for (int kind = 0; kind < 3; ++kind) {
+        if (forced[kind] > 0) {
+            if (forced[kind] > n[kind]) return FC_EINVAL;
+            R.sel[kind] = forced[kind] - 1;
+            continue;
+        }
+        R.sel[kind] = 0;
+        if (n[kind] <= 1) continue;
+        snprintf(keys[kind], sizeof(keys[kind]), "%s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M,
+                 p->L, names[kind], n[kind]);
+        int idx = 0;
+        if (tune_lookup(keys[kind], &idx) && idx >= 0 && idx < n[kind])
+            R.sel[kind] = idx;
+        else
+            need[kind] = timing;
+    }
+    if (!need[0] && !need[1] && !need[2]) return FC_OK;
+    T *x = nullptr, *y = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = FC_OK;
+    const size_t zbytes = sizeof(cpx<T>) * (size_t)(p->M / 2) * p->L;
+    if (cudaMalloc(&x, sizeof(T) * p->N) != cudaSuccess || cudaMalloc(&y, sizeof(T) * p->N) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemsetAsync(x, 0, sizeof(T) * p->N, s) != cudaSuccess || cudaMemsetAsync(R.Z, 0, zbytes, s) != cudaSuccess) {
+        rc = set_cuda_err(cudaGetLastError(), "autotune set-up");
+    }
+    for (int kind = 0; kind < 3 && !rc; ++kind) {
+        if (!need[kind]) continue;
+        float best = 1e30f;
+        int bi = 0;
+        for (int k = 0; k < n[kind] && !rc; ++k) {
+            float ms = 0;
+            rc = time_shape<T>(p, R, kind, k, x, y, s, e0, e1, &ms);
+            if (!rc && ms < best) {
+                best = ms;
+                bi = k;
+            }
+        }
+        if (!rc) {
+            R.sel[kind] = bi;
+            tune_store(keys[kind], bi);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    if (x) cudaFree(x);
+    if (y) cudaFree(y);
+    return rc;
+}
 
 }  // namespace
 
@@ -363,7 +639,6 @@ extern "C" const char* fc_version(void) { return "fftconv-b300 0.1 (sm_103a)"; }
 extern "C" const char* fc_last_error(void) { return g_err; }
 
 extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg_tune* tune) {
-    (void)tune;
     if (!out) return FC_EINVAL;
     *out = nullptr;
     if (L < 1 || L > 4096 || prec < 1 || prec > 3) return FC_EINVAL;
@@ -399,12 +674,12 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
     // both precisions need FP64 set-up: the spectrum is built in FP64
     p->p64.on = true;
     p->p32.on = (prec & FC_F32) != 0;
-    if (!get_set<double>(M, &p->p64.k) || !get_set<float>(M, &p->p32.k)) {
+    if (!get_variants<double>(M, &p->p64.v) || !get_variants<float>(M, &p->p32.v)) {
         rc = FC_EINVAL;
         goto fail;
     }
-    FC_TRY(set_smem_attrs(p->p64.k));
-    if (p->p32.on) FC_TRY(set_smem_attrs(p->p32.k));
+    FC_TRY(set_smem_attrs(p->p64.v));
+    if (p->p32.on) FC_TRY(set_smem_attrs(p->p32.v));
     FC_TRY(dalloc(p, &p->p64.tw, sizeof(cpx<double>) * M));
     FC_TRY(dalloc(p, &p->p64.Gq, sizeof(double) * (size_t)Q * Q));
     if (p->p32.on) {
@@ -426,11 +701,12 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         size_t MM = (size_t)M * M;
         k_kernel_table<<<(unsigned)((MM + 255) / 256), 256>>>(L, M, K);
         FC_TRYC(cudaGetLastError());
-        const KernSet& k = p->p64.k;
+        const KV& kr = p->p64.v.rows_full;
+        const KV& kc = p->p64.v.cols_full;
         void* a1[2] = {(void*)&K, (void*)&p->p64.tw};
-        FC_TRYC(cudaLaunchKernel(k.rows_full, dim3((M + k.rb - 1) / k.rb), dim3(k.row_threads), a1, k.row_smem, 0));
-        FC_TRYC(cudaLaunchKernel(k.cols_full, dim3(M / k.cb), dim3(k.col_threads), a1, k.col_smem, 0));
-        k_spectrum_quarter<<<(unsigned)((MM + 255) / 256), 256>>>(M, K, (double*)p->p64.Gq, (float*)p->p32.Gq,
+        FC_TRYC(cudaLaunchKernel(kr.f, dim3((M + kr.per - 1) / kr.per), dim3(kr.threads), a1, kr.smem, 0));
+        FC_TRYC(cudaLaunchKernel(kc.f, dim3(M / kc.per), dim3(kc.threads), a1, kc.smem, 0));
+        k_spectrum_quarter<<<grid_1d((long)MM, 256), 256>>>(M, K, (double*)p->p64.Gq, (float*)p->p32.Gq,
                                                                    maxes);
         FC_TRYC(cudaGetLastError());
         FC_TRYC(cudaMemcpy(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost));
@@ -444,12 +720,9 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         rc = FC_ENANINF;
         goto fail;
     }
-    if (!(prec & FC_F64)) {
-        // an FP32-only plan keeps no FP64 spectrum or intermediate
-    }
-    // intermediates and solve workspace
-    if (prec & FC_F64) FC_TRY(dalloc(p, &p->p64.Z, sizeof(cpx<double>) * (size_t)L * M));
-    if (p->p32.on) FC_TRY(dalloc(p, &p->p32.Z, sizeof(cpx<float>) * (size_t)L * M));
+    // intermediates (half spectra, column-major) and solve workspace
+    if (prec & FC_F64) FC_TRY(dalloc(p, &p->p64.Z, sizeof(cpx<double>) * (size_t)L * (M / 2)));
+    if (p->p32.on) FC_TRY(dalloc(p, &p->p32.Z, sizeof(cpx<float>) * (size_t)L * (M / 2)));
     if (prec & FC_F64) {
         FC_TRY(dalloc(p, (void**)&p->x64, sizeof(double) * N));
         FC_TRY(dalloc(p, (void**)&p->r64, sizeof(double) * N));
@@ -487,6 +760,8 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
     }
     FC_TRYC(cudaMallocHost(&p->st_host, sizeof(CgState)));
     FC_TRYC(cudaDeviceSynchronize());
+    if (prec & FC_F64) FC_TRY(autotune<double>(p, p->p64, tune));
+    if (p->p32.on) FC_TRY(autotune<float>(p, p->p32, tune));
     *out = p;
     return FC_OK;
 fail:
@@ -514,11 +789,26 @@ extern "C" int fftconv_plan_info(const fftconv_plan* p, int* L, int* M, int* pre
     return FC_OK;
 }
 
+extern "C" int fftconv_plan_shapes(const fftconv_plan* p, int prec, int n_shapes[3], int chosen[3], int radix[3],
+                                   int per_block[3]) {
+    if (!p || !n_shapes || !chosen || !radix || !per_block) return FC_EINVAL;
+    const PrecRes* R = prec == FC_F32 ? (p->p32.on ? &p->p32 : nullptr) : (prec == FC_F64 && p->p64.on ? &p->p64 : nullptr);
+    if (!R) return FC_EINVAL;
+    const int n[3] = {R->v.n_rfwd, R->v.n_colc, R->v.n_rinv};
+    const KV* k3[3] = {&R->rfwd(), &R->colc(), &R->rinv()};
+    for (int i = 0; i < 3; ++i) {
+        n_shapes[i] = n[i];
+        chosen[i] = R->sel[i];
+        radix[i] = k3[i]->E;
+        per_block[i] = k3[i]->per;
+    }
+    return FC_OK;
+}
+
 namespace {
 
 template <typename T>
 int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
-    const KernSet& k = R.k;
     RowFwdArgs<T> a{};
     a.L = p->L;
     a.mode = RF_PLAIN;
@@ -527,10 +817,11 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     a.part = p->part;
     a.Z = (cpx<T>*)R.Z;
     a.tw = (const cpx<T>*)R.tw;
-    int rc = launch(k.row_fwd, row_grid(p, k), k.row_threads, k.row_smem, s, a);
+    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+    int rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, s, a);
     if (rc) return rc;
     ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
-    rc = launch(k.col_conv, p->M / k.cb, k.col_threads, k.col_smem, s, b);
+    rc = launch(kb.f, col_grid(p, kb), kb.threads, kb.smem, s, b);
     if (rc) return rc;
     RowInvArgs<T> c{};
     c.L = p->L;
@@ -540,7 +831,7 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     c.part = p->part;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = (const cpx<T>*)R.tw;
-    return launch(k.row_inv, row_grid(p, k), k.row_threads, k.row_smem, s, c);
+    return launch(kc.f, row_grid(p, kc), kc.threads, kc.smem, s, c);
 }
 
 }  // namespace
@@ -603,7 +894,7 @@ struct GraphBuilder {
 template <typename T>
 void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp, T* cq,
                     const T* s, const double* r64_start, cudaGraphConditionalHandle h_inner) {
-    const KernSet& k = R.k;
+    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
     RowFwdArgs<T> a{};
     a.L = p->L;
     a.mode = RF_CG;
@@ -616,9 +907,9 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     a.part = p->part;
     a.Z = (cpx<T>*)R.Z;
     a.tw = (const cpx<T>*)R.tw;
-    cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, k.row_fwd, row_grid(p, k), k.row_threads, k.row_smem, a);
+    cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
     ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
-    cudaGraphNode_t nB = gb.kernel(body, &nA, 1, k.col_conv, p->M / k.cb, k.col_threads, k.col_smem, b);
+    cudaGraphNode_t nB = gb.kernel(body, &nA, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
     RowInvArgs<T> c{};
     c.L = p->L;
     c.mode = RI_CG;
@@ -632,7 +923,7 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     c.h_inner = h_inner;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = (const cpx<T>*)R.tw;
-    gb.kernel(body, &nB, 1, k.row_inv, row_grid(p, k), k.row_threads, k.row_smem, c);
+    gb.kernel(body, &nB, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
 }
 
 // Build the solve graph for one mode:
@@ -666,7 +957,7 @@ int build_graph(fftconv_plan* p, int mode) {
         if (e != cudaSuccess) gb.rc = set_cuda_err(e, "cudaGraphConditionalHandleCreate(inner)");
     }
     if (!gb.rc) {
-        const KernSet& k = p->p64.k;
+        const KV &ka = p->p64.rfwd(), &kb = p->p64.colc(), &kc = p->p64.rinv();
         RowFwdArgs<double> a{};
         a.L = p->L;
         a.mode = RF_XUPD;
@@ -684,9 +975,9 @@ int build_graph(fftconv_plan* p, int mode) {
         a.cx = nullptr;
         a.r64 = nullptr;
         a.x = nullptr;
-        cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, k.row_fwd, row_grid(p, k), k.row_threads, k.row_smem, a);
+        cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
         ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tw};
-        cudaGraphNode_t nB = gb.kernel(outer, &nA, 1, k.col_conv, p->M / k.cb, k.col_threads, k.col_smem, b);
+        cudaGraphNode_t nB = gb.kernel(outer, &nA, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
         RowInvArgs<double> c{};
         c.L = p->L;
         c.mode = RI_RESID;
@@ -701,7 +992,7 @@ int build_graph(fftconv_plan* p, int mode) {
         c.h_inner = h_inner;
         c.Z = (const cpx<double>*)p->p64.Z;
         c.tw = (const cpx<double>*)p->p64.tw;
-        cudaGraphNode_t nC = gb.kernel(outer, &nB, 1, k.row_inv, row_grid(p, k), k.row_threads, k.row_smem, c);
+        cudaGraphNode_t nC = gb.kernel(outer, &nB, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
         cudaGraphNode_t nInner = nullptr;
         cudaGraph_t inner = gb.while_node(outer, &nC, 1, h_inner, &nInner);
         if (!gb.rc) {

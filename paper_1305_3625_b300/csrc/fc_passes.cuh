@@ -3,48 +3,34 @@
 // -> cpyReal, Section 3) on the zero-padded M x M grid, with the CG vector
 // work of Listing 2 fused into the first and last pass.
 //
-//   pass A (k_row_fwd): for each of the L data rows, form the input (plain x,
-//       or the CG update x += a p, r -= a q, p = r + b p), zero-extend to M,
-//       forward FFT along x, store the row of the L x M intermediate Z.
-//   pass B (k_col_conv): for each of the M columns, forward FFT of the L
-//       non-zero rows along y, multiply by the real kernel spectrum, inverse
-//       FFT along y, keep rows [0, L) of Z.
-//   pass C (k_row_inv): for each of the L rows, inverse FFT along x, keep
-//       columns [0, L) (the crop of cpyReal) and apply the epilogue:
-//       plain y = C x, the CG product q = P (C p + s p) with the dot products
-//       p.q, r.q, q.q, or the true residual r = P (b - C x - s x).
+// The field is real, so its row transforms are Hermitian: two rows share one
+// complex FFT (x_r + i x_{r+1}) and only the half spectrum kx in [0, M/2) is
+// kept, with the two real values X[0] and X[M/2] packed into slot 0 as
+// X[0] + i X[M/2].  The intermediate is stored column-major, Zt[kx][iy]
+// (M/2 columns of L rows), so the column pass reads contiguous columns.
 //
-// Z is row-major [L][M] complex; the spectrum is stored as its symmetric
-// quarter Gq[(M/2+1)^2] (the kernel is even in each coordinate, so its
-// transform is real and even in each frequency).
+//   pass A (k_rfwd): per pair of data rows, form the input (plain x, or the
+//       CG update x += a p, r -= a q, p = r + b p), FFT the zero-padded pair,
+//       split it into the two rows' half spectra, store them column-major.
+//   pass B (k_colc): per column kx < M/2, forward FFT of the L non-zero rows
+//       along y, multiply by the real kernel spectrum, inverse FFT, keep rows
+//       [0, L).  Column 0 carries the packed pair (kx = 0, kx = M/2) and is
+//       split, multiplied and re-packed in the frequency domain.
+//   pass C (k_rinv): per pair of rows, rebuild the full Hermitian spectra,
+//       inverse FFT both rows in one complex transform, keep columns [0, L)
+//       (the crop of cpyReal) and apply the epilogue: plain y = C x, the CG
+//       product q = P (C p + s p) with p.q, r.q, q.q, or the true residual
+//       r = P (b - C x - s x).
+//
+// The kernel spectrum is stored as its (M/2+1)^2 quarter Gq (the kernel is
+// even in each coordinate and symmetric in x <-> y, so Ghat is real, even in
+// each frequency and Ghat[ky][kx] = Ghat[kx][ky]).
 #pragma once
 
 #include "fc_fft.cuh"
 #include "fc_internal.h"
 
 namespace fc {
-
-// ------------------------------------------------------------ shapes ----
-
-constexpr int pow2floor(int n) { return n < 2 ? 1 : 2 * pow2floor(n / 2); }
-
-template <typename T, int M>
-struct Cfg {
-    static constexpr int E = Shape<T, M>::E;
-    static constexpr int G = Shape<T, M>::G;
-    // rows per CTA in the row passes (about 256 threads)
-    static constexpr int RB = G >= 256 ? 1 : 256 / G;
-    static constexpr int ROW_THREADS = RB * G;
-    // columns per CTA in the column pass
-    static constexpr int CB_RAW = (sizeof(T) == 4 ? 512 : 256) / G;
-    static constexpr int CB_SMEM = (150 * 1024) / (seg_len(M) * (int)sizeof(cpx<T>));
-    static constexpr int CB0 = CB_RAW < CB_SMEM ? CB_RAW : CB_SMEM;
-    static constexpr int CB1 = CB0 < 1 ? 1 : CB0;
-    static constexpr int CB = pow2floor(CB1 > M ? M : CB1);
-    static constexpr int COL_THREADS = CB * G;
-    static constexpr size_t ROW_SMEM = (size_t)RB * seg_len(M) * sizeof(cpx<T>);
-    static constexpr size_t COL_SMEM = (size_t)CB * seg_len(M) * sizeof(cpx<T>);
-};
 
 // ------------------------------------------------------- loads/stores ---
 
@@ -65,6 +51,8 @@ __device__ __forceinline__ void stc(cpx<T>* p, cpx<T> v) {
     else
         *reinterpret_cast<double2*>(p) = make_double2(v.x, v.y);
 }
+template <typename T>
+__device__ __forceinline__ cpx<T> conjc(cpx<T> a) { return {a.x, -a.y}; }
 
 // ------------------------------------------------ block reductions -----
 
@@ -98,8 +86,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*scratch)[NV]
 // last block) with the totals in tot (valid in thread 0).  Deterministic:
 // the reduction order depends only on the grid and block sizes.
 template <int NV>
-__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, unsigned* cnt,
-                                              double (&tot)[NV]) {
+__device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, unsigned* cnt, double (&tot)[NV]) {
     __shared__ double scratch[32][NV];
     __shared__ bool is_last;
     block_sum<NV>(v, scratch);
@@ -124,81 +111,104 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, uns
     return true;
 }
 
+// --------------------------------------------------- per-element input ---
+
+// The value pass A transforms at flat index i (row-major L x L): the plain
+// input, the CG update of Listing 2 (x += a p, r -= a q, p = r + b p; or p = r
+// on the first pass of a run), or the FP64 iterate with the folded-in
+// correction of the last inner run (masked).  acc collects r.r.
+template <typename T>
+__device__ __forceinline__ T pass_a_value(const RowFwdArgs<T>& a, size_t i, int first, T alpha, T beta,
+                                          double inv_sigma, double sig, T& acc) {
+    if (a.mode == RF_PLAIN) return a.x[i];
+    if (a.mode == RF_XUPD) {
+        double xv = a.x64[i];
+        if (a.d32 && sig != 0.0) xv += sig * (double)a.d32[i];
+        if (a.mask && !a.mask[i]) xv = 0.0;
+        a.x64[i] = xv;
+        return (T)xv;
+    }
+    T r, p;
+    if (first) {
+        if (a.r64) {
+            r = (T)(a.r64[i] * inv_sigma);
+            a.cr[i] = r;
+            a.cx[i] = 0;
+        } else {
+            r = a.cr[i];
+        }
+        p = r;
+    } else {
+        p = a.cp[i];
+        a.cx[i] = a.cx[i] + alpha * p;
+        r = a.cr[i] - alpha * a.cq[i];
+        a.cr[i] = r;
+        p = r + beta * p;
+    }
+    a.cp[i] = p;
+    acc += r * r;
+    return p;
+}
+
 // ------------------------------------------------------------ pass A ----
 
-template <typename T, int M>
-__global__ void __launch_bounds__(Cfg<T, M>::ROW_THREADS) k_row_fwd(RowFwdArgs<T> a) {
+// RB row pairs per block, G = M/E threads per pair.
+template <typename T, int M, int E, int RB>
+__global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
     using C = cpx<T>;
-    constexpr int E = Cfg<T, M>::E, G = Cfg<T, M>::G, RB = Cfg<T, M>::RB;
+    constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
-    const int t = threadIdx.x, j = t % G, c = t / G;
+    const int t = threadIdx.x, j = t % G, pl = t / G;
     const int L = a.L;
-    const int iy = blockIdx.x * RB + c;
-    const bool row_ok = iy < L;
+    const int r0 = (blockIdx.x * RB + pl) * 2;
 
-    // CG scalars (read once; written only by other kernels)
     T alpha = 0, beta = 0;
     int first = 0;
-    double inv_sigma = 1.0;
+    double inv_sigma = 1.0, sig = 0.0;
     if (a.mode == RF_CG) {
         first = a.st->first;
         alpha = (T)a.st->alpha;
         beta = (T)a.st->beta;
         if (a.r64) inv_sigma = 1.0 / a.st->sigma;
+    } else if (a.mode == RF_XUPD) {
+        sig = a.st->sigma;  // scale of the inner run that produced d32
     }
-    double sig = 0.0;
-    if (a.mode == RF_XUPD) sig = a.st->sigma;  // scale of the inner run that produced d32
 
     C v[E];
-    T acc = 0;  // partial r.r of this thread (short run, then FP64)
+    T acc = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         v[e] = C{0, 0};
-        if (e < E / 2) {
-            const int n = j + e * G;
-            if (row_ok && n < L) {
-                const size_t i = (size_t)iy * L + n;
-                T val;
-                if (a.mode == RF_PLAIN) {
-                    val = a.x[i];
-                } else if (a.mode == RF_XUPD) {
-                    double xv = a.x64[i];
-                    if (a.d32 && sig != 0.0) xv += sig * (double)a.d32[i];
-                    if (a.mask && !a.mask[i]) xv = 0.0;
-                    a.x64[i] = xv;
-                    val = (T)xv;
-                } else {  // RF_CG
-                    T r, p;
-                    if (first) {
-                        if (a.r64) {
-                            r = (T)(a.r64[i] * inv_sigma);
-                            a.cr[i] = r;
-                            a.cx[i] = 0;
-                        } else {
-                            r = a.cr[i];
-                        }
-                        p = r;
-                    } else {
-                        p = a.cp[i];
-                        a.cx[i] = a.cx[i] + alpha * p;
-                        r = a.cr[i] - alpha * a.cq[i];
-                        a.cr[i] = r;
-                        p = r + beta * p;
-                    }
-                    a.cp[i] = p;
-                    acc += r * r;
-                    val = p;
-                }
-                v[e].x = val;
-            }
+        const int n = j + e * G;
+        if (e < E / 2 && n < L) {  // n >= M/2 >= L for e >= E/2: the zero padding
+            if (r0 < L) v[e].x = pass_a_value(a, (size_t)r0 * L + n, first, alpha, beta, inv_sigma, sig, acc);
+            if (r0 + 1 < L) v[e].y = pass_a_value(a, (size_t)(r0 + 1) * L + n, first, alpha, beta, inv_sigma, sig, acc);
         }
     }
-    fft_stages<T, M, false>(v, j, sm + c * seg_len(M), a.tw);
-    if (row_ok) {
-        C* zr = a.Z + (size_t)iy * M;
+    C* seg = sm + pl * SEG;
+    fft_stages<T, M, E, false>(v, j, seg, a.tw);
 #pragma unroll
-        for (int e = 0; e < E; ++e) stc(zr + j + e * G, v[e]);
+    for (int e = 0; e < E; ++e) seg[spad(j + e * G)] = v[e];
+    __syncthreads();
+    // split the pair into the two rows' half spectra, store column-major
+    const int row_base = blockIdx.x * 2 * RB;
+    const T half = (T)0.5;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int idx = t + q * NT;
+        const int r = idx % (2 * RB), kx = idx / (2 * RB);
+        const int row = row_base + r;
+        const C* sg = sm + (r >> 1) * SEG;
+        C out;
+        if (kx == 0) {
+            const C z0 = sg[spad(0)], zh = sg[spad(H)];
+            out = (r & 1) ? C{z0.y, zh.y} : C{z0.x, zh.x};
+        } else {
+            const C z = sg[spad(kx)], zc = sg[spad(M - kx)];
+            out = (r & 1) ? C{(z.y + zc.y) * half, (zc.x - z.x) * half} : C{(z.x + zc.x) * half, (z.y - zc.y) * half};
+        }
+        if (row < L) stc(a.Z + (size_t)kx * L + row, out);
     }
     if (a.mode == RF_CG) {
         double pv[1] = {(double)acc}, tot[1];
@@ -208,92 +218,149 @@ __global__ void __launch_bounds__(Cfg<T, M>::ROW_THREADS) k_row_fwd(RowFwdArgs<T
 
 // ------------------------------------------------------------ pass B ----
 
-template <typename T, int M>
-__global__ void __launch_bounds__(Cfg<T, M>::COL_THREADS) k_col_conv(ColArgs<T> a) {
+// CB columns per block, G = M/E threads per column (j fastest).
+template <typename T, int M, int E, int CB>
+__global__ void __launch_bounds__(CB*(M / E)) k_colc(ColArgs<T> a) {
     using C = cpx<T>;
-    constexpr int E = Cfg<T, M>::E, G = Cfg<T, M>::G, CB = Cfg<T, M>::CB;
-    constexpr int Q = M / 2 + 1;
+    constexpr int G = M / E, H = M / 2, Q = M / 2 + 1, SEG = seg_len(M);
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
-    const int t = threadIdx.x, c = t % CB, j = t / CB;
+    const int t = threadIdx.x, j = t % G, c = t / G;
     const int L = a.L;
     const int kx = blockIdx.x * CB + c;
-    const int fx = kx <= M / 2 ? kx : M - kx;
+    C* col = a.Z + (size_t)kx * L;
 
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        v[e] = C{0, 0};
         const int n = j + e * G;
-        if (e < E / 2 && n < L) v[e] = ldc_cg(a.Z + (size_t)n * M + kx);
+        v[e] = (e < E / 2 && n < L) ? ldc_cg(col + n) : C{0, 0};
     }
-    C* seg = sm + c * seg_len(M);
-    fft_stages<T, M, false>(v, j, seg, a.tw);
+    C* seg = sm + c * SEG;
+    fft_stages<T, M, E, false>(v, j, seg, a.tw);
+    if (blockIdx.x == 0) {
+        // column 0 holds P = F0 + i FN (kx = 0 and kx = M/2, both real along y);
+        // with the Hermitian partner P[M - ky]: W = P (g0 + gN)/2 + conj(P[M-ky]) (g0 - gN)/2
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        const int ky = j + e * G;
-        const int fy = ky <= M / 2 ? ky : M - ky;
-        const T g = __ldg(a.Gq + (size_t)fy * Q + fx);
-        v[e].x *= g;
-        v[e].y *= g;
+        for (int e = 0; e < E; ++e) seg[spad(j + e * G)] = v[e];
+        __syncthreads();
+        if (c == 0) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ky = j + e * G;
+                const int fy = ky <= H ? ky : M - ky;
+                const C pc = conjc(seg[spad((M - ky) & (M - 1))]);
+                const T g0 = __ldg(a.Gq + fy), gN = __ldg(a.Gq + (size_t)H * Q + fy);
+                const T sp = (g0 + gN) * (T)0.5, sd = (g0 - gN) * (T)0.5;
+                v[e] = C{v[e].x * sp + pc.x * sd, v[e].y * sp + pc.y * sd};
+            }
+        } else {
+            const T* gk = a.Gq + (size_t)kx * Q;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int ky = j + e * G;
+                const T g = __ldg(gk + (ky <= H ? ky : M - ky));
+                v[e].x *= g;
+                v[e].y *= g;
+            }
+        }
+        __syncthreads();
+    } else {
+        const T* gk = a.Gq + (size_t)kx * Q;  // Ghat[ky][kx] = Ghat[kx][ky]: contiguous in ky
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int ky = j + e * G;
+            const T g = __ldg(gk + (ky <= H ? ky : M - ky));
+            v[e].x *= g;
+            v[e].y *= g;
+        }
     }
-    fft_stages<T, M, true>(v, j, seg, a.tw);
+    fft_stages<T, M, E, true>(v, j, seg, a.tw);
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
         const int n = j + e * G;
-        if (n < L) stc(a.Z + (size_t)n * M + kx, v[e]);
+        if (n < L) stc(col + n, v[e]);
     }
 }
 
 // ------------------------------------------------------------ pass C ----
 
-template <typename T, int M>
-__global__ void __launch_bounds__(Cfg<T, M>::ROW_THREADS) k_row_inv(RowInvArgs<T> a) {
+template <typename T>
+__device__ __forceinline__ void pass_c_value(const RowInvArgs<T>& a, size_t i, T y, T& s0, T& s1, T& s2) {
+    const bool act = a.mask == nullptr || a.mask[i] != 0;
+    if (a.mode == RI_PLAIN) {
+        a.y[i] = y;
+    } else if (a.mode == RI_CG) {
+        const T p = a.cp[i];
+        const T q = act ? y + a.s[i] * p : (T)0;
+        a.cq[i] = q;
+        s0 += p * q;
+        s1 += a.cr[i] * q;
+        s2 += q * q;
+    } else {  // RI_RESID (T = double)
+        const double xv = a.x64[i];
+        const double bv = act ? a.b64[i] : 0.0;
+        const double r = act ? bv - ((double)y + a.s64[i] * xv) : 0.0;
+        a.r64[i] = r;
+        s0 += (T)(r * r);
+        s1 += (T)(bv * bv);
+    }
+}
+
+template <typename T, int M, int E, int RB>
+__global__ void __launch_bounds__(RB*(M / E)) k_rinv(RowInvArgs<T> a) {
     using C = cpx<T>;
-    constexpr int E = Cfg<T, M>::E, G = Cfg<T, M>::G, RB = Cfg<T, M>::RB;
+    constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
-    const int t = threadIdx.x, j = t % G, c = t / G;
+    const int t = threadIdx.x, j = t % G, pl = t / G;
     const int L = a.L;
-    const int iy = blockIdx.x * RB + c;
-    const bool row_ok = iy < L;
+    const int row_base = blockIdx.x * 2 * RB;
+    const int r0 = row_base + 2 * pl;
 
-    C v[E];
-    if (row_ok) {
-        const C* zr = a.Z + (size_t)iy * M;
+    // the 2*RB rows' half spectra (column-major) into the pair segments:
+    // row 2p at [0, H), row 2p+1 at [H, M)
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = ldc_cg(zr + j + e * G);
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = C{0, 0};
+    for (int q = 0; q < E; ++q) {
+        const int idx = t + q * NT;
+        const int r = idx % (2 * RB), kx = idx / (2 * RB);
+        const int row = row_base + r;
+        const C y = row < L ? ldc_cg(a.Z + (size_t)kx * L + row) : C{0, 0};
+        sm[(r >> 1) * SEG + spad((r & 1) * H + kx)] = y;
     }
-    fft_stages<T, M, true>(v, j, sm + c * seg_len(M), a.tw);
+    __syncthreads();
+    // Hermitian extension of both rows and pair packing W = Y0 + i Y1
+    C* seg = sm + pl * SEG;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k = j + e * G;
+        C y0, y1;
+        if (k == 0) {
+            y0 = C{seg[spad(0)].x, 0};
+            y1 = C{seg[spad(H)].x, 0};
+        } else if (k == H) {
+            y0 = C{seg[spad(0)].y, 0};
+            y1 = C{seg[spad(H)].y, 0};
+        } else if (k < H) {
+            y0 = seg[spad(k)];
+            y1 = seg[spad(H + k)];
+        } else {
+            y0 = conjc(seg[spad(M - k)]);
+            y1 = conjc(seg[spad(H + M - k)]);
+        }
+        v[e] = C{y0.x - y1.y, y0.y + y1.x};
+    }
+    __syncthreads();
+    fft_stages<T, M, E, true>(v, j, seg, a.tw);
 
     T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
         const int n = j + e * G;
-        if (row_ok && n < L) {
-            const size_t i = (size_t)iy * L + n;
-            const T y = v[e].x;
-            const bool act = a.mask == nullptr || a.mask[i] != 0;
-            if (a.mode == RI_PLAIN) {
-                a.y[i] = y;
-            } else if (a.mode == RI_CG) {
-                const T p = a.cp[i];
-                const T q = act ? y + a.s[i] * p : (T)0;
-                a.cq[i] = q;
-                s0 += p * q;
-                s1 += a.cr[i] * q;
-                s2 += q * q;
-            } else {  // RI_RESID (T = double)
-                const double xv = a.x64[i];
-                const double bv = act ? a.b64[i] : 0.0;
-                const double r = act ? bv - ((double)y + a.s64[i] * xv) : 0.0;
-                a.r64[i] = r;
-                s0 += (T)(r * r);
-                s1 += (T)(bv * bv);
-            }
+        if (n < L) {
+            if (r0 < L) pass_c_value(a, (size_t)r0 * L + n, v[e].x, s0, s1, s2);
+            if (r0 + 1 < L) pass_c_value(a, (size_t)(r0 + 1) * L + n, v[e].y, s0, s1, s2);
         }
     }
     if (a.mode == RI_CG) {

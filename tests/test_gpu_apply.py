@@ -120,3 +120,40 @@ def test_f32_only_plan_applies():
     # an FP32-only plan has no FP64 operator
     with pytest.raises(fc.FcError):
         fc.fftconv_apply_prec(p, fc.FC_F64, dev(x), torch.empty(L * L, device="cuda", dtype=torch.float64))
+
+
+@pytest.mark.parametrize("L", [3, 100, 128, 1024])
+def test_every_compiled_shape_matches(L):
+    """Each launch shape the autotuner may pick gives the same operator."""
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(L * L)
+    x32 = dev(x, torch.float32)
+    xr = host(x32).astype(np.float64)
+    ref32 = oracle.conv_fft(L, xr)
+    M = fc_inputs.padded_side(L)
+    p0 = plan(L)
+    n = fc.fftconv_plan_shapes(p0, fc.FC_F32)["n_shapes"]
+    for k in range(max(n)):
+        shapes = tuple(min(k, n[i] - 1) for i in range(3))
+        p = fc.fftconv_plan_create(L, fc.FC_F32, shapes=shapes)
+        info = fc.fftconv_plan_shapes(p, fc.FC_F32)
+        assert info["chosen"] == list(shapes)
+        y = torch.empty_like(x32)
+        fc.fftconv_apply(p, x32, y)
+        check(host(y).astype(np.float64), ref32, U32, M, f"L={L} shapes {shapes} {info['radix']} {info['per_block']}")
+
+
+def test_autotune_writes_cache(tmp_path, monkeypatch):
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = ("import paper_1305_3625_b300 as fc; p = fc.fftconv_plan_create(512, fc.FC_F32); "
+            "print(fc.fftconv_plan_shapes(p, fc.FC_F32))")
+    env = dict(__import__("os").environ, FC_TUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    lines = cache.read_text().splitlines()
+    assert any("f32 M=1024 L=512 colc" in ln for ln in lines), lines
+    # a second plan reads the cached choice instead of timing again
+    out2 = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    assert out.stdout == out2.stdout
+    assert len(cache.read_text().splitlines()) == len(lines)
