@@ -82,7 +82,7 @@ typedef struct cg_opts {
     int refine_every;  /* cap on inner iterations between two true residuals
                           (0: 100000)                                           */
     int max_refine;    /* cap on true-residual evaluations (0: 60)              */
-    double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 1e-4)    */
+    double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 3e-3)    */
     int x0_zero;       /* 1: start from x = 0 and ignore the input x            */
     int reserved;
 } cg_opts;

@@ -17,12 +17,14 @@ struct cpx;
 // that another block of the same kernel may be writing.
 struct CgState {
     double rr;           // r.r of the current inner residual (pass A, direct sum)
+    double rp;           // r.p of the current residual and direction (pass A)
     double alpha, beta;  // CG step length and direction update of the last product
     double tol2;         // inner stop: recursive r.r <= tol2
     double sigma;        // norm of the true residual the inner run started from
     double rr64, bb;     // last true residual r.r and masked b.b (FP64)
     double rtol2;        // target: rr64 <= rtol2 * bb
     double inner_rtol2;  // mixed: inner target relative to the unit right-hand side
+    double beta_carry;   // direction kept across a true-residual replacement (0: restart)
     int iter;            // products spent in inner loops (all cycles)
     int max_iter;
     int cycle_iter, cycle_max;
@@ -82,13 +84,15 @@ struct RowInvArgs {
 };
 
 // Decide the CG step after the product q = A p of one iteration of Listing 2.
-// With pq = p.q, rq = r.q, qq = q.q: alpha = rr/pq and the new residual norm
-// |r - alpha q|^2 = rr - 2 alpha rq + alpha^2 qq, which gives beta without a
-// second pass over the vectors.
+// alpha = r.p / p.q, the exact minimiser along p (equal to r.r / p.q in exact
+// CG, where r is orthogonal to the previous direction, and still right after
+// a true-residual replacement); the new residual norm
+// |r - alpha q|^2 = rr - 2 alpha rq + alpha^2 qq gives beta = |r'|^2 / |r|^2
+// without a second pass over the vectors.
 __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq, double qq,
                                                unsigned long long h_inner) {
     const double rr = st->rr;
-    double alpha = rr / pq;
+    double alpha = st->rp / pq;
     double rrn = rr - 2.0 * alpha * rq + alpha * alpha * qq;
     if (rrn < 0.0) rrn = 0.0;
     int d = 0;
@@ -126,16 +130,25 @@ __device__ __forceinline__ void refine_decide(CgState* st, double rr64, double b
         go = 1;
     }
     if (go) {
+        // Reliable update: the true residual replaces the recursive one and
+        // the search direction is kept, p = r + beta' p_old with
+        // beta' = |r_true|^2 / |r_i|^2 (physical units), so refinement does
+        // not restart the Krylov space.  When the true residual did not drop
+        // below the last recursive one (beta' >= 1: rounding floor or drift)
+        // CG restarts from p = r instead.  The inner vectors are scaled by
+        // 1/sigma (mixed) or 1 (FP64): in scaled units
+        // beta_carry = rr64 / (sigma_old sigma_new rr_i).
+        const double s_old = st->sigma;
+        const double s_new = st->mixed ? sqrt(rr64) : 1.0;
+        const double bphys = (st->rr > 0.0 && s_old > 0.0) ? rr64 / (s_old * s_old * st->rr) : 2.0;
+        const bool carry =
+            st->cycles > 1 && (st->inner_done == 1 || st->inner_done == 2) && bphys < 1.0 && s_new > 0.0;
+        st->beta_carry = carry ? rr64 / (s_old * s_new * st->rr) : 0.0;
         st->first = 1;
         st->cycle_iter = 0;
         st->inner_done = 0;
-        if (st->mixed) {
-            st->sigma = sqrt(rr64);
-            st->tol2 = st->inner_rtol2;
-        } else {
-            st->sigma = 1.0;
-            st->tol2 = st->rtol2 * bb;
-        }
+        st->sigma = s_new;
+        st->tol2 = st->mixed ? st->inner_rtol2 : st->rtol2 * bb;
     }
     if (!go) st->first = 1;  // no inner run follows: the final update is a no-op
     st->finished = go ? 0 : 1;

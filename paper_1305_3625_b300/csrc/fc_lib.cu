@@ -1063,7 +1063,7 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     }
     CgState h{};
     h.rtol2 = o->rtol * o->rtol;
-    const double irt = o->inner_rtol > 0 ? o->inner_rtol : 1e-4;
+    const double irt = o->inner_rtol > 0 ? o->inner_rtol : 3e-3;
     h.inner_rtol2 = irt * irt;
     h.max_iter = o->max_iter > 0 ? o->max_iter : 1000000;
     h.cycle_max = o->refine_every > 0 ? o->refine_every : 100000;

@@ -114,12 +114,13 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, uns
 // --------------------------------------------------- per-element input ---
 
 // The value pass A transforms at flat index i (row-major L x L): the plain
-// input, the CG update of Listing 2 (x += a p, r -= a q, p = r + b p; or p = r
-// on the first pass of a run), or the FP64 iterate with the folded-in
-// correction of the last inner run (masked).  acc collects r.r.
+// input, the CG update of Listing 2 (x += a p, r -= a q, p = r + b p; on the
+// first pass of a run p = r, or p = r + b' p_old when the direction is kept
+// across a true-residual replacement), or the FP64 iterate with the
+// folded-in correction of the last inner run (masked).  acc collects r.r.
 template <typename T>
 __device__ __forceinline__ T pass_a_value(const RowFwdArgs<T>& a, size_t i, int first, T alpha, T beta,
-                                          double inv_sigma, double sig, T& acc) {
+                                          double inv_sigma, double sig, T& acc, T& acc_rp, T bcarry) {
     if (a.mode == RF_PLAIN) return a.x[i];
     if (a.mode == RF_XUPD) {
         double xv = a.x64[i];
@@ -137,7 +138,7 @@ __device__ __forceinline__ T pass_a_value(const RowFwdArgs<T>& a, size_t i, int 
         } else {
             r = a.cr[i];
         }
-        p = r;
+        p = bcarry != (T)0 ? r + bcarry * a.cp[i] : r;
     } else {
         p = a.cp[i];
         a.cx[i] = a.cx[i] + alpha * p;
@@ -147,6 +148,7 @@ __device__ __forceinline__ T pass_a_value(const RowFwdArgs<T>& a, size_t i, int 
     }
     a.cp[i] = p;
     acc += r * r;
+    acc_rp += r * p;
     return p;
 }
 
@@ -163,27 +165,31 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
     const int L = a.L;
     const int r0 = (blockIdx.x * RB + pl) * 2;
 
-    T alpha = 0, beta = 0;
+    T alpha = 0, beta = 0, bcarry = 0;
     int first = 0;
     double inv_sigma = 1.0, sig = 0.0;
     if (a.mode == RF_CG) {
         first = a.st->first;
         alpha = (T)a.st->alpha;
         beta = (T)a.st->beta;
+        bcarry = (T)a.st->beta_carry;
         if (a.r64) inv_sigma = 1.0 / a.st->sigma;
     } else if (a.mode == RF_XUPD) {
         sig = a.st->sigma;  // scale of the inner run that produced d32
     }
 
     C v[E];
-    T acc = 0;
+    T acc = 0, acc_rp = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         v[e] = C{0, 0};
         const int n = j + e * G;
         if (e < E / 2 && n < L) {  // n >= M/2 >= L for e >= E/2: the zero padding
-            if (r0 < L) v[e].x = pass_a_value(a, (size_t)r0 * L + n, first, alpha, beta, inv_sigma, sig, acc);
-            if (r0 + 1 < L) v[e].y = pass_a_value(a, (size_t)(r0 + 1) * L + n, first, alpha, beta, inv_sigma, sig, acc);
+            if (r0 < L)
+                v[e].x = pass_a_value(a, (size_t)r0 * L + n, first, alpha, beta, inv_sigma, sig, acc, acc_rp, bcarry);
+            if (r0 + 1 < L)
+                v[e].y = pass_a_value(a, (size_t)(r0 + 1) * L + n, first, alpha, beta, inv_sigma, sig, acc, acc_rp,
+                                      bcarry);
         }
     }
     C* seg = sm + pl * SEG;
@@ -211,8 +217,11 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
         if (row < L) stc(a.Z + (size_t)kx * L + row, out);
     }
     if (a.mode == RF_CG) {
-        double pv[1] = {(double)acc}, tot[1];
-        if (grid_sum_last<1>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) a.st->rr = tot[0];
+        double pv[2] = {(double)acc, (double)acc_rp}, tot[2];
+        if (grid_sum_last<2>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) {
+            a.st->rr = tot[0];
+            a.st->rp = tot[1];
+        }
     }
 }
 
