@@ -71,7 +71,9 @@ typedef struct cg_tune {
     int shape_col;   /* 0: tuned; k > 0: shape k-1 of the column pass B      */
     int shape_rinv;  /* 0: tuned; k > 0: shape k-1 of the row pass C         */
     int no_autotune; /* 1: no timing (cached choice or shape 0)             */
-    int reserved[4];
+    int shape_pers;  /* inner CG loop: 0 tuned persistent kernel, k > 0 compiled
+                        persistent kernel k-1, -1 one graph node per pass   */
+    int reserved[3];
 } cg_tune;
 
 typedef struct cg_opts {
@@ -94,6 +96,8 @@ typedef struct cg_result {
     int reserved;
     double true_rel_resid; /* ||P(b - A x)|| / ||P b|| from the last FP64 residual */
     double bnorm;          /* ||P b||                                           */
+    double latency_s;      /* server: submit to completion; cg_solve: call time */
+    double run_s;          /* server: admission to completion; cg_solve: call time */
 } cg_result;
 
 /* Library version string and the last CUDA error text of this thread. */
@@ -126,6 +130,12 @@ int fftconv_plan_info(const fftconv_plan *p, int *L, int *M, int *prec, size_t *
  * its values per thread and rows-pairs / columns per block.  Host only. */
 int fftconv_plan_shapes(const fftconv_plan *p, int prec, int n_shapes[3], int chosen[3], int radix[3],
                         int per_block[3]);
+
+/* The inner CG loop of a solve in precision prec runs either as one
+ * persistent cooperative kernel per inner run (chosen >= 0: which of n
+ * compiled kernels, its block size and resident grid) or, when chosen is -1,
+ * as one graph node per pass inside a device-side while loop.  Host only. */
+int fftconv_plan_solver(const fftconv_plan *p, int prec, int *n, int *chosen, int *threads, int *grid);
 
 /*
  * fftconv_apply -- y = C x (Listing 3: cpyComplex, FFT, elementMult, inverse
@@ -197,6 +207,50 @@ int fc_masked_step(fftconv_plan *p, const double *t, uint8_t *mask, double *x, i
  */
 int fc_masked_step_static(int64_t N, const double *t, uint8_t *mask, double *x, int64_t *removed,
                           fc_stream_t stream);
+
+/* ------------------------------------------------------------- serving -- */
+
+/* One solve request.  Host pointers: s and b (L*L doubles) are copied at
+ * submit; x (L*L doubles) receives the solution before cg_poll reports done. */
+typedef struct cg_request {
+    int L;           /* 1..4096                                              */
+    int mode;        /* FC_MODE_F64 or FC_MODE_MIXED                         */
+    double rtol;     /* target relative residual (FP64 recomputed)           */
+    const double *s; /* host, compliances s_i > 0                            */
+    const double *b; /* host, right-hand side                                */
+    double *x;       /* host, receives the solution (may be NULL)            */
+    uint64_t tag;    /* caller's tag                                         */
+} cg_request;
+
+/*
+ * cg_server_create -- a continuous-batching solve server on the current
+ * device (the paper has no serving layer; this is the many-solve workload
+ * around its Listing 2 solver).
+ *   mem_budget_bytes  device memory the server may hold for plans and staging.
+ *   max_slots         concurrent solves (worker slots, each with its own
+ *                     non-blocking stream), 1..256.
+ *   stream            unused (each slot owns a stream).
+ * A request is admitted when a slot is free and its plan fits the budget
+ * (idle plans of other sizes are evicted if needed); plans stay resident and
+ * are reused by later requests of the same L.  Work of different requests
+ * overlaps on the device; each result depends only on its own inputs.
+ */
+int cg_server_create(cg_server **sv, size_t mem_budget_bytes, int max_slots, fc_stream_t stream);
+
+/* Queue a request; *ticket identifies it.  FC_EBUDGET if its plan can never
+ * fit the budget, FC_EINVAL for bad arguments.  Returns at once. */
+int cg_batch_submit(cg_server *sv, const cg_request *rq, uint64_t *ticket);
+
+/* Non-blocking: *done = 1 once the request finished; then r (may be NULL)
+ * receives its result (status, iterations, residual, latency) and the ticket
+ * is released.  FC_ENOTFOUND for an unknown or released ticket. */
+int cg_poll(cg_server *sv, uint64_t ticket, cg_result *r, int *done);
+
+/* Memory held now and at peak, queued requests, resident plans. */
+int cg_server_stats(cg_server *sv, size_t *used, size_t *peak, int *queued, int *plans);
+
+/* Stop the workers (running solves finish), free plans and buffers. */
+int cg_server_destroy(cg_server *sv);
 
 #ifdef __cplusplus
 }

@@ -52,17 +52,24 @@ class cg_opts(ctypes.Structure):
 
 class cg_tune(ctypes.Structure):
     _fields_ = [("shape_rfwd", ctypes.c_int), ("shape_col", ctypes.c_int), ("shape_rinv", ctypes.c_int),
-                ("no_autotune", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("no_autotune", ctypes.c_int), ("shape_pers", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class cg_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("reserved", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
-                ("bnorm", ctypes.c_double)]
+                ("bnorm", ctypes.c_double), ("latency_s", ctypes.c_double), ("run_s", ctypes.c_double)]
 
     def as_dict(self):
         return {"status": self.status, "iters": self.iters, "refinements": self.refinements,
-                "true_rel_resid": self.true_rel_resid, "bnorm": self.bnorm}
+                "true_rel_resid": self.true_rel_resid, "bnorm": self.bnorm,
+                "latency_s": self.latency_s, "run_s": self.run_s}
+
+
+class cg_request(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("mode", ctypes.c_int), ("rtol", ctypes.c_double),
+                ("s", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("tag", ctypes.c_uint64)]
 
 
 LIB_PATH = _build.LIB
@@ -79,6 +86,8 @@ def _load():
     lib.fftconv_plan_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(cg_tune)]
     ip3 = ctypes.c_int * 3
     lib.fftconv_plan_shapes.argtypes = [vp, i, ip3, ip3, ip3, ip3]
+    ipt = ctypes.POINTER(ctypes.c_int)
+    lib.fftconv_plan_solver.argtypes = [vp, i, ipt, ipt, ipt, ipt]
     lib.fftconv_plan_destroy.argtypes = [vp]
     lib.fftconv_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(sz)]
@@ -87,6 +96,11 @@ def _load():
     lib.cg_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
     lib.fc_masked_step.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.fc_masked_step_static.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp]
+    lib.cg_server_create.argtypes = [ctypes.POINTER(vp), sz, i, vp]
+    lib.cg_batch_submit.argtypes = [vp, ctypes.POINTER(cg_request), ctypes.POINTER(ctypes.c_uint64)]
+    lib.cg_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(cg_result), ctypes.POINTER(i)]
+    lib.cg_server_stats.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.cg_server_destroy.argtypes = [vp]
     return lib
 
 
@@ -149,16 +163,20 @@ class Plan:
             pass
 
 
-def fftconv_plan_create(L: int, prec: int = FC_F32 | FC_F64, shapes=None, no_autotune: bool = False) -> Plan:
+def fftconv_plan_create(L: int, prec: int = FC_F32 | FC_F64, shapes=None, no_autotune: bool = False,
+                        persistent=None) -> Plan:
     """shapes: optional (pass A, pass B, pass C) compiled-shape indices (0-based)
-    to force instead of the tuned choice."""
+    to force instead of the tuned choice; persistent: index of the persistent
+    inner-CG kernel to force, or -1 for the per-pass graph loop."""
     h = ctypes.c_void_p()
     tune = None
-    if shapes is not None or no_autotune:
+    if shapes is not None or no_autotune or persistent is not None:
         tune = cg_tune()
         if shapes is not None:
             tune.shape_rfwd, tune.shape_col, tune.shape_rinv = (int(k) + 1 for k in shapes)
         tune.no_autotune = int(bool(no_autotune))
+        if persistent is not None:
+            tune.shape_pers = -1 if persistent < 0 else int(persistent) + 1
     rc = _lib.fftconv_plan_create(ctypes.byref(h), int(L), int(prec),
                                   ctypes.byref(tune) if tune is not None else None)
     if rc != FC_OK:
@@ -241,3 +259,96 @@ def fftconv_plan_shapes(plan: Plan, prec: int) -> dict:
     if rc != FC_OK:
         raise FcError(rc, "fftconv_plan_shapes")
     return {"n_shapes": list(n), "chosen": list(ch), "radix": list(rad), "per_block": list(per)}
+
+
+def fftconv_plan_solver(plan: Plan, prec: int) -> dict:
+    """How the inner CG loop runs: persistent kernel index (-1: graph loop)."""
+    n, ch, th, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = _lib.fftconv_plan_solver(plan.handle, int(prec), ctypes.byref(n), ctypes.byref(ch), ctypes.byref(th),
+                                  ctypes.byref(gr))
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_plan_solver")
+    return {"n": n.value, "chosen": ch.value, "threads": th.value, "grid": gr.value}
+
+
+
+class Server:
+    """Owning handle of a cg_server (continuous-batching solve server)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        self._keep = {}  # ticket -> host arrays that must outlive the request
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.cg_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cg_server_create(mem_budget_bytes: int, max_slots: int = 16) -> Server:
+    h = ctypes.c_void_p()
+    rc = _lib.cg_server_create(ctypes.byref(h), ctypes.c_size_t(int(mem_budget_bytes)), int(max_slots), None)
+    if rc != FC_OK:
+        raise FcError(rc, "cg_server_create")
+    return Server(h)
+
+
+def cg_batch_submit(sv: Server, L: int, s, b, x_out=None, rtol: float = 1e-8, mode: int = FC_MODE_MIXED,
+                    tag: int = 0) -> int:
+    """Queue one solve (host float64 arrays of L*L); x_out (float64, L*L,
+    C-contiguous numpy array) receives the solution.  Returns the ticket."""
+    import numpy as np
+    n = int(L) * int(L)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if s.size != n or b.size != n:
+        raise ValueError("s and b need L*L values")
+    if x_out is not None and (x_out.dtype != np.float64 or not x_out.flags.c_contiguous or x_out.size != n):
+        raise ValueError("x_out must be a contiguous float64 array of L*L values")
+    rq = cg_request(L=int(L), mode=int(mode), rtol=float(rtol), s=s.ctypes.data, b=b.ctypes.data,
+                    x=x_out.ctypes.data if x_out is not None else None, tag=int(tag))
+    t = ctypes.c_uint64()
+    rc = _lib.cg_batch_submit(sv.handle, ctypes.byref(rq), ctypes.byref(t))
+    if rc != FC_OK:
+        raise FcError(rc, "cg_batch_submit")
+    sv._keep[t.value] = x_out
+    return t.value
+
+
+def cg_poll(sv: Server, ticket: int):
+    """Non-blocking: None while running, else the result dict."""
+    r = cg_result()
+    done = ctypes.c_int()
+    rc = _lib.cg_poll(sv.handle, ctypes.c_uint64(ticket), ctypes.byref(r), ctypes.byref(done))
+    if rc not in (FC_OK,) and not done.value:
+        raise FcError(rc, "cg_poll")
+    if not done.value:
+        return None
+    sv._keep.pop(ticket, None)
+    out = r.as_dict()
+    out["rc"] = rc
+    return out
+
+
+def cg_server_stats(sv: Server) -> dict:
+    used, peak = ctypes.c_size_t(), ctypes.c_size_t()
+    q, pl = ctypes.c_int(), ctypes.c_int()
+    rc = _lib.cg_server_stats(sv.handle, ctypes.byref(used), ctypes.byref(peak), ctypes.byref(q), ctypes.byref(pl))
+    if rc != FC_OK:
+        raise FcError(rc, "cg_server_stats")
+    return {"used": used.value, "peak": peak.value, "queued": q.value, "plans": pl.value}
+
+
+def cg_server_destroy(sv: Server) -> None:
+    sv.close()

@@ -131,40 +131,80 @@ struct Dft<2, INV, T> {
 };
 
 // Shared-memory index with one padding slot every 16 elements; it spreads the
-// radix-16 "expand" writes (stride 16) over the banks.
-__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+// radix-16 "expand" writes (stride 16) over the banks.  For every access
+// pattern of the stages below, spad(base + c) = spad(base) + c + (c >> 4)
+// with c a compile-time multiple of the stride (checked exhaustively for all
+// M <= 8192, E in {2,4,8,16}), so addresses are a base plus immediates.
+__host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int seg_len(int M) { return M + (M >> 4) + 2; }
+__host__ __device__ constexpr int pofs(int c) { return c + (c >> 4); }
 
-constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+// Stage structure of a length-M transform with E values per thread: stages
+// NS = 1, E, E^2, ... of radix E, the last one of radix M/NS if smaller.
+__host__ __device__ constexpr int stage_radix(int M, int E, int NS) { return NS * E <= M ? E : M / NS; }
+__host__ __device__ constexpr int n_exchanges(int M, int E) {
+    int n = 0;
+    for (int ns = 1; ns * E < M; ns *= E) ++n;
+    return n;
+}
+// Stage twiddle table: for each stage with NS > 1 a block of NS x R entries,
+// entry [k][e] = exp(-2 pi i e k / (NS R)) (R the stage radix); the offset of
+// stage NS's block, and the whole table's length.
+__host__ __device__ constexpr int tw_offset(int M, int E, int NS) {
+    int off = 0;
+    for (int ns = E; ns < NS && ns < M; ns *= stage_radix(M, E, ns)) off += ns * stage_radix(M, E, ns);
+    return off;
+}
+__host__ __device__ constexpr int tw_len(int M, int E) { return tw_offset(M, E, M); }
+
+// Load the R-1 twiddles e = 1..R-1 of one table row (16-byte loads).
+template <typename T, int R>
+__device__ __forceinline__ void load_twiddles(const cpx<T>* __restrict__ row, cpx<T> (&w)[R]) {
+    if constexpr (sizeof(T) == 4 && R % 2 == 0) {
+        const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+        for (int h = 0; h < R / 2; ++h) {
+            const float4 q = __ldg(r4 + h);
+            w[2 * h] = cpx<T>{q.x, q.y};
+            w[2 * h + 1] = cpx<T>{q.z, q.w};
+        }
+    } else {
+#pragma unroll
+        for (int e = 1; e < R; ++e) w[e] = ldg_c(row + e);
+    }
+}
 
 // Stockham transform of one length-M sequence held by G = M/E threads as
 // v[e] = x[j + e*G] (thread j of its group); on return v[e] = X[j + e*G].
-// sm is this group's shared segment (seg_len(M) elements); tw[m] =
-// exp(-2 pi i m / M).  All threads of the block call this together (it uses
-// __syncthreads between the exchanges).
-template <typename T, int M, int E, bool INV, int NS = 1>
-__device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm, const cpx<T>* __restrict__ tw) {
+// sm0/sm1: this group's two shared segments (seg_len(M) elements each).
+// With DB the exchanges alternate between them (starting with BUF) and need
+// one barrier each; without DB only sm0 is used and each exchange ends with
+// a second barrier.  tws: the stage twiddle table of (M, E).  All threads of
+// the block call this together.
+template <typename T, int M, int E, bool INV, bool DB, int BUF = 0, int NS = 1>
+__device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, cpx<T>* sm1,
+                                           const cpx<T>* __restrict__ tws) {
     constexpr int G = M / E;
     if constexpr (NS * E <= M) {
         const int k = j & (NS - 1);
         if constexpr (NS > 1) {
-            constexpr int step = M / (NS * E);
+            cpx<T> w[E];
+            load_twiddles<T, E>(tws + tw_offset(M, E, NS) + k * E, w);
 #pragma unroll
-            for (int e = 1; e < E; ++e) {
-                cpx<T> w = ldg_c(tw + e * k * step);
-                v[e] = INV ? cmulc(v[e], w) : cmul(v[e], w);
-            }
+            for (int e = 1; e < E; ++e) v[e] = INV ? cmulc(v[e], w[e]) : cmul(v[e], w[e]);
         }
         Dft<E, INV, T>::run(v);
         if constexpr (NS * E < M) {
-            const int idxD = (j / NS) * NS * E + k;
+            cpx<T>* sm = (DB && BUF) ? sm1 : sm0;
+            cpx<T>* wp = sm + spad((j / NS) * NS * E + k);
 #pragma unroll
-            for (int e = 0; e < E; ++e) sm[spad(idxD + e * NS)] = v[e];
+            for (int e = 0; e < E; ++e) wp[pofs(e * NS)] = v[e];
             __syncthreads();
+            const cpx<T>* rp = sm + spad(j);
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = sm[spad(j + e * G)];
-            __syncthreads();
-            fft_stages<T, M, E, INV, NS * E>(v, j, sm, tw);
+            for (int e = 0; e < E; ++e) v[e] = rp[pofs(e * G)];
+            if constexpr (!DB) __syncthreads();
+            fft_stages<T, M, E, INV, DB, DB ? 1 - BUF : 0, NS * E>(v, j, sm0, sm1, tws);
         }
     } else {
         constexpr int R = M / NS;  // 2 <= R < E, last stage
@@ -172,20 +212,24 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm, co
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             const int jj = j + b * G;
-            cpx<T> u[R];
+            cpx<T> u[R], w[R];
+            load_twiddles<T, R>(tws + tw_offset(M, E, NS) + jj * R, w);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 u[r] = v[b + r * B];
-                if (r > 0) {
-                    cpx<T> w = ldg_c(tw + r * jj);
-                    u[r] = INV ? cmulc(u[r], w) : cmul(u[r], w);
-                }
+                if (r > 0) u[r] = INV ? cmulc(u[r], w[r]) : cmul(u[r], w[r]);
             }
             Dft<R, INV, T>::run(u);
 #pragma unroll
             for (int r = 0; r < R; ++r) v[b + r * B] = u[r];
         }
     }
+}
+
+// Buffer a caller may write right after fft_stages<..., DB, BUF> returns
+// (the one the next exchange would use).
+__host__ __device__ constexpr int next_buf(int M, int E, bool DB, int BUF) {
+    return DB ? (BUF + n_exchanges(M, E)) % 2 : 0;
 }
 
 }  // namespace fc

@@ -30,8 +30,8 @@ struct CgState {
     int cycle_iter, cycle_max;
     int cycles, max_cycles;  // true-residual evaluations
     int first;               // 1: the next pass A starts a new inner run (p = r)
-    int inner_done;          // 0 running, 1 converged, 2 cap reached, 3 breakdown
-    int status;              // FC_OK, FC_ENOCONV or FC_ENANINF once finished
+    int inner_done;          // 0 running, 1 converged, 2 cap reached, 3 breakdown, 4 barrier timeout
+    int status;              // FC_OK, FC_ENOCONV, FC_ENANINF or FC_ETIMEOUT once finished
     int mixed;               // 1: inner runs in FP32 on the scaled residual
     int finished;
     int pad_;
@@ -120,7 +120,9 @@ __device__ __forceinline__ void refine_decide(CgState* st, double rr64, double b
     st->bb = bb;
     st->cycles += 1;
     int go = 0;
-    if (!isfinite(rr64) || !isfinite(bb)) {
+    if (st->inner_done == 4) {
+        st->status = FC_ETIMEOUT;  // the persistent inner loop's grid barrier ran out
+    } else if (!isfinite(rr64) || !isfinite(bb)) {
         st->status = FC_ENANINF;
     } else if (bb == 0.0 || rr64 <= st->rtol2 * bb) {
         st->status = FC_OK;

@@ -14,10 +14,11 @@
 
 #include <sys/stat.h>
 
+#include <chrono>
 #include <mutex>
 #include <new>
 
-#include "fc_passes.cuh"
+#include "fc_persist.cuh"
 
 using namespace fc;
 
@@ -46,6 +47,18 @@ __global__ void k_twiddles(int M, cpx<double>* tw64, cpx<float>* tw32) {
     sincospi(2.0 * (double)m / (double)M, &s, &c);
     if (tw64) tw64[m] = cpx<double>{c, -s};
     if (tw32) tw32[m] = cpx<float>{(float)c, (float)-s};
+}
+
+// Stage twiddle table of a (M, E) transform from the FP64 base table
+// tw64[m] = exp(-2 pi i m / M): entry [k][e] of the stage with span NS and
+// radix R is tw64[e k M / (NS R)], rounded to T.
+template <typename T>
+__global__ void k_stage_twiddles(int M, int NS, int R, int off, const cpx<double>* tw64, cpx<T>* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= NS * R) return;
+    const int k = i / R, e = i % R;
+    const cpx<double> w = tw64[(size_t)e * k * (M / (NS * R))];
+    out[off + i] = cpx<T>{(T)w.x, (T)w.y};
 }
 
 // Green's function of Eq. 1c (a = 1, (1-nu^2)/E = 1): point form 1/(pi r) and
@@ -79,7 +92,7 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rows_full(cpx<double>* K, const 
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = ok ? K[(size_t)row * M + j + e * G] : C{0, 0};
-    fft_stages<double, M, E, false>(v, j, sm + c * seg_len(M), tw);
+    fft_stages<double, M, E, false, false, 0>(v, j, sm + c * seg_len(M), sm + c * seg_len(M), tw);
     if (ok)
 #pragma unroll
         for (int e = 0; e < E; ++e) K[(size_t)row * M + j + e * G] = v[e];
@@ -96,7 +109,7 @@ __global__ void __launch_bounds__(CB*(M / E)) k_cols_full(cpx<double>* K, const 
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = K[(size_t)(j + e * G) * M + col];
-    fft_stages<double, M, E, false>(v, j, sm + c * seg_len(M), tw);
+    fft_stages<double, M, E, false, false, 0>(v, j, sm + c * seg_len(M), sm + c * seg_len(M), tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) K[(size_t)(j + e * G) * M + col] = v[e];
 }
@@ -157,6 +170,11 @@ __global__ void k_cg_final(long N, const CgState* st, T* x, const T* p) {
 __global__ void k_f64_to_f32(long N, const double* a, float* b) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
+}
+
+template <typename T>
+__global__ void k_fill(long N, T* a, T v) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) a[i] = v;
 }
 
 __global__ void k_fill_u8(long N, uint8_t* m, uint8_t v) {
@@ -254,9 +272,19 @@ struct KV {
     size_t smem = 0;
 };
 
+// One compiled persistent inner-CG kernel: pass A/C shape (EA, RB) and
+// pass B shape (EB, CB) with the same block size.
+struct KVP {
+    const void* f = nullptr;
+    int threads = 0, EA = 0, RB = 0, EB = 0, CB = 0;
+    size_t smem = 0;
+};
+
 struct Variants {
-    KV rfwd[4], colc[4], rinv[4];
+    KV rfwd[8], colc[8], rinv[8];
     int n_rfwd = 0, n_colc = 0, n_rinv = 0;
+    KVP pers[6];
+    int n_pers = 0;
     KV rows_full, cols_full;  // FP64 only: spectrum set-up
 };
 
@@ -264,20 +292,37 @@ constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi 
 
 template <typename T, int M, int E, int RB>
 void add_row(Variants& v) {
-    KV f{(const void*)k_rfwd<T, M, E, RB>, RB * (M / E), RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<T>)};
-    KV i{(const void*)k_rinv<T, M, E, RB>, RB * (M / E), RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<T>)};
-    for (int k = 0; k < v.n_rfwd; ++k)
-        if (v.rfwd[k].f == f.f) return;
-    v.rfwd[v.n_rfwd++] = f;
-    v.rinv[v.n_rinv++] = i;
+    if constexpr (RB * (M / E) <= 1024 && pass_smem<T, M, RB>() <= 200 * 1024) {
+        KV f{(const void*)k_rfwd<T, M, E, RB>, RB * (M / E), RB, E, pass_smem<T, M, RB>()};
+        KV i{(const void*)k_rinv<T, M, E, RB>, RB * (M / E), RB, E, pass_smem<T, M, RB>()};
+        for (int k = 0; k < v.n_rfwd; ++k)
+            if (v.rfwd[k].f == f.f) return;
+        v.rfwd[v.n_rfwd++] = f;
+        v.rinv[v.n_rinv++] = i;
+    }
 }
 
 template <typename T, int M, int E, int CB>
 void add_col(Variants& v) {
-    KV c{(const void*)k_colc<T, M, E, CB>, CB * (M / E), CB, E, (size_t)CB * seg_len(M) * sizeof(cpx<T>)};
-    for (int k = 0; k < v.n_colc; ++k)
-        if (v.colc[k].f == c.f) return;
-    v.colc[v.n_colc++] = c;
+    if constexpr (CB * (M / E) <= 1024 && pass_smem<T, M, CB>() <= 200 * 1024) {
+        KV c{(const void*)k_colc<T, M, E, CB>, CB * (M / E), CB, E, pass_smem<T, M, CB>()};
+        for (int k = 0; k < v.n_colc; ++k)
+            if (v.colc[k].f == c.f) return;
+        v.colc[v.n_colc++] = c;
+    }
+}
+
+template <typename T, int M, int EA, int EB, int NT>
+void add_pers(Variants& v) {
+    constexpr int GA = EA <= M ? M / EA : 1, GB = EB <= M ? M / EB : 1;
+    constexpr int RB = NT / GA, CB = NT / GB;
+    constexpr size_t SA = pass_smem<T, M, (RB > 0 ? RB : 1)>(), SB = pass_smem<T, M, (CB > 0 ? CB : 1)>();
+    constexpr size_t SM = SA > SB ? SA : SB;
+    if constexpr (M >= 64 && EA <= M && EB <= M && RB >= 1 && CB >= 1 && RB * GA == NT && CB * GB == NT &&
+                  CB <= M / 2 && NT <= 1024 && NT % 32 == 0 && SM <= 200 * 1024) {
+        if (v.n_pers < 6)
+            v.pers[v.n_pers++] = KVP{(const void*)k_cg_persist<T, M, EA, RB, EB, CB>, NT, EA, RB, EB, CB, SM};
+    }
 }
 
 // Launch shapes compiled for each (precision, M).  FP32 sizes from 256 up
@@ -295,14 +340,24 @@ void make_variants(Variants& v) {
             add_row<T, M, 16, clampi(128 / G, 1, 128)>(v);
             add_col<T, M, 16, clampi(256 / G, 1, H)>(v);
         } else {
-            constexpr int G16 = M / 16, G8 = M / 8;
+            constexpr int G16 = M / 16, G8 = M / 8, G4 = M / 4;
             add_row<T, M, 16, clampi(256 / G16, 1, 64)>(v);
-            add_row<T, M, 8, clampi(256 / G8, 1, 64)>(v);
             add_row<T, M, 16, clampi(512 / G16, 1, 64)>(v);
+            add_row<T, M, 8, clampi(256 / G8, 1, 64)>(v);
+            add_row<T, M, 8, clampi(512 / G8, 1, 64)>(v);
+            add_row<T, M, 4, clampi(512 / G4, 1, 64)>(v);
+            add_col<T, M, 16, clampi(128 / G16, 1, H)>(v);
             add_col<T, M, 16, clampi(256 / G16, 1, H)>(v);
             add_col<T, M, 8, clampi(256 / G8, 1, H)>(v);
-            add_col<T, M, 16, clampi(512 / G16, 1, H)>(v);
+            add_col<T, M, 8, clampi(512 / G8, 1, H)>(v);
+            add_col<T, M, 4, clampi(512 / G4, 1, H)>(v);
         }
+        add_pers<T, M, 16, 16, (M * M / 32 < 256 ? M * M / 32 : 256)>(v);
+        add_pers<T, M, 16, 8, 256>(v);
+        add_pers<T, M, 8, 8, 256>(v);
+        add_pers<T, M, 16, 16, 512>(v);
+        add_pers<T, M, 8, 8, 512>(v);
+        add_pers<T, M, 8, 8, 1024>(v);
     } else {
         constexpr int E = M <= 8 ? M : (M <= 2048 ? 8 : 16);
         constexpr int G = M / E;
@@ -313,6 +368,8 @@ void make_variants(Variants& v) {
         constexpr int CBF = clampi(256 / G, 1, M);
         v.rows_full = KV{(const void*)k_rows_full<M, E, RB>, RB * G, RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<double>)};
         v.cols_full = KV{(const void*)k_cols_full<M, E, CBF>, CBF * G, CBF, E, (size_t)CBF * seg_len(M) * sizeof(cpx<double>)};
+        add_pers<T, M, E, E, (M / E) * 4 <= 256 ? (M / E) * 4 : (M / E)>(v);
+        add_pers<T, M, E, E, 256>(v);
     }
 }
 
@@ -348,10 +405,17 @@ int set_smem_attrs(const Variants& v) {
     for (int k = 0; k < v.n_rfwd && !rc; ++k) rc = set_smem_attr(v.rfwd[k]);
     for (int k = 0; k < v.n_rinv && !rc; ++k) rc = set_smem_attr(v.rinv[k]);
     for (int k = 0; k < v.n_colc && !rc; ++k) rc = set_smem_attr(v.colc[k]);
+    for (int k = 0; k < v.n_pers && !rc; ++k)
+        if (v.pers[k].smem > 48 * 1024)
+            if (cudaFuncSetAttribute(v.pers[k].f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.pers[k].smem) !=
+                cudaSuccess)
+                rc = set_cuda_err(cudaGetLastError(), "cudaFuncSetAttribute(persistent)");
     if (!rc) rc = set_smem_attr(v.rows_full);
     if (!rc) rc = set_smem_attr(v.cols_full);
     return rc;
 }
+
+constexpr int kMaxPersistGrid = 148 * 16;
 
 int grid_1d(long n, int threads) {
     long g = (n + threads - 1) / threads;
@@ -367,12 +431,27 @@ struct PrecRes {
     bool on = false;
     Variants v;
     int sel[3] = {0, 0, 0};  // chosen shape of pass A, B, C
+    int sel_pers = -1;       // chosen persistent inner-CG kernel (-1: graph loop)
+    int pers_grid = 0;       // its cooperative grid (resident blocks)
     void* Z = nullptr;       // cpx<T>[(M/2) * L], column-major half spectra
-    void* tw = nullptr;      // cpx<T>[M]
+    void* tw = nullptr;      // FP64 only: base table exp(-2 pi i m/M), m < M
+    void* twst[5] = {};      // stage twiddle tables for E = 2, 4, 8, 16 (index log2 E)
     void* Gq = nullptr;      // T[(M/2+1)^2]
     const KV& rfwd() const { return v.rfwd[sel[0]]; }
     const KV& colc() const { return v.colc[sel[1]]; }
     const KV& rinv() const { return v.rinv[sel[2]]; }
+    const void* tws(int E) const { return twst[E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : 0]; }
+    // every shape this precision may launch has its stage twiddle table
+    bool tables_ok(int M) const {
+        auto ok = [&](int E) { return E >= M || tws(E) != nullptr; };
+        for (int k = 0; k < v.n_rfwd; ++k)
+            if (!ok(v.rfwd[k].E)) return false;
+        for (int k = 0; k < v.n_colc; ++k)
+            if (!ok(v.colc[k].E)) return false;
+        for (int k = 0; k < v.n_pers; ++k)
+            if (!ok(v.pers[k].EA) || !ok(v.pers[k].EB)) return false;
+        return true;
+    }
 };
 
 struct fftconv_plan {
@@ -388,6 +467,9 @@ struct fftconv_plan {
     CgState* st = nullptr;
     CgState* st_host = nullptr;  // pinned
     double* part = nullptr;
+    double* partA = nullptr;  // persistent kernel: per-block partial sums
+    double* partC = nullptr;
+    PersistCtl* pctl = nullptr;
     double* am_v = nullptr;
     long long* am_i = nullptr;
     ArgmaxCtl* am_ctl = nullptr;
@@ -414,11 +496,15 @@ void plan_free(fftconv_plan* p) {
         if (p->gexec[m]) cudaGraphExecDestroy(p->gexec[m]);
         if (p->graph[m]) cudaGraphDestroy(p->graph[m]);
     }
-    void* ptrs[] = {p->p32.Z, p->p32.tw, p->p32.Gq, p->p64.Z, p->p64.tw, p->p64.Gq, p->x64, p->r64,
+    void* ptrs[] = {p->p32.Z, p->p32.Gq, p->p64.Z, p->p64.tw, p->p64.Gq, p->x64, p->r64,
                     p->p64v, p->q64, p->b64, p->s64, p->mask, p->d32, p->r32, p->p32v, p->q32, p->s32,
-                    p->st, p->part, p->am_v, p->am_i, p->am_ctl};
+                    p->st, p->part, p->partA, p->partC, p->pctl, p->am_v, p->am_i, p->am_ctl};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    for (int i = 0; i < 5; ++i) {
+        if (p->p32.twst[i]) cudaFree(p->p32.twst[i]);
+        if (p->p64.twst[i]) cudaFree(p->p64.twst[i]);
+    }
     if (p->st_host) cudaFreeHost(p->st_host);
     delete p;
 }
@@ -432,6 +518,42 @@ int launch(const void* f, int grid, int threads, size_t smem, cudaStream_t s, T&
 
 int row_grid(const fftconv_plan* p, const KV& k) { return ((p->L + 1) / 2 + k.per - 1) / k.per; }
 int col_grid(const fftconv_plan* p, const KV& k) { return (p->M / 2) / k.per; }
+
+// Stage twiddle tables for every value-per-thread count E that a compiled
+// shape of this precision uses.
+template <typename T>
+int build_stage_tables(fftconv_plan* p, PrecRes& R, const cpx<double>* tw64, cudaStream_t cs) {
+    int Es[8], nE = 0;
+    auto addE = [&](int E) {
+        if (E < 2) return;
+        for (int i = 0; i < nE; ++i)
+            if (Es[i] == E) return;
+        Es[nE++] = E;
+    };
+    for (int k = 0; k < R.v.n_rfwd; ++k) addE(R.v.rfwd[k].E);
+    for (int k = 0; k < R.v.n_colc; ++k) addE(R.v.colc[k].E);
+    for (int k = 0; k < R.v.n_pers; ++k) {
+        addE(R.v.pers[k].EA);
+        addE(R.v.pers[k].EB);
+    }
+    addE(R.v.rows_full.E);
+    addE(R.v.cols_full.E);
+    const int M = p->M;
+    for (int i = 0; i < nE; ++i) {
+        const int E = Es[i];
+        const int len = tw_len(M, E);
+        const int idx = E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4;
+        int rc = dalloc(p, &R.twst[idx], sizeof(cpx<T>) * (size_t)(len > 2 ? len : 2));
+        if (rc) return rc;
+        for (int ns = E; ns < M; ns *= stage_radix(M, E, ns)) {
+            const int rad = stage_radix(M, E, ns), n = ns * rad;
+            k_stage_twiddles<T><<<(n + 255) / 256, 256, 0, cs>>>(M, ns, rad, tw_offset(M, E, ns), tw64,
+                                                                 (cpx<T>*)R.twst[idx]);
+            FC_CK(cudaGetLastError());
+        }
+    }
+    return FC_OK;
+}
 
 }  // namespace
 
@@ -535,20 +657,21 @@ void tune_store(const char* key, int idx) {
 template <typename T>
 int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStream_t s, cudaEvent_t e0,
                cudaEvent_t e1, float* ms) {
+    const KV& kv = kind == 0 ? R.v.rfwd[k] : (kind == 1 ? R.v.colc[k] : R.v.rinv[k]);
+    const cpx<T>* tw = (const cpx<T>*)R.tws(kv.E);
     RowFwdArgs<T> a{};
     a.L = p->L;
     a.mode = RF_PLAIN;
     a.x = x;
     a.Z = (cpx<T>*)R.Z;
-    a.tw = (const cpx<T>*)R.tw;
-    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
+    a.tw = tw;
+    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, tw};
     RowInvArgs<T> c{};
     c.L = p->L;
     c.mode = RI_PLAIN;
     c.y = y;
     c.Z = (const cpx<T>*)R.Z;
-    c.tw = (const cpx<T>*)R.tw;
-    const KV& kv = kind == 0 ? R.v.rfwd[k] : (kind == 1 ? R.v.colc[k] : R.v.rinv[k]);
+    c.tw = tw;
     const int grid = kind == 1 ? col_grid(p, kv) : row_grid(p, kv);
     auto go = [&]() -> int {
         if (kind == 0) return launch(kv.f, grid, kv.threads, kv.smem, s, a);
@@ -574,6 +697,8 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     const int forced[3] = {tune ? tune->shape_rfwd : 0, tune ? tune->shape_col : 0, tune ? tune->shape_rinv : 0};
     const char* env = getenv("FC_AUTOTUNE");
     const bool timing = !(tune && tune->no_autotune) && !(env && !strcmp(env, "0"));
+    const char* venv = getenv("FC_TUNE_VERBOSE");
+    const bool verbose = venv && strcmp(venv, "0");
     const char* names[3] = {"rfwd", "colc", "rinv"};
     bool need[3] = {false, false, false};
     char keys[3][96];
@@ -599,8 +724,9 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = FC_OK;
     const size_t zbytes = sizeof(cpx<T>) * (size_t)(p->M / 2) * p->L;
-    if (cudaMalloc(&x, sizeof(T) * p->N) != cudaSuccess || cudaMalloc(&y, sizeof(T) * p->N) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMallocAsync((void**)&x, sizeof(T) * p->N, s) != cudaSuccess ||
+        cudaMallocAsync((void**)&y, sizeof(T) * p->N, s) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
         cudaMemsetAsync(x, 0, sizeof(T) * p->N, s) != cudaSuccess || cudaMemsetAsync(R.Z, 0, zbytes, s) != cudaSuccess) {
         rc = set_cuda_err(cudaGetLastError(), "autotune set-up");
@@ -612,6 +738,11 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
         for (int k = 0; k < n[kind] && !rc; ++k) {
             float ms = 0;
             rc = time_shape<T>(p, R, kind, k, x, y, s, e0, e1, &ms);
+            if (!rc && verbose) {
+                const KV& kv = kind == 0 ? R.v.rfwd[k] : (kind == 1 ? R.v.colc[k] : R.v.rinv[k]);
+                fprintf(stderr, "[fftconv tune] %s shape %d (E=%d, per=%d, threads=%d, smem=%zu): %.3f us\n",
+                        keys[kind], k, kv.E, kv.per, kv.threads, kv.smem, ms * 1e3f);
+            }
             if (!rc && ms < best) {
                 best = ms;
                 bi = k;
@@ -625,11 +756,11 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (s) {
+        if (x) cudaFreeAsync(x, s);
+        if (y) cudaFreeAsync(y, s);
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
-    if (x) cudaFree(x);
-    if (y) cudaFree(y);
     return rc;
 }
 
@@ -637,6 +768,12 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
 
 extern "C" const char* fc_version(void) { return "fftconv-b300 0.1 (sm_103a)"; }
 extern "C" const char* fc_last_error(void) { return g_err; }
+
+namespace {
+template <typename T>
+int choose_persistent(fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp, T* cq, T* s, int forced, bool timing,
+                      bool verbose);
+}  // namespace
 
 extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg_tune* tune) {
     if (!out) return FC_EINVAL;
@@ -656,6 +793,7 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
     cpx<double>* K = nullptr;
     double* maxes = nullptr;
     double hmax[2] = {0, 0};
+    cudaStream_t cs = nullptr;  // set-up work stays off other streams (no device-wide syncs)
     cudaError_t e;
 #define FC_TRY(x)                     \
     do {                              \
@@ -671,6 +809,7 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         }                                                \
     } while (0)
     FC_TRYC(cudaGetDevice(&p->dev));
+    FC_TRYC(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     // both precisions need FP64 set-up: the spectrum is built in FP64
     p->p64.on = true;
     p->p32.on = (prec & FC_F32) != 0;
@@ -682,39 +821,47 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
     if (p->p32.on) FC_TRY(set_smem_attrs(p->p32.v));
     FC_TRY(dalloc(p, &p->p64.tw, sizeof(cpx<double>) * M));
     FC_TRY(dalloc(p, &p->p64.Gq, sizeof(double) * (size_t)Q * Q));
-    if (p->p32.on) {
-        FC_TRY(dalloc(p, &p->p32.tw, sizeof(cpx<float>) * M));
-        FC_TRY(dalloc(p, &p->p32.Gq, sizeof(float) * (size_t)Q * Q));
-    }
+    if (p->p32.on) FC_TRY(dalloc(p, &p->p32.Gq, sizeof(float) * (size_t)Q * Q));
     // spectrum: kernel table -> unpruned FP64 2D FFT -> quarter / M^2
-    e = cudaMalloc(&K, sizeof(cpx<double>) * (size_t)M * M);
+    e = cudaMallocAsync((void**)&K, sizeof(cpx<double>) * (size_t)M * M, cs);
     if (e != cudaSuccess) {
         rc = FC_ENOMEM;
-        set_cuda_err(e, "cudaMalloc(spectrum grid)");
+        set_cuda_err(e, "cudaMallocAsync(spectrum grid)");
         goto fail;
     }
-    FC_TRYC(cudaMalloc(&maxes, 2 * sizeof(double)));
-    FC_TRYC(cudaMemset(maxes, 0, 2 * sizeof(double)));
-    k_twiddles<<<(M + 255) / 256, 256>>>(M, (cpx<double>*)p->p64.tw, (cpx<float>*)p->p32.tw);
+    FC_TRYC(cudaMallocAsync((void**)&maxes, 2 * sizeof(double), cs));
+    FC_TRYC(cudaMemsetAsync(maxes, 0, 2 * sizeof(double), cs));
+    k_twiddles<<<(M + 255) / 256, 256, 0, cs>>>(M, (cpx<double>*)p->p64.tw, nullptr);
     FC_TRYC(cudaGetLastError());
+    FC_TRY(build_stage_tables<double>(p, p->p64, (const cpx<double>*)p->p64.tw, cs));
+    if (p->p32.on) FC_TRY(build_stage_tables<float>(p, p->p32, (const cpx<double>*)p->p64.tw, cs));
+    if (!p->p64.tables_ok(M) || (p->p32.on && !p->p32.tables_ok(M))) {
+        snprintf(g_err, sizeof(g_err), "internal: a launch shape has no stage twiddle table (M=%d)", M);
+        rc = FC_EINVAL;
+        goto fail;
+    }
     {
         size_t MM = (size_t)M * M;
-        k_kernel_table<<<(unsigned)((MM + 255) / 256), 256>>>(L, M, K);
+        k_kernel_table<<<(unsigned)((MM + 255) / 256), 256, 0, cs>>>(L, M, K);
         FC_TRYC(cudaGetLastError());
         const KV& kr = p->p64.v.rows_full;
         const KV& kc = p->p64.v.cols_full;
-        void* a1[2] = {(void*)&K, (void*)&p->p64.tw};
-        FC_TRYC(cudaLaunchKernel(kr.f, dim3((M + kr.per - 1) / kr.per), dim3(kr.threads), a1, kr.smem, 0));
-        FC_TRYC(cudaLaunchKernel(kc.f, dim3(M / kc.per), dim3(kc.threads), a1, kc.smem, 0));
-        k_spectrum_quarter<<<grid_1d((long)MM, 256), 256>>>(M, K, (double*)p->p64.Gq, (float*)p->p32.Gq,
-                                                                   maxes);
+        const void* twr = p->p64.tws(kr.E);
+        const void* twc = p->p64.tws(kc.E);
+        void* a1[2] = {(void*)&K, (void*)&twr};
+        void* a2[2] = {(void*)&K, (void*)&twc};
+        FC_TRYC(cudaLaunchKernel(kr.f, dim3((M + kr.per - 1) / kr.per), dim3(kr.threads), a1, kr.smem, cs));
+        FC_TRYC(cudaLaunchKernel(kc.f, dim3(M / kc.per), dim3(kc.threads), a2, kc.smem, cs));
+        k_spectrum_quarter<<<grid_1d((long)MM, 256), 256, 0, cs>>>(M, K, (double*)p->p64.Gq, (float*)p->p32.Gq,
+                                                                         maxes);
         FC_TRYC(cudaGetLastError());
-        FC_TRYC(cudaMemcpy(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost));
+        FC_TRYC(cudaMemcpyAsync(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost, cs));
     }
-    cudaFree(K);
+    FC_TRYC(cudaFreeAsync(K, cs));
     K = nullptr;
-    cudaFree(maxes);
+    FC_TRYC(cudaFreeAsync(maxes, cs));
     maxes = nullptr;
+    FC_TRYC(cudaStreamSynchronize(cs));
     if (!(hmax[0] <= 1e-12 * hmax[1])) {
         snprintf(g_err, sizeof(g_err), "kernel spectrum not real: max|Im| %.3e, max|Re| %.3e", hmax[0], hmax[1]);
         rc = FC_ENANINF;
@@ -740,7 +887,7 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         }
     }
     FC_TRY(dalloc(p, (void**)&p->st, sizeof(CgState)));
-    FC_TRYC(cudaMemset(p->st, 0, sizeof(CgState)));
+    FC_TRYC(cudaMemsetAsync(p->st, 0, sizeof(CgState), cs));
     {
         int g = L;  // row passes never use more blocks than rows
         FC_TRY(dalloc(p, (void**)&p->part, sizeof(double) * 3 * (size_t)(g + 1)));
@@ -748,25 +895,51 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         FC_TRY(dalloc(p, (void**)&p->am_v, sizeof(double) * p->am_grid));
         FC_TRY(dalloc(p, (void**)&p->am_i, sizeof(long long) * p->am_grid));
         FC_TRY(dalloc(p, (void**)&p->am_ctl, sizeof(ArgmaxCtl)));
-        FC_TRYC(cudaMemset(p->am_ctl, 0, sizeof(ArgmaxCtl)));
+        FC_TRYC(cudaMemsetAsync(p->am_ctl, 0, sizeof(ArgmaxCtl), cs));
+        FC_TRY(dalloc(p, (void**)&p->partA, sizeof(double) * 2 * kMaxPersistGrid));
+        FC_TRY(dalloc(p, (void**)&p->partC, sizeof(double) * 3 * kMaxPersistGrid));
+        FC_TRY(dalloc(p, (void**)&p->pctl, sizeof(PersistCtl)));
+        FC_TRYC(cudaMemsetAsync(p->pctl, 0, sizeof(PersistCtl), cs));
     }
     if (!(prec & FC_F64)) {
         // FP32-only plan: drop the FP64 tables once the FP32 ones exist
+        FC_TRYC(cudaStreamSynchronize(cs));
         cudaFree(p->p64.tw);
         cudaFree(p->p64.Gq);
         p->bytes -= sizeof(cpx<double>) * M + sizeof(double) * (size_t)Q * Q;
         p->p64.tw = p->p64.Gq = nullptr;
+        for (int i = 0; i < 5; ++i)
+            if (p->p64.twst[i]) {
+                cudaFree(p->p64.twst[i]);
+                p->p64.twst[i] = nullptr;
+            }
         p->p64.on = false;
     }
     FC_TRYC(cudaMallocHost(&p->st_host, sizeof(CgState)));
-    FC_TRYC(cudaDeviceSynchronize());
+    FC_TRYC(cudaStreamSynchronize(cs));
     if (prec & FC_F64) FC_TRY(autotune<double>(p, p->p64, tune));
     if (p->p32.on) FC_TRY(autotune<float>(p, p->p32, tune));
+    if (prec & FC_F64) {
+        const char* env = getenv("FC_AUTOTUNE");
+        const bool timing = !(tune && tune->no_autotune) && !(env && !strcmp(env, "0"));
+        const char* venv = getenv("FC_TUNE_VERBOSE");
+        const bool verbose = venv && strcmp(venv, "0");
+        const int forced = tune ? tune->shape_pers : 0;
+        FC_TRY(choose_persistent<double>(p, p->p64, p->x64, p->r64, p->p64v, p->q64, p->s64, forced, timing, verbose));
+        if (p->p32.on)
+            FC_TRY(choose_persistent<float>(p, p->p32, p->d32, p->r32, p->p32v, p->q32, p->s32, forced, timing,
+                                            verbose));
+    }
+    cudaStreamDestroy(cs);
     *out = p;
     return FC_OK;
 fail:
-    if (K) cudaFree(K);
-    if (maxes) cudaFree(maxes);
+    if (cs) {
+        if (K) cudaFreeAsync(K, cs);
+        if (maxes) cudaFreeAsync(maxes, cs);
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
     plan_free(p);
     return rc;
 #undef FC_TRY
@@ -805,6 +978,17 @@ extern "C" int fftconv_plan_shapes(const fftconv_plan* p, int prec, int n_shapes
     return FC_OK;
 }
 
+extern "C" int fftconv_plan_solver(const fftconv_plan* p, int prec, int* n, int* chosen, int* threads, int* grid) {
+    if (!p || !n || !chosen || !threads || !grid) return FC_EINVAL;
+    const PrecRes* R = prec == FC_F32 ? (p->p32.on ? &p->p32 : nullptr) : (prec == FC_F64 && p->p64.on ? &p->p64 : nullptr);
+    if (!R) return FC_EINVAL;
+    *n = R->v.n_pers;
+    *chosen = R->sel_pers;
+    *threads = R->sel_pers >= 0 ? R->v.pers[R->sel_pers].threads : 0;
+    *grid = R->sel_pers >= 0 ? R->pers_grid : 0;
+    return FC_OK;
+}
+
 namespace {
 
 template <typename T>
@@ -815,12 +999,12 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     a.x = x;
     a.st = p->st;
     a.part = p->part;
-    a.Z = (cpx<T>*)R.Z;
-    a.tw = (const cpx<T>*)R.tw;
     const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+    a.Z = (cpx<T>*)R.Z;
+    a.tw = (const cpx<T>*)R.tws(ka.E);
     int rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, s, a);
     if (rc) return rc;
-    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
+    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
     rc = launch(kb.f, col_grid(p, kb), kb.threads, kb.smem, s, b);
     if (rc) return rc;
     RowInvArgs<T> c{};
@@ -830,7 +1014,7 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     c.st = p->st;
     c.part = p->part;
     c.Z = (const cpx<T>*)R.Z;
-    c.tw = (const cpx<T>*)R.tw;
+    c.tw = (const cpx<T>*)R.tws(kc.E);
     return launch(kc.f, row_grid(p, kc), kc.threads, kc.smem, s, c);
 }
 
@@ -849,6 +1033,156 @@ extern "C" int fftconv_apply(fftconv_plan* p, const void* x, void* y, fc_stream_
     if (!p) return FC_EINVAL;
     return fftconv_apply_prec(p, (p->prec & FC_F32) ? FC_F32 : FC_F64, x, y, stream);
 }
+
+// ------------------------------------------------- persistent inner CG --
+
+namespace {
+
+template <typename T>
+PersistArgs<T> make_pargs(fftconv_plan* p, PrecRes& R, const KVP& kp, T* cx, T* cr, T* cp, T* cq, const T* s,
+                          const double* r64start) {
+    PersistArgs<T> P{};
+    P.A.L = p->L;
+    P.A.mode = RF_CG;
+    P.A.cx = cx;
+    P.A.cr = cr;
+    P.A.cp = cp;
+    P.A.cq = cq;
+    P.A.r64 = r64start;
+    P.A.st = p->st;
+    P.A.part = p->part;
+    P.A.Z = (cpx<T>*)R.Z;
+    P.A.tw = (const cpx<T>*)R.tws(kp.EA);
+    P.B = ColArgs<T>{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kp.EB)};
+    P.C.L = p->L;
+    P.C.mode = RI_CG;
+    P.C.s = s;
+    P.C.cp = cp;
+    P.C.cr = cr;
+    P.C.cq = cq;
+    P.C.mask = p->mask;
+    P.C.st = p->st;
+    P.C.part = p->part;
+    P.C.Z = (const cpx<T>*)R.Z;
+    P.C.tw = (const cpx<T>*)R.tws(kp.EA);
+    P.nA = ((p->L + 1) / 2 + kp.RB - 1) / kp.RB;
+    P.nB = (p->M / 2) / kp.CB;
+    P.partA = p->partA;
+    P.partC = p->partC;
+    P.ctl = p->pctl;
+    P.N = p->N;
+    return P;
+}
+
+// Resident blocks of a persistent kernel (its cooperative grid), at most one
+// per unit of work; 0 if it cannot be resident at all.
+int pers_grid(fftconv_plan* p, const KVP& kp) {
+    int nb = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kp.f, kp.threads, kp.smem) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev) != cudaSuccess) return 0;
+    long g = (long)nb * sms;
+    const long nA = ((p->L + 1) / 2 + kp.RB - 1) / kp.RB, nB = (p->M / 2) / kp.CB;
+    const long units = nA > nB ? nA : nB;
+    if (g > units) g = units;
+    if (g > kMaxPersistGrid) g = kMaxPersistGrid;
+    return (int)g;
+}
+
+// Time K inner iterations of each persistent variant on the plan's own size
+// (r = 1, s = 1, all sites active) and keep the fastest; cached like the
+// pass shapes.  forced: 0 tuned, k > 0 variant k-1, < 0 none (graph loop).
+template <typename T>
+int choose_persistent(fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp, T* cq, T* s, int forced, bool timing,
+                      bool verbose) {
+    R.sel_pers = -1;
+    const int n = R.v.n_pers;
+    if (n == 0 || forced < 0) return FC_OK;
+    if (forced > 0) {
+        if (forced > n) return FC_OK;  // this precision has fewer kernels: graph loop
+        R.sel_pers = forced - 1;
+        R.pers_grid = pers_grid(p, R.v.pers[R.sel_pers]);
+        if (R.pers_grid < 1) R.sel_pers = -1;
+        return FC_OK;
+    }
+    char key[96];
+    snprintf(key, sizeof(key), "%s M=%d L=%d pers n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M, p->L, n);
+    int idx = -1;
+    if (tune_lookup(key, &idx) && idx >= 0 && idx < n && pers_grid(p, R.v.pers[idx]) > 0) {
+        R.sel_pers = idx;
+        R.pers_grid = pers_grid(p, R.v.pers[idx]);
+        return FC_OK;
+    }
+    if (!timing) {
+        for (int k = 0; k < n; ++k)
+            if (pers_grid(p, R.v.pers[k]) > 0) {
+                R.sel_pers = k;
+                R.pers_grid = pers_grid(p, R.v.pers[k]);
+                return FC_OK;
+            }
+        return FC_OK;
+    }
+    const long N = p->N;
+    const int K = 12;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    FC_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    FC_CK(cudaEventCreate(&e0));
+    FC_CK(cudaEventCreate(&e1));
+    const int g1 = grid_1d(N, 256);
+    k_fill<T><<<g1, 256, 0, st>>>(N, cr, (T)1);
+    k_fill<T><<<g1, 256, 0, st>>>(N, cp, (T)0);
+    k_fill<T><<<g1, 256, 0, st>>>(N, cq, (T)0);
+    k_fill<T><<<g1, 256, 0, st>>>(N, cx, (T)0);
+    k_fill<T><<<g1, 256, 0, st>>>(N, s, (T)1);
+    k_fill_u8<<<g1, 256, 0, st>>>(N, p->mask, 1);
+    CgState h{};
+    h.first = 1;
+    h.tol2 = 0.0;
+    h.cycle_max = K;
+    h.max_iter = 1 << 30;
+    h.sigma = 1.0;
+    *p->st_host = h;
+    float best = 1e30f;
+    int bi = -1, rc = FC_OK;
+    for (int k = 0; k < n && !rc; ++k) {
+        const KVP& kp = R.v.pers[k];
+        const int grid = pers_grid(p, kp);
+        if (grid < 1) continue;
+        PersistArgs<T> P = make_pargs<T>(p, R, kp, cx, cr, cp, cq, s, nullptr);
+        void* args[1] = {(void*)&P};
+        float ms = 0;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            if (cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                cudaMemsetAsync(p->pctl, 0, sizeof(PersistCtl), st) != cudaSuccess ||
+                cudaEventRecord(e0, st) != cudaSuccess ||
+                cudaLaunchCooperativeKernel(kp.f, dim3(grid), dim3(kp.threads), args, kp.smem, st) != cudaSuccess ||
+                cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                rc = set_cuda_err(cudaGetLastError(), "persistent tuning launch");
+        }
+        if (rc) break;
+        if (verbose)
+            fprintf(stderr, "[fftconv tune] %spersistent %d (EA=%d RB=%d EB=%d CB=%d threads=%d grid=%d smem=%zu): %.3f us/iter\n",
+                    key, k, kp.EA, kp.RB, kp.EB, kp.CB, kp.threads, grid, kp.smem, ms * 1e3f / K);
+        if (ms < best) {
+            best = ms;
+            bi = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+    if (rc) return rc;
+    if (bi >= 0) {
+        R.sel_pers = bi;
+        R.pers_grid = pers_grid(p, R.v.pers[bi]);
+        tune_store(key, bi);
+    }
+    return FC_OK;
+}
+
+}  // namespace
 
 // ------------------------------------------------------------- CG graph --
 
@@ -906,9 +1240,9 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     a.st = p->st;
     a.part = p->part;
     a.Z = (cpx<T>*)R.Z;
-    a.tw = (const cpx<T>*)R.tw;
+    a.tw = (const cpx<T>*)R.tws(ka.E);
     cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
-    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tw};
+    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
     cudaGraphNode_t nB = gb.kernel(body, &nA, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
     RowInvArgs<T> c{};
     c.L = p->L;
@@ -922,7 +1256,7 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     c.part = p->part;
     c.h_inner = h_inner;
     c.Z = (const cpx<T>*)R.Z;
-    c.tw = (const cpx<T>*)R.tw;
+    c.tw = (const cpx<T>*)R.tws(kc.E);
     gb.kernel(body, &nB, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
 }
 
@@ -967,7 +1301,7 @@ int build_graph(fftconv_plan* p, int mode) {
         a.st = p->st;
         a.part = p->part;
         a.Z = (cpx<double>*)p->p64.Z;
-        a.tw = (const cpx<double>*)p->p64.tw;
+        a.tw = (const cpx<double>*)p->p64.tws(ka.E);
         // the mask is applied to x in the same pass (x = 0 off the active set)
         a.cq = nullptr;
         a.cp = nullptr;
@@ -976,7 +1310,8 @@ int build_graph(fftconv_plan* p, int mode) {
         a.r64 = nullptr;
         a.x = nullptr;
         cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
-        ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tw};
+        ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq,
+                          (const cpx<double>*)p->p64.tws(kb.E)};
         cudaGraphNode_t nB = gb.kernel(outer, &nA, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
         RowInvArgs<double> c{};
         c.L = p->L;
@@ -991,7 +1326,7 @@ int build_graph(fftconv_plan* p, int mode) {
         c.h_outer = h_outer;
         c.h_inner = h_inner;
         c.Z = (const cpx<double>*)p->p64.Z;
-        c.tw = (const cpx<double>*)p->p64.tw;
+        c.tw = (const cpx<double>*)p->p64.tws(kc.E);
         cudaGraphNode_t nC = gb.kernel(outer, &nB, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
         cudaGraphNode_t nInner = nullptr;
         cudaGraph_t inner = gb.while_node(outer, &nC, 1, h_inner, &nInner);
@@ -1030,6 +1365,61 @@ int build_graph(fftconv_plan* p, int mode) {
 
 }  // namespace
 
+namespace {
+
+// FP64 true residual r = P (b - A x) after folding the last correction into
+// x, with the refinement decision (passes A, B, C in RESID mode).
+int launch_resid_chain(fftconv_plan* p, bool mixed, cudaStream_t st) {
+    const KV &ka = p->p64.rfwd(), &kb = p->p64.colc(), &kc = p->p64.rinv();
+    RowFwdArgs<double> a{};
+    a.L = p->L;
+    a.mode = RF_XUPD;
+    a.x64 = p->x64;
+    a.d32 = mixed ? p->d32 : nullptr;
+    a.mask = p->mask;
+    a.st = p->st;
+    a.part = p->part;
+    a.Z = (cpx<double>*)p->p64.Z;
+    a.tw = (const cpx<double>*)p->p64.tws(ka.E);
+    int rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, st, a);
+    if (rc) return rc;
+    ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tws(kb.E)};
+    rc = launch(kb.f, col_grid(p, kb), kb.threads, kb.smem, st, b);
+    if (rc) return rc;
+    RowInvArgs<double> c{};
+    c.L = p->L;
+    c.mode = RI_RESID;
+    c.mask = p->mask;
+    c.x64 = p->x64;
+    c.b64 = p->b64;
+    c.s64 = p->s64;
+    c.r64 = p->r64;
+    c.st = p->st;
+    c.part = p->part;
+    c.Z = (const cpx<double>*)p->p64.Z;
+    c.tw = (const cpx<double>*)p->p64.tws(kc.E);
+    return launch(kc.f, row_grid(p, kc), kc.threads, kc.smem, st, c);
+}
+
+// One inner CG run as a cooperative launch of the persistent kernel (it
+// returns at once when the outer loop has finished).
+int launch_persistent(fftconv_plan* p, bool mixed, cudaStream_t st) {
+    PrecRes& R = mixed ? p->p32 : p->p64;
+    const KVP& kp = R.v.pers[R.sel_pers];
+    if (mixed) {
+        PersistArgs<float> pa = make_pargs<float>(p, R, kp, p->d32, p->r32, p->p32v, p->q32, p->s32, p->r64);
+        void* args[1] = {(void*)&pa};
+        FC_CK(cudaLaunchCooperativeKernel(kp.f, dim3(R.pers_grid), dim3(kp.threads), args, kp.smem, st));
+    } else {
+        PersistArgs<double> pa = make_pargs<double>(p, R, kp, p->x64, p->r64, p->p64v, p->q64, p->s64, nullptr);
+        void* args[1] = {(void*)&pa};
+        FC_CK(cudaLaunchCooperativeKernel(kp.f, dim3(R.pers_grid), dim3(kp.threads), args, kp.smem, st));
+    }
+    return FC_OK;
+}
+
+}  // namespace
+
 extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, double* x, const uint8_t* mask,
                         const cg_opts* o, cg_result* r, fc_stream_t stream) {
     if (!p || !s || !b || !x) return FC_EINVAL;
@@ -1044,7 +1434,10 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     if (!(o->rtol >= 0.0)) return FC_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const long N = p->N;
-    if (!p->gexec[mode]) {
+    const bool mixed = mode == FC_MODE_MIXED;
+    const auto t_call = std::chrono::steady_clock::now();
+    const bool persistent = (mixed ? p->p32.sel_pers : p->p64.sel_pers) >= 0;
+    if (!persistent && !p->gexec[mode]) {
         int rc = build_graph(p, mode);
         if (rc) return rc;
     }
@@ -1073,7 +1466,26 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     h.first = 1;
     *p->st_host = h;
     FC_CK(cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st));
-    FC_CK(cudaGraphLaunch(p->gexec[mode], st));
+    if (persistent) {
+        // Host-driven refinement loop: per cycle the FP64 true residual
+        // (3 passes, device-side decision) and one cooperative launch that
+        // runs the whole inner CG run; one status read per cycle.
+        FC_CK(cudaMemsetAsync(p->pctl, 0, sizeof(PersistCtl), st));
+        if (mixed) {
+            k_f64_to_f32<<<grid_1d(N, 256), 256, 0, st>>>(N, p->s64, p->s32);
+            FC_CK(cudaGetLastError());
+        }
+        for (int cyc = 0; cyc <= h.max_cycles + 1; ++cyc) {
+            int rc = launch_resid_chain(p, mixed, st);
+            if (!rc) rc = launch_persistent(p, mixed, st);
+            if (rc) return rc;
+            FC_CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+            FC_CK(cudaStreamSynchronize(st));
+            if (p->st_host->finished) break;
+        }
+    } else {
+        FC_CK(cudaGraphLaunch(p->gexec[mode], st));
+    }
     FC_CK(cudaMemcpyAsync(x, p->x64, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     FC_CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaStreamSynchronize(st));
@@ -1084,6 +1496,8 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
         r->refinements = f.cycles;
         r->true_rel_resid = f.bb > 0 ? sqrt(f.rr64 / f.bb) : 0.0;
         r->bnorm = sqrt(f.bb);
+        r->latency_s = r->run_s =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call).count();
     }
     return f.status;
 }

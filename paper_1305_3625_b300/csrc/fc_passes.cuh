@@ -32,6 +32,16 @@
 
 namespace fc {
 
+// Double-buffered exchanges when PER groups' two segments fit in 160 KB.
+template <typename T, int M, int PER>
+__host__ __device__ constexpr bool use_db() {
+    return (size_t)PER * 2 * seg_len(M) * sizeof(cpx<T>) <= 160 * 1024;
+}
+template <typename T, int M, int PER>
+__host__ __device__ constexpr size_t pass_smem() {
+    return (size_t)PER * (use_db<T, M, PER>() ? 2 : 1) * seg_len(M) * sizeof(cpx<T>);
+}
+
 // ------------------------------------------------------- loads/stores ---
 
 template <typename T>
@@ -154,58 +164,74 @@ __device__ __forceinline__ T pass_a_value(const RowFwdArgs<T>& a, size_t i, int 
 
 // ------------------------------------------------------------ pass A ----
 
-// RB row pairs per block, G = M/E threads per pair.
+// Block-uniform scalars of a pass-A unit (the CG step of the last product,
+// or the scale of the correction folded into x).
+template <typename T>
+struct AScal {
+    int first;
+    T alpha, beta, bcarry;
+    double inv_sigma, sig;
+};
+
+template <typename T>
+__device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a) {
+    AScal<T> sc{0, 0, 0, 0, 1.0, 0.0};
+    if (a.mode == RF_CG) {
+        sc.first = a.st->first;
+        sc.alpha = (T)a.st->alpha;
+        sc.beta = (T)a.st->beta;
+        sc.bcarry = (T)a.st->beta_carry;
+        if (a.r64) sc.inv_sigma = 1.0 / a.st->sigma;
+    } else if (a.mode == RF_XUPD) {
+        sc.sig = a.st->sigma;  // scale of the inner run that produced d32
+    }
+    return sc;
+}
+
+// One unit of pass A: RB row pairs starting at pair unit*RB, G = M/E threads
+// per pair.  Adds this thread's r.r and r.p to acc, acc_rp.  Leaves shared
+// memory in use: the caller synchronises before the block reuses it.
 template <typename T, int M, int E, int RB>
-__global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
+__device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm, T& acc,
+                                          T& acc_rp) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
+    constexpr bool DB = use_db<T, M, RB>();
+    constexpr int GS = (DB ? 2 : 1) * SEG;  // shared elements per pair
+    constexpr int NB = next_buf(M, E, DB, 0);
     const int t = threadIdx.x, j = t % G, pl = t / G;
     const int L = a.L;
-    const int r0 = (blockIdx.x * RB + pl) * 2;
-
-    T alpha = 0, beta = 0, bcarry = 0;
-    int first = 0;
-    double inv_sigma = 1.0, sig = 0.0;
-    if (a.mode == RF_CG) {
-        first = a.st->first;
-        alpha = (T)a.st->alpha;
-        beta = (T)a.st->beta;
-        bcarry = (T)a.st->beta_carry;
-        if (a.r64) inv_sigma = 1.0 / a.st->sigma;
-    } else if (a.mode == RF_XUPD) {
-        sig = a.st->sigma;  // scale of the inner run that produced d32
-    }
+    const int r0 = (unit * RB + pl) * 2;
 
     C v[E];
-    T acc = 0, acc_rp = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         v[e] = C{0, 0};
         const int n = j + e * G;
         if (e < E / 2 && n < L) {  // n >= M/2 >= L for e >= E/2: the zero padding
             if (r0 < L)
-                v[e].x = pass_a_value(a, (size_t)r0 * L + n, first, alpha, beta, inv_sigma, sig, acc, acc_rp, bcarry);
+                v[e].x = pass_a_value(a, (size_t)r0 * L + n, sc.first, sc.alpha, sc.beta, sc.inv_sigma, sc.sig, acc,
+                                      acc_rp, sc.bcarry);
             if (r0 + 1 < L)
-                v[e].y = pass_a_value(a, (size_t)(r0 + 1) * L + n, first, alpha, beta, inv_sigma, sig, acc, acc_rp,
-                                      bcarry);
+                v[e].y = pass_a_value(a, (size_t)(r0 + 1) * L + n, sc.first, sc.alpha, sc.beta, sc.inv_sigma, sc.sig,
+                                      acc, acc_rp, sc.bcarry);
         }
     }
-    C* seg = sm + pl * SEG;
-    fft_stages<T, M, E, false>(v, j, seg, a.tw);
+    C* g0 = sm + pl * GS;
+    fft_stages<T, M, E, false, DB, 0>(v, j, g0, g0 + SEG, a.tw);
+    C* wp = g0 + NB * SEG + spad(j);
 #pragma unroll
-    for (int e = 0; e < E; ++e) seg[spad(j + e * G)] = v[e];
+    for (int e = 0; e < E; ++e) wp[pofs(e * G)] = v[e];
     __syncthreads();
     // split the pair into the two rows' half spectra, store column-major
-    const int row_base = blockIdx.x * 2 * RB;
+    const int row_base = unit * 2 * RB;
     const T half = (T)0.5;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
         const int idx = t + q * NT;
         const int r = idx % (2 * RB), kx = idx / (2 * RB);
         const int row = row_base + r;
-        const C* sg = sm + (r >> 1) * SEG;
+        const C* sg = sm + (r >> 1) * GS + NB * SEG;
         C out;
         if (kx == 0) {
             const C z0 = sg[spad(0)], zh = sg[spad(H)];
@@ -216,6 +242,14 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
         }
         if (row < L) stc(a.Z + (size_t)kx * L + row, out);
     }
+}
+
+template <typename T, int M, int E, int RB>
+__global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const AScal<T> sc = ascal_from_state(a);
+    T acc = 0, acc_rp = 0;
+    rfwd_unit<T, M, E, RB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
     if (a.mode == RF_CG) {
         double pv[2] = {(double)acc, (double)acc_rp}, tot[2];
         if (grid_sum_last<2>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) {
@@ -227,16 +261,18 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
 
 // ------------------------------------------------------------ pass B ----
 
-// CB columns per block, G = M/E threads per column (j fastest).
+// One unit of pass B: CB columns starting at column unit*CB, G = M/E threads
+// per column (j fastest).  Unit 0 holds the packed column 0.
 template <typename T, int M, int E, int CB>
-__global__ void __launch_bounds__(CB*(M / E)) k_colc(ColArgs<T> a) {
+__device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>* sm) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, Q = M / 2 + 1, SEG = seg_len(M);
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
+    constexpr bool DB = use_db<T, M, CB>();
+    constexpr int GS = (DB ? 2 : 1) * SEG;
+    constexpr int NB = next_buf(M, E, DB, 0);
     const int t = threadIdx.x, j = t % G, c = t / G;
     const int L = a.L;
-    const int kx = blockIdx.x * CB + c;
+    const int kx = unit * CB + c;
     C* col = a.Z + (size_t)kx * L;
 
     C v[E];
@@ -245,11 +281,12 @@ __global__ void __launch_bounds__(CB*(M / E)) k_colc(ColArgs<T> a) {
         const int n = j + e * G;
         v[e] = (e < E / 2 && n < L) ? ldc_cg(col + n) : C{0, 0};
     }
-    C* seg = sm + c * SEG;
-    fft_stages<T, M, E, false>(v, j, seg, a.tw);
-    if (blockIdx.x == 0) {
+    C* g0 = sm + c * GS;
+    fft_stages<T, M, E, false, DB, 0>(v, j, g0, g0 + SEG, a.tw);
+    if (unit == 0) {
         // column 0 holds P = F0 + i FN (kx = 0 and kx = M/2, both real along y);
         // with the Hermitian partner P[M - ky]: W = P (g0 + gN)/2 + conj(P[M-ky]) (g0 - gN)/2
+        C* seg = g0 + NB * SEG;
 #pragma unroll
         for (int e = 0; e < E; ++e) seg[spad(j + e * G)] = v[e];
         __syncthreads();
@@ -284,12 +321,18 @@ __global__ void __launch_bounds__(CB*(M / E)) k_colc(ColArgs<T> a) {
             v[e].y *= g;
         }
     }
-    fft_stages<T, M, E, true>(v, j, seg, a.tw);
+    fft_stages<T, M, E, true, DB, NB>(v, j, g0, g0 + SEG, a.tw);
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
         const int n = j + e * G;
         if (n < L) stc(col + n, v[e]);
     }
+}
+
+template <typename T, int M, int E, int CB>
+__global__ void __launch_bounds__(CB*(M / E)) k_colc(ColArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    colc_unit<T, M, E, CB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
 }
 
 // ------------------------------------------------------------ pass C ----
@@ -316,54 +359,59 @@ __device__ __forceinline__ void pass_c_value(const RowInvArgs<T>& a, size_t i, T
     }
 }
 
+// One unit of pass C: RB row pairs starting at pair unit*RB.  Adds this
+// thread's partial sums to s0, s1, s2.
 template <typename T, int M, int E, int RB>
-__global__ void __launch_bounds__(RB*(M / E)) k_rinv(RowInvArgs<T> a) {
+__device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, T& s0, T& s1, T& s2) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
+    constexpr bool DB = use_db<T, M, RB>();
+    constexpr int GS = (DB ? 2 : 1) * SEG;
+    constexpr int HS = H + (H >> 4) + 1;  // staging: second row of a pair at an odd bank offset
     const int t = threadIdx.x, j = t % G, pl = t / G;
     const int L = a.L;
-    const int row_base = blockIdx.x * 2 * RB;
+    const int row_base = unit * 2 * RB;
     const int r0 = row_base + 2 * pl;
 
-    // the 2*RB rows' half spectra (column-major) into the pair segments:
-    // row 2p at [0, H), row 2p+1 at [H, M)
+    // the 2*RB rows' half spectra (column-major) into the pair segments
+    // (buffer 0): row 2p at st(0, kx), row 2p+1 at st(1, kx), st(h, kx) =
+    // h*HS + spad(kx)
 #pragma unroll
     for (int q = 0; q < E; ++q) {
         const int idx = t + q * NT;
         const int r = idx % (2 * RB), kx = idx / (2 * RB);
         const int row = row_base + r;
         const C y = row < L ? ldc_cg(a.Z + (size_t)kx * L + row) : C{0, 0};
-        sm[(r >> 1) * SEG + spad((r & 1) * H + kx)] = y;
+        sm[(r >> 1) * GS + (r & 1) * HS + spad(kx)] = y;
     }
     __syncthreads();
     // Hermitian extension of both rows and pair packing W = Y0 + i Y1
-    C* seg = sm + pl * SEG;
+    C* g0 = sm + pl * GS;
+    const C* h0 = g0;
+    const C* h1 = g0 + HS;
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int k = j + e * G;
         C y0, y1;
         if (k == 0) {
-            y0 = C{seg[spad(0)].x, 0};
-            y1 = C{seg[spad(H)].x, 0};
+            y0 = C{h0[0].x, 0};
+            y1 = C{h1[0].x, 0};
         } else if (k == H) {
-            y0 = C{seg[spad(0)].y, 0};
-            y1 = C{seg[spad(H)].y, 0};
+            y0 = C{h0[0].y, 0};
+            y1 = C{h1[0].y, 0};
         } else if (k < H) {
-            y0 = seg[spad(k)];
-            y1 = seg[spad(H + k)];
+            y0 = h0[spad(k)];
+            y1 = h1[spad(k)];
         } else {
-            y0 = conjc(seg[spad(M - k)]);
-            y1 = conjc(seg[spad(H + M - k)]);
+            y0 = conjc(h0[spad(M - k)]);
+            y1 = conjc(h1[spad(M - k)]);
         }
         v[e] = C{y0.x - y1.y, y0.y + y1.x};
     }
-    __syncthreads();
-    fft_stages<T, M, E, true>(v, j, seg, a.tw);
-
-    T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
+    if constexpr (!DB) __syncthreads();
+    // with two buffers the first exchange writes buffer 1 while buffer 0 is still being read
+    fft_stages<T, M, E, true, DB, DB ? 1 : 0>(v, j, g0, g0 + SEG, a.tw);
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
         const int n = j + e * G;
@@ -372,6 +420,13 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rinv(RowInvArgs<T> a) {
             if (r0 + 1 < L) pass_c_value(a, (size_t)(r0 + 1) * L + n, v[e].y, s0, s1, s2);
         }
     }
+}
+
+template <typename T, int M, int E, int RB>
+__global__ void __launch_bounds__(RB*(M / E)) k_rinv(RowInvArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
+    rinv_unit<T, M, E, RB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
     if (a.mode == RI_CG) {
         double pv[3] = {(double)s0, (double)s1, (double)s2}, tot[3];
         if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)

@@ -215,3 +215,26 @@ def test_masked_loop_against_oracle(mode, rtol, rel_tie):
         x = xo.copy()
         x[ko] = 0.0
     assert diverged <= 1
+
+
+@pytest.mark.parametrize("L", [32, 100, 256])
+def test_every_inner_loop_variant_solves(L):
+    """The per-pass graph loop and every compiled persistent inner-CG kernel
+    reach the same solution (dense solve at L = 32, FP64 solve otherwise)."""
+    p = fc_inputs.problem(L, seed=7, b_kind="normal")
+    if L <= 32:
+        want = dense_solution(L, p["s"], p["b"])
+    else:
+        want, r = solve(L, p["s"], p["b"], fc.FC_MODE_F64, 1e-13)
+        assert r["status"] == fc.FC_OK
+    n = fc.fftconv_plan_solver(plan(L), fc.FC_F32)["n"]
+    assert n >= 1
+    for k in [-1] + list(range(n)):
+        pl = fc.fftconv_plan_create(L, persistent=k)
+        info = fc.fftconv_plan_solver(pl, fc.FC_F32)
+        assert info["chosen"] == k or (k >= 0 and info["chosen"] == -1)
+        for mode, rtol, err in ((fc.FC_MODE_F64, F64_RTOL, F64_ERR), (fc.FC_MODE_MIXED, MIX_RTOL, MIX_ERR)):
+            x = dev(np.zeros(L * L))
+            res = fc.cg_solve(pl, dev(p["s"]), dev(p["b"]), x, rtol=rtol, mode=mode)
+            assert res["status"] == fc.FC_OK, (k, mode, res)
+            assert rel2(host(x), want) <= (err if L <= 32 else 10 * err), (k, mode)
