@@ -116,6 +116,21 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def aggregate_rate(units: float, local_ms: float, pg=None, device="cpu"):
+    """Whole-job rate over the ranks of a replica run: units summed over
+    ranks, time = the slowest rank's timed region.  Returns (rate per s,
+    max ms, total units)."""
+    if pg is None:
+        return units / (local_ms * 1e-3), local_ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) * 1e-3), float(t.item()), float(u.item())
+
+
 # ---------------------------------------------------------------- oracle --
 
 def oracle_iteration_time(L, budget_s):
@@ -279,14 +294,116 @@ def run_ours(args, world, rank, local, pg):
         e2e = {"value": round(ke / e2e_s, 3), "unit": "solves/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke}
 
-    # aggregate over ranks (max time)
-    tot_ms = sum(ms_mixed)
-    if pg:
-        import torch.distributed as dist
-        tt = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_ms = float(tt.item())
-    value = world * args.steps / (tot_ms * 1e-3)
+    # batched workload: 256 independent mixed solves, L ~ U{64,128,256,512},
+    # b ~ N(0,1), rtol 1e-8, all submitted at once to the solve server
+    batched = None
+    serving = None
+    if args.batch_solves > 0 or args.serve_requests > 0:
+        sv = fc.cg_server_create(150 << 30, max_slots=args.slots)
+
+        def drain(tickets, t_arrival=None):
+            done, lat = {}, []
+            while len(done) < len(tickets):
+                progressed = False
+                for t in tickets:
+                    if t in done:
+                        continue
+                    r = fc.cg_poll(sv, t)
+                    if r is not None:
+                        done[t] = r
+                        progressed = True
+                if not progressed:
+                    time.sleep(0.0002)
+            return done
+
+        sizes = [64, 128, 256, 512]
+        rng_l = fc_inputs.uniform(12345, 0, max(args.batch_solves, 1))
+        breqs = []
+        for k in range(args.batch_solves):
+            Lk = sizes[min(int(rng_l[k] * 4), 3)]
+            pk = fc_inputs.problem(Lk, seed=10_000 + k, b_kind="normal")
+            breqs.append((Lk, pk))
+        if breqs:
+            # warm the server: one plan per (slot, size) is created on first use
+            warm = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED)
+                    for Lk, pk in breqs[:min(len(breqs), 4 * args.slots)]]
+            drain(warm)
+            t0 = time.perf_counter()
+            tk = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED)
+                  for Lk, pk in breqs]
+            res = drain(tk)
+            dt = time.perf_counter() - t0
+            assert all(r["status"] == fc.FC_OK for r in res.values())
+            batched = {"solves": len(breqs), "L": "U{64,128,256,512}", "rtol": 1e-8, "mode": "mixed",
+                       "slots": args.slots, "seconds": round(dt, 4), "solves_per_s": round(len(breqs) / dt, 2),
+                       "iters_mean": round(statistics.mean(r["iters"] for r in res.values()), 1)}
+        if args.serve_requests > 0:
+            base = fc_inputs.request_stream(args.serve_requests, seed=777, rate_per_s=1.0)
+            probs = {}
+            for rq in base:
+                probs[rq["k"]] = fc_inputs.problem(rq["L"], seed=rq["seed"], b_kind="normal")
+            # warm plans for every size in the stream
+            wl = sorted({rq["L"] for rq in base})
+            warm = []
+            for Lw in wl:
+                pw = fc_inputs.problem(Lw, seed=1, b_kind="normal")
+                warm += [fc.cg_batch_submit(sv, Lw, pw["s"], pw["b"], rtol=1e-6) for _ in range(args.slots)]
+            drain(warm)
+            # closed-loop capacity on this mix (all submitted at once), then
+            # Poisson arrivals at 0.7 of it
+            ncap = min(len(base), args.serve_f64)
+            c0 = time.perf_counter()
+            drain([fc.cg_batch_submit(sv, rq["L"], probs[rq["k"]]["s"], probs[rq["k"]]["b"], rtol=rq["tol"],
+                                      mode=fc.FC_MODE_MIXED) for rq in base[:ncap]])
+            cap = ncap / (time.perf_counter() - c0)
+            stream_ = fc_inputs.request_stream(args.serve_requests, seed=777, rate_per_s=0.7 * cap)
+            t0 = time.perf_counter()
+            tickets = []
+            for rq in stream_:
+                while time.perf_counter() - t0 < rq["arrival_s"]:
+                    time.sleep(0.0001)
+                pk = probs[rq["k"]]
+                tickets.append(fc.cg_batch_submit(sv, rq["L"], pk["s"], pk["b"], rtol=rq["tol"],
+                                                  mode=fc.FC_MODE_MIXED))
+            res = drain(tickets)
+            dt = time.perf_counter() - t0
+            lat = sorted(r["latency_s"] * 1e3 for r in res.values())
+            st = fc.cg_server_stats(sv)
+            # plain one-at-a-time FP64 on exactly the requests of the capacity run
+            n64 = ncap
+            t64, lat64 = 0.0, []
+            plans64 = {}
+            for rq in base[:n64]:
+                Lq = rq["L"]
+                if Lq not in plans64:
+                    plans64[Lq] = fc.fftconv_plan_create(Lq, fc.FC_F64)
+                pk = probs[rq["k"]]
+                sd, bd = torch.tensor(pk["s"], device=dev), torch.tensor(pk["b"], device=dev)
+                xd = torch.zeros_like(sd)
+                torch.cuda.synchronize()
+                a0 = time.perf_counter()
+                fc.cg_solve(plans64[Lq], sd, bd, xd, rtol=rq["tol"], mode=fc.FC_MODE_F64, x0_zero=True)
+                xh = xd.cpu()
+                a1 = time.perf_counter()
+                t64 += a1 - a0
+                lat64.append((a1 - a0) * 1e3)
+            serving = {"requests": len(stream_), "capacity_per_s": round(cap, 1), "rate_per_s": round(0.7 * cap, 1),
+                       "L": "2^round(U[5,11])", "tol": "{1e-6,1e-8}", "slots": args.slots,
+                       "solves_per_s": round(len(stream_) / dt, 2),
+                       "p50_ms": round(lat[len(lat) // 2], 3),
+                       "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+                       "mem_peak_GB": round(st["peak"] / 1e9, 2),
+                       "f64_one_at_a_time": {"requests": n64,
+                                             "solves_per_s": round(n64 / t64, 2) if t64 > 0 else None,
+                                             "p50_ms": round(sorted(lat64)[len(lat64) // 2], 3) if lat64 else None}}
+            if serving["f64_one_at_a_time"]["solves_per_s"]:
+                # same requests, same tolerances: closed-loop server capacity vs one-at-a-time FP64
+                serving["capacity_vs_f64_one_at_a_time"] = round(
+                    cap / serving["f64_one_at_a_time"]["solves_per_s"], 2)
+        sv.close()
+
+    # aggregate over ranks: units summed, slowest rank's time
+    value, tot_ms, _ = aggregate_rate(args.steps, sum(ms_mixed), pg, dev)
 
     out = None
     if rank == 0:
@@ -328,6 +445,8 @@ def run_ours(args, world, rank, local, pg):
                        "frac_of_hbm": round(mv_gbs / peak, 3),
                        "effective_frac_88N": round(88 * N / (mv_ms * 1e-3) / 1e9 / peak, 3)},
             "matvec_L4096": big,
+            "batched": batched,
+            "serving": serving,
             "roofline": {"bound": "hbm", "kernel": "fftconv_apply FP32 (3 passes), L=1024",
                          "achieved": round(mv_gbs, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(mv_gbs / peak, 3), "traffic": args.traffic,
@@ -387,6 +506,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5, dest="e2e_steps")
     ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget")
     ap.add_argument("--big", type=int, default=1)
+    ap.add_argument("--batch-solves", type=int, default=256, dest="batch_solves")
+    ap.add_argument("--serve-requests", type=int, default=600, dest="serve_requests")
+    ap.add_argument("--serve-f64", type=int, default=160, dest="serve_f64",
+                    help="requests of the serving mix solved closed-loop and by one-at-a-time FP64")
+    ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per matvec from a capture of the current kernels")
     ap.add_argument("--ref-sample-iters", type=int, default=3, dest="ref_sample_iters")
