@@ -38,7 +38,7 @@ import numpy as np  # noqa: E402
 L_BENCH = 1024
 RTOL = 1e-10
 METRIC = "CG matvec GB/s vs HBM peak; solves/sec + p50/p99 latency, mixed vs FP64 plain"
-WORKLOAD = ("quasi-static breaking loop, L=1024 (padded 2048^2 FFT): warm-started CG to "
+WORKLOAD = ("quasi-static breaking loop, L=1024 (padded 2048^2 FFT): warm-started (preconditioned) CG to "
             "rtol 1e-10 + argmax |x|/t removal per step; s~U[0.5,1.5] seed 0, b=1, t~U(0,1)")
 
 
@@ -176,17 +176,19 @@ def run_ours(args, world, rank, local, pg):
     removed = torch.empty(1, device=dev, dtype=torch.int64)
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)  # > 126 MB L2
 
-    def step(mode, x_, mask_):
-        r = fc.cg_solve(plan, s, b, x_, mask=mask_, rtol=RTOL, mode=mode)
+    def step(mode, x_, mask_, precond=True):
+        r = fc.cg_solve(plan, s, b, x_, mask=mask_, rtol=RTOL, mode=mode, precond=precond)
         if r["status"] != fc.FC_OK:
             raise RuntimeError(f"solve failed: {r}")
         fc.fc_masked_step(plan, t, mask_, x_, removed)
         return r
 
-    def launches(r, mode):
-        # prologue (mixed) + per true residual 3 passes + final update, 3 passes
-        # per CG iteration, 1 removal kernel
-        return (1 if mode == fc.FC_MODE_MIXED else 0) + 4 * r["refinements"] + 3 * r["iters"] + 1
+    def launches(r, mode, precond=True):
+        # prologue (FP32 copy of s; preconditioner shift and spectrum), per true
+        # residual 3 passes + final update, 3 passes per product (6 per
+        # preconditioned iteration), 1 removal kernel
+        pro = (1 if mode == fc.FC_MODE_MIXED else 0) + (2 if precond else 0)
+        return pro + 4 * r["refinements"] + (6 if precond else 3) * r["iters"] + 1
 
     # warm-up: the cold first solve plus W-1 warm steps
     for _ in range(max(args.warmup, 3)):
@@ -194,13 +196,13 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     x_start, mask_start = x.clone(), mask.clone()
 
-    def timed_loop(mode, K):
+    def timed_loop(mode, K, precond=True):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         res = []
         for k in range(K):
             flush.zero_()
             ev[k][0].record(stream)
-            res.append(step(mode, x, mask))
+            res.append(step(mode, x, mask, precond))
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         ms = [a.elapsed_time(bb) for a, bb in ev]
@@ -218,11 +220,19 @@ def run_ours(args, world, rank, local, pg):
     if pg:
         pg.barrier()
 
-    # the same K steps from the same state with the plain FP64 path
+    # the same steps from the same state: plain FP64 CG (Listing 2, the
+    # baseline), FP64 with the preconditioner, mixed without it
     x.copy_(x_start)
     mask.copy_(mask_start)
     k64 = max(1, min(args.steps, args.f64_steps))
-    ms_f64, res_f64 = timed_loop(fc.FC_MODE_F64, k64)
+    ms_f64, res_f64 = timed_loop(fc.FC_MODE_F64, k64, precond=False)
+    x.copy_(x_start)
+    mask.copy_(mask_start)
+    ms_f64p, res_f64p = timed_loop(fc.FC_MODE_F64, k64, precond=True)
+    x.copy_(x_start)
+    mask.copy_(mask_start)
+    kmc = max(1, min(args.steps, 10))
+    ms_mcg, res_mcg = timed_loop(fc.FC_MODE_MIXED, kmc, precond=False)
 
     # matvec roofline: FP32 fftconv_apply (3 passes), L2 flushed before each
     xin = torch.rand(N, device=dev, dtype=torch.float32)
@@ -282,7 +292,7 @@ def run_ours(args, world, rank, local, pg):
             dt_.copy_(ht, non_blocking=True)
             x.copy_(hx, non_blocking=True)
             mask.copy_(hm, non_blocking=True)
-            r = fc.cg_solve(plan, ds, db, x, mask=mask, rtol=RTOL, mode=fc.FC_MODE_MIXED)
+            r = fc.cg_solve(plan, ds, db, x, mask=mask, rtol=RTOL, mode=fc.FC_MODE_MIXED, precond=True)
             fc.fc_masked_step(plan, dt_, mask, x, removed)
             hx.copy_(x, non_blocking=True)
             hm.copy_(mask, non_blocking=True)
@@ -325,11 +335,12 @@ def run_ours(args, world, rank, local, pg):
             breqs.append((Lk, pk))
         if breqs:
             # warm the server: one plan per (slot, size) is created on first use
-            warm = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED)
+            warm = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED,
+                                      precond=True)
                     for Lk, pk in breqs[:min(len(breqs), 4 * args.slots)]]
             drain(warm)
             t0 = time.perf_counter()
-            tk = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED)
+            tk = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True)
                   for Lk, pk in breqs]
             res = drain(tk)
             dt = time.perf_counter() - t0
@@ -347,14 +358,15 @@ def run_ours(args, world, rank, local, pg):
             warm = []
             for Lw in wl:
                 pw = fc_inputs.problem(Lw, seed=1, b_kind="normal")
-                warm += [fc.cg_batch_submit(sv, Lw, pw["s"], pw["b"], rtol=1e-6) for _ in range(args.slots)]
+                warm += [fc.cg_batch_submit(sv, Lw, pw["s"], pw["b"], rtol=1e-6, precond=True)
+                         for _ in range(args.slots)]
             drain(warm)
             # closed-loop capacity on this mix (all submitted at once), then
             # Poisson arrivals at 0.7 of it
             ncap = min(len(base), args.serve_f64)
             c0 = time.perf_counter()
             drain([fc.cg_batch_submit(sv, rq["L"], probs[rq["k"]]["s"], probs[rq["k"]]["b"], rtol=rq["tol"],
-                                      mode=fc.FC_MODE_MIXED) for rq in base[:ncap]])
+                                      mode=fc.FC_MODE_MIXED, precond=True) for rq in base[:ncap]])
             cap = ncap / (time.perf_counter() - c0)
             stream_ = fc_inputs.request_stream(args.serve_requests, seed=777, rate_per_s=0.7 * cap)
             t0 = time.perf_counter()
@@ -364,7 +376,7 @@ def run_ours(args, world, rank, local, pg):
                     time.sleep(0.0001)
                 pk = probs[rq["k"]]
                 tickets.append(fc.cg_batch_submit(sv, rq["L"], pk["s"], pk["b"], rtol=rq["tol"],
-                                                  mode=fc.FC_MODE_MIXED))
+                                                  mode=fc.FC_MODE_MIXED, precond=True))
             res = drain(tickets)
             dt = time.perf_counter() - t0
             lat = sorted(r["latency_s"] * 1e3 for r in res.values())
@@ -430,7 +442,8 @@ def run_ours(args, world, rank, local, pg):
             "vs_baseline": None,
             "dtype": "f32+f64 (mixed: FP32 FFT/vectors, FP64 reductions and true residuals)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L, "M": M, "rtol": RTOL, "mode": "mixed",
+            "config": {"workload": WORKLOAD, "L": L, "M": M, "rtol": RTOL,
+                       "mode": "mixed FP32/FP64, Fourier-preconditioned CG",
                        "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
             "p50_ms": round(pct(srt, 0.5), 4),
             "p99_ms": round(pct(srt, 0.99), 4),
@@ -441,6 +454,12 @@ def run_ours(args, world, rank, local, pg):
                           "p99_ms": round(max(ms_f64), 3),
                           "iters_per_solve": round(statistics.mean(iters64), 2)},
             "mixed_over_f64": round(value / world / f64_rate, 2),
+            "f64_pcg": {"value": round(k64 / (sum(ms_f64p) * 1e-3), 3), "unit": "solves/s",
+                        "iters_per_solve": round(statistics.mean(r["iters"] for r in res_f64p), 2)},
+            "mixed_cg_no_precond": {"value": round(kmc / (sum(ms_mcg) * 1e-3), 3), "unit": "solves/s",
+                                    "iters_per_solve": round(statistics.mean(r["iters"] for r in res_mcg), 2),
+                                    "true_residuals_per_solve": round(
+                                        statistics.mean(r["refinements"] for r in res_mcg), 2)},
             "matvec": {"L": L, "ms": round(mv_ms, 4), "bytes": mv_bytes, "GB_s": round(mv_gbs, 1),
                        "frac_of_hbm": round(mv_gbs / peak, 3),
                        "effective_frac_88N": round(88 * N / (mv_ms * 1e-3) / 1e9 / peak, 3)},

@@ -84,9 +84,13 @@ typedef struct cg_opts {
     int refine_every;  /* cap on inner iterations between two true residuals
                           (0: 100000)                                           */
     int max_refine;    /* cap on true-residual evaluations (0: 60)              */
-    double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 3e-3)    */
+    double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 1e-5 with
+                          the preconditioner, 3e-3 without)                     */
     int x0_zero;       /* 1: start from x = 0 and ignore the input x            */
-    int reserved;
+    int precond;       /* 1: preconditioned CG with the Fourier preconditioner
+                          M^-1 = P crop (C_M + c I)^-1 pad P, C_M the padded
+                          circulant of C (its spectrum, shifted), c = mean of s
+                          over active sites; 0: plain CG as in Listing 2     */
 } cg_opts;
 
 typedef struct cg_result {
@@ -220,6 +224,8 @@ typedef struct cg_request {
     const double *b; /* host, right-hand side                                */
     double *x;       /* host, receives the solution (may be NULL)            */
     uint64_t tag;    /* caller's tag                                         */
+    int precond;     /* 1: Fourier-preconditioned CG (see cg_opts.precond)   */
+    int reserved;
 } cg_request;
 
 /*

@@ -47,7 +47,7 @@ class FcError(RuntimeError):
 class cg_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("refine_every", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("inner_rtol", ctypes.c_double), ("x0_zero", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("x0_zero", ctypes.c_int), ("precond", ctypes.c_int)]
 
 
 class cg_tune(ctypes.Structure):
@@ -69,7 +69,7 @@ class cg_result(ctypes.Structure):
 class cg_request(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("s", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
-                ("tag", ctypes.c_uint64)]
+                ("tag", ctypes.c_uint64), ("precond", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 LIB_PATH = _build.LIB
@@ -204,12 +204,13 @@ def fftconv_apply(plan: Plan, x, y, stream=None) -> None:
 
 def cg_solve(plan: Plan, s, b, x, mask=None, rtol: float = 1e-10, mode: int = FC_MODE_F64,
              max_iter: int = 0, refine_every: int = 0, max_refine: int = 0,
-             inner_rtol: float = 0.0, x0_zero: bool = False, stream=None, check: bool = False) -> dict:
+             inner_rtol: float = 0.0, x0_zero: bool = False, precond: bool = False, stream=None,
+             check: bool = False) -> dict:
     """Solve P (C + S) P x = P b in place in x; returns the cg_result fields."""
     n = plan.L * plan.L
     o = cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode),
                 refine_every=int(refine_every), max_refine=int(max_refine),
-                inner_rtol=float(inner_rtol), x0_zero=int(bool(x0_zero)), reserved=0)
+                inner_rtol=float(inner_rtol), x0_zero=int(bool(x0_zero)), precond=int(bool(precond)))
     r = cg_result()
     rc = _lib.cg_solve(plan.handle, _ptr(s, torch.float64, n, "s"), _ptr(b, torch.float64, n, "b"),
                        _ptr(x, torch.float64, n, "x"), _ptr(mask, torch.uint8, n, "mask"),
@@ -305,7 +306,7 @@ def cg_server_create(mem_budget_bytes: int, max_slots: int = 16) -> Server:
 
 
 def cg_batch_submit(sv: Server, L: int, s, b, x_out=None, rtol: float = 1e-8, mode: int = FC_MODE_MIXED,
-                    tag: int = 0) -> int:
+                    tag: int = 0, precond: bool = False) -> int:
     """Queue one solve (host float64 arrays of L*L); x_out (float64, L*L,
     C-contiguous numpy array) receives the solution.  Returns the ticket."""
     import numpy as np
@@ -317,7 +318,8 @@ def cg_batch_submit(sv: Server, L: int, s, b, x_out=None, rtol: float = 1e-8, mo
     if x_out is not None and (x_out.dtype != np.float64 or not x_out.flags.c_contiguous or x_out.size != n):
         raise ValueError("x_out must be a contiguous float64 array of L*L values")
     rq = cg_request(L=int(L), mode=int(mode), rtol=float(rtol), s=s.ctypes.data, b=b.ctypes.data,
-                    x=x_out.ctypes.data if x_out is not None else None, tag=int(tag))
+                    x=x_out.ctypes.data if x_out is not None else None, tag=int(tag),
+                    precond=int(bool(precond)), reserved=0)
     t = ctypes.c_uint64()
     rc = _lib.cg_batch_submit(sv.handle, ctypes.byref(rq), ctypes.byref(t))
     if rc != FC_OK:

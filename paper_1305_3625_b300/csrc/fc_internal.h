@@ -25,6 +25,8 @@ struct CgState {
     double rtol2;        // target: rr64 <= rtol2 * bb
     double inner_rtol2;  // mixed: inner target relative to the unit right-hand side
     double beta_carry;   // direction kept across a true-residual replacement (0: restart)
+    double rz, rz_prev;  // PCG: r.z of the current and of the previous iteration
+    double pshift;       // PCG: shift c of the preconditioner (C_M + c I)^-1
     int iter;            // products spent in inner loops (all cycles)
     int max_iter;
     int cycle_iter, cycle_max;
@@ -38,8 +40,13 @@ struct CgState {
     unsigned cntA, cntC;  // last-block counters of passes A and C
 };
 
-enum { RF_PLAIN = 0, RF_CG = 1, RF_XUPD = 2 };
-enum { RI_PLAIN = 0, RI_CG = 1, RI_RESID = 2 };
+// Pass A modes: plain input; CG update (x, r, p) + transform p; FP64 iterate
+// with the folded correction; PCG first half (x, r update, transform r);
+// PCG second half (p = z + beta p, transform p).
+enum { RF_PLAIN = 0, RF_CG = 1, RF_XUPD = 2, RF_PCG_R = 3, RF_PCG_P = 4 };
+// Pass C modes: plain output; CG product q; FP64 true residual; PCG
+// preconditioned residual z = P M^-1 r.
+enum { RI_PLAIN = 0, RI_CG = 1, RI_RESID = 2, RI_PCG_Z = 3 };
 
 template <typename T>
 struct RowFwdArgs {
@@ -47,6 +54,7 @@ struct RowFwdArgs {
     const T* x;                  // RF_PLAIN: input field
     T *cx, *cr, *cp;             // RF_CG: CG vectors updated in place
     const T* cq;                 // RF_CG: last product
+    const T* cz;                 // RF_PCG_P: preconditioned residual
     const double* r64;           // RF_CG, mixed: first pass starts from r64/sigma
     double* x64;                 // RF_XUPD: FP64 iterate (updated, then transformed)
     const float* d32;            // RF_XUPD: correction from the last inner run (or null)
@@ -73,6 +81,7 @@ struct RowInvArgs {
     const T* cp;
     const T* cr;
     T* cq;                       // RI_CG: product q = P (C p + s p)
+    T* cz;                       // RI_PCG_Z: preconditioned residual
     const uint8_t* mask;         // 1 = active fibre (null: all active)
     const double *x64, *b64, *s64;
     double* r64;                 // RI_RESID: r = P (b - C x - s x)
@@ -110,6 +119,14 @@ __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq
     st->first = 0;
     st->inner_done = d;
     if (h_inner) cudaGraphSetConditional(h_inner, d == 0 ? 1u : 0u);
+}
+
+// PCG (Fourier preconditioner): after z = M^-1 r, beta = r.z / r_prev.z_prev
+// for the direction update of the next pass.
+__device__ __forceinline__ void pcg_z_decide(CgState* st, double rz) {
+    st->beta = (st->first || !(st->rz > 0.0)) ? 0.0 : rz / st->rz;
+    st->rz_prev = st->rz;
+    st->rz = rz;
 }
 
 // Decide the outer loop after a true residual r = P (b - A x): stop when

@@ -172,6 +172,28 @@ __global__ void k_f64_to_f32(long N, const double* a, float* b) {
         b[i] = (float)a[i];
 }
 
+// Shift of the Fourier preconditioner: c = mean of s over active sites
+// (last block writes it).
+__global__ void __launch_bounds__(256) k_active_mean(long N, const double* s, const uint8_t* mask, double* part,
+                                                     CgState* st) {
+    double v[2] = {0.0, 0.0}, tot[2];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
+        if (!mask || mask[i]) {
+            v[0] += s[i];
+            v[1] += 1.0;
+        }
+    if (grid_sum_last<2>(v, part, &st->cntA, tot) && threadIdx.x == 0) st->pshift = tot[1] > 0 ? tot[0] / tot[1] : 1.0;
+}
+
+// Spectrum quarter of the preconditioner (C_M + c I)^-1 in the scaling of
+// the stored kernel spectrum: Gq = eig(C_M)/M^2, so Pq = 1/((M^2 Gq + c) M^2).
+template <typename T>
+__global__ void k_precond_spectrum(long QQ, double MM, const double* gq64, const CgState* st, T* pq) {
+    const double c = st->pshift;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < QQ; i += (long)gridDim.x * blockDim.x)
+        pq[i] = (T)(1.0 / ((MM * gq64[i] + c) * MM));
+}
+
 template <typename T>
 __global__ void k_fill(long N, T* a, T v) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) a[i] = v;
@@ -464,6 +486,9 @@ struct fftconv_plan {
     uint8_t* mask = nullptr;
     // solve workspace (FP32 side, mixed mode)
     float *d32 = nullptr, *r32 = nullptr, *p32v = nullptr, *q32 = nullptr, *s32 = nullptr;
+    // preconditioned CG: preconditioned residuals and preconditioner spectra
+    double *z64 = nullptr, *pq64 = nullptr;
+    float *z32 = nullptr, *pq32 = nullptr;
     CgState* st = nullptr;
     CgState* st_host = nullptr;  // pinned
     double* part = nullptr;
@@ -474,8 +499,8 @@ struct fftconv_plan {
     long long* am_i = nullptr;
     ArgmaxCtl* am_ctl = nullptr;
     int am_grid = 0;
-    cudaGraph_t graph[2] = {nullptr, nullptr};
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraph_t graph[4] = {};      // index mode + 2 * precond
+    cudaGraphExec_t gexec[4] = {};
 };
 
 namespace {
@@ -492,13 +517,14 @@ int dalloc(fftconv_plan* p, void** ptr, size_t bytes) {
 
 void plan_free(fftconv_plan* p) {
     if (!p) return;
-    for (int m = 0; m < 2; ++m) {
+    for (int m = 0; m < 4; ++m) {
         if (p->gexec[m]) cudaGraphExecDestroy(p->gexec[m]);
         if (p->graph[m]) cudaGraphDestroy(p->graph[m]);
     }
     void* ptrs[] = {p->p32.Z, p->p32.Gq, p->p64.Z, p->p64.tw, p->p64.Gq, p->x64, p->r64,
                     p->p64v, p->q64, p->b64, p->s64, p->mask, p->d32, p->r32, p->p32v, p->q32, p->s32,
-                    p->st, p->part, p->partA, p->partC, p->pctl, p->am_v, p->am_i, p->am_ctl};
+                    p->st, p->part, p->partA, p->partC, p->pctl, p->am_v, p->am_i, p->am_ctl,
+                    p->z64, p->pq64, p->z32, p->pq32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 5; ++i) {
@@ -878,7 +904,11 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         FC_TRY(dalloc(p, (void**)&p->b64, sizeof(double) * N));
         FC_TRY(dalloc(p, (void**)&p->s64, sizeof(double) * N));
         FC_TRY(dalloc(p, (void**)&p->mask, N));
+        FC_TRY(dalloc(p, (void**)&p->z64, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->pq64, sizeof(double) * (size_t)Q * Q));
         if (p->p32.on) {
+            FC_TRY(dalloc(p, (void**)&p->z32, sizeof(float) * N));
+            FC_TRY(dalloc(p, (void**)&p->pq32, sizeof(float) * (size_t)Q * Q));
             FC_TRY(dalloc(p, (void**)&p->d32, sizeof(float) * N));
             FC_TRY(dalloc(p, (void**)&p->r32, sizeof(float) * N));
             FC_TRY(dalloc(p, (void**)&p->p32v, sizeof(float) * N));
@@ -1260,11 +1290,74 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     gb.kernel(body, &nB, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
 }
 
+// Inner body of preconditioned CG: A1 (x, r update; transform r) -> B1 with
+// the preconditioner spectrum -> C1 (z = M^-1 r, r.z, beta) -> A2 (p = z +
+// beta p; transform p) -> B2 with the kernel spectrum -> C2 (q, step decision).
+template <typename T>
+void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp,
+                        T* cq, T* cz, const T* s, const T* pq, const double* r64_start,
+                        cudaGraphConditionalHandle h_inner) {
+    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+    RowFwdArgs<T> a1{};
+    a1.L = p->L;
+    a1.mode = RF_PCG_R;
+    a1.cx = cx;
+    a1.cr = cr;
+    a1.cp = cp;
+    a1.cq = cq;
+    a1.r64 = r64_start;
+    a1.st = p->st;
+    a1.part = p->part;
+    a1.Z = (cpx<T>*)R.Z;
+    a1.tw = (const cpx<T>*)R.tws(ka.E);
+    cudaGraphNode_t n1 = gb.kernel(body, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a1);
+    ColArgs<T> b1{p->L, (cpx<T>*)R.Z, pq, (const cpx<T>*)R.tws(kb.E)};
+    cudaGraphNode_t n2 = gb.kernel(body, &n1, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b1);
+    RowInvArgs<T> c1{};
+    c1.L = p->L;
+    c1.mode = RI_PCG_Z;
+    c1.cr = cr;
+    c1.cz = cz;
+    c1.mask = p->mask;
+    c1.st = p->st;
+    c1.part = p->part;
+    c1.Z = (const cpx<T>*)R.Z;
+    c1.tw = (const cpx<T>*)R.tws(kc.E);
+    cudaGraphNode_t n3 = gb.kernel(body, &n2, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c1);
+    RowFwdArgs<T> a2{};
+    a2.L = p->L;
+    a2.mode = RF_PCG_P;
+    a2.cp = cp;
+    a2.cr = cr;
+    a2.cz = cz;
+    a2.st = p->st;
+    a2.part = p->part;
+    a2.Z = (cpx<T>*)R.Z;
+    a2.tw = (const cpx<T>*)R.tws(ka.E);
+    cudaGraphNode_t n4 = gb.kernel(body, &n3, 1, ka.f, row_grid(p, ka), ka.threads, ka.smem, a2);
+    ColArgs<T> b2{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
+    cudaGraphNode_t n5 = gb.kernel(body, &n4, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b2);
+    RowInvArgs<T> c2{};
+    c2.L = p->L;
+    c2.mode = RI_CG;
+    c2.s = s;
+    c2.cp = cp;
+    c2.cr = cr;
+    c2.cq = cq;
+    c2.mask = p->mask;
+    c2.st = p->st;
+    c2.part = p->part;
+    c2.h_inner = h_inner;
+    c2.Z = (const cpx<T>*)R.Z;
+    c2.tw = (const cpx<T>*)R.tws(kc.E);
+    gb.kernel(body, &n5, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c2);
+}
+
 // Build the solve graph for one mode:
 //   [prologue] -> while(outer) { A64 (fold correction, mask, FFT x) -> B64 ->
 //                                C64 (true residual, decide) ->
 //                                while(inner) { A -> B -> C } -> final }
-int build_graph(fftconv_plan* p, int mode) {
+int build_graph(fftconv_plan* p, int mode, bool precond) {
     GraphBuilder gb;
     cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
@@ -1283,6 +1376,32 @@ int build_graph(fftconv_plan* p, int mode) {
         const double* sa = p->s64;
         float* sb = p->s32;
         nPro = gb.kernel(g, nullptr, 0, (const void*)k_f64_to_f32, grid_1d(N, 256), 256, 0, N, sa, sb);
+        ndeps = 1;
+    }
+    if (precond) {
+        // preconditioner shift c = mean active s, then its spectrum quarter
+        const double* sa = p->s64;
+        const uint8_t* mk = p->mask;
+        double* pt = p->part;
+        CgState* cst = p->st;
+        int gm = grid_1d(N, 256);
+        if (gm > 512) gm = 512;
+        if (gm > 3 * (p->L + 1) / 2) gm = 3 * (p->L + 1) / 2;  // the partial-sum buffer holds 3 (L+1) doubles
+        cudaGraphNode_t nm = gb.kernel(g, ndeps ? &nPro : nullptr, ndeps, (const void*)k_active_mean, gm, 256, 0, N,
+                                       sa, mk, pt, cst);
+        const long QQ = (long)(p->M / 2 + 1) * (p->M / 2 + 1);
+        const double MM = (double)p->M * (double)p->M;
+        const double* g64 = (const double*)p->p64.Gq;
+        const CgState* ccst = p->st;
+        if (mixed) {
+            float* pq = p->pq32;
+            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<float>, grid_1d(QQ, 256), 256, 0, QQ, MM,
+                             g64, ccst, pq);
+        } else {
+            double* pq = p->pq64;
+            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<double>, grid_1d(QQ, 256), 256, 0, QQ, MM,
+                             g64, ccst, pq);
+        }
         ndeps = 1;
     }
     cudaGraph_t outer = gb.while_node(g, ndeps ? &nPro : nullptr, ndeps, h_outer, &nOuter);
@@ -1331,7 +1450,13 @@ int build_graph(fftconv_plan* p, int mode) {
         cudaGraphNode_t nInner = nullptr;
         cudaGraph_t inner = gb.while_node(outer, &nC, 1, h_inner, &nInner);
         if (!gb.rc) {
-            if (mixed)
+            if (mixed && precond)
+                add_inner_body_pcg<float>(gb, inner, p, p->p32, p->d32, p->r32, p->p32v, p->q32, p->z32, p->s32,
+                                          p->pq32, p->r64, h_inner);
+            else if (precond)
+                add_inner_body_pcg<double>(gb, inner, p, p->p64, p->x64, p->r64, p->p64v, p->q64, p->z64, p->s64,
+                                           p->pq64, nullptr, h_inner);
+            else if (mixed)
                 add_inner_body<float>(gb, inner, p, p->p32, p->d32, p->r32, p->p32v, p->q32, p->s32, p->r64, h_inner);
             else
                 add_inner_body<double>(gb, inner, p, p->p64, p->x64, p->r64, p->p64v, p->q64, p->s64, nullptr,
@@ -1358,8 +1483,8 @@ int build_graph(fftconv_plan* p, int mode) {
         cudaGraphDestroy(g);
         return set_cuda_err(e, "cudaGraphInstantiate");
     }
-    p->graph[mode] = g;
-    p->gexec[mode] = ex;
+    p->graph[mode + 2 * precond] = g;
+    p->gexec[mode + 2 * precond] = ex;
     return FC_OK;
 }
 
@@ -1436,9 +1561,12 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     const long N = p->N;
     const bool mixed = mode == FC_MODE_MIXED;
     const auto t_call = std::chrono::steady_clock::now();
-    const bool persistent = (mixed ? p->p32.sel_pers : p->p64.sel_pers) >= 0;
-    if (!persistent && !p->gexec[mode]) {
-        int rc = build_graph(p, mode);
+    const bool precond = o->precond != 0;
+    const int gi = mode + 2 * (precond ? 1 : 0);
+    // the persistent inner kernel runs plain CG; preconditioned CG uses the graph loop
+    const bool persistent = !precond && (mixed ? p->p32.sel_pers : p->p64.sel_pers) >= 0;
+    if (!persistent && !p->gexec[gi]) {
+        int rc = build_graph(p, mode, precond);
         if (rc) return rc;
     }
     // inputs into the plan's buffers (the graph is built on them)
@@ -1456,7 +1584,9 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     }
     CgState h{};
     h.rtol2 = o->rtol * o->rtol;
-    const double irt = o->inner_rtol > 0 ? o->inner_rtol : 3e-3;
+    // default inner reduction per refinement cycle: the preconditioned FP32
+    // solve stays accurate to 1e-5, plain FP32 CG drifts beyond about 3e-3
+    const double irt = o->inner_rtol > 0 ? o->inner_rtol : (o->precond ? 1e-5 : 3e-3);
     h.inner_rtol2 = irt * irt;
     h.max_iter = o->max_iter > 0 ? o->max_iter : 1000000;
     h.cycle_max = o->refine_every > 0 ? o->refine_every : 100000;
@@ -1484,7 +1614,7 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
             if (p->st_host->finished) break;
         }
     } else {
-        FC_CK(cudaGraphLaunch(p->gexec[mode], st));
+        FC_CK(cudaGraphLaunch(p->gexec[gi], st));
     }
     FC_CK(cudaMemcpyAsync(x, p->x64, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     FC_CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(CgState), cudaMemcpyDeviceToHost, st));

@@ -139,6 +139,32 @@ __device__ __forceinline__ T pass_a_value(const RowFwdArgs<T>& a, size_t i, int 
         a.x64[i] = xv;
         return (T)xv;
     }
+    if (a.mode == RF_PCG_R) {  // PCG: x += alpha p, r -= alpha q; transform r
+        T r;
+        if (first) {
+            if (a.r64) {
+                r = (T)(a.r64[i] * inv_sigma);
+                a.cr[i] = r;
+                a.cx[i] = 0;
+            } else {
+                r = a.cr[i];
+            }
+        } else {
+            const T p = a.cp[i];
+            a.cx[i] = a.cx[i] + alpha * p;
+            r = a.cr[i] - alpha * a.cq[i];
+            a.cr[i] = r;
+        }
+        acc += r * r;
+        return r;
+    }
+    if (a.mode == RF_PCG_P) {  // PCG: p = z + beta p; transform p
+        const T z = a.cz[i];
+        const T p = first ? z : z + beta * a.cp[i];
+        a.cp[i] = p;
+        acc_rp += a.cr[i] * p;
+        return p;
+    }
     T r, p;
     if (first) {
         if (a.r64) {
@@ -176,11 +202,11 @@ struct AScal {
 template <typename T>
 __device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a) {
     AScal<T> sc{0, 0, 0, 0, 1.0, 0.0};
-    if (a.mode == RF_CG) {
+    if (a.mode == RF_CG || a.mode == RF_PCG_R || a.mode == RF_PCG_P) {
         sc.first = a.st->first;
         sc.alpha = (T)a.st->alpha;
         sc.beta = (T)a.st->beta;
-        sc.bcarry = (T)a.st->beta_carry;
+        sc.bcarry = a.mode == RF_CG ? (T)a.st->beta_carry : (T)0;
         if (a.r64) sc.inv_sigma = 1.0 / a.st->sigma;
     } else if (a.mode == RF_XUPD) {
         sc.sig = a.st->sigma;  // scale of the inner run that produced d32
@@ -256,6 +282,12 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
             a.st->rr = tot[0];
             a.st->rp = tot[1];
         }
+    } else if (a.mode == RF_PCG_R) {
+        double pv[1] = {(double)acc}, tot[1];
+        if (grid_sum_last<1>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) a.st->rr = tot[0];
+    } else if (a.mode == RF_PCG_P) {
+        double pv[1] = {(double)acc_rp}, tot[1];
+        if (grid_sum_last<1>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) a.st->rp = tot[0];
     }
 }
 
@@ -349,6 +381,10 @@ __device__ __forceinline__ void pass_c_value(const RowInvArgs<T>& a, size_t i, T
         s0 += p * q;
         s1 += a.cr[i] * q;
         s2 += q * q;
+    } else if (a.mode == RI_PCG_Z) {
+        const T z = act ? y : (T)0;
+        a.cz[i] = z;
+        s0 += a.cr[i] * z;
     } else {  // RI_RESID (T = double)
         const double xv = a.x64[i];
         const double bv = act ? a.b64[i] : 0.0;
@@ -435,6 +471,9 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rinv(RowInvArgs<T> a) {
         double pv[2] = {(double)s0, (double)s1}, tot[2];
         if (grid_sum_last<2>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
             refine_decide(a.st, tot[0], tot[1], a.h_outer, a.h_inner);
+    } else if (a.mode == RI_PCG_Z) {
+        double pv[1] = {(double)s0}, tot[1];
+        if (grid_sum_last<1>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(a.st, tot[0]);
     }
 }
 

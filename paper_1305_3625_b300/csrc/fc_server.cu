@@ -185,6 +185,7 @@ void worker(cg_server* sv, Slot* sl) {
             o.rtol = r->rq.rtol;
             o.mode = r->rq.mode;
             o.x0_zero = 1;
+            o.precond = r->rq.precond;
             rc = cg_solve(plan, sl->ds, sl->db, sl->dx, nullptr, &o, &r->res, sl->stream);
             if (rc == FC_OK || rc == FC_ENOCONV || rc == FC_ENANINF) {
                 cudaMemcpyAsync(sl->hx, sl->dx, sizeof(double) * N, cudaMemcpyDeviceToHost, sl->stream);

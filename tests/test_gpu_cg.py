@@ -239,3 +239,44 @@ def test_every_inner_loop_variant_solves(L):
             res = fc.cg_solve(pl, dev(p["s"]), dev(p["b"]), x, rtol=rtol, mode=mode)
             assert res["status"] == fc.FC_OK, (k, mode, res)
             assert rel2(host(x), want) <= (err if L <= 32 else 10 * err), (k, mode)
+
+
+# ------------------------------------------------ preconditioned CG --------
+
+@pytest.mark.parametrize("L", [1, 3, 8, 32])
+def test_pcg_matches_dense(L):
+    p = fc_inputs.problem(L, seed=40 + L, b_kind="normal")
+    want = dense_solution(L, p["s"], p["b"])
+    for mode, rtol, err in ((fc.FC_MODE_F64, F64_RTOL, F64_ERR), (fc.FC_MODE_MIXED, MIX_RTOL, MIX_ERR)):
+        x, res = solve(L, p["s"], p["b"], mode, rtol, precond=True)
+        assert res["status"] == fc.FC_OK, (mode, res)
+        assert rel2(x, want) <= err
+
+
+def test_pcg_masked_warm_start():
+    L = 16
+    p = fc_inputs.problem(L, seed=8, b_kind="normal")
+    rng = np.random.default_rng(2)
+    mask = (rng.random(L * L) > 0.2).astype(np.uint8)
+    want = dense_solution(L, p["s"], p["b"], mask)
+    x0 = rng.standard_normal(L * L)
+    for mode, rtol, err in ((fc.FC_MODE_F64, F64_RTOL, F64_ERR), (fc.FC_MODE_MIXED, MIX_RTOL, MIX_ERR)):
+        x, res = solve(L, p["s"], p["b"], mode, rtol, x0=x0, mask=mask, precond=True)
+        assert res["status"] == fc.FC_OK
+        assert np.all(x[mask == 0] == 0.0)
+        assert rel2(x, want) <= err
+
+
+@pytest.mark.parametrize("L", [256, 1024])
+def test_pcg_residual_and_fewer_iterations(L):
+    """Same solution (residual recomputed by the oracle's operator) in far
+    fewer iterations: the preconditioned spectrum does not grow with L."""
+    p = fc_inputs.problem(L, seed=0)
+    x_cg, r_cg = solve(L, p["s"], p["b"], fc.FC_MODE_F64, 1e-10)
+    for mode in (fc.FC_MODE_F64, fc.FC_MODE_MIXED):
+        x, res = solve(L, p["s"], p["b"], mode, 1e-10, precond=True)
+        assert res["status"] == fc.FC_OK
+        r = p["b"] - oracle.apply_A(L, p["s"], x)
+        assert np.linalg.norm(r) / np.linalg.norm(p["b"]) <= 1e-10 * 1.01
+        assert rel2(x, x_cg) <= 2 * 0.8 * L * 1e-10
+        assert res["iters"] * 2 < r_cg["iters"], (res["iters"], r_cg["iters"])
