@@ -91,13 +91,24 @@ typedef struct cg_opts {
                           M^-1 = P crop (C_M + c I)^-1 pad P, C_M the padded
                           circulant of C (its spectrum, shifted), c = mean of s
                           over active sites; 0: plain CG as in Listing 2     */
+    int warm_resid;    /* 0: when this solve follows a finished solve on the same
+                          plan with bitwise the same s and b, an active set that
+                          only shrank and at most 32 changed entries of the
+                          masked x (a breaking step), the first true residual is
+                          that solve's final FP64 residual updated by the exact
+                          rank-K correction P'(r - A D), D = P'x - x_old, with
+                          the FP64 Green's function table instead of an FP64
+                          product; -1: always recompute it.  The residual that
+                          certifies convergence is always a full FP64 product. */
 } cg_opts;
 
 typedef struct cg_result {
     int status;            /* FC_OK, FC_ENOCONV or FC_ENANINF                    */
     int iters;             /* CG iterations (products in the inner loops)        */
-    int refinements;       /* true-residual evaluations (FP64 products)          */
-    int reserved;
+    int refinements;       /* true-residual evaluations (FP64 products, plus the
+                              update when resid_updated is 1)                   */
+    int resid_updated;     /* 1: the first true residual came from the warm-start
+                              update (see cg_opts.warm_resid), not a product    */
     double true_rel_resid; /* ||P(b - A x)|| / ||P b|| from the last FP64 residual */
     double bnorm;          /* ||P b||                                           */
     double latency_s;      /* server: submit to completion; cg_solve: call time */
@@ -168,6 +179,11 @@ int fftconv_apply_prec(fftconv_plan *p, int prec, const void *x, void *y, fc_str
  * The whole solve is one CUDA graph launch on stream (device-side while
  * loops; no host round trip per iteration).  The call blocks the host
  * thread until the solve ends, then returns the status also stored in r.
+ * The plan keeps copies of s, b, mask, x and the final FP64 residual; a
+ * warm-started solve after a breaking step updates that residual instead of
+ * recomputing it (cg_opts.warm_resid; the paper has no such step: it is an
+ * exact rewriting of the first residual).  The plan is therefore not shared
+ * by concurrent solves.
  * Errors: FC_EINVAL, FC_ECUDA; FC_ENOCONV / FC_ENANINF from the iteration
  * (x then holds the last iterate).
  */

@@ -47,7 +47,8 @@ class FcError(RuntimeError):
 class cg_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("refine_every", ctypes.c_int), ("max_refine", ctypes.c_int),
-                ("inner_rtol", ctypes.c_double), ("x0_zero", ctypes.c_int), ("precond", ctypes.c_int)]
+                ("inner_rtol", ctypes.c_double), ("x0_zero", ctypes.c_int), ("precond", ctypes.c_int),
+                ("warm_resid", ctypes.c_int)]
 
 
 class cg_tune(ctypes.Structure):
@@ -57,11 +58,12 @@ class cg_tune(ctypes.Structure):
 
 class cg_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("resid_updated", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("latency_s", ctypes.c_double), ("run_s", ctypes.c_double)]
 
     def as_dict(self):
         return {"status": self.status, "iters": self.iters, "refinements": self.refinements,
+                "resid_updated": self.resid_updated,
                 "true_rel_resid": self.true_rel_resid, "bnorm": self.bnorm,
                 "latency_s": self.latency_s, "run_s": self.run_s}
 
@@ -205,12 +207,15 @@ def fftconv_apply(plan: Plan, x, y, stream=None) -> None:
 def cg_solve(plan: Plan, s, b, x, mask=None, rtol: float = 1e-10, mode: int = FC_MODE_F64,
              max_iter: int = 0, refine_every: int = 0, max_refine: int = 0,
              inner_rtol: float = 0.0, x0_zero: bool = False, precond: bool = False, stream=None,
-             check: bool = False) -> dict:
-    """Solve P (C + S) P x = P b in place in x; returns the cg_result fields."""
+             check: bool = False, warm_resid: bool = True) -> dict:
+    """Solve P (C + S) P x = P b in place in x; returns the cg_result fields.
+    warm_resid=False always recomputes the first true residual (no update from
+    the plan's previous solve)."""
     n = plan.L * plan.L
     o = cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode),
                 refine_every=int(refine_every), max_refine=int(max_refine),
-                inner_rtol=float(inner_rtol), x0_zero=int(bool(x0_zero)), precond=int(bool(precond)))
+                inner_rtol=float(inner_rtol), x0_zero=int(bool(x0_zero)), precond=int(bool(precond)),
+                warm_resid=0 if warm_resid else -1)
     r = cg_result()
     rc = _lib.cg_solve(plan.handle, _ptr(s, torch.float64, n, "s"), _ptr(b, torch.float64, n, "b"),
                        _ptr(x, torch.float64, n, "x"), _ptr(mask, torch.uint8, n, "mask"),

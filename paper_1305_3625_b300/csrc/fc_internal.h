@@ -36,9 +36,20 @@ struct CgState {
     int status;              // FC_OK, FC_ENOCONV, FC_ENANINF or FC_ETIMEOUT once finished
     int mixed;               // 1: inner runs in FP32 on the scaled residual
     int finished;
-    int pad_;
+    // Warm-start residual update (a solve that follows another on the same
+    // plan with the same s and b): the check kernel counts the changed
+    // entries of x and flags a changed s, b or a grown active set; the update
+    // kernel then sets warm, which makes the first residual passes A, B, C
+    // skip their products (pass C takes rr64 and bb as given and clears warm).
+    int warm;
+    int warm_used;       // 1: this solve's first true residual was updated, not recomputed
+    int wbad;            // the update does not apply (s or b changed, active set grew)
+    unsigned wcount;     // entries of x that changed (the list holds the first kWarmMax)
     unsigned cntA, cntC;  // last-block counters of passes A and C
 };
+
+// Largest number of changed iterate entries the residual update takes.
+constexpr int kWarmMax = 32;
 
 // Pass A modes: plain input; CG update (x, r, p) + transform p; FP64 iterate
 // with the folded correction; PCG first half (x, r update, transform r);
@@ -71,6 +82,7 @@ struct ColArgs {
     cpx<T>* Z;
     const T* Gq;                 // (M/2+1)^2 real spectrum quarter, 1/M^2 folded in
     const cpx<T>* tw;
+    const int* skip;             // non-null and nonzero: the pass does nothing (warm residual)
 };
 
 template <typename T>

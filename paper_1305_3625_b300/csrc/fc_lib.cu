@@ -203,6 +203,110 @@ __global__ void k_fill_u8(long N, uint8_t* m, uint8_t v) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) m[i] = v;
 }
 
+// Green's function on the non-negative site offsets: gt[dy * L + dx] =
+// G(dx, dy), dx, dy < L (the values the kernel table embeds).
+__global__ void k_green_table(int L, double* gt) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)L * L) return;
+    gt[idx] = green((long)(idx % L), (long)(idx / L));
+}
+
+// ------------------------------------------- warm-start residual update --
+//
+// A solve that follows another solve on the same plan, with the same s and b,
+// an active set that only shrank (P' <= P) and an iterate that differs from
+// the last one, x_old, in a few entries (a breaking step removes one fibre
+// and zeroes its x), needs no FP64 product for its first true residual:
+// with D = P' x - x_old (nonzero at the changed entries k only),
+//   P' (b - A P' x) = P' (P (b - A x_old) - A D),
+//   (A D)_i = sum_k D_k (G(r_i - r_k) + s_k [i = k]),
+// where P (b - A x_old) is the last solve's final FP64 residual r64, still in
+// the plan.  The check kernel compares the new inputs with the plan's copies
+// while copying them in; the update kernel applies the rank-K correction with
+// the FP64 Green's function table.  Later residuals (and the final one that
+// certifies convergence) are full FP64 products.
+
+// Copies s, b, the masked x and the mask into the plan's buffers (writing
+// only entries that changed) and records: st->wbad when s or b differ bitwise
+// or a site became active, st->wcount changed entries of x with the first
+// kWarmMax of them (flat index, x_new - x_old) in widx, wdx.
+__global__ void __launch_bounds__(256) k_warm_check(long N, const double* s, const double* b, const double* x,
+                                                    const uint8_t* mask_in, double* s64, double* b64, double* x64,
+                                                    uint8_t* mask, CgState* st, long long* widx, double* wdx) {
+    int bad = 0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const double sn = s[i], bn = b[i];
+        const uint8_t mo = mask[i];
+        const uint8_t mn = mask_in ? mask_in[i] : (uint8_t)1;
+        if (__double_as_longlong(sn) != __double_as_longlong(s64[i])) {
+            bad = 1;
+            s64[i] = sn;
+        }
+        if (__double_as_longlong(bn) != __double_as_longlong(b64[i])) {
+            bad = 1;
+            b64[i] = bn;
+        }
+        if (mn && !mo) bad = 1;
+        if (mn != mo) mask[i] = mn;
+        const double xn = mn ? x[i] : 0.0, xo = x64[i];
+        if (__double_as_longlong(xn) != __double_as_longlong(xo)) {
+            x64[i] = xn;
+            const unsigned k = atomicAdd(&st->wcount, 1u);
+            if (k < (unsigned)kWarmMax) {
+                widx[k] = i;
+                wdx[k] = xn - xo;
+            }
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->wbad, 1);
+}
+
+// r64 <- P' (r64 - A D) with the recorded changes, and its sums rr64 = |r|^2,
+// bb = |P' b|^2; the last block sets st->warm so that the first residual
+// passes hand these to the refinement decision.  Does nothing (the passes
+// then compute the residual) when the check found the update inapplicable.
+__global__ void __launch_bounds__(256) k_warm_resid(long N, int L, const double* gt, const uint8_t* mask,
+                                                    const double* s64, const double* b64, double* r64,
+                                                    double* part, CgState* st, const long long* widx,
+                                                    const double* wdx) {
+    __shared__ long long ki[kWarmMax];
+    __shared__ int ky[kWarmMax], kx[kWarmMax];
+    __shared__ double kd[kWarmMax];
+    const unsigned K = st->wcount;
+    if (st->wbad || K > (unsigned)kWarmMax) return;  // the same in every block
+    if (threadIdx.x < K) {
+        const long long i = widx[threadIdx.x];
+        ki[threadIdx.x] = i;
+        ky[threadIdx.x] = (int)(i / L);
+        kx[threadIdx.x] = (int)(i % L);
+        kd[threadIdx.x] = wdx[threadIdx.x];
+    }
+    __syncthreads();
+    double v[2] = {0.0, 0.0}, tot[2];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        double r = 0.0;
+        if (mask[i]) {
+            const int iy = (int)(i / L), ix = (int)(i % L);
+            r = r64[i];
+            for (unsigned k = 0; k < K; ++k) {
+                double a = __ldg(gt + (size_t)abs(iy - ky[k]) * L + abs(ix - kx[k]));
+                if (i == ki[k]) a += s64[i];
+                r -= kd[k] * a;
+            }
+            const double bv = b64[i];
+            v[1] += bv * bv;
+        }
+        r64[i] = r;
+        v[0] += r * r;
+    }
+    if (grid_sum_last<2>(v, part, &st->cntC, tot) && threadIdx.x == 0) {
+        st->rr64 = tot[0];
+        st->bb = tot[1];
+        st->warm = 1;
+        st->warm_used = 1;
+    }
+}
+
 struct ArgmaxCtl {
     unsigned cnt;
     int pad;
@@ -501,6 +605,13 @@ struct fftconv_plan {
     int am_grid = 0;
     cudaGraph_t graph[4] = {};      // index mode + 2 * precond
     cudaGraphExec_t gexec[4] = {};
+    // warm-start residual update: FP64 Green's function table [L][L], the
+    // changed-entry list, and whether r64 is the final true residual of the
+    // iterate, s, b and mask now in the plan (set after a finished solve)
+    double* gtab = nullptr;
+    long long* widx = nullptr;
+    double* wdx = nullptr;
+    bool warm_ok = false;
 };
 
 namespace {
@@ -524,7 +635,7 @@ void plan_free(fftconv_plan* p) {
     void* ptrs[] = {p->p32.Z, p->p32.Gq, p->p64.Z, p->p64.tw, p->p64.Gq, p->x64, p->r64,
                     p->p64v, p->q64, p->b64, p->s64, p->mask, p->d32, p->r32, p->p32v, p->q32, p->s32,
                     p->st, p->part, p->partA, p->partC, p->pctl, p->am_v, p->am_i, p->am_ctl,
-                    p->z64, p->pq64, p->z32, p->pq32};
+                    p->z64, p->pq64, p->z32, p->pq32, p->gtab, p->widx, p->wdx};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 5; ++i) {
@@ -906,6 +1017,11 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         FC_TRY(dalloc(p, (void**)&p->mask, N));
         FC_TRY(dalloc(p, (void**)&p->z64, sizeof(double) * N));
         FC_TRY(dalloc(p, (void**)&p->pq64, sizeof(double) * (size_t)Q * Q));
+        FC_TRY(dalloc(p, (void**)&p->gtab, sizeof(double) * N));
+        FC_TRY(dalloc(p, (void**)&p->widx, sizeof(long long) * kWarmMax));
+        FC_TRY(dalloc(p, (void**)&p->wdx, sizeof(double) * kWarmMax));
+        k_green_table<<<(unsigned)((N + 255) / 256), 256, 0, cs>>>(L, p->gtab);
+        FC_TRYC(cudaGetLastError());
         if (p->p32.on) {
             FC_TRY(dalloc(p, (void**)&p->z32, sizeof(float) * N));
             FC_TRY(dalloc(p, (void**)&p->pq32, sizeof(float) * (size_t)Q * Q));
@@ -1430,7 +1546,7 @@ int build_graph(fftconv_plan* p, int mode, bool precond) {
         a.x = nullptr;
         cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
         ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq,
-                          (const cpx<double>*)p->p64.tws(kb.E)};
+                          (const cpx<double>*)p->p64.tws(kb.E), &p->st->warm};
         cudaGraphNode_t nB = gb.kernel(outer, &nA, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
         RowInvArgs<double> c{};
         c.L = p->L;
@@ -1508,7 +1624,8 @@ int launch_resid_chain(fftconv_plan* p, bool mixed, cudaStream_t st) {
     a.tw = (const cpx<double>*)p->p64.tws(ka.E);
     int rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, st, a);
     if (rc) return rc;
-    ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tws(kb.E)};
+    ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tws(kb.E),
+                      &p->st->warm};
     rc = launch(kb.f, col_grid(p, kb), kb.threads, kb.smem, st, b);
     if (rc) return rc;
     RowInvArgs<double> c{};
@@ -1569,19 +1686,6 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
         int rc = build_graph(p, mode, precond);
         if (rc) return rc;
     }
-    // inputs into the plan's buffers (the graph is built on them)
-    FC_CK(cudaMemcpyAsync(p->s64, s, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-    FC_CK(cudaMemcpyAsync(p->b64, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-    if (o->x0_zero)
-        FC_CK(cudaMemsetAsync(p->x64, 0, sizeof(double) * N, st));
-    else
-        FC_CK(cudaMemcpyAsync(p->x64, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-    if (mask) {
-        FC_CK(cudaMemcpyAsync(p->mask, mask, N, cudaMemcpyDeviceToDevice, st));
-    } else {
-        k_fill_u8<<<grid_1d(N, 256), 256, 0, st>>>(N, p->mask, 1);
-        FC_CK(cudaGetLastError());
-    }
     CgState h{};
     h.rtol2 = o->rtol * o->rtol;
     // default inner reduction per refinement cycle: the preconditioned FP32
@@ -1596,6 +1700,34 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     h.first = 1;
     *p->st_host = h;
     FC_CK(cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st));
+    // inputs into the plan's buffers (the graph is built on them); after a
+    // finished solve, through the check that may replace the first FP64
+    // residual product by the update from the last residual
+    const bool try_warm = p->warm_ok && !o->x0_zero && o->warm_resid == 0;
+    p->warm_ok = false;  // the buffers change from here on
+    if (try_warm) {
+        k_warm_check<<<grid_1d(N, 256), 256, 0, st>>>(N, s, b, x, mask, p->s64, p->b64, p->x64, p->mask, p->st,
+                                                       p->widx, p->wdx);
+        FC_CK(cudaGetLastError());
+        int g = grid_1d(N, 256);
+        if (g > p->L + 1) g = p->L + 1;  // the partial-sum buffer holds 3 (L+1) doubles
+        k_warm_resid<<<g, 256, 0, st>>>(N, p->L, p->gtab, p->mask, p->s64, p->b64, p->r64, p->part, p->st, p->widx,
+                                        p->wdx);
+        FC_CK(cudaGetLastError());
+    } else {
+        FC_CK(cudaMemcpyAsync(p->s64, s, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        FC_CK(cudaMemcpyAsync(p->b64, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        if (o->x0_zero)
+            FC_CK(cudaMemsetAsync(p->x64, 0, sizeof(double) * N, st));
+        else
+            FC_CK(cudaMemcpyAsync(p->x64, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        if (mask) {
+            FC_CK(cudaMemcpyAsync(p->mask, mask, N, cudaMemcpyDeviceToDevice, st));
+        } else {
+            k_fill_u8<<<grid_1d(N, 256), 256, 0, st>>>(N, p->mask, 1);
+            FC_CK(cudaGetLastError());
+        }
+    }
     if (persistent) {
         // Host-driven refinement loop: per cycle the FP64 true residual
         // (3 passes, device-side decision) and one cooperative launch that
@@ -1620,10 +1752,14 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     FC_CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
     FC_CK(cudaStreamSynchronize(st));
     const CgState& f = *p->st_host;
+    // r64 is the true residual of the final x64 whenever the refinement
+    // decision finished the solve
+    p->warm_ok = f.finished && (f.status == FC_OK || f.status == FC_ENOCONV);
     if (r) {
         r->status = f.status;
         r->iters = f.iter;
         r->refinements = f.cycles;
+        r->resid_updated = f.warm_used;
         r->true_rel_resid = f.bb > 0 ? sqrt(f.rr64 / f.bb) : 0.0;
         r->bnorm = sqrt(f.bb);
         r->latency_s = r->run_s =

@@ -273,6 +273,7 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
 template <typename T, int M, int E, int RB>
 __global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
     const AScal<T> sc = ascal_from_state(a);
     T acc = 0, acc_rp = 0;
     rfwd_unit<T, M, E, RB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
@@ -364,6 +365,7 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
 template <typename T, int M, int E, int CB>
 __global__ void __launch_bounds__(CB*(M / E)) k_colc(ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    if (a.skip && *a.skip) return;
     colc_unit<T, M, E, CB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
 }
 
@@ -462,15 +464,25 @@ template <typename T, int M, int E, int RB>
 __global__ void __launch_bounds__(RB*(M / E)) k_rinv(RowInvArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
-    rinv_unit<T, M, E, RB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
+    // warm residual: r64 and its sums (rr64, bb) are already in place, and
+    // block 0 alone hands them to the decision
+    const bool warm = a.mode == RI_RESID && a.st->warm;
+    if (!warm) {
+        rinv_unit<T, M, E, RB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s0 = (T)a.st->rr64;
+        s1 = (T)a.st->bb;
+    }
     if (a.mode == RI_CG) {
         double pv[3] = {(double)s0, (double)s1, (double)s2}, tot[3];
         if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
             cg_step_decide(a.st, tot[0], tot[1], tot[2], a.h_inner);
     } else if (a.mode == RI_RESID) {
         double pv[2] = {(double)s0, (double)s1}, tot[2];
-        if (grid_sum_last<2>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
+        if (grid_sum_last<2>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) {
             refine_decide(a.st, tot[0], tot[1], a.h_outer, a.h_inner);
+            a.st->warm = 0;  // every block has read it: later cycles recompute the residual
+        }
     } else if (a.mode == RI_PCG_Z) {
         double pv[1] = {(double)s0}, tot[1];
         if (grid_sum_last<1>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(a.st, tot[0]);
