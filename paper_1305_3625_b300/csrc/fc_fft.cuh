@@ -147,8 +147,9 @@ __host__ __device__ constexpr int n_exchanges(int M, int E) {
     for (int ns = 1; ns * E < M; ns *= E) ++n;
     return n;
 }
-// Stage twiddle table: for each stage with NS > 1 a block of NS x R entries,
-// entry [k][e] = exp(-2 pi i e k / (NS R)) (R the stage radix); the offset of
+// Stage twiddle table: for each stage with NS > 1 a block of R x NS entries,
+// entry [e][k] = exp(-2 pi i e k / (NS R)) (R the stage radix), so that the
+// threads of a warp (consecutive k) read consecutive entries; the offset of
 // stage NS's block, and the whole table's length.
 __host__ __device__ constexpr int tw_offset(int M, int E, int NS) {
     int off = 0;
@@ -157,21 +158,12 @@ __host__ __device__ constexpr int tw_offset(int M, int E, int NS) {
 }
 __host__ __device__ constexpr int tw_len(int M, int E) { return tw_offset(M, E, M); }
 
-// Load the R-1 twiddles e = 1..R-1 of one table row (16-byte loads).
-template <typename T, int R>
-__device__ __forceinline__ void load_twiddles(const cpx<T>* __restrict__ row, cpx<T> (&w)[R]) {
-    if constexpr (sizeof(T) == 4 && R % 2 == 0) {
-        const float4* r4 = reinterpret_cast<const float4*>(row);
+// Load the R-1 twiddles e = 1..R-1 of column k of a stage block (entry
+// [e][k] at blk[e*NS + k]): one coalesced load per e across the warp.
+template <typename T, int R, int NS>
+__device__ __forceinline__ void load_twiddles(const cpx<T>* __restrict__ blk, int k, cpx<T> (&w)[R]) {
 #pragma unroll
-        for (int h = 0; h < R / 2; ++h) {
-            const float4 q = __ldg(r4 + h);
-            w[2 * h] = cpx<T>{q.x, q.y};
-            w[2 * h + 1] = cpx<T>{q.z, q.w};
-        }
-    } else {
-#pragma unroll
-        for (int e = 1; e < R; ++e) w[e] = ldg_c(row + e);
-    }
+    for (int e = 1; e < R; ++e) w[e] = ldg_c(blk + e * NS + k);
 }
 
 // Stockham transform of one length-M sequence held by G = M/E threads as
@@ -189,7 +181,7 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, c
         const int k = j & (NS - 1);
         if constexpr (NS > 1) {
             cpx<T> w[E];
-            load_twiddles<T, E>(tws + tw_offset(M, E, NS) + k * E, w);
+            load_twiddles<T, E, NS>(tws + tw_offset(M, E, NS), k, w);
 #pragma unroll
             for (int e = 1; e < E; ++e) v[e] = INV ? cmulc(v[e], w[e]) : cmul(v[e], w[e]);
         }
@@ -213,7 +205,7 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, c
         for (int b = 0; b < B; ++b) {
             const int jj = j + b * G;
             cpx<T> u[R], w[R];
-            load_twiddles<T, R>(tws + tw_offset(M, E, NS) + jj * R, w);
+            load_twiddles<T, R, NS>(tws + tw_offset(M, E, NS), jj, w);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 u[r] = v[b + r * B];

@@ -50,13 +50,13 @@ __global__ void k_twiddles(int M, cpx<double>* tw64, cpx<float>* tw32) {
 }
 
 // Stage twiddle table of a (M, E) transform from the FP64 base table
-// tw64[m] = exp(-2 pi i m / M): entry [k][e] of the stage with span NS and
-// radix R is tw64[e k M / (NS R)], rounded to T.
+// tw64[m] = exp(-2 pi i m / M): entry [e][k] (at e*NS + k) of the stage with
+// span NS and radix R is tw64[e k M / (NS R)], rounded to T.
 template <typename T>
 __global__ void k_stage_twiddles(int M, int NS, int R, int off, const cpx<double>* tw64, cpx<T>* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NS * R) return;
-    const int k = i / R, e = i % R;
+    const int e = i / NS, k = i % NS;
     const cpx<double> w = tw64[(size_t)e * k * (M / (NS * R))];
     out[off + i] = cpx<T>{(T)w.x, (T)w.y};
 }
