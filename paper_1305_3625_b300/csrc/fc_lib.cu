@@ -416,11 +416,11 @@ struct Variants {
 
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-template <typename T, int M, int E, int RB>
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
 void add_row(Variants& v) {
-    if constexpr (RB * (M / E) <= 1024 && pass_smem<T, M, RB>() <= 200 * 1024) {
-        KV f{(const void*)k_rfwd<T, M, E, RB>, RB * (M / E), RB, E, pass_smem<T, M, RB>()};
-        KV i{(const void*)k_rinv<T, M, E, RB>, RB * (M / E), RB, E, pass_smem<T, M, RB>()};
+    if constexpr (RB * (M / E) <= 1024 && pass_smem<T, M, RB, DB>() <= 200 * 1024) {
+        KV f{(const void*)k_rfwd<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
+        KV i{(const void*)k_rinv<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
         for (int k = 0; k < v.n_rfwd; ++k)
             if (v.rfwd[k].f == f.f) return;
         v.rfwd[v.n_rfwd++] = f;
@@ -428,10 +428,10 @@ void add_row(Variants& v) {
     }
 }
 
-template <typename T, int M, int E, int CB>
+template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
 void add_col(Variants& v) {
-    if constexpr (CB * (M / E) <= 1024 && pass_smem<T, M, CB>() <= 200 * 1024) {
-        KV c{(const void*)k_colc<T, M, E, CB>, CB * (M / E), CB, E, pass_smem<T, M, CB>()};
+    if constexpr (CB * (M / E) <= 1024 && pass_smem<T, M, CB, DB>() <= 200 * 1024) {
+        KV c{(const void*)k_colc<T, M, E, CB, MINB, DB>, CB * (M / E), CB, E, pass_smem<T, M, CB, DB>()};
         for (int k = 0; k < v.n_colc; ++k)
             if (v.colc[k].f == c.f) return;
         v.colc[v.n_colc++] = c;
@@ -477,6 +477,14 @@ void make_variants(Variants& v) {
             add_col<T, M, 8, clampi(256 / G8, 1, H)>(v);
             add_col<T, M, 8, clampi(512 / G8, 1, H)>(v);
             add_col<T, M, 4, clampi(512 / G4, 1, H)>(v);
+            // single-buffered, at most 64 registers: more resident blocks
+            // (a one-wave grid where the default shapes need 1.15 waves)
+            constexpr int C1 = clampi(128 / G16, 1, H), C2 = clampi(256 / G16, 1, H);
+            constexpr int R1 = clampi(128 / G16, 1, 64), R2 = clampi(256 / G16, 1, 64);
+            add_col<T, M, 16, C1, clampi(65536 / (C1 * G16 * 64), 1, 16), false>(v);
+            add_col<T, M, 16, C2, clampi(65536 / (C2 * G16 * 64), 1, 16), false>(v);
+            add_row<T, M, 16, R1, clampi(65536 / (R1 * G16 * 64), 1, 16), false>(v);
+            add_row<T, M, 16, R2, clampi(65536 / (R2 * G16 * 64), 1, 16), false>(v);
         }
         add_pers<T, M, 16, 16, (M * M / 32 < 256 ? M * M / 32 : 256)>(v);
         add_pers<T, M, 16, 8, 256>(v);
@@ -650,6 +658,37 @@ template <typename T>
 int launch(const void* f, int grid, int threads, size_t smem, cudaStream_t s, T& args) {
     void* kp[1] = {(void*)&args};
     FC_CK(cudaLaunchKernel(f, dim3(grid), dim3(threads), kp, smem, s));
+    return FC_OK;
+}
+
+// Programmatic dependent launches between consecutive passes (FC_PDL=0 turns
+// them off): the next pass's blocks are scheduled while the previous pass
+// drains and wait on the device for its completion.
+bool pdl_on() {
+    static const bool on = [] {
+        const char* e = getenv("FC_PDL");
+        return !(e && !strcmp(e, "0"));
+    }();
+    return on;
+}
+
+// A pass launched as a programmatic dependent of the previous kernel on s
+// (the passes wait for it before touching memory).
+template <typename T>
+int launch_dep(const void* f, int grid, int threads, size_t smem, cudaStream_t s, T& args) {
+    if (!pdl_on()) return launch(f, grid, threads, smem, s, args);
+    void* kp[1] = {(void*)&args};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    FC_CK(cudaLaunchKernelExC(&cfg, f, kp));
     return FC_OK;
 }
 
@@ -1151,7 +1190,7 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     int rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, s, a);
     if (rc) return rc;
     ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
-    rc = launch(kb.f, col_grid(p, kb), kb.threads, kb.smem, s, b);
+    rc = launch_dep(kb.f, col_grid(p, kb), kb.threads, kb.smem, s, b);
     if (rc) return rc;
     RowInvArgs<T> c{};
     c.L = p->L;
@@ -1161,7 +1200,7 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     c.part = p->part;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = (const cpx<T>*)R.tws(kc.E);
-    return launch(kc.f, row_grid(p, kc), kc.threads, kc.smem, s, c);
+    return launch_dep(kc.f, row_grid(p, kc), kc.threads, kc.smem, s, c);
 }
 
 }  // namespace
@@ -1336,6 +1375,7 @@ namespace {
 
 struct GraphBuilder {
     int rc = FC_OK;
+    bool pdl = false;  // programmatic edges between consecutive passes
     template <typename... A>
     cudaGraphNode_t kernel(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const void* f, int grid, int threads,
                            size_t smem, const A&... args) {
@@ -1350,6 +1390,22 @@ struct GraphBuilder {
         kp.kernelParams = args_;
         cudaError_t e = cudaGraphAddKernelNode(&n, g, deps, ndeps, &kp);
         if (e != cudaSuccess) rc = set_cuda_err(e, "cudaGraphAddKernelNode");
+        return n;
+    }
+    // A pass that follows another pass (a kernel node that starts with
+    // pdl_enter): with pdl, a programmatic edge from the previous pass's
+    // trigger port, otherwise an ordinary edge.
+    template <typename... A>
+    cudaGraphNode_t pass(cudaGraph_t g, cudaGraphNode_t prev, const void* f, int grid, int threads, size_t smem,
+                         const A&... args) {
+        if (!pdl) return kernel(g, &prev, 1, f, grid, threads, smem, args...);
+        cudaGraphNode_t n = kernel(g, nullptr, 0, f, grid, threads, smem, args...);
+        if (rc) return n;
+        cudaGraphEdgeData ed{};
+        ed.from_port = cudaGraphKernelNodePortProgrammatic;
+        ed.type = cudaGraphDependencyTypeProgrammatic;
+        cudaError_t e = cudaGraphAddDependencies(g, &prev, &n, &ed, 1);
+        if (e != cudaSuccess) rc = set_cuda_err(e, "cudaGraphAddDependencies(programmatic)");
         return n;
     }
     cudaGraph_t while_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, cudaGraphConditionalHandle h,
@@ -1389,7 +1445,7 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     a.tw = (const cpx<T>*)R.tws(ka.E);
     cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
     ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
-    cudaGraphNode_t nB = gb.kernel(body, &nA, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
+    cudaGraphNode_t nB = gb.pass(body, nA, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
     RowInvArgs<T> c{};
     c.L = p->L;
     c.mode = RI_CG;
@@ -1403,7 +1459,7 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     c.h_inner = h_inner;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = (const cpx<T>*)R.tws(kc.E);
-    gb.kernel(body, &nB, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
+    gb.pass(body, nB, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
 }
 
 // Inner body of preconditioned CG: A1 (x, r update; transform r) -> B1 with
@@ -1428,7 +1484,7 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a1.tw = (const cpx<T>*)R.tws(ka.E);
     cudaGraphNode_t n1 = gb.kernel(body, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a1);
     ColArgs<T> b1{p->L, (cpx<T>*)R.Z, pq, (const cpx<T>*)R.tws(kb.E)};
-    cudaGraphNode_t n2 = gb.kernel(body, &n1, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b1);
+    cudaGraphNode_t n2 = gb.pass(body, n1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b1);
     RowInvArgs<T> c1{};
     c1.L = p->L;
     c1.mode = RI_PCG_Z;
@@ -1439,7 +1495,7 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c1.part = p->part;
     c1.Z = (const cpx<T>*)R.Z;
     c1.tw = (const cpx<T>*)R.tws(kc.E);
-    cudaGraphNode_t n3 = gb.kernel(body, &n2, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c1);
+    cudaGraphNode_t n3 = gb.pass(body, n2, kc.f, row_grid(p, kc), kc.threads, kc.smem, c1);
     RowFwdArgs<T> a2{};
     a2.L = p->L;
     a2.mode = RF_PCG_P;
@@ -1450,9 +1506,9 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a2.part = p->part;
     a2.Z = (cpx<T>*)R.Z;
     a2.tw = (const cpx<T>*)R.tws(ka.E);
-    cudaGraphNode_t n4 = gb.kernel(body, &n3, 1, ka.f, row_grid(p, ka), ka.threads, ka.smem, a2);
+    cudaGraphNode_t n4 = gb.pass(body, n3, ka.f, row_grid(p, ka), ka.threads, ka.smem, a2);
     ColArgs<T> b2{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
-    cudaGraphNode_t n5 = gb.kernel(body, &n4, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b2);
+    cudaGraphNode_t n5 = gb.pass(body, n4, kb.f, col_grid(p, kb), kb.threads, kb.smem, b2);
     RowInvArgs<T> c2{};
     c2.L = p->L;
     c2.mode = RI_CG;
@@ -1466,15 +1522,16 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c2.h_inner = h_inner;
     c2.Z = (const cpx<T>*)R.Z;
     c2.tw = (const cpx<T>*)R.tws(kc.E);
-    gb.kernel(body, &n5, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c2);
+    gb.pass(body, n5, kc.f, row_grid(p, kc), kc.threads, kc.smem, c2);
 }
 
 // Build the solve graph for one mode:
 //   [prologue] -> while(outer) { A64 (fold correction, mask, FFT x) -> B64 ->
 //                                C64 (true residual, decide) ->
 //                                while(inner) { A -> B -> C } -> final }
-int build_graph(fftconv_plan* p, int mode, bool precond) {
+int build_graph_with(fftconv_plan* p, int mode, bool precond, bool pdl) {
     GraphBuilder gb;
+    gb.pdl = pdl;
     cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
     cudaGraphNode_t nPro = nullptr, nOuter = nullptr;
@@ -1547,7 +1604,7 @@ int build_graph(fftconv_plan* p, int mode, bool precond) {
         cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
         ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq,
                           (const cpx<double>*)p->p64.tws(kb.E), &p->st->warm};
-        cudaGraphNode_t nB = gb.kernel(outer, &nA, 1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
+        cudaGraphNode_t nB = gb.pass(outer, nA, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
         RowInvArgs<double> c{};
         c.L = p->L;
         c.mode = RI_RESID;
@@ -1562,7 +1619,7 @@ int build_graph(fftconv_plan* p, int mode, bool precond) {
         c.h_inner = h_inner;
         c.Z = (const cpx<double>*)p->p64.Z;
         c.tw = (const cpx<double>*)p->p64.tws(kc.E);
-        cudaGraphNode_t nC = gb.kernel(outer, &nB, 1, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
+        cudaGraphNode_t nC = gb.pass(outer, nB, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
         cudaGraphNode_t nInner = nullptr;
         cudaGraph_t inner = gb.while_node(outer, &nC, 1, h_inner, &nInner);
         if (!gb.rc) {
@@ -1602,6 +1659,13 @@ int build_graph(fftconv_plan* p, int mode, bool precond) {
     p->graph[mode + 2 * precond] = g;
     p->gexec[mode + 2 * precond] = ex;
     return FC_OK;
+}
+
+// The solve graph with programmatic edges between passes where the driver
+// accepts them inside the conditional bodies, else with ordinary edges.
+int build_graph(fftconv_plan* p, int mode, bool precond) {
+    if (pdl_on() && build_graph_with(p, mode, precond, true) == FC_OK) return FC_OK;
+    return build_graph_with(p, mode, precond, false);
 }
 
 }  // namespace

@@ -37,10 +37,23 @@ template <typename T, int M, int PER>
 __host__ __device__ constexpr bool use_db() {
     return (size_t)PER * 2 * seg_len(M) * sizeof(cpx<T>) <= 160 * 1024;
 }
-template <typename T, int M, int PER>
+template <typename T, int M, int PER, bool DB = use_db<T, M, PER>()>
 __host__ __device__ constexpr size_t pass_smem() {
-    return (size_t)PER * (use_db<T, M, PER>() ? 2 : 1) * seg_len(M) * sizeof(cpx<T>);
+    return (size_t)PER * (DB ? 2 : 1) * seg_len(M) * sizeof(cpx<T>);
 }
+
+// ------------------------------------------- programmatic dependencies ---
+//
+// The passes may be launched as programmatic dependents of the previous pass
+// (graph edges of programmatic type, or the stream attribute): each block
+// waits until the previous grid has completed and its writes are visible
+// before any global memory access, and signals the next pass once its own
+// transform is done, so that the next pass's launch overlaps this pass's
+// tail (its last blocks and the grid reduction).  Signalling at block entry
+// instead measured slower inside the solve graphs.  Without a programmatic
+// launch both are no-ops.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_leave() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // ------------------------------------------------------- loads/stores ---
 
@@ -217,12 +230,11 @@ __device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a) {
 // One unit of pass A: RB row pairs starting at pair unit*RB, G = M/E threads
 // per pair.  Adds this thread's r.r and r.p to acc, acc_rp.  Leaves shared
 // memory in use: the caller synchronises before the block reuses it.
-template <typename T, int M, int E, int RB>
+template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
 __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm, T& acc,
                                           T& acc_rp) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
-    constexpr bool DB = use_db<T, M, RB>();
     constexpr int GS = (DB ? 2 : 1) * SEG;  // shared elements per pair
     constexpr int NB = next_buf(M, E, DB, 0);
     const int t = threadIdx.x, j = t % G, pl = t / G;
@@ -270,13 +282,17 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
     }
 }
 
-template <typename T, int M, int E, int RB>
-__global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
+// MINB: blocks per SM the register allocation must allow; DB: double-buffered
+// exchanges (default: when they fit, see use_db).
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(RowFwdArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
     if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
     const AScal<T> sc = ascal_from_state(a);
     T acc = 0, acc_rp = 0;
-    rfwd_unit<T, M, E, RB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
+    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
+    pdl_leave();
     if (a.mode == RF_CG) {
         double pv[2] = {(double)acc, (double)acc_rp}, tot[2];
         if (grid_sum_last<2>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) {
@@ -296,11 +312,10 @@ __global__ void __launch_bounds__(RB*(M / E)) k_rfwd(RowFwdArgs<T> a) {
 
 // One unit of pass B: CB columns starting at column unit*CB, G = M/E threads
 // per column (j fastest).  Unit 0 holds the packed column 0.
-template <typename T, int M, int E, int CB>
+template <typename T, int M, int E, int CB, bool DB = use_db<T, M, CB>()>
 __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>* sm) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, Q = M / 2 + 1, SEG = seg_len(M);
-    constexpr bool DB = use_db<T, M, CB>();
     constexpr int GS = (DB ? 2 : 1) * SEG;
     constexpr int NB = next_buf(M, E, DB, 0);
     const int t = threadIdx.x, j = t % G, c = t / G;
@@ -362,11 +377,13 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
     }
 }
 
-template <typename T, int M, int E, int CB>
-__global__ void __launch_bounds__(CB*(M / E)) k_colc(ColArgs<T> a) {
+template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
+__global__ void __launch_bounds__(CB*(M / E), MINB) k_colc(ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
     if (a.skip && *a.skip) return;
-    colc_unit<T, M, E, CB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    pdl_leave();
 }
 
 // ------------------------------------------------------------ pass C ----
@@ -399,11 +416,10 @@ __device__ __forceinline__ void pass_c_value(const RowInvArgs<T>& a, size_t i, T
 
 // One unit of pass C: RB row pairs starting at pair unit*RB.  Adds this
 // thread's partial sums to s0, s1, s2.
-template <typename T, int M, int E, int RB>
+template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
 __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, T& s0, T& s1, T& s2) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
-    constexpr bool DB = use_db<T, M, RB>();
     constexpr int GS = (DB ? 2 : 1) * SEG;
     constexpr int HS = H + (H >> 4) + 1;  // staging: second row of a pair at an odd bank offset
     const int t = threadIdx.x, j = t % G, pl = t / G;
@@ -460,19 +476,21 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
     }
 }
 
-template <typename T, int M, int E, int RB>
-__global__ void __launch_bounds__(RB*(M / E)) k_rinv(RowInvArgs<T> a) {
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(RowInvArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
     T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
     // warm residual: r64 and its sums (rr64, bb) are already in place, and
     // block 0 alone hands them to the decision
     const bool warm = a.mode == RI_RESID && a.st->warm;
     if (!warm) {
-        rinv_unit<T, M, E, RB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
+        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
         s0 = (T)a.st->rr64;
         s1 = (T)a.st->bb;
     }
+    pdl_leave();
     if (a.mode == RI_CG) {
         double pv[3] = {(double)s0, (double)s1, (double)s2}, tot[3];
         if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
