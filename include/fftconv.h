@@ -53,6 +53,10 @@ typedef struct CUstream_st *fc_stream_t; /* identical to cudaStream_t */
 #define FC_F32 1
 #define FC_F64 2
 
+/* Green's function of Eq. 1c (a = 1, (1 - nu^2)/E = 1) */
+#define FC_GREEN_POINT 0 /* 1/(pi r) for r > 0, the exact cell integral at r = 0 */
+#define FC_GREEN_CELL 1  /* the cell integral of Eq. 1c for every offset      */
+
 /* solve modes */
 #define FC_MODE_F64 0   /* plain FP64: FFTs, vectors and reductions in FP64   */
 #define FC_MODE_MIXED 1 /* FP32 FFTs and vectors, FP64 reductions, FP64 true
@@ -133,6 +137,21 @@ const char *fc_last_error(void);
  * (spectrum not real to 1e-12).
  */
 int fftconv_plan_create(fftconv_plan **p, int L, int prec, const cg_tune *tune);
+
+/*
+ * fftconv_plan_create_green -- as fftconv_plan_create (which uses
+ * FC_GREEN_POINT) with the Green's function chosen:
+ *   green  FC_GREEN_POINT: G = 1/(pi r), r > 0, and the exact self term
+ *          4 ln(1 + sqrt 2)/pi;
+ *          FC_GREEN_CELL: G = (1/pi) * integral over the unit cell around
+ *          the offset of dA/r (Eq. 1c as printed), by the closed form at r = 0
+ *          and 16-, 8- or 4-point Gauss-Legendre tensor quadrature elsewhere
+ *          (relative error below 1e-16).
+ * Only the offset table and its spectrum differ; every call on the plan
+ * (apply, cg_solve, fc_masked_step) then uses that operator.
+ * Errors: as fftconv_plan_create; FC_EINVAL for another green value.
+ */
+int fftconv_plan_create_green(fftconv_plan **p, int L, int prec, int green, const cg_tune *tune);
 
 /* Free a plan and its device memory (synchronises the device first). */
 int fftconv_plan_destroy(fftconv_plan *p);

@@ -10,6 +10,8 @@ compiles it with gcc on first use and wraps it with ctypes.
 
 Parity status of each function (what pins it, in tests/test_oracle_*.py):
   G                 closed form of the self term and quadrature of Eq. 1c
+  G_cell            self term closed form, adaptive quadrature of Eq. 1c,
+                    additivity over 3x3 and 5x5 blocks of cells, far field
   fft, fft2         naive DFT, Parseval, inverse round trip
   conv_direct       delta response, translation invariance, symmetry,
                     positivity, quadrature-built Eq. 1c operator at small L
@@ -21,6 +23,7 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -32,6 +35,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
+_green_lock = threading.RLock()
 _lib = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -47,7 +51,7 @@ def build(force: bool = False) -> str:
         return _LIB
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lquadmath", "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -60,6 +64,9 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.orc_G.restype = ctypes.c_double
             lib.orc_G.argtypes = [ctypes.c_long, ctypes.c_long]
+            lib.orc_G_cell.restype = ctypes.c_double
+            lib.orc_G_cell.argtypes = [ctypes.c_long, ctypes.c_long]
+            lib.orc_set_green.argtypes = [ctypes.c_int, ctypes.c_long]
             lib.orc_padded_side.argtypes = [ctypes.c_int]
             lib.orc_kernel_table.argtypes = [ctypes.c_int, _dp]
             lib.orc_conv_direct_at.restype = ctypes.c_double
@@ -112,6 +119,28 @@ def _check(rc, what):
 def G(dx: int, dy: int) -> float:
     """Green's function of Eq. 1c (a = 1, (1-nu^2)/E = 1), point form + exact self term."""
     return _load().orc_G(int(dx), int(dy))
+
+
+GREEN_POINT, GREEN_CELL = 0, 1
+
+
+def G_cell(dx: int, dy: int) -> float:
+    """The cell integral of Eq. 1c itself for offset (dx, dy) (closed-form
+    antiderivative at the cell corners, quad precision)."""
+    return _load().orc_G_cell(int(dx), int(dy))
+
+
+@contextlib.contextmanager
+def use_green(kind: int, L: int = 1):
+    """Make the oracle calls inside use GREEN_POINT (the default) or
+    GREEN_CELL (Eq. 1c's cell integral, tabulated for offsets below L)."""
+    lib = _load()
+    with _green_lock:
+        _check(lib.orc_set_green(int(kind), int(max(L, 1))), "set_green")
+        try:
+            yield
+        finally:
+            lib.orc_set_green(GREEN_POINT, 1)
 
 
 def padded_side(L: int) -> int:

@@ -27,6 +27,8 @@ FC_ECUDA = -7
 FC_ENOTFOUND = -8
 FC_F32 = 1
 FC_F64 = 2
+FC_GREEN_POINT = 0
+FC_GREEN_CELL = 1
 FC_MODE_F64 = 0
 FC_MODE_MIXED = 1
 
@@ -86,6 +88,7 @@ def _load():
     lib.fc_version.restype = ctypes.c_char_p
     lib.fc_last_error.restype = ctypes.c_char_p
     lib.fftconv_plan_create.argtypes = [ctypes.POINTER(vp), i, i, ctypes.POINTER(cg_tune)]
+    lib.fftconv_plan_create_green.argtypes = [ctypes.POINTER(vp), i, i, i, ctypes.POINTER(cg_tune)]
     ip3 = ctypes.c_int * 3
     lib.fftconv_plan_shapes.argtypes = [vp, i, ip3, ip3, ip3, ip3]
     ipt = ctypes.POINTER(ctypes.c_int)
@@ -166,10 +169,11 @@ class Plan:
 
 
 def fftconv_plan_create(L: int, prec: int = FC_F32 | FC_F64, shapes=None, no_autotune: bool = False,
-                        persistent=None) -> Plan:
+                        persistent=None, green: int = None) -> Plan:
     """shapes: optional (pass A, pass B, pass C) compiled-shape indices (0-based)
     to force instead of the tuned choice; persistent: index of the persistent
-    inner-CG kernel to force, or -1 for the per-pass graph loop."""
+    inner-CG kernel to force, or -1 for the per-pass graph loop; green:
+    FC_GREEN_POINT (default) or FC_GREEN_CELL, the Green's function of Eq. 1c."""
     h = ctypes.c_void_p()
     tune = None
     if shapes is not None or no_autotune or persistent is not None:
@@ -179,11 +183,21 @@ def fftconv_plan_create(L: int, prec: int = FC_F32 | FC_F64, shapes=None, no_aut
         tune.no_autotune = int(bool(no_autotune))
         if persistent is not None:
             tune.shape_pers = -1 if persistent < 0 else int(persistent) + 1
-    rc = _lib.fftconv_plan_create(ctypes.byref(h), int(L), int(prec),
-                                  ctypes.byref(tune) if tune is not None else None)
+    if green is None:
+        rc = _lib.fftconv_plan_create(ctypes.byref(h), int(L), int(prec),
+                                      ctypes.byref(tune) if tune is not None else None)
+    else:
+        rc = _lib.fftconv_plan_create_green(ctypes.byref(h), int(L), int(prec), int(green),
+                                            ctypes.byref(tune) if tune is not None else None)
     if rc != FC_OK:
         raise FcError(rc, "fftconv_plan_create")
     return Plan(h, int(L), int(prec))
+
+
+def fftconv_plan_create_green(L: int, prec: int = FC_F32 | FC_F64, green: int = FC_GREEN_POINT,
+                              **kw) -> Plan:
+    """fftconv_plan_create with the Green's function of Eq. 1c chosen."""
+    return fftconv_plan_create(L, prec, green=green, **kw)
 
 
 def fftconv_plan_destroy(plan: Plan) -> None:

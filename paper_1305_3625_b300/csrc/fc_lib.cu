@@ -68,16 +68,66 @@ __device__ double green(long dx, long dy) {
     return 1.0 / (3.14159265358979323846 * sqrt((double)(dx * dx + dy * dy)));
 }
 
+// Gauss-Legendre rules on [-1, 1] with 16, 8 and 4 nodes (nodes and weights
+// from the host, see gauss_legendre).
+struct GaussLeg {
+    double x16[16], w16[16], x8[8], w8[8], x4[4], w4[4];
+};
+
+// (1/pi) times the integral of 1/r over the unit cell centred at (cx, cy) by
+// the N-point tensor rule (the cell's half width 1/2 is the Jacobian of each
+// coordinate).
+template <int N>
+__device__ double cell_quadrature(double cx, double cy, const double* xs, const double* ws) {
+    double acc = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double x = cx + 0.5 * xs[i];
+        double row = 0.0;
+        for (int j = 0; j < N; ++j) {
+            const double y = cy + 0.5 * xs[j];
+            row += ws[j] * rsqrt(x * x + y * y);
+        }
+        acc += ws[i] * row;
+    }
+    return 0.25 * acc / 3.14159265358979323846;
+}
+
+// Eq. 1c's cell integral for every offset (a = 1, (1-nu^2)/E = 1): the closed
+// form at r = 0, else Gauss-Legendre quadrature of the (then smooth)
+// integrand.  The rule's error falls like rho^(-2n), rho ~ 4 max(|dx|, |dy|)
+// the Bernstein-ellipse parameter of the nearest singularity (the origin), so
+// 16 nodes for the cells next to the origin, 8 up to a distance of 31 and 4
+// beyond keep it below 1e-17 relative.
+__device__ double green_cell(long dx, long dy, const GaussLeg& gl) {
+    if (dx == 0 && dy == 0) return green(0, 0);
+    const long ax = dx < 0 ? -dx : dx, ay = dy < 0 ? -dy : dy;
+    const long m = ax > ay ? ax : ay;
+    if (m <= 2) return cell_quadrature<16>((double)ax, (double)ay, gl.x16, gl.w16);
+    if (m <= 31) return cell_quadrature<8>((double)ax, (double)ay, gl.x8, gl.w8);
+    return cell_quadrature<4>((double)ax, (double)ay, gl.x4, gl.w4);
+}
+
+// The Green's function on the non-negative site offsets, gt[dy * L + dx] =
+// G(dx, dy) for dx, dy < L: the point form with exact self term
+// (FC_GREEN_POINT) or the cell integral (FC_GREEN_CELL).
+__global__ void k_green_table(int L, int kind, GaussLeg gl, double* gt) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)L * L) return;
+    const long dx = (long)(idx % L), dy = (long)(idx / L);
+    gt[idx] = kind == FC_GREEN_CELL ? green_cell(dx, dy, gl) : green(dx, dy);
+}
+
 // Circulant embedding on the M x M grid: index j < L is offset j, index
 // j > M - L is offset j - M; indices in between are reached by no pair of
-// sites and hold 0.
-__global__ void k_kernel_table(int L, int M, cpx<double>* K) {
+// sites and hold 0.  Values from the offset table gt (G is even in each
+// coordinate).
+__global__ void k_kernel_table(int L, int M, const double* gt, cpx<double>* K) {
     size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)M * M) return;
     int jy = (int)(idx / M), jx = (int)(idx % M);
     bool okx = jx < L || jx > M - L, oky = jy < L || jy > M - L;
-    long dx = jx < L ? jx : (long)jx - M, dy = jy < L ? jy : (long)jy - M;
-    K[idx] = cpx<double>{(okx && oky) ? green(dx, dy) : 0.0, 0.0};
+    int ax = jx < L ? jx : M - jx, ay = jy < L ? jy : M - jy;
+    K[idx] = cpx<double>{(okx && oky) ? gt[(size_t)ay * L + ax] : 0.0, 0.0};
 }
 
 // Unpruned forward FFT of every row of an M x M grid (spectrum set-up only).
@@ -201,14 +251,6 @@ __global__ void k_fill(long N, T* a, T v) {
 
 __global__ void k_fill_u8(long N, uint8_t* m, uint8_t v) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) m[i] = v;
-}
-
-// Green's function on the non-negative site offsets: gt[dy * L + dx] =
-// G(dx, dy), dx, dy < L (the values the kernel table embeds).
-__global__ void k_green_table(int L, double* gt) {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (size_t)L * L) return;
-    gt[idx] = green((long)(idx % L), (long)(idx / L));
 }
 
 // ------------------------------------------- warm-start residual update --
@@ -590,6 +632,7 @@ struct PrecRes {
 
 struct fftconv_plan {
     int L = 0, M = 0, prec = 0, dev = 0;
+    int green = FC_GREEN_POINT;  // Green's function of Eq. 1c: point form or cell integral
     long N = 0;
     size_t bytes = 0;
     PrecRes p32, p64;
@@ -951,14 +994,57 @@ int choose_persistent(fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp, T* cq, T
                       bool verbose);
 }  // namespace
 
+namespace {
+
+// Nodes and weights of the n-point Gauss-Legendre rule on [-1, 1]: the roots
+// of the Legendre polynomial P_n by Newton's method from the asymptotic
+// guess cos(pi (i - 1/4) / (n + 1/2)), P_n and P_n' from the three-term
+// recurrence, weights 2 / ((1 - x^2) P_n'(x)^2); in long double.
+void gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        long double t = cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (n + 0.5L));
+        long double dp = 1.0L;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1.0L, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const long double pk = ((2 * k - 1) * t * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = pk;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0L);
+            const long double step = p1 / dp;
+            t -= step;
+            if (fabsl(step) < 1e-19L) break;
+        }
+        x[i] = (double)t;
+        w[i] = (double)(2.0L / ((1.0L - t * t) * dp * dp));
+    }
+}
+
+GaussLeg make_gauss_legendre() {
+    GaussLeg g;
+    gauss_legendre(16, g.x16, g.w16);
+    gauss_legendre(8, g.x8, g.w8);
+    gauss_legendre(4, g.x4, g.w4);
+    return g;
+}
+
+}  // namespace
+
 extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg_tune* tune) {
+    return fftconv_plan_create_green(out, L, prec, FC_GREEN_POINT, tune);
+}
+
+extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, int green_kind, const cg_tune* tune) {
     if (!out) return FC_EINVAL;
     *out = nullptr;
     if (L < 1 || L > 4096 || prec < 1 || prec > 3) return FC_EINVAL;
+    if (green_kind != FC_GREEN_POINT && green_kind != FC_GREEN_CELL) return FC_EINVAL;
     fftconv_plan* p = new (std::nothrow) fftconv_plan();
     if (!p) return FC_ENOMEM;
     p->L = L;
     p->prec = prec;
+    p->green = green_kind;
     p->M = 2;
     while (p->M < 2 * L) p->M *= 2;
     p->N = (long)L * L;
@@ -968,6 +1054,7 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
     int rc = FC_OK;
     cpx<double>* K = nullptr;
     double* maxes = nullptr;
+    double* gt_tmp = nullptr;  // offset table of an FP32-only plan (kept as gtab otherwise)
     double hmax[2] = {0, 0};
     cudaStream_t cs = nullptr;  // set-up work stays off other streams (no device-wide syncs)
     cudaError_t e;
@@ -1016,9 +1103,19 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         rc = FC_EINVAL;
         goto fail;
     }
+    // Green's function on the site offsets (kept for the warm-start residual
+    // update of FP64 plans), then its circulant embedding
+    if (prec & FC_F64) {
+        FC_TRY(dalloc(p, (void**)&p->gtab, sizeof(double) * N));
+    } else {
+        FC_TRYC(cudaMallocAsync((void**)&gt_tmp, sizeof(double) * N, cs));
+    }
     {
+        double* gt = (prec & FC_F64) ? p->gtab : gt_tmp;
+        k_green_table<<<(unsigned)((N + 255) / 256), 256, 0, cs>>>(L, p->green, make_gauss_legendre(), gt);
+        FC_TRYC(cudaGetLastError());
         size_t MM = (size_t)M * M;
-        k_kernel_table<<<(unsigned)((MM + 255) / 256), 256, 0, cs>>>(L, M, K);
+        k_kernel_table<<<(unsigned)((MM + 255) / 256), 256, 0, cs>>>(L, M, gt, K);
         FC_TRYC(cudaGetLastError());
         const KV& kr = p->p64.v.rows_full;
         const KV& kc = p->p64.v.cols_full;
@@ -1035,6 +1132,10 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
     }
     FC_TRYC(cudaFreeAsync(K, cs));
     K = nullptr;
+    if (gt_tmp) {
+        FC_TRYC(cudaFreeAsync(gt_tmp, cs));
+        gt_tmp = nullptr;
+    }
     FC_TRYC(cudaFreeAsync(maxes, cs));
     maxes = nullptr;
     FC_TRYC(cudaStreamSynchronize(cs));
@@ -1056,11 +1157,8 @@ extern "C" int fftconv_plan_create(fftconv_plan** out, int L, int prec, const cg
         FC_TRY(dalloc(p, (void**)&p->mask, N));
         FC_TRY(dalloc(p, (void**)&p->z64, sizeof(double) * N));
         FC_TRY(dalloc(p, (void**)&p->pq64, sizeof(double) * (size_t)Q * Q));
-        FC_TRY(dalloc(p, (void**)&p->gtab, sizeof(double) * N));
         FC_TRY(dalloc(p, (void**)&p->widx, sizeof(long long) * kWarmMax));
         FC_TRY(dalloc(p, (void**)&p->wdx, sizeof(double) * kWarmMax));
-        k_green_table<<<(unsigned)((N + 255) / 256), 256, 0, cs>>>(L, p->gtab);
-        FC_TRYC(cudaGetLastError());
         if (p->p32.on) {
             FC_TRY(dalloc(p, (void**)&p->z32, sizeof(float) * N));
             FC_TRY(dalloc(p, (void**)&p->pq32, sizeof(float) * (size_t)Q * Q));
@@ -1122,6 +1220,7 @@ fail:
     if (cs) {
         if (K) cudaFreeAsync(K, cs);
         if (maxes) cudaFreeAsync(maxes, cs);
+        if (gt_tmp) cudaFreeAsync(gt_tmp, cs);
         cudaStreamSynchronize(cs);
         cudaStreamDestroy(cs);
     }
