@@ -41,6 +41,7 @@ import numpy as np  # noqa: E402
 
 L_BENCH = 1024
 RTOL = 1e-10
+FRAC_GRADIENT = 2.0  # thresholds xi + 2 (iy + 1/2)/L in the fracture-run section
 METRIC = "CG matvec GB/s vs HBM peak; solves/sec + p50/p99 latency, mixed vs FP64 plain"
 WORKLOAD = ("quasi-static breaking loop, L=1024 (padded 2048^2 FFT): warm-started (preconditioned) CG to "
             "rtol 1e-10 + argmax |x|/t removal per step; s~U[0.5,1.5] seed 0, b=1, t~U(0,1)")
@@ -424,6 +425,35 @@ def run_ours(args, world, rank, local, pg):
                     cap / serving["f64_one_at_a_time"]["solves_per_s"], 2)
         sv.close()
 
+    # a fracture run under a threshold gradient (fc_fracture_run): the
+    # breaking loop driven inside the library, front read out at the end
+    frac = None
+    if args.frac_steps > 0:
+        pg_ = fc_inputs.problem(L, seed=rank, with_t=True, t_gradient=FRAC_GRADIENT)
+        fs, fb, ft = (torch.tensor(pg_[k], device=dev) for k in ("s", "b", "t"))
+        fmask = torch.ones(N, device=dev, dtype=torch.uint8)
+        fx = torch.zeros(N, device=dev, dtype=torch.float64)
+        frem = torch.empty(args.frac_steps, device=dev, dtype=torch.int64)
+        frat = torch.empty(args.frac_steps, device=dev, dtype=torch.float64)
+        fr = fc.fc_fracture_run(plan, fs, fb, ft, fmask, fx, args.frac_steps, frem, frat, rtol=RTOL,
+                                mode=fc.FC_MODE_MIXED, precond=True)
+        fi = torch.empty(L, device=dev, dtype=torch.int32)
+        de = torch.empty(L, device=dev, dtype=torch.int32)
+        fc.fc_front(plan, fmask, fi, de)
+        torch.cuda.synchronize()
+        rows = (frem[:fr["steps_done"]] // L).float()
+        frac = {"L": L, "t_gradient": FRAC_GRADIENT, "steps": fr["steps_done"], "status": fr["status"],
+                "steps_per_s": round(fr["steps_done"] / fr["seconds"], 2),
+                "iters_per_step": round(fr["iters"] / max(fr["steps_done"], 1), 2),
+                "fp64_products_per_step": round(fr["fp64_products"] / max(fr["steps_done"], 1), 2),
+                "mean_broken_row": round(float(rows.mean()), 2) if fr["steps_done"] else None,
+                "front_first_intact_mean": round(float(fi.float().mean()), 3),
+                "front_damage_end_mean": round(float(de.float().mean()), 3),
+                "load_1_over_ratio_first_last": [round(1.0 / float(frat[0]), 6),
+                                                 round(1.0 / float(frat[fr["steps_done"] - 1]), 6)]
+                if fr["steps_done"] else None}
+        del fs, fb, ft, fmask, fx
+
     # aggregate over ranks: units summed, slowest rank's time
     value, tot_ms, _ = aggregate_rate(args.steps, sum(ms_mixed), pg, dev)
 
@@ -493,6 +523,7 @@ def run_ours(args, world, rank, local, pg):
                                         f"({cpu_s:.1f} s), scaled by the FP64 path's "
                                         f"{statistics.mean(iters64):.1f} iterations per solve")},
             "e2e": e2e,
+            "fracture_run": frac,
             "gpu_launches": sum(launches(r, fc.FC_MODE_MIXED) for r in res_mixed),
             "clocks": clk,
             "wall_s_timed_region": round(wall_mixed, 3),
@@ -542,6 +573,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5, dest="e2e_steps")
     ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget")
     ap.add_argument("--big", type=int, default=1)
+    ap.add_argument("--frac-steps", type=int, default=100, dest="frac_steps")
     ap.add_argument("--batch-solves", type=int, default=256, dest="batch_solves")
     ap.add_argument("--serve-requests", type=int, default=600, dest="serve_requests")
     ap.add_argument("--serve-f64", type=int, default=160, dest="serve_f64",

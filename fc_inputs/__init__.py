@@ -75,12 +75,16 @@ def padded_side(L: int) -> int:
 
 
 def problem(L: int, seed: int, b_kind: str = "ones", with_t: bool = False,
-            s_lo: float = 0.5, s_hi: float = 1.5) -> dict:
+            s_lo: float = 0.5, s_hi: float = 1.5, t_gradient: float = 0.0) -> dict:
     """One synthetic system (C + diag(s)) x = b on an L x L grid.
 
     s ~ U[s_lo, s_hi] (the fibres' compliances), b = 1 (uniform plate
     displacement) or b ~ N(0, 1), and optionally breaking thresholds
-    t ~ U(0, 1).  All arrays are float64 of length L*L, row-major.
+    t = xi + t_gradient (iy + 1/2) / L with xi ~ U(0, 1): a threshold
+    gradient along y directs the fracture front (Section 2 of the paper
+    names a gradient in the threshold distribution as the simplest way to
+    load the system with one).  All arrays are float64 of length L*L,
+    row-major.
     """
     n = L * L
     pos = 0
@@ -95,8 +99,11 @@ def problem(L: int, seed: int, b_kind: str = "ones", with_t: bool = False,
         raise ValueError(f"unknown b_kind {b_kind!r}")
     out = {"L": L, "seed": seed, "s": s, "b": b}
     if with_t:
-        out["t"] = uniform(seed, pos, n)
+        t = uniform(seed, pos, n)
         pos += n
+        if t_gradient:
+            t = t + t_gradient * (np.arange(n) // L + 0.5) / L
+        out["t"] = t
     return out
 
 

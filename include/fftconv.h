@@ -106,6 +106,15 @@ typedef struct cg_opts {
                           certifies convergence is always a full FP64 product. */
 } cg_opts;
 
+typedef struct fc_run_result {
+    int status;            /* FC_OK, or the status of the solve that stopped the run */
+    int steps_done;        /* fibres removed                                     */
+    long long iters;       /* CG iterations over all solves                      */
+    int fp64_products;     /* FP64 true-residual products over all solves        */
+    int resid_updated;     /* solves whose first residual was updated            */
+    double seconds;        /* wall time of the run                               */
+} fc_run_result;
+
 typedef struct cg_result {
     int status;            /* FC_OK, FC_ENOCONV or FC_ENANINF                    */
     int iters;             /* CG iterations (products in the inner loops)        */
@@ -223,6 +232,42 @@ int cg_solve(fftconv_plan *p, const double *s, const double *b, double *x, const
  */
 int fc_masked_step(fftconv_plan *p, const double *t, uint8_t *mask, double *x, int64_t *removed,
                    fc_stream_t stream);
+
+/*
+ * fc_front -- front readout of a breaking run (Section 2: the front between
+ * wholly broken and wholly intact material, driven across the grid by a
+ * threshold gradient along y).  For every column ix of the L x L grid:
+ *   first_intact[ix]  smallest iy with mask = 1 (L if the column is broken
+ *                     through): the edge of the wholly broken region;
+ *   damage_end[ix]    1 + largest iy with mask = 0 (0 if intact): the edge of
+ *                     the wholly intact region.
+ *   mask          device, L*L bytes (1 = intact).
+ *   first_intact, damage_end  device, L int32 each.
+ * Asynchronous.  Errors: FC_EINVAL, FC_ECUDA.
+ */
+int fc_front(fftconv_plan *p, const uint8_t *mask, int32_t *first_intact, int32_t *damage_end,
+             fc_stream_t stream);
+
+/*
+ * fc_fracture_run -- `steps` quasi-static breaking steps (Section 2): solve
+ * (cg_solve with o, warm-started from x; the first residual of every solve
+ * after the first is the updated one), then remove the fibre with the
+ * largest |x|/t (fc_masked_step).  Stops early when no active fibre is left
+ * or a solve does not converge.
+ *   s, b, t   device, L*L doubles; t the thresholds (any gradient is in t).
+ *   mask, x   device, updated in place (intact set and last solution).
+ *   removed   device, steps int64: index removed at each step (-1: none).
+ *   ratio     device, steps doubles, or NULL: max |x|/t at each step, i.e.
+ *             the inverse of the load D at which that fibre breaks (x is
+ *             linear in D).
+ *   res       host, may be NULL: totals of the run.
+ * Blocks until the run ends (one host synchronisation per step).  Returns
+ * res->status.  Errors: FC_EINVAL, FC_ECUDA, FC_ENOMEM; FC_ENOCONV /
+ * FC_ENANINF from a solve.
+ */
+int fc_fracture_run(fftconv_plan *p, const double *s, const double *b, const double *t, uint8_t *mask,
+                    double *x, int steps, const cg_opts *o, int64_t *removed, double *ratio,
+                    fc_run_result *res, fc_stream_t stream);
 
 /*
  * fc_masked_step_static -- the same breaking step as fc_masked_step, for

@@ -20,6 +20,7 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
   cg                L = 1 closed form, dense Cholesky and LAPACK solves
   cholesky_solve    LAPACK solve (library routine) on random SPD matrices
   masked_loop       brute force with dense re-solves, L <= 6
+  front             brute force over every column of small masks
 """
 from __future__ import annotations
 
@@ -83,6 +84,7 @@ def _load():
             lib.orc_cholesky_solve.argtypes = [ctypes.c_int, _dp, _dp, _dp]
             lib.orc_argmax_ratio.restype = ctypes.c_long
             lib.orc_argmax_ratio.argtypes = [ctypes.c_long, _dp, _dp, _ucp, _dp]
+            lib.orc_front.argtypes = [ctypes.c_int, _ucp, _ip, _ip]
             lib.orc_masked_loop.argtypes = [ctypes.c_int, _dp, _dp, _dp, _ucp, _dp,
                                             ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                             _lp, _dp, _ip]
@@ -266,3 +268,15 @@ def masked_loop(L: int, s, b, t, steps: int, x0=None, mask=None, rtol: float = 1
                                    picks.ctypes.data_as(_lp), _d(ratios),
                                    iters.ctypes.data_as(_ip)), "masked_loop")
     return {"x": x, "mask": m, "picks": picks, "ratios": ratios, "iters": iters}
+
+
+def front(L: int, mask):
+    """(first_intact, damage_end) per column of the L x L mask."""
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    if m.size != L * L:
+        raise ValueError("mask size")
+    fi = np.empty(L, dtype=np.int32)
+    de = np.empty(L, dtype=np.int32)
+    _check(_load().orc_front(L, m.ctypes.data_as(_ucp), fi.ctypes.data_as(_ip), de.ctypes.data_as(_ip)),
+           "front")
+    return fi, de

@@ -610,6 +610,29 @@ long orc_argmax_ratio(long N, const double *x, const double *t, const unsigned c
  * i* = argmax |x_i|/t_i, record it, set mask[i*] = 0 and x[i*] = 0.
  * picks, ratios and iters receive one entry per step.  mask and x are
  * updated in place. */
+/* Front of a breaking run (Section 2: the front separates wholly broken from
+ * wholly intact material).  Per column ix: first_intact = smallest iy with
+ * mask 1 (L if none), damage_end = 1 + largest iy with mask 0 (0 if none). */
+int orc_front(int L, const unsigned char *mask, int *first_intact, int *damage_end)
+{
+    if (L < 1 || !mask || !first_intact || !damage_end)
+        return -1;
+    for (int ix = 0; ix < L; ++ix) {
+        int fi = L, de = 0;
+        for (int iy = 0; iy < L; ++iy) {
+            if (mask[(size_t)iy * L + ix]) {
+                if (fi == L)
+                    fi = iy;
+            } else {
+                de = iy + 1;
+            }
+        }
+        first_intact[ix] = fi;
+        damage_end[ix] = de;
+    }
+    return 0;
+}
+
 int orc_masked_loop(int L, const double *s, const double *b, const double *t, unsigned char *mask,
                     double *x, int steps, double rtol, int maxit, long *picks, double *ratios,
                     int *iters)

@@ -70,6 +70,14 @@ class cg_result(ctypes.Structure):
                 "latency_s": self.latency_s, "run_s": self.run_s}
 
 
+class fc_run_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("iters", ctypes.c_longlong),
+                ("fp64_products", ctypes.c_int), ("resid_updated", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class cg_request(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("s", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
@@ -100,6 +108,9 @@ def _load():
     lib.fftconv_apply_prec.argtypes = [vp, i, vp, vp, vp]
     lib.cg_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
     lib.fc_masked_step.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.fc_front.argtypes = [vp, vp, vp, vp, vp]
+    lib.fc_fracture_run.argtypes = [vp, vp, vp, vp, vp, vp, i, ctypes.POINTER(cg_opts), vp, vp,
+                                    ctypes.POINTER(fc_run_result), vp]
     lib.fc_masked_step_static.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp]
     lib.cg_server_create.argtypes = [ctypes.POINTER(vp), sz, i, vp]
     lib.cg_batch_submit.argtypes = [vp, ctypes.POINTER(cg_request), ctypes.POINTER(ctypes.c_uint64)]
@@ -248,6 +259,36 @@ def fc_masked_step(plan: Plan, t, mask, x, removed, stream=None) -> None:
                              _ptr(removed, torch.int64, 1, "removed"), _stream(stream))
     if rc != FC_OK:
         raise FcError(rc, "fc_masked_step")
+
+
+def fc_front(plan: Plan, mask, first_intact, damage_end, stream=None) -> None:
+    """Front readout per column (int32 tensors of L): first intact row and
+    one past the last broken row."""
+    L = plan.L
+    rc = _lib.fc_front(plan.handle, _ptr(mask, torch.uint8, L * L, "mask"),
+                       _ptr(first_intact, torch.int32, L, "first_intact"),
+                       _ptr(damage_end, torch.int32, L, "damage_end"), _stream(stream))
+    if rc != FC_OK:
+        raise FcError(rc, "fc_front")
+
+
+def fc_fracture_run(plan: Plan, s, b, t, mask, x, steps: int, removed, ratio=None, rtol: float = 1e-10,
+                    mode: int = FC_MODE_F64, precond: bool = False, inner_rtol: float = 0.0,
+                    max_iter: int = 0, warm_resid: bool = True, stream=None) -> dict:
+    """`steps` breaking steps (solve, remove argmax |x|/t); removed (int64,
+    steps) and ratio (float64, steps, optional) receive the per-step record."""
+    n = plan.L * plan.L
+    o = cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode), inner_rtol=float(inner_rtol),
+                precond=int(bool(precond)), warm_resid=0 if warm_resid else -1)
+    r = fc_run_result()
+    rc = _lib.fc_fracture_run(plan.handle, _ptr(s, torch.float64, n, "s"), _ptr(b, torch.float64, n, "b"),
+                              _ptr(t, torch.float64, n, "t"), _ptr(mask, torch.uint8, n, "mask"),
+                              _ptr(x, torch.float64, n, "x"), int(steps), ctypes.byref(o),
+                              _ptr(removed, torch.int64, int(steps), "removed"),
+                              _ptr(ratio, torch.float64, int(steps), "ratio"), ctypes.byref(r), _stream(stream))
+    if rc in (FC_EINVAL, FC_ECUDA, FC_ENOMEM):
+        raise FcError(rc, "fc_fracture_run")
+    return r.as_dict()
 
 
 def fftconv_plan_info(plan: Plan) -> dict:

@@ -379,8 +379,8 @@ __device__ __forceinline__ void am_block_reduce(double* sv, long long* si) {
 // its sites; the last block to finish reduces the per-block winners.  The
 // order is total, so the result does not depend on the reduction order.
 __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, uint8_t* mask, double* x,
-                                                       int64_t* removed, double* pv, long long* pi,
-                                                       ArgmaxCtl* ctl) {
+                                                       int64_t* removed, double* ratio, double* pv,
+                                                       long long* pi, ArgmaxCtl* ctl) {
     __shared__ double sv[256];
     __shared__ long long si[256];
     __shared__ bool is_last;
@@ -422,11 +422,46 @@ __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, 
     if (threadIdx.x == 0) {
         const long long gi = si[0];
         *removed = gi;
+        if (ratio) *ratio = sv[0];  // max |x|/t (-1 with no active site)
         if (gi >= 0) {
             mask[gi] = 0;
             x[gi] = 0.0;
         }
         ctl->cnt = 0u;
+    }
+}
+
+// Front readout of a breaking run (Section 2: the front separates wholly
+// broken from wholly intact material).  Column ix of the L x L grid:
+// first_intact = smallest iy with mask = 1 (L when broken through),
+// damage_end = 1 + largest iy with mask = 0 (0 when intact).  A block covers
+// 32 columns (one per lane, so each row read is 32 contiguous bytes) and its
+// 16 warps split the rows.
+__global__ void __launch_bounds__(512) k_front(int L, const uint8_t* mask, int32_t* first_intact,
+                                               int32_t* damage_end) {
+    __shared__ int s_first[16][32], s_end[16][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ix = blockIdx.x * 32 + lane;
+    int fi = L, de = 0;
+    if (ix < L) {
+        for (int iy = w; iy < L; iy += 16) {
+            if (mask[(size_t)iy * L + ix]) {
+                if (iy < fi) fi = iy;
+            } else {
+                de = iy + 1;
+            }
+        }
+    }
+    s_first[w][lane] = fi;
+    s_end[w][lane] = de;
+    __syncthreads();
+    if (w == 0 && ix < L) {
+        for (int k = 1; k < 16; ++k) {
+            fi = min(fi, s_first[k][lane]);
+            de = max(de, s_end[k][lane]);
+        }
+        first_intact[ix] = fi;
+        damage_end[ix] = de;
     }
 }
 
@@ -663,6 +698,7 @@ struct fftconv_plan {
     long long* widx = nullptr;
     double* wdx = nullptr;
     bool warm_ok = false;
+    int64_t* rm_host = nullptr;  // pinned: last removed index of a fracture run
 };
 
 namespace {
@@ -694,6 +730,7 @@ void plan_free(fftconv_plan* p) {
         if (p->p64.twst[i]) cudaFree(p->p64.twst[i]);
     }
     if (p->st_host) cudaFreeHost(p->st_host);
+    if (p->rm_host) cudaFreeHost(p->rm_host);
     delete p;
 }
 
@@ -1199,6 +1236,7 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
         p->p64.on = false;
     }
     FC_TRYC(cudaMallocHost(&p->st_host, sizeof(CgState)));
+    FC_TRYC(cudaMallocHost(&p->rm_host, sizeof(int64_t)));
     FC_TRYC(cudaStreamSynchronize(cs));
     if (prec & FC_F64) FC_TRY(autotune<double>(p, p->p64, tune));
     if (p->p32.on) FC_TRY(autotune<float>(p, p->p32, tune));
@@ -1934,10 +1972,50 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
 extern "C" int fc_masked_step(fftconv_plan* p, const double* t, uint8_t* mask, double* x, int64_t* removed,
                               fc_stream_t stream) {
     if (!p || !t || !mask || !x || !removed) return FC_EINVAL;
-    k_masked_argmax<<<p->am_grid, 256, 0, (cudaStream_t)stream>>>(p->N, t, mask, x, removed, p->am_v, p->am_i,
-                                                                   p->am_ctl);
+    k_masked_argmax<<<p->am_grid, 256, 0, (cudaStream_t)stream>>>(p->N, t, mask, x, removed, nullptr, p->am_v,
+                                                                   p->am_i, p->am_ctl);
     FC_CK(cudaGetLastError());
     return FC_OK;
+}
+
+extern "C" int fc_front(fftconv_plan* p, const uint8_t* mask, int32_t* first_intact, int32_t* damage_end,
+                        fc_stream_t stream) {
+    if (!p || !mask || !first_intact || !damage_end) return FC_EINVAL;
+    k_front<<<(p->L + 31) / 32, 512, 0, (cudaStream_t)stream>>>(p->L, mask, first_intact, damage_end);
+    FC_CK(cudaGetLastError());
+    return FC_OK;
+}
+
+extern "C" int fc_fracture_run(fftconv_plan* p, const double* s, const double* b, const double* t, uint8_t* mask,
+                               double* x, int steps, const cg_opts* o, int64_t* removed, double* ratio,
+                               fc_run_result* res, fc_stream_t stream) {
+    if (!p || !s || !b || !t || !mask || !x || !removed || steps < 0) return FC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    fc_run_result acc{};
+    acc.status = FC_OK;
+    for (int k = 0; k < steps; ++k) {
+        cg_result r{};
+        const int rc = cg_solve(p, s, b, x, mask, o, &r, stream);  // returns with the stream drained
+        if (rc == FC_EINVAL || rc == FC_ECUDA || rc == FC_ENOMEM) return rc;
+        acc.iters += r.iters;
+        acc.fp64_products += r.refinements - r.resid_updated;
+        acc.resid_updated += r.resid_updated;
+        if (rc != FC_OK) {
+            acc.status = rc;
+            break;
+        }
+        k_masked_argmax<<<p->am_grid, 256, 0, st>>>(p->N, t, mask, x, removed + k, ratio ? ratio + k : nullptr,
+                                                    p->am_v, p->am_i, p->am_ctl);
+        FC_CK(cudaGetLastError());
+        FC_CK(cudaMemcpyAsync(p->rm_host, removed + k, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        FC_CK(cudaStreamSynchronize(st));
+        if (*p->rm_host < 0) break;  // no active fibre left
+        acc.steps_done = k + 1;
+    }
+    acc.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res) *res = acc;
+    return acc.status;
 }
 
 // ------------------------------------------- allocation-free masked step --
@@ -1995,7 +2073,7 @@ extern "C" int fc_masked_step_static(int64_t N, const double* t, uint8_t* mask, 
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's contents: the counter must start at 0
     FC_CK(cudaMemsetAsync(ctl, 0, sizeof(ArgmaxCtl), s));
-    k_masked_argmax<<<grid, 256, 0, s>>>((long)N, t, mask, x, removed, pv, pi, ctl);
+    k_masked_argmax<<<grid, 256, 0, s>>>((long)N, t, mask, x, removed, nullptr, pv, pi, ctl);
     FC_CK(cudaGetLastError());
     return FC_OK;
 }

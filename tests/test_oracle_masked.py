@@ -35,3 +35,29 @@ def test_argmax_ties_to_lowest_index():
     assert k == 1 and r == 2.0
     k, _ = oracle.argmax_ratio(x, t, mask=np.array([1, 0, 1, 1], np.uint8))
     assert k == 2
+
+
+@pytest.mark.parametrize("L", [1, 2, 5, 9])
+def test_front_brute_force(L):
+    """Front readout against a direct scan of each column."""
+    rng = np.random.default_rng(L)
+    for dens in (0.0, 0.3, 0.7, 1.0):
+        m = (rng.random(L * L) >= dens).astype(np.uint8)
+        fi, de = oracle.front(L, m)
+        g = m.reshape(L, L)
+        for ix in range(L):
+            col = g[:, ix]
+            intact = np.flatnonzero(col == 1)
+            broken = np.flatnonzero(col == 0)
+            assert fi[ix] == (intact[0] if intact.size else L)
+            assert de[ix] == (broken[-1] + 1 if broken.size else 0)
+
+
+def test_threshold_gradient_inputs():
+    """t = xi + g (iy + 1/2)/L with the same xi as the gradient-free draw."""
+    L, g = 8, 3.0
+    a = fc_inputs.problem(L, seed=4, with_t=True)
+    b = fc_inputs.problem(L, seed=4, with_t=True, t_gradient=g)
+    iy = np.arange(L * L) // L
+    assert np.allclose(b["t"] - a["t"], g * (iy + 0.5) / L, rtol=0, atol=1e-15)
+    assert np.array_equal(a["s"], b["s"])
