@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libfftconv.so")
 SOURCES = ["fc_lib.cu", "fc_server.cu"]
-HEADERS = ["fc_fft.cuh", "fc_passes.cuh", "fc_internal.h", "fc_persist.cuh"]
+HEADERS = ["fc_fft.cuh", "fc_passes.cuh", "fc_internal.h", "fc_persist.cuh", "fc_tma.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
 

@@ -45,6 +45,8 @@ struct CgState {
     int warm_used;       // 1: this solve's first true residual was updated, not recomputed
     int wbad;            // the update does not apply (s or b changed, active set grew)
     unsigned wcount;     // entries of x that changed (the list holds the first kWarmMax)
+    int tma_err;         // 1: a staged TMA copy never arrived (the solve ends with FC_ETIMEOUT)
+    int pad_;
     unsigned cntA, cntC;  // last-block counters of passes A and C
 };
 
@@ -126,6 +128,7 @@ __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq
     st->iter += 1;
     st->cycle_iter += 1;
     if (d == 0 && (st->iter >= st->max_iter || st->cycle_iter >= st->cycle_max)) d = 2;
+    if (st->tma_err) d = 4;  // a staged copy never arrived: end the inner run
     st->alpha = alpha;
     st->beta = rr > 0.0 ? rrn / rr : 0.0;
     st->first = 0;
@@ -149,8 +152,8 @@ __device__ __forceinline__ void refine_decide(CgState* st, double rr64, double b
     st->bb = bb;
     st->cycles += 1;
     int go = 0;
-    if (st->inner_done == 4) {
-        st->status = FC_ETIMEOUT;  // the persistent inner loop's grid barrier ran out
+    if (st->inner_done == 4 || st->tma_err) {
+        st->status = FC_ETIMEOUT;  // a grid barrier or a staged copy wait ran out
     } else if (!isfinite(rr64) || !isfinite(bb)) {
         st->status = FC_ENANINF;
     } else if (bb == 0.0 || rr64 <= st->rtol2 * bb) {

@@ -19,6 +19,7 @@
 #include <new>
 
 #include "fc_persist.cuh"
+#include "fc_tma.cuh"
 
 using namespace fc;
 
@@ -473,6 +474,7 @@ struct KV {
     const void* f = nullptr;
     int threads = 0, per = 0, E = 0;
     size_t smem = 0;
+    int tma = 0;  // 1: TMA-staged persistent pass C (k_rinv_tma; needs the plan's tensor map)
 };
 
 // One compiled persistent inner-CG kernel: pass A/C shape (EA, RB) and
@@ -484,7 +486,8 @@ struct KVP {
 };
 
 struct Variants {
-    KV rfwd[8], colc[8], rinv[8];
+    static constexpr int kMax = 12;  // compiled shapes per pass and size (at most)
+    KV rfwd[kMax], colc[kMax], rinv[kMax];
     int n_rfwd = 0, n_colc = 0, n_rinv = 0;
     KVP pers[6];
     int n_pers = 0;
@@ -500,8 +503,17 @@ void add_row(Variants& v) {
         KV i{(const void*)k_rinv<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
         for (int k = 0; k < v.n_rfwd; ++k)
             if (v.rfwd[k].f == f.f) return;
+        if (v.n_rfwd >= Variants::kMax || v.n_rinv >= Variants::kMax) return;
         v.rfwd[v.n_rfwd++] = f;
         v.rinv[v.n_rinv++] = i;
+    }
+}
+
+// TMA-staged pass C (FP32): one row pair per loop iteration, M/16 threads.
+template <int M>
+void add_rinv_tma(Variants& v) {
+    if constexpr (M >= 256 && tma_smem_bytes(M) <= 200 * 1024) {
+        if (v.n_rinv < Variants::kMax) v.rinv[v.n_rinv++] = KV{(const void*)k_rinv_tma<M, 16>, M / 16, 1, 16, tma_smem_bytes(M), 1};
     }
 }
 
@@ -511,7 +523,7 @@ void add_col(Variants& v) {
         KV c{(const void*)k_colc<T, M, E, CB, MINB, DB>, CB * (M / E), CB, E, pass_smem<T, M, CB, DB>()};
         for (int k = 0; k < v.n_colc; ++k)
             if (v.colc[k].f == c.f) return;
-        v.colc[v.n_colc++] = c;
+        if (v.n_colc < Variants::kMax) v.colc[v.n_colc++] = c;
     }
 }
 
@@ -562,6 +574,10 @@ void make_variants(Variants& v) {
             add_col<T, M, 16, C2, clampi(65536 / (C2 * G16 * 64), 1, 16), false>(v);
             add_row<T, M, 16, R1, clampi(65536 / (R1 * G16 * 64), 1, 16), false>(v);
             add_row<T, M, 16, R2, clampi(65536 / (R2 * G16 * 64), 1, 16), false>(v);
+            // 1024-thread row blocks: more rows per block make the column-major
+            // intermediate's row segments longer (full 32-byte sectors at M = 8192)
+            add_row<T, M, 16, clampi(1024 / G16, 1, 64), 1, false>(v);
+            add_rinv_tma<M>(v);
         }
         add_pers<T, M, 16, 16, (M * M / 32 < 256 ? M * M / 32 : 256)>(v);
         add_pers<T, M, 16, 8, 256>(v);
@@ -648,6 +664,9 @@ struct PrecRes {
     void* tw = nullptr;      // FP64 only: base table exp(-2 pi i m/M), m < M
     void* twst[5] = {};      // stage twiddle tables for E = 2, 4, 8, 16 (index log2 E)
     void* Gq = nullptr;      // T[(M/2+1)^2]
+    CUtensorMap zmap;        // FP32: Zt as floats [M/2][2L] for the TMA pass C
+    bool tma_ok = false;     // zmap encoded (L even, M >= 256)
+    int tma_grid = 0;        // resident blocks of the TMA pass C (its persistent grid)
     const KV& rfwd() const { return v.rfwd[sel[0]]; }
     const KV& colc() const { return v.colc[sel[1]]; }
     const KV& rinv() const { return v.rinv[sel[2]]; }
@@ -774,6 +793,32 @@ int launch_dep(const void* f, int grid, int threads, size_t smem, cudaStream_t s
 
 int row_grid(const fftconv_plan* p, const KV& k) { return ((p->L + 1) / 2 + k.per - 1) / k.per; }
 int col_grid(const fftconv_plan* p, const KV& k) { return (p->M / 2) / k.per; }
+
+// Arguments of the TMA-staged pass C for the FP32 intermediate of a plan.
+RowInvTma tma_args(const fftconv_plan* p, const PrecRes& R, const RowInvArgs<float>& c) {
+    RowInvTma P;
+    memset(&P, 0, sizeof(P));
+    P.map = R.zmap;
+    P.a = c;
+    P.units = (p->L + 1) / 2;
+    return P;
+}
+
+// Pass C on a stream in the shape k (dep: as a programmatic dependent of the
+// previous pass).
+template <typename T>
+int launch_rinv(fftconv_plan* p, PrecRes& R, const KV& k, RowInvArgs<T>& c, cudaStream_t s, bool dep) {
+    if constexpr (sizeof(T) == 4) {
+        if (k.tma) {
+            if (!R.tma_ok) return FC_EINVAL;
+            RowInvTma P = tma_args(p, R, c);
+            return dep ? launch_dep(k.f, R.tma_grid, k.threads, k.smem, s, P)
+                       : launch(k.f, R.tma_grid, k.threads, k.smem, s, P);
+        }
+    }
+    return dep ? launch_dep(k.f, row_grid(p, k), k.threads, k.smem, s, c)
+               : launch(k.f, row_grid(p, k), k.threads, k.smem, s, c);
+}
 
 // Stage twiddle tables for every value-per-thread count E that a compiled
 // shape of this precision uses.
@@ -926,13 +971,18 @@ int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStr
     c.L = p->L;
     c.mode = RI_PLAIN;
     c.y = y;
+    c.st = p->st;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = tw;
+    if (kv.tma && !R.tma_ok) {  // no tensor map for this size: never chosen
+        *ms = 1e30f;
+        return FC_OK;
+    }
     const int grid = kind == 1 ? col_grid(p, kv) : row_grid(p, kv);
     auto go = [&]() -> int {
         if (kind == 0) return launch(kv.f, grid, kv.threads, kv.smem, s, a);
         if (kind == 1) return launch(kv.f, grid, kv.threads, kv.smem, s, b);
-        return launch(kv.f, grid, kv.threads, kv.smem, s, c);
+        return launch_rinv<T>(p, R, kv, c, s, false);
     };
     int rc = FC_OK;
     for (int w = 0; w < 2 && !rc; ++w) rc = go();
@@ -961,6 +1011,7 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     for (int kind = 0; kind < 3; ++kind) {
         if (forced[kind] > 0) {
             if (forced[kind] > n[kind]) return FC_EINVAL;
+            if (kind == 2 && R.v.rinv[forced[kind] - 1].tma && !R.tma_ok) return FC_EINVAL;
             R.sel[kind] = forced[kind] - 1;
             continue;
         }
@@ -969,7 +1020,7 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
         snprintf(keys[kind], sizeof(keys[kind]), "%s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M,
                  p->L, names[kind], n[kind]);
         int idx = 0;
-        if (tune_lookup(keys[kind], &idx) && idx >= 0 && idx < n[kind])
+        if (tune_lookup(keys[kind], &idx) && idx >= 0 && idx < n[kind] && !(kind == 2 && R.v.rinv[idx].tma && !R.tma_ok))
             R.sel[kind] = idx;
         else
             need[kind] = timing;
@@ -1032,6 +1083,58 @@ int choose_persistent(fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp, T* cq, T
 }  // namespace
 
 namespace {
+
+// cuTensorMapEncodeTiled, looked up once through the runtime's driver entry
+// point (no link against the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of the FP32 intermediate Zt, viewed as floats [M/2][2L], with
+// boxes of 4 floats (the two complex values of a row pair) by up to 256
+// columns, and the resident grid of the TMA pass C.  The row stride 8L bytes
+// must be a multiple of 16 and a box starts at float 4u (byte 16u): L even.
+// Without a map (odd L, small M, no driver entry point) that shape is never
+// launched.
+int setup_tma(fftconv_plan* p) {
+    PrecRes& R = p->p32;
+    R.tma_ok = false;
+    int k = -1;
+    for (int i = 0; i < R.v.n_rinv; ++i)
+        if (R.v.rinv[i].tma) k = i;
+    if (k < 0 || (p->L & 1) || p->M < 256) return FC_OK;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return FC_OK;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * p->L, (cuuint64_t)(p->M / 2)};
+    const cuuint64_t strides[1] = {(cuuint64_t)2 * p->L * sizeof(float)};
+    const cuuint32_t box[2] = {4, (cuuint32_t)tma_box_cols(p->M)};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&R.zmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, R.Z, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return FC_OK;
+    int per_sm = 0, sms = 0;
+    FC_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, R.v.rinv[k].f, R.v.rinv[k].threads,
+                                                         R.v.rinv[k].smem));
+    FC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev));
+    const int units = (p->L + 1) / 2;
+    R.tma_grid = per_sm * sms < units ? per_sm * sms : units;
+    R.tma_ok = R.tma_grid > 0;
+    return FC_OK;
+}
 
 // Nodes and weights of the n-point Gauss-Legendre rule on [-1, 1]: the roots
 // of the Legendre polynomial P_n by Newton's method from the asymptotic
@@ -1184,6 +1287,7 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
     // intermediates (half spectra, column-major) and solve workspace
     if (prec & FC_F64) FC_TRY(dalloc(p, &p->p64.Z, sizeof(cpx<double>) * (size_t)L * (M / 2)));
     if (p->p32.on) FC_TRY(dalloc(p, &p->p32.Z, sizeof(cpx<float>) * (size_t)L * (M / 2)));
+    if (p->p32.on) FC_TRY(setup_tma(p));
     if (prec & FC_F64) {
         FC_TRY(dalloc(p, (void**)&p->x64, sizeof(double) * N));
         FC_TRY(dalloc(p, (void**)&p->r64, sizeof(double) * N));
@@ -1337,7 +1441,7 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     c.part = p->part;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = (const cpx<T>*)R.tws(kc.E);
-    return launch_dep(kc.f, row_grid(p, kc), kc.threads, kc.smem, s, c);
+    return launch_rinv<T>(p, R, kc, c, s, true);
 }
 
 }  // namespace
@@ -1562,6 +1666,21 @@ struct GraphBuilder {
     }
 };
 
+// Pass C as a graph node following prev (the TMA-staged shape gets its
+// tensor-map arguments).
+template <typename T>
+cudaGraphNode_t graph_rinv(GraphBuilder& gb, cudaGraph_t g, cudaGraphNode_t prev, fftconv_plan* p, PrecRes& R,
+                           const RowInvArgs<T>& c) {
+    const KV& kc = R.rinv();
+    if constexpr (sizeof(T) == 4) {
+        if (kc.tma) {
+            const RowInvTma P = tma_args(p, R, c);
+            return gb.pass(g, prev, kc.f, R.tma_grid, kc.threads, kc.smem, P);
+        }
+    }
+    return gb.pass(g, prev, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
+}
+
 // Inner CG loop body (Listing 2): pass A (update + row FFT), B, C (product,
 // dot products, step decision).
 template <typename T>
@@ -1596,7 +1715,7 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     c.h_inner = h_inner;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = (const cpx<T>*)R.tws(kc.E);
-    gb.pass(body, nB, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
+    graph_rinv<T>(gb, body, nB, p, R, c);
 }
 
 // Inner body of preconditioned CG: A1 (x, r update; transform r) -> B1 with
@@ -1632,7 +1751,7 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c1.part = p->part;
     c1.Z = (const cpx<T>*)R.Z;
     c1.tw = (const cpx<T>*)R.tws(kc.E);
-    cudaGraphNode_t n3 = gb.pass(body, n2, kc.f, row_grid(p, kc), kc.threads, kc.smem, c1);
+    cudaGraphNode_t n3 = graph_rinv<T>(gb, body, n2, p, R, c1);
     RowFwdArgs<T> a2{};
     a2.L = p->L;
     a2.mode = RF_PCG_P;
@@ -1659,7 +1778,7 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c2.h_inner = h_inner;
     c2.Z = (const cpx<T>*)R.Z;
     c2.tw = (const cpx<T>*)R.tws(kc.E);
-    gb.pass(body, n5, kc.f, row_grid(p, kc), kc.threads, kc.smem, c2);
+    graph_rinv<T>(gb, body, n5, p, R, c2);
 }
 
 // Build the solve graph for one mode:
