@@ -89,6 +89,9 @@ __host__ __device__ constexpr size_t tma_buf_bytes(int M) {
     const size_t b = stage > seg ? stage : seg;
     return (b + 127) / 128 * 128;
 }
+// Two staging buffers.  (A third buffer for double-buffered exchanges, one
+// barrier per exchange, measured slower at M = 8192: the shared-memory
+// carve-out it takes leaves too little L1 for the twiddle tables.)
 __host__ __device__ constexpr size_t tma_smem_bytes(int M) { return 2 * tma_buf_bytes(M) + 128; }
 __host__ __device__ constexpr int tma_box_cols(int M) { return M / 2 < 256 ? M / 2 : 256; }
 
