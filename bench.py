@@ -353,11 +353,14 @@ def run_ours(args, world, rank, local, pg):
             pk = fc_inputs.problem(Lk, seed=10_000 + k, b_kind="normal")
             breqs.append((Lk, pk))
         if breqs:
-            # warm the server: one plan per (slot, size) is created on first use
-            warm = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED,
-                                      precond=True)
-                    for Lk, pk in breqs[:min(len(breqs), 4 * args.slots)]]
-            drain(warm)
+            # warm the server outside the timed region: for each size, as many
+            # concurrent requests as slots, so that every slot's staging holds
+            # the largest size and each size has a plan per slot (plan set-up
+            # allocates device memory, which would stall the other slots)
+            for Lw in sorted(set(Lk for Lk, _ in breqs), reverse=True):
+                pw = next(pk for Lk, pk in breqs if Lk == Lw)
+                drain([fc.cg_batch_submit(sv, Lw, pw["s"], pw["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED,
+                                          precond=True) for _ in range(args.slots)])
             t0 = time.perf_counter()
             tk = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True)
                   for Lk, pk in breqs]
@@ -586,7 +589,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=600, dest="serve_requests")
     ap.add_argument("--serve-f64", type=int, default=160, dest="serve_f64",
                     help="requests of the serving mix solved closed-loop and by one-at-a-time FP64")
-    ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=MATVEC_TRAFFIC_L1024,
                     help="ncu dram bytes per matvec from a capture of the current kernels")
     ap.add_argument("--ref-sample-iters", type=int, default=3, dest="ref_sample_iters")

@@ -165,6 +165,13 @@ int fftconv_plan_create_green(fftconv_plan **p, int L, int prec, int green, cons
 /* Free a plan and its device memory (synchronises the device first). */
 int fftconv_plan_destroy(fftconv_plan *p);
 
+/* How the calls that wait for the device on this plan (cg_solve,
+ * fc_fracture_run) wait: blocking = 0 spins (the default, lowest latency);
+ * blocking = 1 blocks the calling thread on an event (for many host threads
+ * each driving solves, as the server's slots do, so that waiting threads do
+ * not compete for the host's cores).  Errors: FC_EINVAL, FC_ECUDA. */
+int fftconv_plan_sync_mode(fftconv_plan *p, int blocking);
+
 /* Query a plan: side L, padded side M, precision flags, device bytes held. */
 int fftconv_plan_info(const fftconv_plan *p, int *L, int *M, int *prec, size_t *device_bytes);
 

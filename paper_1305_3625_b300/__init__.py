@@ -109,6 +109,7 @@ def _load():
     lib.cg_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
     lib.fc_masked_step.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.fc_front.argtypes = [vp, vp, vp, vp, vp]
+    lib.fftconv_plan_sync_mode.argtypes = [vp, i]
     lib.fc_fracture_run.argtypes = [vp, vp, vp, vp, vp, vp, i, ctypes.POINTER(cg_opts), vp, vp,
                                     ctypes.POINTER(fc_run_result), vp]
     lib.fc_masked_step_static.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp]
@@ -259,6 +260,13 @@ def fc_masked_step(plan: Plan, t, mask, x, removed, stream=None) -> None:
                              _ptr(removed, torch.int64, 1, "removed"), _stream(stream))
     if rc != FC_OK:
         raise FcError(rc, "fc_masked_step")
+
+
+def fftconv_plan_sync_mode(plan: Plan, blocking: bool) -> None:
+    """Waits on this plan spin (False, default) or block the thread (True)."""
+    rc = _lib.fftconv_plan_sync_mode(plan.handle, int(bool(blocking)))
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_plan_sync_mode")
 
 
 def fc_front(plan: Plan, mask, first_intact, damage_end, stream=None) -> None:

@@ -718,6 +718,8 @@ struct fftconv_plan {
     double* wdx = nullptr;
     bool warm_ok = false;
     int64_t* rm_host = nullptr;  // pinned: last removed index of a fracture run
+    bool blocking = false;       // waits block the host thread (event with blocking sync)
+    cudaEvent_t ev_wait = nullptr;
 };
 
 namespace {
@@ -750,6 +752,7 @@ void plan_free(fftconv_plan* p) {
     }
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->rm_host) cudaFreeHost(p->rm_host);
+    if (p->ev_wait) cudaEventDestroy(p->ev_wait);
     delete p;
 }
 
@@ -1982,6 +1985,22 @@ int launch_persistent(fftconv_plan* p, bool mixed, cudaStream_t st) {
 
 }  // namespace
 
+// Wait until the work queued on st is done: spinning (the default, lowest
+// latency) or, after fftconv_plan_sync_mode(p, 1), blocking the thread.
+static cudaError_t wait_stream(fftconv_plan* p, cudaStream_t st) {
+    if (!p->blocking) return cudaStreamSynchronize(st);
+    cudaError_t e = cudaEventRecord(p->ev_wait, st);
+    return e != cudaSuccess ? e : cudaEventSynchronize(p->ev_wait);
+}
+
+extern "C" int fftconv_plan_sync_mode(fftconv_plan* p, int blocking) {
+    if (!p || (blocking != 0 && blocking != 1)) return FC_EINVAL;
+    if (blocking && !p->ev_wait)
+        FC_CK(cudaEventCreateWithFlags(&p->ev_wait, cudaEventBlockingSync | cudaEventDisableTiming));
+    p->blocking = blocking != 0;
+    return FC_OK;
+}
+
 extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, double* x, const uint8_t* mask,
                         const cg_opts* o, cg_result* r, fc_stream_t stream) {
     if (!p || !s || !b || !x) return FC_EINVAL;
@@ -2062,7 +2081,7 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
             if (!rc) rc = launch_persistent(p, mixed, st);
             if (rc) return rc;
             FC_CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
-            FC_CK(cudaStreamSynchronize(st));
+            FC_CK(wait_stream(p, st));
             if (p->st_host->finished) break;
         }
     } else {
@@ -2070,7 +2089,7 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     }
     FC_CK(cudaMemcpyAsync(x, p->x64, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
     FC_CK(cudaMemcpyAsync(p->st_host, p->st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
-    FC_CK(cudaStreamSynchronize(st));
+    FC_CK(wait_stream(p, st));
     const CgState& f = *p->st_host;
     // r64 is the true residual of the final x64 whenever the refinement
     // decision finished the solve
@@ -2128,7 +2147,7 @@ extern "C" int fc_fracture_run(fftconv_plan* p, const double* s, const double* b
                                                     p->am_v, p->am_i, p->am_ctl);
         FC_CK(cudaGetLastError());
         FC_CK(cudaMemcpyAsync(p->rm_host, removed + k, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        FC_CK(cudaStreamSynchronize(st));
+        FC_CK(wait_stream(p, st));
         if (*p->rm_host < 0) break;  // no active fibre left
         acc.steps_done = k + 1;
     }

@@ -47,6 +47,7 @@ struct Req {
 struct Slot {
     std::thread th;
     cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;  // blocking-sync event: a waiting slot thread sleeps
     double *ds = nullptr, *db = nullptr, *dx = nullptr;  // device staging
     double *hs = nullptr, *hb = nullptr, *hx = nullptr;  // pinned host staging
     long cap = 0;
@@ -165,6 +166,8 @@ void worker(cg_server* sv, Slot* sl) {
         int rc = FC_OK;
         if (!plan) {
             rc = fftconv_plan_create(&plan, L, FC_F32 | FC_F64, nullptr);
+            // many slot threads wait at once: let them sleep, not spin
+            if (rc == FC_OK) rc = fftconv_plan_sync_mode(plan, 1);
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->used -= r->est;
             if (rc == FC_OK) {
@@ -189,7 +192,8 @@ void worker(cg_server* sv, Slot* sl) {
             rc = cg_solve(plan, sl->ds, sl->db, sl->dx, nullptr, &o, &r->res, sl->stream);
             if (rc == FC_OK || rc == FC_ENOCONV || rc == FC_ENANINF) {
                 cudaMemcpyAsync(sl->hx, sl->dx, sizeof(double) * N, cudaMemcpyDeviceToHost, sl->stream);
-                if (cudaStreamSynchronize(sl->stream) != cudaSuccess) rc = FC_ECUDA;
+                if (cudaEventRecord(sl->done, sl->stream) != cudaSuccess || cudaEventSynchronize(sl->done) != cudaSuccess)
+                    rc = FC_ECUDA;
                 if (r->rq.x) memcpy(r->rq.x, sl->hx, sizeof(double) * N);
             }
         }
@@ -223,7 +227,9 @@ extern "C" int cg_server_create(cg_server** out, size_t mem_budget_bytes, int ma
     sv->max_slots = max_slots;
     for (int i = 0; i < max_slots; ++i) {
         Slot* sl = new (std::nothrow) Slot();
-        if (!sl || cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (!sl || cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl->done, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
+            if (sl && sl->stream) cudaStreamDestroy(sl->stream);
             delete sl;
             cg_server_destroy(sv);
             return FC_ECUDA;
@@ -311,6 +317,7 @@ extern "C" int cg_server_destroy(cg_server* sv) {
         cudaFreeHost(sl->hb);
         cudaFreeHost(sl->hx);
         if (sl->stream) cudaStreamDestroy(sl->stream);
+        if (sl->done) cudaEventDestroy(sl->done);
         delete sl;
     }
     for (auto& kv : sv->reqs) delete kv.second;  // every request, queued or not, is in reqs
