@@ -898,7 +898,7 @@ void tune_load_locked() {
     tune_path(path, sizeof(path));
     FILE* f = fopen(path, "r");
     if (!f) return;
-    char line[160];
+    char line[sizeof(g_tune[0].key) - 1];  // a longer line is no entry of ours
     while (g_ntune < 512 && fgets(line, sizeof(line), f)) {
         // "<key>| <index>"; keys contain no '|'
         char* bar = strrchr(line, '|');

@@ -136,73 +136,6 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, uns
 
 // --------------------------------------------------- per-element input ---
 
-// The value pass A transforms at flat index i (row-major L x L): the plain
-// input, the CG update of Listing 2 (x += a p, r -= a q, p = r + b p; on the
-// first pass of a run p = r, or p = r + b' p_old when the direction is kept
-// across a true-residual replacement), or the FP64 iterate with the
-// folded-in correction of the last inner run (masked).  acc collects r.r.
-template <typename T>
-__device__ __forceinline__ T pass_a_value(const RowFwdArgs<T>& a, size_t i, int first, T alpha, T beta,
-                                          double inv_sigma, double sig, T& acc, T& acc_rp, T bcarry) {
-    if (a.mode == RF_PLAIN) return a.x[i];
-    if (a.mode == RF_XUPD) {
-        double xv = a.x64[i];
-        if (a.d32 && sig != 0.0) xv += sig * (double)a.d32[i];
-        if (a.mask && !a.mask[i]) xv = 0.0;
-        a.x64[i] = xv;
-        return (T)xv;
-    }
-    if (a.mode == RF_PCG_R) {  // PCG: x += alpha p, r -= alpha q; transform r
-        T r;
-        if (first) {
-            if (a.r64) {
-                r = (T)(a.r64[i] * inv_sigma);
-                a.cr[i] = r;
-                a.cx[i] = 0;
-            } else {
-                r = a.cr[i];
-            }
-        } else {
-            const T p = a.cp[i];
-            a.cx[i] = a.cx[i] + alpha * p;
-            r = a.cr[i] - alpha * a.cq[i];
-            a.cr[i] = r;
-        }
-        acc += r * r;
-        return r;
-    }
-    if (a.mode == RF_PCG_P) {  // PCG: p = z + beta p; transform p
-        const T z = a.cz[i];
-        const T p = first ? z : z + beta * a.cp[i];
-        a.cp[i] = p;
-        acc_rp += a.cr[i] * p;
-        return p;
-    }
-    T r, p;
-    if (first) {
-        if (a.r64) {
-            r = (T)(a.r64[i] * inv_sigma);
-            a.cr[i] = r;
-            a.cx[i] = 0;
-        } else {
-            r = a.cr[i];
-        }
-        p = bcarry != (T)0 ? r + bcarry * a.cp[i] : r;
-    } else {
-        p = a.cp[i];
-        a.cx[i] = a.cx[i] + alpha * p;
-        r = a.cr[i] - alpha * a.cq[i];
-        a.cr[i] = r;
-        p = r + beta * p;
-    }
-    a.cp[i] = p;
-    acc += r * r;
-    acc_rp += r * p;
-    return p;
-}
-
-// ------------------------------------------------------------ pass A ----
-
 // Block-uniform scalars of a pass-A unit (the CG step of the last product,
 // or the scale of the correction folded into x).
 template <typename T>
@@ -211,6 +144,106 @@ struct AScal {
     T alpha, beta, bcarry;
     double inv_sigma, sig;
 };
+
+// The value pass A transforms at flat index i (row-major L x L): the plain
+// input, the CG update of Listing 2 (x += a p, r -= a q, p = r + b p; on the
+// first pass of a run p = r, or p = r + b' p_old when the direction is kept
+// across a true-residual replacement), or the FP64 iterate with the
+// folded-in correction of the last inner run (masked).  acc collects r.r.
+// The arrays are restrict-qualified parameters here and in pass_a_inputs:
+// they never overlap, so the compiler may issue the loads of all of a
+// thread's elements before the first store, instead of one element's memory
+// round trip after another.
+template <typename T>
+__device__ __forceinline__ T pass_a_value(int mode, const T* __restrict__ xin, T* __restrict__ cx,
+                                          T* __restrict__ cr, T* __restrict__ cp, const T* __restrict__ cq,
+                                          const T* __restrict__ cz, const double* __restrict__ r64,
+                                          double* __restrict__ x64, const float* __restrict__ d32,
+                                          const uint8_t* __restrict__ mask, size_t i, const AScal<T>& sc, T& acc,
+                                          T& acc_rp) {
+    if (mode == RF_PLAIN) return xin[i];
+    if (mode == RF_XUPD) {
+        double xv = x64[i];
+        if (d32 && sc.sig != 0.0) xv += sc.sig * (double)d32[i];
+        if (mask && !mask[i]) xv = 0.0;
+        x64[i] = xv;
+        return (T)xv;
+    }
+    if (mode == RF_PCG_R) {  // PCG: x += alpha p, r -= alpha q; transform r
+        T r;
+        if (sc.first) {
+            if (r64) {
+                r = (T)(r64[i] * sc.inv_sigma);
+                cr[i] = r;
+                cx[i] = 0;
+            } else {
+                r = cr[i];
+            }
+        } else {
+            const T p = cp[i];
+            cx[i] = cx[i] + sc.alpha * p;
+            r = cr[i] - sc.alpha * cq[i];
+            cr[i] = r;
+        }
+        acc += r * r;
+        return r;
+    }
+    if (mode == RF_PCG_P) {  // PCG: p = z + beta p; transform p
+        const T z = cz[i];
+        const T p = sc.first ? z : z + sc.beta * cp[i];
+        cp[i] = p;
+        acc_rp += cr[i] * p;
+        return p;
+    }
+    T r, p;
+    if (sc.first) {
+        if (r64) {
+            r = (T)(r64[i] * sc.inv_sigma);
+            cr[i] = r;
+            cx[i] = 0;
+        } else {
+            r = cr[i];
+        }
+        p = sc.bcarry != (T)0 ? r + sc.bcarry * cp[i] : r;
+    } else {
+        p = cp[i];
+        cx[i] = cx[i] + sc.alpha * p;
+        r = cr[i] - sc.alpha * cq[i];
+        cr[i] = r;
+        p = r + sc.beta * p;
+    }
+    cp[i] = p;
+    acc += r * r;
+    acc_rp += r * p;
+    return p;
+}
+
+// Pass A's inputs of one thread: elements j + e*G (e < E/2, the rest is the
+// zero padding) of rows r0 and r0 + 1, packed as v[e] = row r0 + i row r0+1.
+template <typename T, int M, int E>
+__device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xin, T* __restrict__ cx,
+                                              T* __restrict__ cr, T* __restrict__ cp, const T* __restrict__ cq,
+                                              const T* __restrict__ cz, const double* __restrict__ r64,
+                                              double* __restrict__ x64, const float* __restrict__ d32,
+                                              const uint8_t* __restrict__ mask, const AScal<T>& sc, int j, int r0,
+                                              int L, cpx<T> (&v)[E], T& acc, T& acc_rp) {
+    constexpr int G = M / E;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        v[e] = cpx<T>{0, 0};
+        const int n = j + e * G;
+        if (e < E / 2 && n < L) {  // n >= M/2 >= L for e >= E/2: the zero padding
+            if (r0 < L)
+                v[e].x = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask, (size_t)r0 * L + n, sc,
+                                      acc, acc_rp);
+            if (r0 + 1 < L)
+                v[e].y = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask, (size_t)(r0 + 1) * L + n,
+                                      sc, acc, acc_rp);
+        }
+    }
+}
+
+// ------------------------------------------------------------ pass A ----
 
 template <typename T>
 __device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a) {
@@ -242,19 +275,8 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
     const int r0 = (unit * RB + pl) * 2;
 
     C v[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-        v[e] = C{0, 0};
-        const int n = j + e * G;
-        if (e < E / 2 && n < L) {  // n >= M/2 >= L for e >= E/2: the zero padding
-            if (r0 < L)
-                v[e].x = pass_a_value(a, (size_t)r0 * L + n, sc.first, sc.alpha, sc.beta, sc.inv_sigma, sc.sig, acc,
-                                      acc_rp, sc.bcarry);
-            if (r0 + 1 < L)
-                v[e].y = pass_a_value(a, (size_t)(r0 + 1) * L + n, sc.first, sc.alpha, sc.beta, sc.inv_sigma, sc.sig,
-                                      acc, acc_rp, sc.bcarry);
-        }
-    }
+    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, L, v, acc,
+                           acc_rp);
     C* g0 = sm + pl * GS;
     fft_stages<T, M, E, false, DB, 0>(v, j, g0, g0 + SEG, a.tw);
     C* wp = g0 + NB * SEG + spad(j);
@@ -388,29 +410,63 @@ __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc(ColArgs<T> a) {
 
 // ------------------------------------------------------------ pass C ----
 
+// The epilogue of pass C at flat index i for the transformed value yv: the
+// plain output, the CG product q = P (C p + s p) with its dot products, the
+// preconditioned residual z, or the FP64 true residual r = P (b - C x - s x).
+// Restrict-qualified arrays, as for pass A.
 template <typename T>
-__device__ __forceinline__ void pass_c_value(const RowInvArgs<T>& a, size_t i, T y, T& s0, T& s1, T& s2) {
-    const bool act = a.mask == nullptr || a.mask[i] != 0;
-    if (a.mode == RI_PLAIN) {
-        a.y[i] = y;
-    } else if (a.mode == RI_CG) {
-        const T p = a.cp[i];
-        const T q = act ? y + a.s[i] * p : (T)0;
-        a.cq[i] = q;
+__device__ __forceinline__ void pass_c_value(int mode, T* __restrict__ y, const T* __restrict__ s,
+                                             const T* __restrict__ cp, const T* __restrict__ cr, T* __restrict__ cq,
+                                             T* __restrict__ cz, const uint8_t* __restrict__ mask,
+                                             const double* __restrict__ x64, const double* __restrict__ b64,
+                                             const double* __restrict__ s64, double* __restrict__ r64, size_t i,
+                                             T yv, T& s0, T& s1, T& s2) {
+    const bool act = mask == nullptr || mask[i] != 0;
+    if (mode == RI_PLAIN) {
+        y[i] = yv;
+    } else if (mode == RI_CG) {
+        const T p = cp[i];
+        const T q = act ? yv + s[i] * p : (T)0;
+        cq[i] = q;
         s0 += p * q;
-        s1 += a.cr[i] * q;
+        s1 += cr[i] * q;
         s2 += q * q;
-    } else if (a.mode == RI_PCG_Z) {
-        const T z = act ? y : (T)0;
-        a.cz[i] = z;
-        s0 += a.cr[i] * z;
+    } else if (mode == RI_PCG_Z) {
+        const T z = act ? yv : (T)0;
+        cz[i] = z;
+        s0 += cr[i] * z;
     } else {  // RI_RESID (T = double)
-        const double xv = a.x64[i];
-        const double bv = act ? a.b64[i] : 0.0;
-        const double r = act ? bv - ((double)y + a.s64[i] * xv) : 0.0;
-        a.r64[i] = r;
+        const double xv = x64[i];
+        const double bv = act ? b64[i] : 0.0;
+        const double r = act ? bv - ((double)yv + s64[i] * xv) : 0.0;
+        r64[i] = r;
         s0 += (T)(r * r);
         s1 += (T)(bv * bv);
+    }
+}
+
+// Pass C's outputs of one thread: elements j + e*G < L (e < E/2, the crop)
+// of rows r0 (v[e].x) and r0 + 1 (v[e].y).
+template <typename T, int M, int E>
+__device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, const T* __restrict__ s,
+                                               const T* __restrict__ cp, const T* __restrict__ cr,
+                                               T* __restrict__ cq, T* __restrict__ cz,
+                                               const uint8_t* __restrict__ mask, const double* __restrict__ x64,
+                                               const double* __restrict__ b64, const double* __restrict__ s64,
+                                               double* __restrict__ r64, int j, int r0, int L, const cpx<T> (&v)[E],
+                                               T& s0, T& s1, T& s2) {
+    constexpr int G = M / E;
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {
+        const int n = j + e * G;
+        if (n < L) {
+            if (r0 < L)
+                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, (size_t)r0 * L + n, v[e].x, s0, s1,
+                             s2);
+            if (r0 + 1 < L)
+                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, (size_t)(r0 + 1) * L + n, v[e].y,
+                             s0, s1, s2);
+        }
     }
 }
 
@@ -466,14 +522,8 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
     if constexpr (!DB) __syncthreads();
     // with two buffers the first exchange writes buffer 1 while buffer 0 is still being read
     fft_stages<T, M, E, true, DB, DB ? 1 : 0>(v, j, g0, g0 + SEG, a.tw);
-#pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-        const int n = j + e * G;
-        if (n < L) {
-            if (r0 < L) pass_c_value(a, (size_t)r0 * L + n, v[e].x, s0, s1, s2);
-            if (r0 + 1 < L) pass_c_value(a, (size_t)(r0 + 1) * L + n, v[e].y, s0, s1, s2);
-        }
-    }
+    pass_c_outputs<T, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j, r0, L, v,
+                            s0, s1, s2);
 }
 
 template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>

@@ -175,15 +175,8 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
         }
         __syncthreads();  // staged values consumed: the buffer becomes the exchange buffer
         fft_stages<float, M, E, true, false, 0>(v, j, buf[cur], buf[cur], a.tw);
-        const int r0 = 2 * u;
-#pragma unroll
-        for (int e = 0; e < E / 2; ++e) {
-            const int n = j + e * G;
-            if (n < L) {
-                pass_c_value(a, (size_t)r0 * L + n, v[e].x, s0, s1, s2);
-                pass_c_value(a, (size_t)(r0 + 1) * L + n, v[e].y, s0, s1, s2);
-            }
-        }
+        pass_c_outputs<float, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j,
+                                    2 * u, L, v, s0, s1, s2);
         __syncthreads();  // exchanges done: the buffer may receive the copy issued next
     }
     if (!ok && j == 0) {
