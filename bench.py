@@ -279,9 +279,10 @@ def run_ours(args, world, rank, local, pg):
     mv_gbs = mv_bytes / (mv_ms * 1e-3) / 1e9
 
     big = None
+    large_loop = None
     if args.big:
         L4 = 4096
-        plan4 = fc.fftconv_plan_create(L4, fc.FC_F32)
+        plan4 = fc.fftconv_plan_create(L4, fc.FC_F32 | fc.FC_F64)
         x4 = torch.rand(L4 * L4, device=dev, dtype=torch.float32)
         y4 = torch.empty_like(x4)
         ms4 = time_apply(plan4, x4, y4, 20)
@@ -290,7 +291,31 @@ def run_ours(args, world, rank, local, pg):
         big = {"L": L4, "ms": round(ms4, 4), "bytes": b4, "GB_s": round(b4 / (ms4 * 1e-3) / 1e9, 1),
                "frac_of_hbm": round(b4 / (ms4 * 1e-3) / 1e9 / peak, 3),
                "effective_frac_88N": round(88 * L4 * L4 / (ms4 * 1e-3) / 1e9 / peak, 3)}
-        del plan4, x4, y4
+        del x4, y4
+        if args.big_steps > 0:
+            # the large single instance: a cold mixed solve refined to 1e-8, then a
+            # masked removal loop with t ~ U(0, 1) (fc_fracture_run)
+            p4 = fc_inputs.problem(L4, seed=rank, with_t=True)
+            s4, b4v, t4 = (torch.tensor(p4[k], device=dev) for k in ("s", "b", "t"))
+            m4 = torch.ones(L4 * L4, device=dev, dtype=torch.uint8)
+            xx4 = torch.zeros(L4 * L4, device=dev, dtype=torch.float64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc4 = fc.cg_solve(plan4, s4, b4v, xx4, mask=m4, rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True)
+            cold_s = time.perf_counter() - t0
+            rem4 = torch.empty(args.big_steps, device=dev, dtype=torch.int64)
+            fr4 = fc.fc_fracture_run(plan4, s4, b4v, t4, m4, xx4, args.big_steps, rem4, rtol=1e-8,
+                                     mode=fc.FC_MODE_MIXED, precond=True)
+            steps = max(fr4["steps_done"], 1)
+            large_loop = {"L": L4, "rtol": 1e-8, "mode": "mixed, Fourier-preconditioned",
+                          "cold_solve": {"s": round(cold_s, 4), "iters": rc4["iters"],
+                                         "true_rel_resid": rc4["true_rel_resid"]},
+                          "steps": fr4["steps_done"], "status": fr4["status"],
+                          "steps_per_s": round(fr4["steps_done"] / fr4["seconds"], 2),
+                          "iters_per_step": round(fr4["iters"] / steps, 2),
+                          "fp64_products_per_step": round(fr4["fp64_products"] / steps, 2)}
+            del s4, b4v, t4, m4, xx4, rem4
+        del plan4
 
     # end-to-end through the C ABI with host buffers: inputs up, result down
     e2e = None
@@ -522,6 +547,7 @@ def run_ours(args, world, rank, local, pg):
                        "frac_of_hbm": round(mv_gbs / peak, 3),
                        "effective_frac_88N": round(88 * N / (mv_ms * 1e-3) / 1e9 / peak, 3)},
             "matvec_L4096": big,
+            "large_loop_L4096": large_loop,
             "batched": batched,
             "serving": serving,
             "roofline": {"bound": "hbm", "kernel": "fftconv_apply FP32 (3 passes), L=1024",
@@ -584,6 +610,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5, dest="e2e_steps")
     ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget")
     ap.add_argument("--big", type=int, default=1)
+    ap.add_argument("--big-steps", type=int, default=200, dest="big_steps")
     ap.add_argument("--frac-steps", type=int, default=100, dest="frac_steps")
     ap.add_argument("--batch-solves", type=int, default=256, dest="batch_solves")
     ap.add_argument("--serve-requests", type=int, default=600, dest="serve_requests")
