@@ -326,18 +326,39 @@ def run_ours(args, world, rank, local, pg):
         hx = x_start.cpu().pin_memory()
         hm = mask_start.cpu().pin_memory()
         hrem = torch.empty(1, dtype=torch.int64).pin_memory()
-        ds, db, dt_ = torch.empty_like(s), torch.empty_like(b), torch.empty_like(t)
+        # s, b and t are copied every step into one of two device buffers on a
+        # copy stream, one step ahead, so that their transfer overlaps the
+        # previous step's solve; x and the mask come back from the host each
+        # step (they depend on the previous result)
+        bufs = [(torch.empty_like(s), torch.empty_like(b), torch.empty_like(t)) for _ in range(2)]
+        copy_stream = torch.cuda.Stream(device=dev)
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_used = [torch.cuda.Event() for _ in range(2)]
+        for ev in ev_used:
+            ev.record(stream)
+
+        def stage(k):
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_used[k])
+                for dbuf, hbuf in zip(bufs[k], (hs, hb, ht)):
+                    dbuf.copy_(hbuf, non_blocking=True)
+                ev_in[k].record(copy_stream)
+
         torch.cuda.synchronize()
         e0 = time.perf_counter()
         ke = args.e2e_steps
-        for _ in range(ke):
-            ds.copy_(hs, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            dt_.copy_(ht, non_blocking=True)
+        stage(0)
+        for i in range(ke):
+            k = i & 1
+            if i + 1 < ke:
+                stage(k ^ 1)
+            stream.wait_event(ev_in[k])
+            ds, db, dt_ = bufs[k]
             x.copy_(hx, non_blocking=True)
             mask.copy_(hm, non_blocking=True)
             r = fc.cg_solve(plan, ds, db, x, mask=mask, rtol=RTOL, mode=fc.FC_MODE_MIXED, precond=True)
             fc.fc_masked_step(plan, dt_, mask, x, removed)
+            ev_used[k].record(stream)
             hx.copy_(x, non_blocking=True)
             hm.copy_(mask, non_blocking=True)
             hrem.copy_(removed, non_blocking=True)
@@ -607,7 +628,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--f64-steps", type=int, default=6, dest="f64_steps")
-    ap.add_argument("--e2e-steps", type=int, default=5, dest="e2e_steps")
+    ap.add_argument("--e2e-steps", type=int, default=10, dest="e2e_steps")
     ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget")
     ap.add_argument("--big", type=int, default=1)
     ap.add_argument("--big-steps", type=int, default=200, dest="big_steps")

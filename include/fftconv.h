@@ -81,7 +81,7 @@ typedef struct cg_tune {
 } cg_tune;
 
 typedef struct cg_opts {
-    double rtol;       /* stop when ||P(b - A x)||_2 <= rtol ||P b||_2, judged on the
+    double rtol;       /* stop when ||P(b - A x)||_2 <= rtol ||P b||_2, certified on the
                           FP64 recomputed residual                              */
     int max_iter;      /* cap on CG iterations (matrix-vector products), all cycles */
     int mode;          /* FC_MODE_F64 or FC_MODE_MIXED                           */
