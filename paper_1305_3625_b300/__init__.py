@@ -264,7 +264,7 @@ def fc_masked_step(plan: Plan, t, mask, x, removed, stream=None) -> None:
 
 def fftconv_plan_sync_mode(plan: Plan, blocking: bool) -> None:
     """Waits on this plan spin (False, default) or block the thread (True)."""
-    rc = _lib.fftconv_plan_sync_mode(plan.handle, int(bool(blocking)))
+    rc = _lib.fftconv_plan_sync_mode(plan.handle, int(blocking))
     if rc != FC_OK:
         raise FcError(rc, "fftconv_plan_sync_mode")
 

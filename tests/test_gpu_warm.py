@@ -191,3 +191,21 @@ def test_update_after_capped_solve():
     assert r["status"] == fc.FC_OK and r["resid_updated"] == 1
     want = oracle_rel_resid(L, p["s"], p["b"], x_in, m_in)
     assert abs(r["true_rel_resid"] - want) <= 1e-10 * want
+
+
+def test_blocking_wait_mode_gives_the_same_solve():
+    """fftconv_plan_sync_mode only changes how the host waits: a solve on a
+    plan that blocks returns bitwise the same iterate and status."""
+    L = 48
+    p = fc_inputs.problem(L, seed=12, with_t=True)
+    out = []
+    for blocking in (False, True):
+        pl = fresh(L)
+        fc.fftconv_plan_sync_mode(pl, blocking)
+        x = dev(np.zeros(L * L))
+        r = fc.cg_solve(pl, dev(p["s"]), dev(p["b"]), x, rtol=1e-10, mode=fc.FC_MODE_MIXED, precond=True)
+        assert r["status"] == fc.FC_OK
+        out.append((host(x), r["iters"], r["refinements"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1:] == out[1][1:]
+    with pytest.raises(fc.FcError):
+        fc.fftconv_plan_sync_mode(fresh(8), 2)
