@@ -541,8 +541,10 @@ void add_pers(Variants& v) {
 }
 
 // Launch shapes compiled for each (precision, M).  FP32 sizes from 256 up
-// carry three shapes per pass for the autotuner; FP64 (ALU-bound on this
-// part) carries one.
+// carry seven to nine shapes per pass for the autotuner: E = 16, 8 or 4 with
+// one or more rows or columns per block, single-buffered 64-register shapes
+// (more resident blocks), 1024-thread row blocks, and the TMA-staged pass C.
+// FP64 (ALU-bound on this part) carries one.
 template <typename T, int M>
 void make_variants(Variants& v) {
     constexpr int H = M / 2;
@@ -572,6 +574,9 @@ void make_variants(Variants& v) {
             constexpr int R1 = clampi(128 / G16, 1, 64), R2 = clampi(256 / G16, 1, 64);
             add_col<T, M, 16, C1, clampi(65536 / (C1 * G16 * 64), 1, 16), false>(v);
             add_col<T, M, 16, C2, clampi(65536 / (C2 * G16 * 64), 1, 16), false>(v);
+            // the same with a 72-register cap (fewer spills, one block fewer per SM)
+            constexpr int MB72 = clampi(65536 / (C1 * G16 * 72), 1, 16);
+            if constexpr (MB72 > 1) add_col<T, M, 16, C1, MB72, false>(v);
             add_row<T, M, 16, R1, clampi(65536 / (R1 * G16 * 64), 1, 16), false>(v);
             add_row<T, M, 16, R2, clampi(65536 / (R2 * G16 * 64), 1, 16), false>(v);
             // 1024-thread row blocks: more rows per block make the column-major
