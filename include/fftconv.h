@@ -69,7 +69,8 @@ typedef struct cg_server cg_server;
  * shapes (values per thread, rows or columns per block); by default the plan
  * times them on its own size and keeps the fastest (cached in the file named
  * by FC_TUNE_CACHE, default $HOME/.cache/fftconv/tune_sm103.txt; FC_AUTOTUNE=0
- * disables the timing).  All zero = that default. */
+ * disables the timing).  All zero = that default.  Forced shapes apply to the
+ * FP32 passes of a plan that has them (FP64 compiles one shape per size). */
 typedef struct cg_tune {
     int shape_rfwd;  /* 0: tuned; k > 0: compiled shape k-1 of the row pass A */
     int shape_col;   /* 0: tuned; k > 0: shape k-1 of the column pass B      */

@@ -512,7 +512,8 @@ void add_row(Variants& v) {
 // TMA-staged pass C (FP32): one row pair per loop iteration, M/16 threads.
 template <int M>
 void add_rinv_tma(Variants& v) {
-    if constexpr (M >= 256 && tma_smem_bytes(M) <= 200 * 1024) {
+    // whole warps per block (the block reductions shuffle across full warps)
+    if constexpr (M / 16 >= 32 && tma_smem_bytes(M) <= 200 * 1024) {
         if (v.n_rinv < Variants::kMax) v.rinv[v.n_rinv++] = KV{(const void*)k_rinv_tma<M, 16>, M / 16, 1, 16, tma_smem_bytes(M), 1};
     }
 }
@@ -1008,7 +1009,10 @@ int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStr
 template <typename T>
 int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     const int n[3] = {R.v.n_rfwd, R.v.n_colc, R.v.n_rinv};
-    const int forced[3] = {tune ? tune->shape_rfwd : 0, tune ? tune->shape_col : 0, tune ? tune->shape_rinv : 0};
+    // forced shapes select the FP32 passes of a plan that has them (FP64
+    // carries one shape per size); an FP64-only plan applies them to FP64
+    const bool apply = tune && (sizeof(T) == 4 || !(p->prec & FC_F32));
+    const int forced[3] = {apply ? tune->shape_rfwd : 0, apply ? tune->shape_col : 0, apply ? tune->shape_rinv : 0};
     const char* env = getenv("FC_AUTOTUNE");
     const bool timing = !(tune && tune->no_autotune) && !(env && !strcmp(env, "0"));
     const char* venv = getenv("FC_TUNE_VERBOSE");

@@ -122,15 +122,129 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, uns
     }
     __syncthreads();
     if (!is_last) return false;
-    __threadfence();
+    // the grid's partials are added by warp 0 alone (strided runs, one warp tree)
+    if (threadIdx.x < 32) {
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double acc = 0.0;
+            for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) acc += __ldcg(part + (size_t)b * NV + k);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+            tot[k] = acc;
+        }
+        if (threadIdx.x == 0) *cnt = 0u;
+    }
+    return true;
+}
+
+// Two-float sums for the FP32 passes.  FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this part: a tree of FP64 adds over a block's
+// partial sums cost several microseconds per pass.  The per-thread partials
+// are FP32 sums of at most 16 products; they are combined across the block
+// and the grid as unevaluated pairs hi + lo of floats with error-free
+// transformations (Knuth's TwoSum; relative error about 2^-47 per addition,
+// against 2^-53 for an FP64 add), and the totals handed to the step
+// decisions are FP64.
+
+// s + e == a + b exactly (round-to-nearest adds, never contracted).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// (hi, lo) += (h, l) in two-float arithmetic.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float h, float l) {
+    float sum, err;
+    two_sum(hi, h, sum, err);
+    err = __fadd_rn(err, __fadd_rn(lo, l));
+    hi = __fadd_rn(sum, err);
+    lo = __fsub_rn(err, __fsub_rn(hi, sum));
+}
+
+// Sum NV two-float values over the block (fixed order: warp tree, then warp
+// 0 over the warp sums).  Result valid in thread 0.  Whole warps only.
+template <int NV>
+__device__ __forceinline__ void block_sum_ff(float (&hi)[NV], float (&lo)[NV], float2 (*scratch)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float h = __shfl_down_sync(0xffffffffu, hi[k], off), l = __shfl_down_sync(0xffffffffu, lo[k], off);
+            ff_add(hi[k], lo[k], h, l);
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) scratch[warp][k] = make_float2(hi[k], lo[k]);
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const float2 w = lane < nw ? scratch[lane][k] : make_float2(0.f, 0.f);
+            hi[k] = w.x;
+            lo[k] = w.y;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float h = __shfl_down_sync(0xffffffffu, hi[k], off);
+                const float l = __shfl_down_sync(0xffffffffu, lo[k], off);
+                ff_add(hi[k], lo[k], h, l);
+            }
+        }
+    }
+}
+
+// grid_sum_last for FP32 partials: the per-block sums are published as
+// two-float pairs (part holds NV float2 per block, the room of NV doubles)
+// and the last block's warp 0 adds them in block order the same way.  tot:
+// the FP64 totals, valid in thread 0 of the last block.
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(float (&v)[NV], double* part, unsigned* cnt, double (&tot)[NV]) {
+    __shared__ float2 scratch[32][NV];
+    __shared__ bool is_last;
+    float hi[NV], lo[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double acc = 0.0;
-        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) acc += __ldcg(part + (size_t)b * NV + k);
-        tot[k] = acc;
+        hi[k] = v[k];
+        lo[k] = 0.f;
     }
-    block_sum<NV>(tot, scratch);
-    if (threadIdx.x == 0) *cnt = 0u;
+    block_sum_ff<NV>(hi, lo, scratch);
+    float2* pf = reinterpret_cast<float2*>(part);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) pf[(size_t)blockIdx.x * NV + k] = make_float2(hi[k], lo[k]);
+        __threadfence();
+        unsigned prev = atomicAdd(cnt, 1u);
+        is_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    if (threadIdx.x < 32) {
+        __threadfence();
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            hi[k] = 0.f;
+            lo[k] = 0.f;
+            for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) {
+                const float2 q = __ldcg(pf + (size_t)b * NV + k);
+                ff_add(hi[k], lo[k], q.x, q.y);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const float h = __shfl_down_sync(0xffffffffu, hi[k], off);
+                const float l = __shfl_down_sync(0xffffffffu, lo[k], off);
+                ff_add(hi[k], lo[k], h, l);
+            }
+        }
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) tot[k] = (double)hi[k] + (double)lo[k];
+            *cnt = 0u;
+        }
+    }
     return true;
 }
 
@@ -308,6 +422,7 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
 // exchanges (default: when they fit, see use_db).
 template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
 __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(RowFwdArgs<T> a) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
@@ -315,17 +430,22 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(RowFwdArgs<T> a) {
     T acc = 0, acc_rp = 0;
     rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
     pdl_leave();
+    // partial sums in the pass's precision (FP32: two-float combination,
+    // FP64: FP64), totals in FP64
     if (a.mode == RF_CG) {
-        double pv[2] = {(double)acc, (double)acc_rp}, tot[2];
+        T pv[2] = {acc, acc_rp};
+        double tot[2];
         if (grid_sum_last<2>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) {
             a.st->rr = tot[0];
             a.st->rp = tot[1];
         }
     } else if (a.mode == RF_PCG_R) {
-        double pv[1] = {(double)acc}, tot[1];
+        T pv[1] = {acc};
+        double tot[1];
         if (grid_sum_last<1>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) a.st->rr = tot[0];
     } else if (a.mode == RF_PCG_P) {
-        double pv[1] = {(double)acc_rp}, tot[1];
+        T pv[1] = {acc_rp};
+        double tot[1];
         if (grid_sum_last<1>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) a.st->rp = tot[0];
     }
 }
@@ -528,6 +648,7 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
 
 template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
 __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(RowInvArgs<T> a) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
@@ -542,7 +663,8 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(RowInvArgs<T> a) {
     }
     pdl_leave();
     if (a.mode == RI_CG) {
-        double pv[3] = {(double)s0, (double)s1, (double)s2}, tot[3];
+        T pv[3] = {s0, s1, s2};
+        double tot[3];
         if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
             cg_step_decide(a.st, tot[0], tot[1], tot[2], a.h_inner);
     } else if (a.mode == RI_RESID) {
@@ -552,7 +674,8 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(RowInvArgs<T> a) {
             a.st->warm = 0;  // every block has read it: later cycles recompute the residual
         }
     } else if (a.mode == RI_PCG_Z) {
-        double pv[1] = {(double)s0}, tot[1];
+        T pv[1] = {s0};
+        double tot[1];
         if (grid_sum_last<1>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(a.st, tot[0]);
     }
 }

@@ -72,6 +72,63 @@ __device__ __forceinline__ void sum_partials(const double* part, double (&tot)[N
     for (int k = 0; k < NV; ++k) tot[k] = bcast[k];
 }
 
+// Publish this block's NV partial sums in slot blockIdx.x of part: FP32
+// partials as two-float pairs (two_sum / ff_add), FP64 ones as doubles.
+// scratch: the block's shared [32][NV] doubles (reused as float2 pairs).
+template <int NV, typename T>
+__device__ __forceinline__ void publish_partials(const T (&v)[NV], double* part, double (*scratch)[NV]) {
+    if constexpr (sizeof(T) == 4) {
+        float hi[NV], lo[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            hi[k] = v[k];
+            lo[k] = 0.f;
+        }
+        block_sum_ff<NV>(hi, lo, reinterpret_cast<float2(*)[NV]>(scratch));
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                reinterpret_cast<float2*>(part)[(size_t)blockIdx.x * NV + k] = make_float2(hi[k], lo[k]);
+    } else {
+        double d[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) d[k] = v[k];
+        block_sum<NV>(d, scratch);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) part[(size_t)blockIdx.x * NV + k] = d[k];
+    }
+}
+
+// The grid totals of partials published by publish_partials<NV, T>, summed
+// in block order by every block (FP64 results, valid in all threads).
+template <int NV, typename T>
+__device__ __forceinline__ void total_partials(const double* part, double (&tot)[NV], double (*scratch)[NV],
+                                               double* bcast) {
+    if constexpr (sizeof(T) == 4) {
+        float hi[NV], lo[NV];
+        const float2* pf = reinterpret_cast<const float2*>(part);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            hi[k] = 0.f;
+            lo[k] = 0.f;
+            for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+                const float2 q = __ldcg(pf + (size_t)b * NV + k);
+                ff_add(hi[k], lo[k], q.x, q.y);
+            }
+        }
+        block_sum_ff<NV>(hi, lo, reinterpret_cast<float2(*)[NV]>(scratch));
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) bcast[k] = (double)hi[k] + (double)lo[k];
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < NV; ++k) tot[k] = bcast[k];
+    } else {
+        sum_partials<NV>(part, tot, scratch, bcast);
+    }
+}
+
 template <typename T>
 struct PersistArgs {
     RowFwdArgs<T> A;
@@ -115,17 +172,13 @@ __global__ void __launch_bounds__(RB*(M / EA)) k_cg_persist(PersistArgs<T> P) {
             __syncthreads();
         }
         {
-            double pv[2] = {(double)acc, (double)acc_rp};
-            block_sum<2>(pv, reinterpret_cast<double(*)[2]>(scratch));
-            if (threadIdx.x == 0) {
-                P.partA[2 * blockIdx.x] = pv[0];
-                P.partA[2 * blockIdx.x + 1] = pv[1];
-            }
+            const T pv[2] = {acc, acc_rp};
+            publish_partials<2, T>(pv, P.partA, reinterpret_cast<double(*)[2]>(scratch));
         }
         if (!(ok = grid_barrier(P.ctl))) break;
         {
             double tot[2];
-            sum_partials<2>(P.partA, tot, reinterpret_cast<double(*)[2]>(scratch), bcast);
+            total_partials<2, T>(P.partA, tot, reinterpret_cast<double(*)[2]>(scratch), bcast);
             rr = tot[0];
             rp = tot[1];
         }
@@ -142,17 +195,12 @@ __global__ void __launch_bounds__(RB*(M / EA)) k_cg_persist(PersistArgs<T> P) {
             __syncthreads();
         }
         {
-            double pv[3] = {(double)s0, (double)s1, (double)s2};
-            block_sum<3>(pv, scratch);
-            if (threadIdx.x == 0) {
-                P.partC[3 * blockIdx.x] = pv[0];
-                P.partC[3 * blockIdx.x + 1] = pv[1];
-                P.partC[3 * blockIdx.x + 2] = pv[2];
-            }
+            const T pv[3] = {s0, s1, s2};
+            publish_partials<3, T>(pv, P.partC, scratch);
         }
         if (!(ok = grid_barrier(P.ctl))) break;
         double tot[3];
-        sum_partials<3>(P.partC, tot, scratch, bcast);
+        total_partials<3, T>(P.partC, tot, scratch, bcast);
         // the step decision of cg_step_decide, taken identically in every block
         const double pq = tot[0], rq = tot[1], qq = tot[2];
         alpha = rp / pq;

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
     constexpr unsigned UNIT_BYTES = (unsigned)H * 16u;
     constexpr size_t BUF = tma_buf_bytes(M);
     static_assert(H % BK == 0 && (BK * 16) % 128 == 0, "TMA boxes must tile the pair's columns");
+    static_assert(G % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];  // aligned to 128 bytes below
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_ok;
@@ -189,11 +190,13 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
     }
     pdl_leave();  // every block still joins the grid reduction below
     if (a.mode == RI_CG) {
-        double pv[3] = {(double)s0, (double)s1, (double)s2}, tot[3];
+        float pv[3] = {s0, s1, s2};
+        double tot[3];
         if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
             cg_step_decide(a.st, tot[0], tot[1], tot[2], a.h_inner);
     } else if (a.mode == RI_PCG_Z) {
-        double pv[1] = {(double)s0}, tot[1];
+        float pv[1] = {s0};
+        double tot[1];
         if (grid_sum_last<1>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(a.st, tot[0]);
     }
 }

@@ -280,3 +280,17 @@ def test_pcg_residual_and_fewer_iterations(L):
         assert np.linalg.norm(r) / np.linalg.norm(p["b"]) <= 1e-10 * 1.01
         assert rel2(x, x_cg) <= 2 * 0.8 * L * 1e-10
         assert res["iters"] * 2 < r_cg["iters"], (res["iters"], r_cg["iters"])
+
+
+@pytest.mark.parametrize("L", [64, 128, 512])
+def test_every_pass_shape_solves(L):
+    """Each compiled shape of the row passes (whose epilogues carry the CG
+    reductions) solves the preconditioned mixed system to tolerance."""
+    p = fc_inputs.problem(L, seed=31, b_kind="normal")
+    n = fc.fftconv_plan_shapes(plan(L), fc.FC_F32)["n_shapes"]
+    for k in range(max(n[0], n[2])):
+        shapes = (min(k, n[0] - 1), 0, min(k, n[2] - 1))
+        pl = fc.fftconv_plan_create(L, fc.FC_F32 | fc.FC_F64, shapes=shapes)
+        x = dev(np.zeros(L * L))
+        r = fc.cg_solve(pl, dev(p["s"]), dev(p["b"]), x, rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True)
+        assert r["status"] == fc.FC_OK and r["true_rel_resid"] <= 1e-8, (L, shapes, r)
