@@ -24,6 +24,8 @@ struct CgState {
     double rr64, bb;     // last true residual r.r and masked b.b (FP64)
     double rtol2;        // target: rr64 <= rtol2 * bb
     double inner_rtol2;  // mixed: inner target relative to the unit right-hand side
+    double inner_goal2;  // mixed: an inner run may also stop at this fraction (squared) of
+                         // the outer target (0: never)
     double beta_carry;   // direction kept across a true-residual replacement (0: restart)
     double rz, rz_prev;  // PCG: r.z of the current and of the previous iteration
     double pshift;       // PCG: shift c of the preconditioner (C_M + c I)^-1
@@ -182,7 +184,10 @@ __device__ __forceinline__ void refine_decide(CgState* st, double rr64, double b
         st->cycle_iter = 0;
         st->inner_done = 0;
         st->sigma = s_new;
-        st->tol2 = st->mixed ? st->inner_rtol2 : st->rtol2 * bb;
+        // mixed: the inner run (scaled to a unit start) stops after its
+        // reduction inner_rtol, or as soon as it is a safe fraction below the
+        // outer target itself, when that is reached first
+        st->tol2 = st->mixed ? fmax(st->inner_rtol2, st->inner_goal2 * st->rtol2 * bb / rr64) : st->rtol2 * bb;
     }
     if (!go) st->first = 1;  // no inner run follows: the final update is a no-op
     st->finished = go ? 0 : 1;

@@ -2040,6 +2040,16 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     // solve stays accurate to 1e-5, plain FP32 CG drifts beyond about 3e-3
     const double irt = o->inner_rtol > 0 ? o->inner_rtol : (o->precond ? 1e-5 : 3e-3);
     h.inner_rtol2 = irt * irt;
+    {
+        // the fraction of the outer target at which an inner run may stop
+        // early (FC_INNER_GOAL, default 0.5; 0 turns it off)
+        static const double goal = [] {
+            const char* e = getenv("FC_INNER_GOAL");
+            const double v = e ? atof(e) : 0.5;
+            return v > 0.0 && v < 1.0 ? v : 0.0;
+        }();
+        h.inner_goal2 = goal * goal;
+    }
     h.max_iter = o->max_iter > 0 ? o->max_iter : 1000000;
     h.cycle_max = o->refine_every > 0 ? o->refine_every : 100000;
     h.max_cycles = o->max_refine > 0 ? o->max_refine : 60;
