@@ -91,7 +91,8 @@ typedef struct cg_opts {
     int max_refine;    /* cap on true-residual evaluations (0: 60)              */
     double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 1e-5 with
                           the preconditioner, 3e-3 without)                     */
-    int x0_zero;       /* 1: start from x = 0 and ignore the input x            */
+    int x0_zero;       /* 1: start from x = 0 and ignore the input x; the first
+                          true residual is then P b, taken without a product */
     int precond;       /* 1: preconditioned CG with the Fourier preconditioner
                           M^-1 = P crop (C_M + c I)^-1 pad P, C_M the padded
                           circulant of C (its spectrum, shifted), c = mean of s
@@ -123,6 +124,10 @@ typedef struct cg_result {
                               update when resid_updated is 1)                   */
     int resid_updated;     /* 1: the first true residual came from the warm-start
                               update (see cg_opts.warm_resid), not a product    */
+    int zero_start;        /* 1: the first true residual was P b (x0_zero), not a
+                              product                                           */
+    int fp64_products;     /* FP64 operator products spent on true residuals
+                              (refinements minus an updated or zero-start one)  */
     double true_rel_resid; /* ||P(b - A x)|| / ||P b|| from the last FP64 residual */
     double bnorm;          /* ||P b||                                           */
     double latency_s;      /* server: submit to completion; cg_solve: call time */
@@ -225,6 +230,55 @@ int fftconv_apply_prec(fftconv_plan *p, int prec, const void *x, void *y, fc_str
  */
 int cg_solve(fftconv_plan *p, const double *s, const double *b, double *x, const uint8_t *mask,
              const cg_opts *o, cg_result *r, fc_stream_t stream);
+
+/*
+ * cg_solve_batch -- nb independent solves of the plan's size, each as in
+ * cg_solve (Listing 2 with the same options), in one CUDA graph launch.
+ * Every pass of the operator (Section 3) runs over all nb problems at once,
+ * so small systems fill the GPU.  Each problem keeps its own state and step
+ * decisions; a problem that has converged skips the remaining passes and the
+ * loops run until the last problem finishes.  Problem k's result is the one
+ * cg_solve gives with the same launch shapes (pass C takes the thread-load
+ * shape where the plan chose the TMA-staged one).
+ *   nb    1 .. 65535 problems.
+ *   s, b  device, nb*L*L doubles: problem k at offset k*L*L.
+ *   x     device, nb*L*L doubles: in = starts (unless o->x0_zero), out = solutions.
+ *   mask  device, nb*L*L bytes (1 = active), or NULL (all active).
+ *   o     host options shared by all problems (NULL: rtol 1e-10, FC_MODE_F64).
+ *         cg_opts.warm_resid does not apply (every first residual is a
+ *         product, or P b with x0_zero).
+ *   r     host array of nb results (may be NULL).
+ * The plan owns a batch workspace (about 120 bytes per unknown and problem
+ * with FC_MODE_MIXED), allocated on first use and grown to the largest nb;
+ * its graph is rebuilt when nb changes.  The plan's own solve buffers are
+ * not touched.  Blocks the host thread until all problems end.
+ * Returns FC_OK when every problem converged, otherwise the first other
+ * status; errors: FC_EINVAL, FC_ENOMEM, FC_ECUDA.
+ */
+int cg_solve_batch(fftconv_plan *p, int nb, const double *s, const double *b, double *x,
+                   const uint8_t *mask, const cg_opts *o, cg_result *r, fc_stream_t stream);
+
+/* One group of cg_solve_groups: nb problems on plan (layout as in
+ * cg_solve_batch); r: host array of nb results or NULL. */
+typedef struct cg_batch_group {
+    fftconv_plan *plan;
+    int nb;
+    const double *s, *b;
+    double *x;
+    const uint8_t *mask;
+    cg_result *r;
+} cg_batch_group;
+
+/*
+ * cg_solve_groups -- batches of several sizes at once: each group is a
+ * cg_solve_batch on its own plan, launched on the plan's own stream after
+ * the work already queued on stream (fork), and stream waits for all of them
+ * (join), so the groups' graphs run concurrently on the device.  Each group
+ * needs a distinct plan.  Blocks the host thread until every group ends.
+ * Returns FC_OK when every problem converged, otherwise the first other
+ * status; errors: FC_EINVAL (bad group, repeated plan), FC_ENOMEM, FC_ECUDA.
+ */
+int cg_solve_groups(int ngroups, const cg_batch_group *groups, const cg_opts *o, fc_stream_t stream);
 
 /*
  * fc_masked_step -- one quasi-static breaking step (Section 2: for each step

@@ -60,14 +60,21 @@ class cg_tune(ctypes.Structure):
 
 class cg_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("refinements", ctypes.c_int),
-                ("resid_updated", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("resid_updated", ctypes.c_int), ("zero_start", ctypes.c_int), ("fp64_products", ctypes.c_int),
+                ("true_rel_resid", ctypes.c_double),
                 ("bnorm", ctypes.c_double), ("latency_s", ctypes.c_double), ("run_s", ctypes.c_double)]
 
     def as_dict(self):
         return {"status": self.status, "iters": self.iters, "refinements": self.refinements,
-                "resid_updated": self.resid_updated,
+                "resid_updated": self.resid_updated, "zero_start": self.zero_start,
+                "fp64_products": self.fp64_products,
                 "true_rel_resid": self.true_rel_resid, "bnorm": self.bnorm,
                 "latency_s": self.latency_s, "run_s": self.run_s}
+
+
+class cg_batch_group(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("nb", ctypes.c_int), ("s", ctypes.c_void_p), ("b", ctypes.c_void_p),
+                ("x", ctypes.c_void_p), ("mask", ctypes.c_void_p), ("r", ctypes.c_void_p)]
 
 
 class fc_run_result(ctypes.Structure):
@@ -107,6 +114,8 @@ def _load():
     lib.fftconv_apply.argtypes = [vp, vp, vp, vp]
     lib.fftconv_apply_prec.argtypes = [vp, i, vp, vp, vp]
     lib.cg_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
+    lib.cg_solve_batch.argtypes = [vp, i, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
+    lib.cg_solve_groups.argtypes = [i, ctypes.POINTER(cg_batch_group), ctypes.POINTER(cg_opts), vp]
     lib.fc_masked_step.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.fc_front.argtypes = [vp, vp, vp, vp, vp]
     lib.fftconv_plan_sync_mode.argtypes = [vp, i]
@@ -230,6 +239,14 @@ def fftconv_apply(plan: Plan, x, y, stream=None) -> None:
     fftconv_apply_prec(plan, prec, x, y, stream)
 
 
+def _opts(rtol, mode, max_iter=0, refine_every=0, max_refine=0, inner_rtol=0.0, x0_zero=False, precond=False,
+          warm_resid=True):
+    return cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode),
+                   refine_every=int(refine_every), max_refine=int(max_refine),
+                   inner_rtol=float(inner_rtol), x0_zero=int(bool(x0_zero)), precond=int(bool(precond)),
+                   warm_resid=0 if warm_resid else -1)
+
+
 def cg_solve(plan: Plan, s, b, x, mask=None, rtol: float = 1e-10, mode: int = FC_MODE_F64,
              max_iter: int = 0, refine_every: int = 0, max_refine: int = 0,
              inner_rtol: float = 0.0, x0_zero: bool = False, precond: bool = False, stream=None,
@@ -238,10 +255,7 @@ def cg_solve(plan: Plan, s, b, x, mask=None, rtol: float = 1e-10, mode: int = FC
     warm_resid=False always recomputes the first true residual (no update from
     the plan's previous solve)."""
     n = plan.L * plan.L
-    o = cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode),
-                refine_every=int(refine_every), max_refine=int(max_refine),
-                inner_rtol=float(inner_rtol), x0_zero=int(bool(x0_zero)), precond=int(bool(precond)),
-                warm_resid=0 if warm_resid else -1)
+    o = _opts(rtol, mode, max_iter, refine_every, max_refine, inner_rtol, x0_zero, precond, warm_resid)
     r = cg_result()
     rc = _lib.cg_solve(plan.handle, _ptr(s, torch.float64, n, "s"), _ptr(b, torch.float64, n, "b"),
                        _ptr(x, torch.float64, n, "x"), _ptr(mask, torch.uint8, n, "mask"),
@@ -251,6 +265,58 @@ def cg_solve(plan: Plan, s, b, x, mask=None, rtol: float = 1e-10, mode: int = FC
     out = r.as_dict()
     out["rc"] = rc
     return out
+
+
+def cg_solve_batch(plan: Plan, s, b, x, mask=None, rtol: float = 1e-10, mode: int = FC_MODE_F64,
+                   max_iter: int = 0, refine_every: int = 0, max_refine: int = 0, inner_rtol: float = 0.0,
+                   x0_zero: bool = False, precond: bool = False, stream=None, check: bool = False):
+    """nb solves of the plan's size in one launch: s, b, x (float64) and mask
+    (uint8, or None) hold nb*L*L elements, problem k at offset k*L*L (an
+    (nb, L, L) or (nb, L*L) tensor).  Returns (rc, list of nb result dicts)."""
+    n = plan.L * plan.L
+    if not isinstance(x, torch.Tensor) or x.numel() % n or x.numel() == 0:
+        raise ValueError(f"x must hold a positive multiple of {n} elements")
+    nb = x.numel() // n
+    o = _opts(rtol, mode, max_iter, refine_every, max_refine, inner_rtol, x0_zero, precond)
+    rs = (cg_result * nb)()
+    rc = _lib.cg_solve_batch(plan.handle, nb, _ptr(s, torch.float64, nb * n, "s"),
+                             _ptr(b, torch.float64, nb * n, "b"), _ptr(x, torch.float64, nb * n, "x"),
+                             _ptr(mask, torch.uint8, nb * n, "mask"), ctypes.byref(o), rs, _stream(stream))
+    if rc in (FC_EINVAL, FC_ECUDA, FC_ENOMEM) or (check and rc != FC_OK):
+        raise FcError(rc, "cg_solve_batch")
+    return rc, [r.as_dict() for r in rs]
+
+
+def cg_solve_groups(groups, rtol: float = 1e-10, mode: int = FC_MODE_F64, max_iter: int = 0,
+                    refine_every: int = 0, max_refine: int = 0, inner_rtol: float = 0.0, x0_zero: bool = False,
+                    precond: bool = False, stream=None, check: bool = False):
+    """Batches of several sizes at once.  groups: list of (plan, s, b, x, mask)
+    with the layout of cg_solve_batch, one distinct plan per group.  Returns
+    (rc, list of per-group lists of result dicts)."""
+    arr = (cg_batch_group * len(groups))()
+    keep = []
+    for k, (plan, s, b, x, mask) in enumerate(groups):
+        n = plan.L * plan.L
+        if not isinstance(x, torch.Tensor) or x.numel() % n or x.numel() == 0:
+            raise ValueError(f"group {k}: x must hold a positive multiple of {n} elements")
+        nb = x.numel() // n
+        rs = (cg_result * nb)()
+        keep.append(rs)
+        g = arr[k]
+        def val(ptr):
+            return None if ptr is None else ptr.value
+        g.plan = plan.handle.value
+        g.nb = nb
+        g.s = val(_ptr(s, torch.float64, nb * n, "s"))
+        g.b = val(_ptr(b, torch.float64, nb * n, "b"))
+        g.x = val(_ptr(x, torch.float64, nb * n, "x"))
+        g.mask = val(_ptr(mask, torch.uint8, nb * n, "mask"))
+        g.r = ctypes.cast(rs, ctypes.c_void_p).value
+    o = _opts(rtol, mode, max_iter, refine_every, max_refine, inner_rtol, x0_zero, precond)
+    rc = _lib.cg_solve_groups(len(groups), arr, ctypes.byref(o), _stream(stream))
+    if rc in (FC_EINVAL, FC_ECUDA, FC_ENOMEM) or (check and rc != FC_OK):
+        raise FcError(rc, "cg_solve_groups")
+    return rc, [[r.as_dict() for r in rs] for rs in keep]
 
 
 def fc_masked_step(plan: Plan, t, mask, x, removed, stream=None) -> None:

@@ -48,12 +48,35 @@ struct CgState {
     int wbad;            // the update does not apply (s or b changed, active set grew)
     unsigned wcount;     // entries of x that changed (the list holds the first kWarmMax)
     int tma_err;         // 1: a staged TMA copy never arrived (the solve ends with FC_ETIMEOUT)
-    int pad_;
+    int idle;            // 1: no inner run is in progress (batched solves: the inner passes skip
+                         // this problem)
     unsigned cntA, cntC;  // last-block counters of passes A and C
 };
 
 // Largest number of changed iterate entries the residual update takes.
 constexpr int kWarmMax = 32;
+
+// Gates of the passes of a batched solve (several problems of one size per
+// launch, blockIdx.y = problem): a block returns at entry, before any work
+// or reduction, when its problem's state says so.  Every block of a problem
+// reads the same value: the fields are written by the last block of a pass
+// only, after all blocks of that pass have arrived, or by an earlier kernel.
+enum { GATE_WARM = 1, GATE_FINISHED = 2, GATE_IDLE = 4 };
+
+__device__ __forceinline__ bool gate_closed(const CgState* st, int gate) {
+    return ((gate & GATE_WARM) && st->warm) || ((gate & GATE_FINISHED) && st->finished) ||
+           ((gate & GATE_IDLE) && st->idle);
+}
+
+// Per-problem strides of a batched launch (elements; 0 with one problem).
+// The kernels add them as index offsets (problem blockIdx.y), so a pointer
+// argument keeps its meaning as a mode flag when null.
+struct BatchStride {
+    long n;     // L*L vectors (x, r, p, q, z, s, b, mask)
+    long z;     // complex elements of the intermediate
+    long q;     // spectrum quarter (0: one spectrum shared by all problems)
+    long part;  // doubles of partial sums
+};
 
 // Pass A modes: plain input; CG update (x, r, p) + transform p; FP64 iterate
 // with the folded correction; PCG first half (x, r update, transform r);
@@ -78,6 +101,8 @@ struct RowFwdArgs {
     double* part;                // per-block partial sums
     cpx<T>* Z;                   // L x M intermediate
     const cpx<T>* tw;            // exp(-2 pi i m/M), m < M
+    int gate;                    // GATE_* bits (batched solves; 0: none)
+    BatchStride bs;              // problem blockIdx.y: vectors at + y*bs.n, Z at + y*bs.z, ...
 };
 
 template <typename T>
@@ -86,7 +111,9 @@ struct ColArgs {
     cpx<T>* Z;
     const T* Gq;                 // (M/2+1)^2 real spectrum quarter, 1/M^2 folded in
     const cpx<T>* tw;
-    const int* skip;             // non-null and nonzero: the pass does nothing (warm residual)
+    const CgState* st;           // with gate: the state whose fields may skip the pass
+    int gate;                    // GATE_* bits (GATE_WARM: the residual was updated, no product)
+    BatchStride bs;
 };
 
 template <typename T>
@@ -106,6 +133,8 @@ struct RowInvArgs {
     unsigned long long h_outer, h_inner;  // graph conditional handles (0: none)
     const cpx<T>* Z;
     const cpx<T>* tw;
+    int gate;                    // GATE_* bits (batched solves; 0: none)
+    BatchStride bs;
 };
 
 // Decide the CG step after the product q = A p of one iteration of Listing 2.
@@ -135,6 +164,7 @@ __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq
     st->beta = rr > 0.0 ? rrn / rr : 0.0;
     st->first = 0;
     st->inner_done = d;
+    st->idle = d != 0;
     if (h_inner) cudaGraphSetConditional(h_inner, d == 0 ? 1u : 0u);
 }
 
@@ -191,6 +221,7 @@ __device__ __forceinline__ void refine_decide(CgState* st, double rr64, double b
     }
     if (!go) st->first = 1;  // no inner run follows: the final update is a no-op
     st->finished = go ? 0 : 1;
+    st->idle = go ? 0 : 1;
     if (h_outer) cudaGraphSetConditional(h_outer, (unsigned)go);
     if (h_inner) cudaGraphSetConditional(h_inner, (unsigned)go);
 }

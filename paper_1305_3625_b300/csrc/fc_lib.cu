@@ -17,6 +17,7 @@
 #include <chrono>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "fc_persist.cuh"
 #include "fc_tma.cuh"
@@ -210,8 +211,12 @@ __global__ void __launch_bounds__(256) k_spectrum_quarter(int M, const cpx<doubl
 }
 
 // Last step of an inner CG run: x += alpha p (the residual is recomputed).
+// Problem blockIdx.y of a batch (vectors at stride N).
 template <typename T>
 __global__ void k_cg_final(long N, const CgState* st, T* x, const T* p) {
+    st += blockIdx.y;
+    x += blockIdx.y * N;
+    p += blockIdx.y * N;
     if (st->first) return;
     const T alpha = (T)st->alpha;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
@@ -224,9 +229,14 @@ __global__ void k_f64_to_f32(long N, const double* a, float* b) {
 }
 
 // Shift of the Fourier preconditioner: c = mean of s over active sites
-// (last block writes it).
+// (last block writes it).  Problem blockIdx.y of a batch (vectors at stride
+// N, partial sums at stride bpart).
 __global__ void __launch_bounds__(256) k_active_mean(long N, const double* s, const uint8_t* mask, double* part,
-                                                     CgState* st) {
+                                                     CgState* st, long bpart) {
+    s += blockIdx.y * N;
+    if (mask) mask += blockIdx.y * N;
+    part += blockIdx.y * bpart;
+    st += blockIdx.y;
     double v[2] = {0.0, 0.0}, tot[2];
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
         if (!mask || mask[i]) {
@@ -238,11 +248,58 @@ __global__ void __launch_bounds__(256) k_active_mean(long N, const double* s, co
 
 // Spectrum quarter of the preconditioner (C_M + c I)^-1 in the scaling of
 // the stored kernel spectrum: Gq = eig(C_M)/M^2, so Pq = 1/((M^2 Gq + c) M^2).
+// Problem blockIdx.y of a batch writes its own spectrum (stride QQ).
 template <typename T>
 __global__ void k_precond_spectrum(long QQ, double MM, const double* gq64, const CgState* st, T* pq) {
+    st += blockIdx.y;
+    pq += blockIdx.y * QQ;
     const double c = st->pshift;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < QQ; i += (long)gridDim.x * blockDim.x)
         pq[i] = (T)(1.0 / ((MM * gq64[i] + c) * MM));
+}
+
+// A solve from x = 0 needs no product for its first true residual: it is
+// r = P b.  Sets x = 0 and r = P b and hands |r|^2 = |P b|^2 to the first
+// refinement decision, as the warm-start update does (warm_used = 2 marks
+// the zero start).  Problem blockIdx.y of a batch.
+__global__ void __launch_bounds__(256) k_zero_start(long N, const double* b, const uint8_t* mask, double* x,
+                                                    double* r, double* part, long bpart, CgState* st) {
+    const long o = blockIdx.y * N;
+    b += o, x += o, r += o;
+    if (mask) mask += o;
+    part += blockIdx.y * bpart;
+    st += blockIdx.y;
+    double v[1] = {0.0}, tot[1];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const double bv = (!mask || mask[i]) ? b[i] : 0.0;
+        x[i] = 0.0;
+        r[i] = bv;
+        v[0] += bv * bv;
+    }
+    if (grid_sum_last<1>(v, part, &st->cntC, tot) && threadIdx.x == 0) {
+        st->rr64 = tot[0];
+        st->bb = tot[0];
+        st->warm = 1;
+        st->warm_used = 2;
+    }
+}
+
+// Loop control of a batched solve (one node after the deciding pass): the
+// outer loop runs while any problem is unfinished, the inner loop while any
+// problem has an inner run open.  A finished problem is idle.
+__global__ void __launch_bounds__(256) k_batch_ctl(int nb, const CgState* st, unsigned long long h_outer,
+                                                   unsigned long long h_inner) {
+    int open = 0, inner = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        open |= st[i].finished == 0;
+        inner |= st[i].idle == 0;
+    }
+    open = __syncthreads_or(open);
+    inner = __syncthreads_or(inner);
+    if (threadIdx.x == 0) {
+        if (h_outer) cudaGraphSetConditional(h_outer, open ? 1u : 0u);
+        cudaGraphSetConditional(h_inner, inner ? 1u : 0u);
+    }
 }
 
 template <typename T>
@@ -726,6 +783,7 @@ struct fftconv_plan {
     int64_t* rm_host = nullptr;  // pinned: last removed index of a fracture run
     bool blocking = false;       // waits block the host thread (event with blocking sync)
     cudaEvent_t ev_wait = nullptr;
+    struct BatchWs* batch = nullptr;  // batched solves (cg_solve_batch), made on first use
 };
 
 namespace {
@@ -740,8 +798,11 @@ int dalloc(fftconv_plan* p, void** ptr, size_t bytes) {
     return FC_OK;
 }
 
+void batch_free(fftconv_plan* p);
+
 void plan_free(fftconv_plan* p) {
     if (!p) return;
+    batch_free(p);
     for (int m = 0; m < 4; ++m) {
         if (p->gexec[m]) cudaGraphExecDestroy(p->gexec[m]);
         if (p->graph[m]) cudaGraphDestroy(p->graph[m]);
@@ -1630,13 +1691,13 @@ struct GraphBuilder {
     int rc = FC_OK;
     bool pdl = false;  // programmatic edges between consecutive passes
     template <typename... A>
-    cudaGraphNode_t kernel(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const void* f, int grid, int threads,
-                           size_t smem, const A&... args) {
+    cudaGraphNode_t kernel(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, const void* f, dim3 grid,
+                           int threads, size_t smem, const A&... args) {
         cudaGraphNode_t n = nullptr;
         if (rc) return n;
         cudaKernelNodeParams kp{};
         kp.func = (void*)f;
-        kp.gridDim = dim3(grid);
+        kp.gridDim = grid;
         kp.blockDim = dim3(threads);
         kp.sharedMemBytes = (unsigned)smem;
         void* args_[] = {(void*)&args...};
@@ -1649,7 +1710,7 @@ struct GraphBuilder {
     // pdl_enter): with pdl, a programmatic edge from the previous pass's
     // trigger port, otherwise an ordinary edge.
     template <typename... A>
-    cudaGraphNode_t pass(cudaGraph_t g, cudaGraphNode_t prev, const void* f, int grid, int threads, size_t smem,
+    cudaGraphNode_t pass(cudaGraph_t g, cudaGraphNode_t prev, const void* f, dim3 grid, int threads, size_t smem,
                          const A&... args) {
         if (!pdl) return kernel(g, &prev, 1, f, grid, threads, smem, args...);
         cudaGraphNode_t n = kernel(g, nullptr, 0, f, grid, threads, smem, args...);
@@ -1678,27 +1739,91 @@ struct GraphBuilder {
     }
 };
 
+// The buffers a solve graph works on: the plan's own workspace (one problem)
+// or a batch workspace (nb problems of the plan's size; problem k at offset
+// k * stride in every buffer and blockIdx.y = k in every pass).  Batched
+// passes are gated per problem (a finished problem skips the true-residual
+// passes, an idle one the inner passes), and the loops run while any
+// problem needs them (k_batch_ctl).
+struct SolveView {
+    int nb = 1;
+    bool batched = false;
+    BatchStride bs{};
+    double *x64 = nullptr, *r64 = nullptr, *p64v = nullptr, *q64 = nullptr, *b64 = nullptr, *s64 = nullptr;
+    double *z64 = nullptr, *pq64 = nullptr;
+    float *d32 = nullptr, *r32 = nullptr, *p32v = nullptr, *q32 = nullptr, *s32 = nullptr, *z32 = nullptr;
+    float* pq32 = nullptr;
+    uint8_t* mask = nullptr;
+    void *Z32 = nullptr, *Z64 = nullptr;
+    CgState* st = nullptr;
+    double* part = nullptr;
+    template <typename T>
+    cpx<T>* Z() const {
+        return (cpx<T>*)(sizeof(T) == 4 ? Z32 : Z64);
+    }
+    int gate_inner() const { return batched ? GATE_IDLE : 0; }
+    int gate_outer() const { return batched ? GATE_FINISHED : 0; }
+    // the kernel spectrum is one for all problems; the preconditioner's is per problem
+    BatchStride kernel_spectrum() const {
+        BatchStride b = bs;
+        b.q = 0;
+        return b;
+    }
+    dim3 grid(int gx) const { return dim3((unsigned)gx, (unsigned)nb); }
+};
+
+SolveView plan_view(fftconv_plan* p) {
+    SolveView v;
+    v.x64 = p->x64, v.r64 = p->r64, v.p64v = p->p64v, v.q64 = p->q64, v.b64 = p->b64, v.s64 = p->s64;
+    v.z64 = p->z64, v.pq64 = p->pq64;
+    v.d32 = p->d32, v.r32 = p->r32, v.p32v = p->p32v, v.q32 = p->q32, v.s32 = p->s32, v.z32 = p->z32;
+    v.pq32 = p->pq32;
+    v.mask = p->mask;
+    v.Z32 = p->p32.Z, v.Z64 = p->p64.Z;
+    v.st = p->st, v.part = p->part;
+    return v;
+}
+
+// Pass C's launch shape: the tuned one, except that batched solves take the
+// thread-load shape instead of the TMA-staged one (whose tensor map and
+// persistent grid describe one problem).
+const KV& rinv_shape(const PrecRes& R, bool batched) {
+    if (!batched || !R.rinv().tma) return R.rinv();
+    for (int k = 0; k < R.v.n_rinv; ++k)
+        if (!R.v.rinv[k].tma) return R.v.rinv[k];
+    return R.rinv();  // not reached: every size carries thread-load shapes
+}
+
 // Pass C as a graph node following prev (the TMA-staged shape gets its
 // tensor-map arguments).
 template <typename T>
 cudaGraphNode_t graph_rinv(GraphBuilder& gb, cudaGraph_t g, cudaGraphNode_t prev, fftconv_plan* p, PrecRes& R,
-                           const RowInvArgs<T>& c) {
-    const KV& kc = R.rinv();
+                           const KV& kc, const SolveView& V, const RowInvArgs<T>& c) {
     if constexpr (sizeof(T) == 4) {
         if (kc.tma) {
             const RowInvTma P = tma_args(p, R, c);
-            return gb.pass(g, prev, kc.f, R.tma_grid, kc.threads, kc.smem, P);
+            return gb.pass(g, prev, kc.f, dim3(R.tma_grid), kc.threads, kc.smem, P);
         }
     }
-    return gb.pass(g, prev, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
+    return gb.pass(g, prev, kc.f, V.grid(row_grid(p, kc)), kc.threads, kc.smem, c);
+}
+
+// After the deciding pass of a batched loop body: the loop control node.
+void batch_ctl_node(GraphBuilder& gb, cudaGraph_t g, cudaGraphNode_t prev, const SolveView& V,
+                    cudaGraphConditionalHandle h_outer, cudaGraphConditionalHandle h_inner, cudaGraphNode_t* out) {
+    const int nb = V.nb;
+    const CgState* cst = V.st;
+    const unsigned long long ho = h_outer, hi = h_inner;
+    cudaGraphNode_t n = gb.kernel(g, &prev, 1, (const void*)k_batch_ctl, dim3(1), 256, 0, nb, cst, ho, hi);
+    if (out) *out = n;
 }
 
 // Inner CG loop body (Listing 2): pass A (update + row FFT), B, C (product,
 // dot products, step decision).
 template <typename T>
-void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp, T* cq,
-                    const T* s, const double* r64_start, cudaGraphConditionalHandle h_inner) {
-    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, const SolveView& V, T* cx,
+                    T* cr, T* cp, T* cq, const T* s, const double* r64_start, cudaGraphConditionalHandle h_inner) {
+    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = rinv_shape(R, V.batched);
     RowFwdArgs<T> a{};
     a.L = p->L;
     a.mode = RF_CG;
@@ -1707,13 +1832,16 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     a.cp = cp;
     a.cq = cq;
     a.r64 = r64_start;
-    a.st = p->st;
-    a.part = p->part;
-    a.Z = (cpx<T>*)R.Z;
+    a.st = V.st;
+    a.part = V.part;
+    a.Z = V.Z<T>();
     a.tw = (const cpx<T>*)R.tws(ka.E);
-    cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
-    ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
-    cudaGraphNode_t nB = gb.pass(body, nA, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
+    a.gate = V.gate_inner();
+    a.bs = V.bs;
+    cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a);
+    ColArgs<T> b{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, V.gate_inner(),
+                 V.kernel_spectrum()};
+    cudaGraphNode_t nB = gb.pass(body, nA, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b);
     RowInvArgs<T> c{};
     c.L = p->L;
     c.mode = RI_CG;
@@ -1721,23 +1849,27 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     c.cp = cp;
     c.cr = cr;
     c.cq = cq;
-    c.mask = p->mask;
-    c.st = p->st;
-    c.part = p->part;
-    c.h_inner = h_inner;
-    c.Z = (const cpx<T>*)R.Z;
+    c.mask = V.mask;
+    c.st = V.st;
+    c.part = V.part;
+    c.h_inner = V.batched ? 0 : h_inner;
+    c.Z = V.Z<T>();
     c.tw = (const cpx<T>*)R.tws(kc.E);
-    graph_rinv<T>(gb, body, nB, p, R, c);
+    c.gate = V.gate_inner();
+    c.bs = V.bs;
+    cudaGraphNode_t nC = graph_rinv<T>(gb, body, nB, p, R, kc, V, c);
+    if (V.batched) batch_ctl_node(gb, body, nC, V, 0, h_inner, nullptr);
 }
 
 // Inner body of preconditioned CG: A1 (x, r update; transform r) -> B1 with
 // the preconditioner spectrum -> C1 (z = M^-1 r, r.z, beta) -> A2 (p = z +
 // beta p; transform p) -> B2 with the kernel spectrum -> C2 (q, step decision).
 template <typename T>
-void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, T* cx, T* cr, T* cp,
-                        T* cq, T* cz, const T* s, const T* pq, const double* r64_start,
+void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, const SolveView& V, T* cx,
+                        T* cr, T* cp, T* cq, T* cz, const T* s, const T* pq, const double* r64_start,
                         cudaGraphConditionalHandle h_inner) {
-    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = rinv_shape(R, V.batched);
+    const int gi = V.gate_inner();
     RowFwdArgs<T> a1{};
     a1.L = p->L;
     a1.mode = RF_PCG_R;
@@ -1746,37 +1878,43 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a1.cp = cp;
     a1.cq = cq;
     a1.r64 = r64_start;
-    a1.st = p->st;
-    a1.part = p->part;
-    a1.Z = (cpx<T>*)R.Z;
+    a1.st = V.st;
+    a1.part = V.part;
+    a1.Z = V.Z<T>();
     a1.tw = (const cpx<T>*)R.tws(ka.E);
-    cudaGraphNode_t n1 = gb.kernel(body, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a1);
-    ColArgs<T> b1{p->L, (cpx<T>*)R.Z, pq, (const cpx<T>*)R.tws(kb.E)};
-    cudaGraphNode_t n2 = gb.pass(body, n1, kb.f, col_grid(p, kb), kb.threads, kb.smem, b1);
+    a1.gate = gi;
+    a1.bs = V.bs;
+    cudaGraphNode_t n1 = gb.kernel(body, nullptr, 0, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a1);
+    ColArgs<T> b1{p->L, V.Z<T>(), pq, (const cpx<T>*)R.tws(kb.E), V.st, gi, V.bs};
+    cudaGraphNode_t n2 = gb.pass(body, n1, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b1);
     RowInvArgs<T> c1{};
     c1.L = p->L;
     c1.mode = RI_PCG_Z;
     c1.cr = cr;
     c1.cz = cz;
-    c1.mask = p->mask;
-    c1.st = p->st;
-    c1.part = p->part;
-    c1.Z = (const cpx<T>*)R.Z;
+    c1.mask = V.mask;
+    c1.st = V.st;
+    c1.part = V.part;
+    c1.Z = V.Z<T>();
     c1.tw = (const cpx<T>*)R.tws(kc.E);
-    cudaGraphNode_t n3 = graph_rinv<T>(gb, body, n2, p, R, c1);
+    c1.gate = gi;
+    c1.bs = V.bs;
+    cudaGraphNode_t n3 = graph_rinv<T>(gb, body, n2, p, R, kc, V, c1);
     RowFwdArgs<T> a2{};
     a2.L = p->L;
     a2.mode = RF_PCG_P;
     a2.cp = cp;
     a2.cr = cr;
     a2.cz = cz;
-    a2.st = p->st;
-    a2.part = p->part;
-    a2.Z = (cpx<T>*)R.Z;
+    a2.st = V.st;
+    a2.part = V.part;
+    a2.Z = V.Z<T>();
     a2.tw = (const cpx<T>*)R.tws(ka.E);
-    cudaGraphNode_t n4 = gb.pass(body, n3, ka.f, row_grid(p, ka), ka.threads, ka.smem, a2);
-    ColArgs<T> b2{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
-    cudaGraphNode_t n5 = gb.pass(body, n4, kb.f, col_grid(p, kb), kb.threads, kb.smem, b2);
+    a2.gate = gi;
+    a2.bs = V.bs;
+    cudaGraphNode_t n4 = gb.pass(body, n3, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a2);
+    ColArgs<T> b2{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, gi, V.kernel_spectrum()};
+    cudaGraphNode_t n5 = gb.pass(body, n4, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b2);
     RowInvArgs<T> c2{};
     c2.L = p->L;
     c2.mode = RI_CG;
@@ -1784,20 +1922,25 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c2.cp = cp;
     c2.cr = cr;
     c2.cq = cq;
-    c2.mask = p->mask;
-    c2.st = p->st;
-    c2.part = p->part;
-    c2.h_inner = h_inner;
-    c2.Z = (const cpx<T>*)R.Z;
+    c2.mask = V.mask;
+    c2.st = V.st;
+    c2.part = V.part;
+    c2.h_inner = V.batched ? 0 : h_inner;
+    c2.Z = V.Z<T>();
     c2.tw = (const cpx<T>*)R.tws(kc.E);
-    graph_rinv<T>(gb, body, n5, p, R, c2);
+    c2.gate = gi;
+    c2.bs = V.bs;
+    cudaGraphNode_t n6 = graph_rinv<T>(gb, body, n5, p, R, kc, V, c2);
+    if (V.batched) batch_ctl_node(gb, body, n6, V, 0, h_inner, nullptr);
 }
 
-// Build the solve graph for one mode:
+// Build the solve graph for one mode on the buffers of V:
 //   [prologue] -> while(outer) { A64 (fold correction, mask, FFT x) -> B64 ->
 //                                C64 (true residual, decide) ->
 //                                while(inner) { A -> B -> C } -> final }
-int build_graph_with(fftconv_plan* p, int mode, bool precond, bool pdl) {
+// (batched: a loop control node after C64 and after each inner body).
+int build_graph_with(fftconv_plan* p, const SolveView& V, int mode, bool precond, bool pdl, cudaGraph_t* gout,
+                     cudaGraphExec_t* eout) {
     GraphBuilder gb;
     gb.pdl = pdl;
     cudaGraph_t g = nullptr;
@@ -1813,35 +1956,37 @@ int build_graph_with(fftconv_plan* p, int mode, bool precond, bool pdl) {
     }
     int ndeps = 0;
     if (mixed) {
-        // FP32 copy of the diagonal for the inner products
-        const double* sa = p->s64;
-        float* sb = p->s32;
-        nPro = gb.kernel(g, nullptr, 0, (const void*)k_f64_to_f32, grid_1d(N, 256), 256, 0, N, sa, sb);
+        // FP32 copy of the diagonal for the inner products (all problems)
+        const double* sa = V.s64;
+        float* sb = V.s32;
+        const long NA = N * V.nb;
+        nPro = gb.kernel(g, nullptr, 0, (const void*)k_f64_to_f32, dim3(grid_1d(NA, 256)), 256, 0, NA, sa, sb);
         ndeps = 1;
     }
     if (precond) {
         // preconditioner shift c = mean active s, then its spectrum quarter
-        const double* sa = p->s64;
-        const uint8_t* mk = p->mask;
-        double* pt = p->part;
-        CgState* cst = p->st;
+        const double* sa = V.s64;
+        const uint8_t* mk = V.mask;
+        double* pt = V.part;
+        CgState* cst = V.st;
+        const long bpart = V.bs.part;
         int gm = grid_1d(N, 256);
         if (gm > 512) gm = 512;
         if (gm > 3 * (p->L + 1) / 2) gm = 3 * (p->L + 1) / 2;  // the partial-sum buffer holds 3 (L+1) doubles
-        cudaGraphNode_t nm = gb.kernel(g, ndeps ? &nPro : nullptr, ndeps, (const void*)k_active_mean, gm, 256, 0, N,
-                                       sa, mk, pt, cst);
+        cudaGraphNode_t nm = gb.kernel(g, ndeps ? &nPro : nullptr, ndeps, (const void*)k_active_mean, V.grid(gm), 256,
+                                       0, N, sa, mk, pt, cst, bpart);
         const long QQ = (long)(p->M / 2 + 1) * (p->M / 2 + 1);
         const double MM = (double)p->M * (double)p->M;
         const double* g64 = (const double*)p->p64.Gq;
-        const CgState* ccst = p->st;
+        const CgState* ccst = V.st;
         if (mixed) {
-            float* pq = p->pq32;
-            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<float>, grid_1d(QQ, 256), 256, 0, QQ, MM,
-                             g64, ccst, pq);
+            float* pq = V.pq32;
+            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<float>, V.grid(grid_1d(QQ, 256)), 256, 0,
+                             QQ, MM, g64, ccst, pq);
         } else {
-            double* pq = p->pq64;
-            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<double>, grid_1d(QQ, 256), 256, 0, QQ, MM,
-                             g64, ccst, pq);
+            double* pq = V.pq64;
+            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<double>, V.grid(grid_1d(QQ, 256)), 256, 0,
+                             QQ, MM, g64, ccst, pq);
         }
         ndeps = 1;
     }
@@ -1855,63 +2000,64 @@ int build_graph_with(fftconv_plan* p, int mode, bool precond, bool pdl) {
         RowFwdArgs<double> a{};
         a.L = p->L;
         a.mode = RF_XUPD;
-        a.x64 = p->x64;
-        a.d32 = mixed ? p->d32 : nullptr;
-        a.mask = p->mask;
-        a.st = p->st;
-        a.part = p->part;
-        a.Z = (cpx<double>*)p->p64.Z;
+        a.x64 = V.x64;
+        a.d32 = mixed ? V.d32 : nullptr;
+        a.mask = V.mask;
+        a.st = V.st;
+        a.part = V.part;
+        a.Z = V.Z<double>();
         a.tw = (const cpx<double>*)p->p64.tws(ka.E);
+        a.gate = V.gate_outer();
+        a.bs = V.bs;
         // the mask is applied to x in the same pass (x = 0 off the active set)
-        a.cq = nullptr;
-        a.cp = nullptr;
-        a.cr = nullptr;
-        a.cx = nullptr;
-        a.r64 = nullptr;
-        a.x = nullptr;
-        cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, ka.f, row_grid(p, ka), ka.threads, ka.smem, a);
-        ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq,
-                          (const cpx<double>*)p->p64.tws(kb.E), &p->st->warm};
-        cudaGraphNode_t nB = gb.pass(outer, nA, kb.f, col_grid(p, kb), kb.threads, kb.smem, b);
+        cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a);
+        ColArgs<double> b{p->L, V.Z<double>(), (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tws(kb.E), V.st,
+                          GATE_WARM | V.gate_outer(), V.kernel_spectrum()};
+        cudaGraphNode_t nB = gb.pass(outer, nA, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b);
         RowInvArgs<double> c{};
         c.L = p->L;
         c.mode = RI_RESID;
-        c.mask = p->mask;
-        c.x64 = p->x64;
-        c.b64 = p->b64;
-        c.s64 = p->s64;
-        c.r64 = p->r64;
-        c.st = p->st;
-        c.part = p->part;
-        c.h_outer = h_outer;
-        c.h_inner = h_inner;
-        c.Z = (const cpx<double>*)p->p64.Z;
+        c.mask = V.mask;
+        c.x64 = V.x64;
+        c.b64 = V.b64;
+        c.s64 = V.s64;
+        c.r64 = V.r64;
+        c.st = V.st;
+        c.part = V.part;
+        c.h_outer = V.batched ? 0 : h_outer;
+        c.h_inner = V.batched ? 0 : h_inner;
+        c.Z = V.Z<double>();
         c.tw = (const cpx<double>*)p->p64.tws(kc.E);
-        cudaGraphNode_t nC = gb.pass(outer, nB, kc.f, row_grid(p, kc), kc.threads, kc.smem, c);
+        c.gate = V.gate_outer();
+        c.bs = V.bs;
+        cudaGraphNode_t nC = gb.pass(outer, nB, kc.f, V.grid(row_grid(p, kc)), kc.threads, kc.smem, c);
+        if (V.batched) batch_ctl_node(gb, outer, nC, V, h_outer, h_inner, &nC);
         cudaGraphNode_t nInner = nullptr;
         cudaGraph_t inner = gb.while_node(outer, &nC, 1, h_inner, &nInner);
         if (!gb.rc) {
             if (mixed && precond)
-                add_inner_body_pcg<float>(gb, inner, p, p->p32, p->d32, p->r32, p->p32v, p->q32, p->z32, p->s32,
-                                          p->pq32, p->r64, h_inner);
+                add_inner_body_pcg<float>(gb, inner, p, p->p32, V, V.d32, V.r32, V.p32v, V.q32, V.z32, V.s32, V.pq32,
+                                          V.r64, h_inner);
             else if (precond)
-                add_inner_body_pcg<double>(gb, inner, p, p->p64, p->x64, p->r64, p->p64v, p->q64, p->z64, p->s64,
-                                           p->pq64, nullptr, h_inner);
+                add_inner_body_pcg<double>(gb, inner, p, p->p64, V, V.x64, V.r64, V.p64v, V.q64, V.z64, V.s64,
+                                           V.pq64, nullptr, h_inner);
             else if (mixed)
-                add_inner_body<float>(gb, inner, p, p->p32, p->d32, p->r32, p->p32v, p->q32, p->s32, p->r64, h_inner);
+                add_inner_body<float>(gb, inner, p, p->p32, V, V.d32, V.r32, V.p32v, V.q32, V.s32, V.r64, h_inner);
             else
-                add_inner_body<double>(gb, inner, p, p->p64, p->x64, p->r64, p->p64v, p->q64, p->s64, nullptr,
+                add_inner_body<double>(gb, inner, p, p->p64, V, V.x64, V.r64, V.p64v, V.q64, V.s64, nullptr,
                                        h_inner);
         }
-        const CgState* cst = p->st;
+        const CgState* cst = V.st;
         if (mixed) {
-            float* fx = p->d32;
-            const float* fp = p->p32v;
-            gb.kernel(outer, &nInner, 1, (const void*)k_cg_final<float>, grid_1d(N, 256), 256, 0, N, cst, fx, fp);
+            float* fx = V.d32;
+            const float* fp = V.p32v;
+            gb.kernel(outer, &nInner, 1, (const void*)k_cg_final<float>, V.grid(grid_1d(N, 256)), 256, 0, N, cst, fx,
+                      fp);
         } else {
-            double* fx = p->x64;
-            const double* fp = p->p64v;
-            gb.kernel(outer, &nInner, 1, (const void*)k_cg_final<double>, grid_1d(N, 256), 256, 0, N, cst, fx, fp);
+            double* fx = V.x64;
+            const double* fp = V.p64v;
+            gb.kernel(outer, &nInner, 1, (const void*)k_cg_final<double>, V.grid(grid_1d(N, 256)), 256, 0, N, cst,
+                      fx, fp);
         }
     }
     if (gb.rc) {
@@ -1924,16 +2070,22 @@ int build_graph_with(fftconv_plan* p, int mode, bool precond, bool pdl) {
         cudaGraphDestroy(g);
         return set_cuda_err(e, "cudaGraphInstantiate");
     }
-    p->graph[mode + 2 * precond] = g;
-    p->gexec[mode + 2 * precond] = ex;
+    *gout = g;
+    *eout = ex;
     return FC_OK;
 }
 
 // The solve graph with programmatic edges between passes where the driver
 // accepts them inside the conditional bodies, else with ordinary edges.
+int build_graph_view(fftconv_plan* p, const SolveView& V, int mode, bool precond, cudaGraph_t* g,
+                     cudaGraphExec_t* ex) {
+    if (pdl_on() && build_graph_with(p, V, mode, precond, true, g, ex) == FC_OK) return FC_OK;
+    return build_graph_with(p, V, mode, precond, false, g, ex);
+}
+
 int build_graph(fftconv_plan* p, int mode, bool precond) {
-    if (pdl_on() && build_graph_with(p, mode, precond, true) == FC_OK) return FC_OK;
-    return build_graph_with(p, mode, precond, false);
+    const int gi = mode + 2 * precond;
+    return build_graph_view(p, plan_view(p), mode, precond, &p->graph[gi], &p->gexec[gi]);
 }
 
 }  // namespace
@@ -1957,7 +2109,7 @@ int launch_resid_chain(fftconv_plan* p, bool mixed, cudaStream_t st) {
     int rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, st, a);
     if (rc) return rc;
     ColArgs<double> b{p->L, (cpx<double>*)p->p64.Z, (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tws(kb.E),
-                      &p->st->warm};
+                      p->st, GATE_WARM};
     rc = launch(kb.f, col_grid(p, kb), kb.threads, kb.smem, st, b);
     if (rc) return rc;
     RowInvArgs<double> c{};
@@ -2010,6 +2162,57 @@ extern "C" int fftconv_plan_sync_mode(fftconv_plan* p, int blocking) {
     return FC_OK;
 }
 
+namespace {
+
+// Blocks of k_zero_start for one problem (its partial sums fit the plan's
+// 3 (L+1) doubles).
+int zero_start_grid(const fftconv_plan* p) {
+    int g = grid_1d(p->N, 256);
+    if (g > 3 * (p->L + 1)) g = 3 * (p->L + 1);
+    return g;
+}
+
+// The counts of a finished solve's state.
+void fill_result(const CgState& f, cg_result* r) {
+    r->status = f.status;
+    r->iters = f.iter;
+    r->refinements = f.cycles;
+    r->resid_updated = f.warm_used == 1;
+    r->zero_start = f.warm_used == 2;
+    r->fp64_products = f.cycles - (f.warm_used != 0 ? 1 : 0);
+    r->true_rel_resid = f.bb > 0 ? sqrt(f.rr64 / f.bb) : 0.0;
+    r->bnorm = sqrt(f.bb);
+}
+
+// Initial state of a solve with options o.
+int init_state(const cg_opts* o, CgState* h) {
+    *h = CgState{};
+    h->rtol2 = o->rtol * o->rtol;
+    // default inner reduction per refinement cycle: the preconditioned FP32
+    // solve stays accurate to 1e-5, plain FP32 CG drifts beyond about 3e-3
+    const double irt = o->inner_rtol > 0 ? o->inner_rtol : (o->precond ? 1e-5 : 3e-3);
+    h->inner_rtol2 = irt * irt;
+    {
+        // the fraction of the outer target at which an inner run may stop
+        // early (FC_INNER_GOAL, default 0.5; 0 turns it off)
+        static const double goal = [] {
+            const char* e = getenv("FC_INNER_GOAL");
+            const double v = e ? atof(e) : 0.5;
+            return v > 0.0 && v < 1.0 ? v : 0.0;
+        }();
+        h->inner_goal2 = goal * goal;
+    }
+    h->max_iter = o->max_iter > 0 ? o->max_iter : 1000000;
+    h->cycle_max = o->refine_every > 0 ? o->refine_every : 100000;
+    h->max_cycles = o->max_refine > 0 ? o->max_refine : 60;
+    h->mixed = o->mode == FC_MODE_MIXED;
+    h->sigma = 0.0;
+    h->first = 1;
+    return FC_OK;
+}
+
+}  // namespace
+
 extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, double* x, const uint8_t* mask,
                         const cg_opts* o, cg_result* r, fc_stream_t stream) {
     if (!p || !s || !b || !x) return FC_EINVAL;
@@ -2034,28 +2237,8 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
         int rc = build_graph(p, mode, precond);
         if (rc) return rc;
     }
-    CgState h{};
-    h.rtol2 = o->rtol * o->rtol;
-    // default inner reduction per refinement cycle: the preconditioned FP32
-    // solve stays accurate to 1e-5, plain FP32 CG drifts beyond about 3e-3
-    const double irt = o->inner_rtol > 0 ? o->inner_rtol : (o->precond ? 1e-5 : 3e-3);
-    h.inner_rtol2 = irt * irt;
-    {
-        // the fraction of the outer target at which an inner run may stop
-        // early (FC_INNER_GOAL, default 0.5; 0 turns it off)
-        static const double goal = [] {
-            const char* e = getenv("FC_INNER_GOAL");
-            const double v = e ? atof(e) : 0.5;
-            return v > 0.0 && v < 1.0 ? v : 0.0;
-        }();
-        h.inner_goal2 = goal * goal;
-    }
-    h.max_iter = o->max_iter > 0 ? o->max_iter : 1000000;
-    h.cycle_max = o->refine_every > 0 ? o->refine_every : 100000;
-    h.max_cycles = o->max_refine > 0 ? o->max_refine : 60;
-    h.mixed = mode == FC_MODE_MIXED;
-    h.sigma = 0.0;
-    h.first = 1;
+    CgState h;
+    init_state(o, &h);
     *p->st_host = h;
     FC_CK(cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st));
     // inputs into the plan's buffers (the graph is built on them); after a
@@ -2075,14 +2258,17 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     } else {
         FC_CK(cudaMemcpyAsync(p->s64, s, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         FC_CK(cudaMemcpyAsync(p->b64, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-        if (o->x0_zero)
-            FC_CK(cudaMemsetAsync(p->x64, 0, sizeof(double) * N, st));
-        else
-            FC_CK(cudaMemcpyAsync(p->x64, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+        if (!o->x0_zero) FC_CK(cudaMemcpyAsync(p->x64, x, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
         if (mask) {
             FC_CK(cudaMemcpyAsync(p->mask, mask, N, cudaMemcpyDeviceToDevice, st));
         } else {
             k_fill_u8<<<grid_1d(N, 256), 256, 0, st>>>(N, p->mask, 1);
+            FC_CK(cudaGetLastError());
+        }
+        if (o->x0_zero) {
+            // x = 0: the first true residual is P b, no product
+            k_zero_start<<<zero_start_grid(p), 256, 0, st>>>(N, p->b64, p->mask, p->x64, p->r64, p->part, 0,
+                                                             p->st);
             FC_CK(cudaGetLastError());
         }
     }
@@ -2114,16 +2300,289 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     // decision finished the solve
     p->warm_ok = f.finished && (f.status == FC_OK || f.status == FC_ENOCONV);
     if (r) {
-        r->status = f.status;
-        r->iters = f.iter;
-        r->refinements = f.cycles;
-        r->resid_updated = f.warm_used;
-        r->true_rel_resid = f.bb > 0 ? sqrt(f.rr64 / f.bb) : 0.0;
-        r->bnorm = sqrt(f.bb);
+        fill_result(f, r);
         r->latency_s = r->run_s =
             std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call).count();
     }
     return f.status;
+}
+
+// ------------------------------------------------------ batched solves --
+//
+// cg_solve_batch: nb independent systems of the plan's size in one graph
+// launch.  Every pass runs over all problems at once (blockIdx.y = problem),
+// so small systems fill the GPU that one of them alone leaves idle.  Each
+// problem keeps its own state and decisions; a problem that converged skips
+// the remaining passes, and the loops run until the last problem is done.
+// The arithmetic of each problem is that of cg_solve with the same launch
+// shapes (the thread-load pass C in place of the TMA-staged one).
+
+struct BatchWs {
+    int cap = 0;          // problems the buffers hold
+    bool has64 = false;   // FP64 inner vectors (FP64-mode batches) allocated
+    bool has32 = false;   // FP32 inner vectors (mixed batches) allocated
+    SolveView v;
+    CgState* st_host = nullptr;  // pinned, cap states
+    cudaGraph_t graph[4] = {};
+    cudaGraphExec_t gexec[4] = {};
+    int g_nb[4] = {};
+    cudaStream_t stream = nullptr;  // own stream: groups of cg_solve_groups run concurrently
+    cudaEvent_t ev = nullptr;
+    size_t bytes = 0;
+    std::vector<void*> blocks;
+};
+
+namespace {
+
+void batch_graphs_free(BatchWs* w) {
+    for (int m = 0; m < 4; ++m) {
+        if (w->gexec[m]) cudaGraphExecDestroy(w->gexec[m]);
+        if (w->graph[m]) cudaGraphDestroy(w->graph[m]);
+        w->gexec[m] = nullptr;
+        w->graph[m] = nullptr;
+        w->g_nb[m] = 0;
+    }
+}
+
+void batch_buffers_free(BatchWs* w) {
+    batch_graphs_free(w);
+    for (void* q : w->blocks) cudaFree(q);
+    w->blocks.clear();
+    if (w->st_host) cudaFreeHost(w->st_host);
+    w->st_host = nullptr;
+    w->v = SolveView{};
+    w->cap = 0;
+    w->has64 = w->has32 = false;
+    w->bytes = 0;
+}
+
+void batch_free(fftconv_plan* p) {
+    BatchWs* w = p->batch;
+    if (!w) return;
+    batch_buffers_free(w);
+    if (w->ev) cudaEventDestroy(w->ev);
+    if (w->stream) cudaStreamDestroy(w->stream);
+    delete w;
+    p->batch = nullptr;
+}
+
+template <typename P>
+int balloc(BatchWs* w, P** ptr, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        set_cuda_err(e, "cudaMalloc(batch)");
+        return FC_ENOMEM;
+    }
+    w->blocks.push_back(q);
+    w->bytes += bytes;
+    *ptr = (P*)q;
+    return FC_OK;
+}
+
+// Buffers for nb problems in the given mode (grown, never shrunk; graphs
+// are rebuilt after a re-allocation).
+int batch_reserve(fftconv_plan* p, int nb, bool mixed) {
+    if (!p->batch) {
+        p->batch = new (std::nothrow) BatchWs();
+        if (!p->batch) return FC_ENOMEM;
+        FC_CK(cudaStreamCreateWithFlags(&p->batch->stream, cudaStreamNonBlocking));
+        FC_CK(cudaEventCreateWithFlags(&p->batch->ev, cudaEventDisableTiming));
+    }
+    BatchWs* w = p->batch;
+    const bool need64 = !mixed, need32 = mixed;
+    if (w->cap >= nb && (!need64 || w->has64) && (!need32 || w->has32)) return FC_OK;
+    const int cap = nb > w->cap ? nb : w->cap;
+    const bool h64 = w->has64 || need64, h32 = w->has32 || need32;
+    cudaDeviceSynchronize();  // no graph of this workspace may still run
+    batch_buffers_free(w);
+    const long N = p->N, Q = p->M / 2 + 1, QQ = Q * Q;
+    const long zs = (long)(p->M / 2) * p->L;
+    const long ps = 3 * (long)(p->L + 1);
+    const size_t n = (size_t)cap;
+    SolveView& v = w->v;
+    v.nb = cap;
+    v.batched = true;
+    v.bs = BatchStride{N, zs, QQ, ps};
+    int rc = FC_OK;
+    auto A = [&](auto** ptr, size_t bytes) {
+        if (!rc) rc = balloc(w, ptr, bytes);
+    };
+    A(&v.x64, 8 * n * N);
+    A(&v.r64, 8 * n * N);
+    A(&v.b64, 8 * n * N);
+    A(&v.s64, 8 * n * N);
+    A(&v.mask, n * N);
+    A(&v.Z64, 16 * n * zs);
+    A(&v.st, sizeof(CgState) * n);
+    A(&v.part, 8 * n * ps);
+    if (h64) {
+        A(&v.p64v, 8 * n * N);
+        A(&v.q64, 8 * n * N);
+        A(&v.z64, 8 * n * N);
+        A(&v.pq64, 8 * n * QQ);
+    }
+    if (h32) {
+        A(&v.d32, 4 * n * N);
+        A(&v.r32, 4 * n * N);
+        A(&v.p32v, 4 * n * N);
+        A(&v.q32, 4 * n * N);
+        A(&v.s32, 4 * n * N);
+        A(&v.z32, 4 * n * N);
+        A(&v.pq32, 4 * n * QQ);
+        A(&v.Z32, 8 * n * zs);
+    }
+    if (!rc && cudaMallocHost(&w->st_host, sizeof(CgState) * n) != cudaSuccess)
+        rc = set_cuda_err(cudaGetLastError(), "cudaMallocHost(batch states)");
+    if (!rc && cudaMemset(v.st, 0, sizeof(CgState) * n) != cudaSuccess)
+        rc = set_cuda_err(cudaGetLastError(), "cudaMemset(batch states)");
+    if (rc) {
+        batch_buffers_free(w);
+        return rc;
+    }
+    w->cap = cap;
+    w->has64 = h64;
+    w->has32 = h32;
+    return FC_OK;
+}
+
+// Queue one batch on stream st: inputs in, the solve graph, x and the
+// states out.  The caller waits on st and then reads the states.
+int batch_enqueue(fftconv_plan* p, int nb, const double* s, const double* b, double* x, const uint8_t* mask,
+                  const cg_opts* o, cudaStream_t st) {
+    const int mode = o->mode;
+    const bool mixed = mode == FC_MODE_MIXED, precond = o->precond != 0;
+    int rc = batch_reserve(p, nb, mixed);
+    if (rc) return rc;
+    BatchWs* w = p->batch;
+    const int gi = mode + 2 * (precond ? 1 : 0);
+    if (w->gexec[gi] && w->g_nb[gi] != nb) {
+        cudaGraphExecDestroy(w->gexec[gi]);
+        cudaGraphDestroy(w->graph[gi]);
+        w->gexec[gi] = nullptr;
+        w->graph[gi] = nullptr;
+    }
+    if (!w->gexec[gi]) {
+        SolveView V = w->v;
+        V.nb = nb;
+        rc = build_graph_view(p, V, mode, precond, &w->graph[gi], &w->gexec[gi]);
+        if (rc) return rc;
+        w->g_nb[gi] = nb;
+    }
+    const SolveView& v = w->v;
+    const long N = p->N;
+    const size_t nN = (size_t)nb * N;
+    CgState h;
+    init_state(o, &h);
+    for (int k = 0; k < nb; ++k) w->st_host[k] = h;
+    FC_CK(cudaMemcpyAsync(v.st, w->st_host, sizeof(CgState) * nb, cudaMemcpyHostToDevice, st));
+    FC_CK(cudaMemcpyAsync(v.s64, s, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(v.b64, b, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    if (mask) {
+        FC_CK(cudaMemcpyAsync(v.mask, mask, nN, cudaMemcpyDeviceToDevice, st));
+    } else {
+        k_fill_u8<<<grid_1d((long)nN, 256), 256, 0, st>>>((long)nN, v.mask, 1);
+        FC_CK(cudaGetLastError());
+    }
+    if (o->x0_zero) {
+        k_zero_start<<<dim3(zero_start_grid(p), nb), 256, 0, st>>>(N, v.b64, v.mask, v.x64, v.r64, v.part,
+                                                                   v.bs.part, v.st);
+        FC_CK(cudaGetLastError());
+    } else {
+        FC_CK(cudaMemcpyAsync(v.x64, x, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    }
+    FC_CK(cudaGraphLaunch(w->gexec[gi], st));
+    FC_CK(cudaMemcpyAsync(x, v.x64, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(w->st_host, v.st, sizeof(CgState) * nb, cudaMemcpyDeviceToHost, st));
+    return FC_OK;
+}
+
+int batch_check(const fftconv_plan* p, int nb, const double* s, const double* b, double* x, const cg_opts* o) {
+    if (!p || nb < 1 || nb > 65535 || !s || !b || !x || !o) return FC_EINVAL;
+    if (o->mode != FC_MODE_F64 && o->mode != FC_MODE_MIXED) return FC_EINVAL;
+    if (!(p->prec & FC_F64)) return FC_EINVAL;
+    if (o->mode == FC_MODE_MIXED && !(p->prec & FC_F32)) return FC_EINVAL;
+    if (!(o->rtol >= 0.0)) return FC_EINVAL;
+    return FC_OK;
+}
+
+// Results of a finished batch; returns the first status that is not FC_OK.
+int batch_results(fftconv_plan* p, int nb, cg_result* r, double seconds) {
+    int status = FC_OK;
+    for (int k = 0; k < nb; ++k) {
+        const CgState& f = p->batch->st_host[k];
+        if (status == FC_OK && f.status != FC_OK) status = f.status;
+        if (r) {
+            fill_result(f, r + k);
+            r[k].latency_s = r[k].run_s = seconds;
+        }
+    }
+    return status;
+}
+
+}  // namespace
+
+extern "C" int cg_solve_batch(fftconv_plan* p, int nb, const double* s, const double* b, double* x,
+                              const uint8_t* mask, const cg_opts* o, cg_result* r, fc_stream_t stream) {
+    cg_opts def{};
+    def.rtol = 1e-10;
+    def.mode = FC_MODE_F64;
+    if (!o) o = &def;
+    int rc = batch_check(p, nb, s, b, x, o);
+    if (rc) return rc;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    rc = batch_enqueue(p, nb, s, b, x, mask, o, st);
+    if (rc) return rc;
+    FC_CK(wait_stream(p, st));
+    return batch_results(p, nb, r,
+                         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+}
+
+extern "C" int cg_solve_groups(int ngroups, const cg_batch_group* g, const cg_opts* o, fc_stream_t stream) {
+    if (ngroups < 1 || !g) return FC_EINVAL;
+    cg_opts def{};
+    def.rtol = 1e-10;
+    def.mode = FC_MODE_F64;
+    if (!o) o = &def;
+    for (int i = 0; i < ngroups; ++i) {
+        int rc = batch_check(g[i].plan, g[i].nb, g[i].s, g[i].b, g[i].x, o);
+        if (rc) return rc;
+        for (int j = 0; j < i; ++j)
+            if (g[j].plan == g[i].plan) return FC_EINVAL;  // one workspace per plan
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = (cudaStream_t)stream;
+    // fork: every group on its plan's own stream after the caller's work
+    for (int i = 0; i < ngroups; ++i) {
+        int rc = batch_reserve(g[i].plan, g[i].nb, o->mode == FC_MODE_MIXED);
+        if (rc) return rc;
+    }
+    cudaEvent_t fork = g[0].plan->batch->ev;
+    FC_CK(cudaEventRecord(fork, st));
+    for (int i = 0; i < ngroups; ++i) {
+        BatchWs* w = g[i].plan->batch;
+        FC_CK(cudaStreamWaitEvent(w->stream, fork, 0));
+    }
+    for (int i = 0; i < ngroups; ++i) {
+        BatchWs* w = g[i].plan->batch;
+        int rc = batch_enqueue(g[i].plan, g[i].nb, g[i].s, g[i].b, g[i].x, g[i].mask, o, w->stream);
+        if (rc) return rc;
+    }
+    // join
+    for (int i = 0; i < ngroups; ++i) {
+        BatchWs* w = g[i].plan->batch;
+        FC_CK(cudaEventRecord(w->ev, w->stream));
+        FC_CK(cudaStreamWaitEvent(st, w->ev, 0));
+    }
+    FC_CK(wait_stream(g[0].plan, st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int status = FC_OK;
+    for (int i = 0; i < ngroups; ++i) {
+        const int si = batch_results(g[i].plan, g[i].nb, g[i].r, secs);
+        if (status == FC_OK) status = si;
+    }
+    return status;
 }
 
 extern "C" int fc_masked_step(fftconv_plan* p, const double* t, uint8_t* mask, double* x, int64_t* removed,
@@ -2156,7 +2615,7 @@ extern "C" int fc_fracture_run(fftconv_plan* p, const double* s, const double* b
         const int rc = cg_solve(p, s, b, x, mask, o, &r, stream);  // returns with the stream drained
         if (rc == FC_EINVAL || rc == FC_ECUDA || rc == FC_ENOMEM) return rc;
         acc.iters += r.iters;
-        acc.fp64_products += r.refinements - r.resid_updated;
+        acc.fp64_products += r.fp64_products;
         acc.resid_updated += r.resid_updated;
         if (rc != FC_OK) {
             acc.status = rc;

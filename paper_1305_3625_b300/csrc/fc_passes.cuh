@@ -334,13 +334,14 @@ __device__ __forceinline__ T pass_a_value(int mode, const T* __restrict__ xin, T
 
 // Pass A's inputs of one thread: elements j + e*G (e < E/2, the rest is the
 // zero padding) of rows r0 and r0 + 1, packed as v[e] = row r0 + i row r0+1.
+// vo: the problem's offset in the vectors (batched launches).
 template <typename T, int M, int E>
 __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xin, T* __restrict__ cx,
                                               T* __restrict__ cr, T* __restrict__ cp, const T* __restrict__ cq,
                                               const T* __restrict__ cz, const double* __restrict__ r64,
                                               double* __restrict__ x64, const float* __restrict__ d32,
                                               const uint8_t* __restrict__ mask, const AScal<T>& sc, int j, int r0,
-                                              int L, cpx<T> (&v)[E], T& acc, T& acc_rp) {
+                                              int L, size_t vo, cpx<T> (&v)[E], T& acc, T& acc_rp) {
     constexpr int G = M / E;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -348,11 +349,11 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
         const int n = j + e * G;
         if (e < E / 2 && n < L) {  // n >= M/2 >= L for e >= E/2: the zero padding
             if (r0 < L)
-                v[e].x = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask, (size_t)r0 * L + n, sc,
+                v[e].x = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask, vo + (size_t)r0 * L + n, sc,
                                       acc, acc_rp);
             if (r0 + 1 < L)
-                v[e].y = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask, (size_t)(r0 + 1) * L + n,
-                                      sc, acc, acc_rp);
+                v[e].y = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask,
+                                      vo + (size_t)(r0 + 1) * L + n, sc, acc, acc_rp);
         }
     }
 }
@@ -360,26 +361,27 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
 // ------------------------------------------------------------ pass A ----
 
 template <typename T>
-__device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a) {
+__device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a, const CgState* st) {
     AScal<T> sc{0, 0, 0, 0, 1.0, 0.0};
     if (a.mode == RF_CG || a.mode == RF_PCG_R || a.mode == RF_PCG_P) {
-        sc.first = a.st->first;
-        sc.alpha = (T)a.st->alpha;
-        sc.beta = (T)a.st->beta;
-        sc.bcarry = a.mode == RF_CG ? (T)a.st->beta_carry : (T)0;
-        if (a.r64) sc.inv_sigma = 1.0 / a.st->sigma;
+        sc.first = st->first;
+        sc.alpha = (T)st->alpha;
+        sc.beta = (T)st->beta;
+        sc.bcarry = a.mode == RF_CG ? (T)st->beta_carry : (T)0;
+        if (a.r64) sc.inv_sigma = 1.0 / st->sigma;
     } else if (a.mode == RF_XUPD) {
-        sc.sig = a.st->sigma;  // scale of the inner run that produced d32
+        sc.sig = st->sigma;  // scale of the inner run that produced d32
     }
     return sc;
 }
 
 // One unit of pass A: RB row pairs starting at pair unit*RB, G = M/E threads
 // per pair.  Adds this thread's r.r and r.p to acc, acc_rp.  Leaves shared
-// memory in use: the caller synchronises before the block reuses it.
+// memory in use: the caller synchronises before the block reuses it.  vo, zo:
+// the problem's offsets in the vectors and the intermediate.
 template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
 __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm, T& acc,
-                                          T& acc_rp) {
+                                          T& acc_rp, size_t vo = 0, size_t zo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;  // shared elements per pair
@@ -389,8 +391,8 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
     const int r0 = (unit * RB + pl) * 2;
 
     C v[E];
-    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, L, v, acc,
-                           acc_rp);
+    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, L, vo, v,
+                           acc, acc_rp);
     C* g0 = sm + pl * GS;
     fft_stages<T, M, E, false, DB, 0>(v, j, g0, g0 + SEG, a.tw);
     C* wp = g0 + NB * SEG + spad(j);
@@ -414,48 +416,53 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
             const C z = sg[spad(kx)], zc = sg[spad(M - kx)];
             out = (r & 1) ? C{(z.y + zc.y) * half, (zc.x - z.x) * half} : C{(z.x + zc.x) * half, (z.y - zc.y) * half};
         }
-        if (row < L) stc(a.Z + (size_t)kx * L + row, out);
+        if (row < L) stc(a.Z + zo + (size_t)kx * L + row, out);
     }
 }
 
 // MINB: blocks per SM the register allocation must allow; DB: double-buffered
 // exchanges (default: when they fit, see use_db).
 template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
-__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(RowFwdArgs<T> a) {
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a) {
     static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];
+    CgState* const st = a.st + blockIdx.y;  // problem blockIdx.y of a batched launch
     pdl_enter();
-    if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
-    const AScal<T> sc = ascal_from_state(a);
+    if (a.gate && gate_closed(st, a.gate)) return;
+    if (a.mode == RF_XUPD && st->warm) return;  // residual already updated: no product
+    const AScal<T> sc = ascal_from_state(a, st);
     T acc = 0, acc_rp = 0;
-    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
+    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp,
+                               (size_t)blockIdx.y * a.bs.n, (size_t)blockIdx.y * a.bs.z);
     pdl_leave();
     // partial sums in the pass's precision (FP32: two-float combination,
     // FP64: FP64), totals in FP64
+    double* const part = a.part + blockIdx.y * a.bs.part;
     if (a.mode == RF_CG) {
         T pv[2] = {acc, acc_rp};
         double tot[2];
-        if (grid_sum_last<2>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) {
-            a.st->rr = tot[0];
-            a.st->rp = tot[1];
+        if (grid_sum_last<2>(pv, part, &st->cntA, tot) && threadIdx.x == 0) {
+            st->rr = tot[0];
+            st->rp = tot[1];
         }
     } else if (a.mode == RF_PCG_R) {
         T pv[1] = {acc};
         double tot[1];
-        if (grid_sum_last<1>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) a.st->rr = tot[0];
+        if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rr = tot[0];
     } else if (a.mode == RF_PCG_P) {
         T pv[1] = {acc_rp};
         double tot[1];
-        if (grid_sum_last<1>(pv, a.part, &a.st->cntA, tot) && threadIdx.x == 0) a.st->rp = tot[0];
+        if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rp = tot[0];
     }
 }
 
 // ------------------------------------------------------------ pass B ----
 
 // One unit of pass B: CB columns starting at column unit*CB, G = M/E threads
-// per column (j fastest).  Unit 0 holds the packed column 0.
+// per column (j fastest).  Unit 0 holds the packed column 0.  zo, qo: the
+// problem's offsets in the intermediate and the spectrum.
 template <typename T, int M, int E, int CB, bool DB = use_db<T, M, CB>()>
-__device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>* sm) {
+__device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>* sm, size_t zo = 0, size_t qo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, Q = M / 2 + 1, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;
@@ -463,7 +470,8 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
     const int t = threadIdx.x, j = t % G, c = t / G;
     const int L = a.L;
     const int kx = unit * CB + c;
-    C* col = a.Z + (size_t)kx * L;
+    C* col = a.Z + zo + (size_t)kx * L;
+    const T* const Gq = a.Gq + qo;
 
     C v[E];
 #pragma unroll
@@ -486,12 +494,12 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
                 const int ky = j + e * G;
                 const int fy = ky <= H ? ky : M - ky;
                 const C pc = conjc(seg[spad((M - ky) & (M - 1))]);
-                const T g0 = __ldg(a.Gq + fy), gN = __ldg(a.Gq + (size_t)H * Q + fy);
+                const T g0 = __ldg(Gq + fy), gN = __ldg(Gq + (size_t)H * Q + fy);
                 const T sp = (g0 + gN) * (T)0.5, sd = (g0 - gN) * (T)0.5;
                 v[e] = C{v[e].x * sp + pc.x * sd, v[e].y * sp + pc.y * sd};
             }
         } else {
-            const T* gk = a.Gq + (size_t)kx * Q;
+            const T* gk = Gq + (size_t)kx * Q;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int ky = j + e * G;
@@ -502,7 +510,7 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
         }
         __syncthreads();
     } else {
-        const T* gk = a.Gq + (size_t)kx * Q;  // Ghat[ky][kx] = Ghat[kx][ky]: contiguous in ky
+        const T* gk = Gq + (size_t)kx * Q;  // Ghat[ky][kx] = Ghat[kx][ky]: contiguous in ky
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int ky = j + e * G;
@@ -520,11 +528,12 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
 }
 
 template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
-__global__ void __launch_bounds__(CB*(M / E), MINB) k_colc(ColArgs<T> a) {
+__global__ void __launch_bounds__(CB*(M / E), MINB) k_colc(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
-    if (a.skip && *a.skip) return;
-    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    if (a.gate && gate_closed(a.st + blockIdx.y, a.gate)) return;
+    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * a.bs.z,
+                               (size_t)blockIdx.y * a.bs.q);
     pdl_leave();
 }
 
@@ -566,34 +575,35 @@ __device__ __forceinline__ void pass_c_value(int mode, T* __restrict__ y, const 
 }
 
 // Pass C's outputs of one thread: elements j + e*G < L (e < E/2, the crop)
-// of rows r0 (v[e].x) and r0 + 1 (v[e].y).
+// of rows r0 (v[e].x) and r0 + 1 (v[e].y); vo: the problem's vector offset.
 template <typename T, int M, int E>
 __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, const T* __restrict__ s,
                                                const T* __restrict__ cp, const T* __restrict__ cr,
                                                T* __restrict__ cq, T* __restrict__ cz,
                                                const uint8_t* __restrict__ mask, const double* __restrict__ x64,
                                                const double* __restrict__ b64, const double* __restrict__ s64,
-                                               double* __restrict__ r64, int j, int r0, int L, const cpx<T> (&v)[E],
-                                               T& s0, T& s1, T& s2) {
+                                               double* __restrict__ r64, int j, int r0, int L, size_t vo,
+                                               const cpx<T> (&v)[E], T& s0, T& s1, T& s2) {
     constexpr int G = M / E;
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
         const int n = j + e * G;
         if (n < L) {
             if (r0 < L)
-                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, (size_t)r0 * L + n, v[e].x, s0, s1,
-                             s2);
+                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, vo + (size_t)r0 * L + n, v[e].x, s0,
+                             s1, s2);
             if (r0 + 1 < L)
-                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, (size_t)(r0 + 1) * L + n, v[e].y,
-                             s0, s1, s2);
+                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, vo + (size_t)(r0 + 1) * L + n,
+                             v[e].y, s0, s1, s2);
         }
     }
 }
 
 // One unit of pass C: RB row pairs starting at pair unit*RB.  Adds this
-// thread's partial sums to s0, s1, s2.
+// thread's partial sums to s0, s1, s2.  vo, zo: the problem's offsets.
 template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
-__device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, T& s0, T& s1, T& s2) {
+__device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, T& s0, T& s1, T& s2,
+                                          size_t vo = 0, size_t zo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;
@@ -611,7 +621,7 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
         const int idx = t + q * NT;
         const int r = idx % (2 * RB), kx = idx / (2 * RB);
         const int row = row_base + r;
-        const C y = row < L ? ldc_cg(a.Z + (size_t)kx * L + row) : C{0, 0};
+        const C y = row < L ? ldc_cg(a.Z + zo + (size_t)kx * L + row) : C{0, 0};
         sm[(r >> 1) * GS + (r & 1) * HS + spad(kx)] = y;
     }
     __syncthreads();
@@ -642,41 +652,45 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
     if constexpr (!DB) __syncthreads();
     // with two buffers the first exchange writes buffer 1 while buffer 0 is still being read
     fft_stages<T, M, E, true, DB, DB ? 1 : 0>(v, j, g0, g0 + SEG, a.tw);
-    pass_c_outputs<T, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j, r0, L, v,
-                            s0, s1, s2);
+    pass_c_outputs<T, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j, r0, L, vo,
+                            v, s0, s1, s2);
 }
 
 template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
-__global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(RowInvArgs<T> a) {
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a) {
     static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];
+    CgState* const st = a.st + blockIdx.y;  // problem blockIdx.y of a batched launch
     pdl_enter();
+    if (a.gate && gate_closed(st, a.gate)) return;
     T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
     // warm residual: r64 and its sums (rr64, bb) are already in place, and
     // block 0 alone hands them to the decision
-    const bool warm = a.mode == RI_RESID && a.st->warm;
+    const bool warm = a.mode == RI_RESID && st->warm;
     if (!warm) {
-        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
+        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2,
+                                   (size_t)blockIdx.y * a.bs.n, (size_t)blockIdx.y * a.bs.z);
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-        s0 = (T)a.st->rr64;
-        s1 = (T)a.st->bb;
+        s0 = (T)st->rr64;
+        s1 = (T)st->bb;
     }
     pdl_leave();
+    double* const part = a.part + blockIdx.y * a.bs.part;
     if (a.mode == RI_CG) {
         T pv[3] = {s0, s1, s2};
         double tot[3];
-        if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
-            cg_step_decide(a.st, tot[0], tot[1], tot[2], a.h_inner);
+        if (grid_sum_last<3>(pv, part, &st->cntC, tot) && threadIdx.x == 0)
+            cg_step_decide(st, tot[0], tot[1], tot[2], a.h_inner);
     } else if (a.mode == RI_RESID) {
         double pv[2] = {(double)s0, (double)s1}, tot[2];
-        if (grid_sum_last<2>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) {
-            refine_decide(a.st, tot[0], tot[1], a.h_outer, a.h_inner);
-            a.st->warm = 0;  // every block has read it: later cycles recompute the residual
+        if (grid_sum_last<2>(pv, part, &st->cntC, tot) && threadIdx.x == 0) {
+            refine_decide(st, tot[0], tot[1], a.h_outer, a.h_inner);
+            st->warm = 0;  // every block has read it: later cycles recompute the residual
         }
     } else if (a.mode == RI_PCG_Z) {
         T pv[1] = {s0};
         double tot[1];
-        if (grid_sum_last<1>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(a.st, tot[0]);
+        if (grid_sum_last<1>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(st, tot[0]);
     }
 }
 

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
         __syncthreads();  // staged values consumed: the buffer becomes the exchange buffer
         fft_stages<float, M, E, true, false, 0>(v, j, buf[cur], buf[cur], a.tw);
         pass_c_outputs<float, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j,
-                                    2 * u, L, v, s0, s1, s2);
+                                    2 * u, L, 0, v, s0, s1, s2);
         __syncthreads();  // exchanges done: the buffer may receive the copy issued next
     }
     if (!ok && j == 0) {

@@ -1,0 +1,176 @@
+"""Batched solves (cg_solve_batch, cg_solve_groups): nb problems of one size
+per launch, each against the same problem solved alone by cg_solve with the
+same launch shapes (bitwise), and against the oracle's dense solves."""
+import numpy as np
+import pytest
+import torch
+
+import fc_inputs
+import oracle
+import paper_1305_3625_b300 as fc
+from gpu_util import dev, host, rel2
+
+pytestmark = pytest.mark.gpu
+
+MODES = [(fc.FC_MODE_F64, False), (fc.FC_MODE_F64, True), (fc.FC_MODE_MIXED, False), (fc.FC_MODE_MIXED, True)]
+_plans = {}
+
+
+def plan(L):
+    """Standard shapes (index 0) and the per-pass graph loop, so that a
+    problem solved alone runs exactly the kernels of the batched launch."""
+    if L not in _plans:
+        _plans[L] = fc.fftconv_plan_create(L, fc.FC_F32 | fc.FC_F64, shapes=(0, 0, 0), persistent=-1)
+    return _plans[L]
+
+
+def problems(L, nb, seed0, masked=False, b_kind="normal"):
+    ps = [fc_inputs.problem(L, seed=seed0 + k, b_kind=b_kind) for k in range(nb)]
+    s = np.stack([p["s"] for p in ps])
+    b = np.stack([p["b"] for p in ps])
+    mask = None
+    if masked:
+        rng = np.random.default_rng(seed0)
+        mask = (rng.random((nb, L * L)) >= 0.1).astype(np.uint8)
+    return s, b, mask
+
+
+def solve_alone(L, s, b, mask, mode, precond, rtol, x0=None):
+    x = dev(np.zeros(L * L) if x0 is None else x0)
+    m = None if mask is None else dev(mask, torch.uint8)
+    r = fc.cg_solve(plan(L), dev(s), dev(b), x, mask=m, rtol=rtol, mode=mode, precond=precond,
+                    x0_zero=x0 is None, warm_resid=False)
+    return host(x), r
+
+
+def rtol_of(mode):
+    return 1e-11 if mode == fc.FC_MODE_F64 else 1e-9
+
+
+@pytest.mark.parametrize("mode,precond", MODES)
+@pytest.mark.parametrize("L", [16, 33, 100])
+def test_batch_equals_solves_alone(L, mode, precond):
+    """Every problem of the batch: bitwise the iterate, iterations and
+    refinements of the same problem solved alone (the problems converge
+    after different numbers of iterations, masked and unmasked)."""
+    nb = 5
+    rtol = rtol_of(mode)
+    s, b, mask = problems(L, nb, 100 * L, masked=(L == 33))
+    # spread the conditioning: problem k's diagonal scaled by 4^-k
+    s = s * (0.25 ** np.arange(nb))[:, None]
+    x = dev(np.zeros((nb, L * L)))
+    rc, rs = fc.cg_solve_batch(plan(L), dev(s), dev(b), x, mask=None if mask is None else dev(mask, torch.uint8),
+                               rtol=rtol, mode=mode, precond=precond, x0_zero=True)
+    assert rc == fc.FC_OK
+    xb = host(x)
+    iters = set()
+    for k in range(nb):
+        xa, ra = solve_alone(L, s[k], b[k], None if mask is None else mask[k], mode, precond, rtol)
+        r = rs[k]
+        assert r["status"] == ra["status"] == fc.FC_OK
+        assert (r["iters"], r["refinements"], r["fp64_products"]) == (ra["iters"], ra["refinements"],
+                                                                     ra["fp64_products"])
+        assert r["zero_start"] == 1 and r["fp64_products"] == r["refinements"] - 1
+        assert r["true_rel_resid"] == ra["true_rel_resid"] and r["true_rel_resid"] <= rtol
+        assert np.array_equal(xb[k], xa)
+        iters.add(r["iters"])
+    assert len(iters) > 1  # the problems did not all stop together
+
+
+@pytest.mark.parametrize("mode,precond", [(fc.FC_MODE_F64, False), (fc.FC_MODE_MIXED, True)])
+def test_batch_matches_dense(mode, precond):
+    L, nb = 12, 3
+    s, b, mask = problems(L, nb, 7, masked=True)
+    x = dev(np.zeros((nb, L * L)))
+    rtol = 1e-12 if mode == fc.FC_MODE_F64 else 1e-10
+    rc, rs = fc.cg_solve_batch(plan(L), dev(s), dev(b), x, mask=dev(mask, torch.uint8), rtol=rtol, mode=mode,
+                               precond=precond, x0_zero=True)
+    assert rc == fc.FC_OK
+    xb = host(x)
+    for k in range(nb):
+        A = oracle.dense_operator(L, s[k])
+        act = np.flatnonzero(mask[k])
+        want = np.zeros(L * L)
+        want[act] = np.linalg.solve(A[np.ix_(act, act)], b[k][act])
+        assert rel2(xb[k], want) <= 100 * rtol
+        assert np.all(xb[k][mask[k] == 0] == 0.0)
+
+
+def test_warm_starts_zero_rhs_and_sizes():
+    """Given starts (no zero start), a problem with b = 0 (finished at its
+    first residual), and batch sizes that change between calls (graph
+    rebuilt) on one plan."""
+    L = 24
+    rtol = 1e-10
+    for nb in (3, 6, 1, 6):
+        s, b, _ = problems(L, nb, 40 + nb)
+        b[0] = 0.0
+        x0 = np.random.default_rng(nb).standard_normal((nb, L * L)) * 0.1
+        x0[0] = 0.0
+        x = dev(x0)
+        rc, rs = fc.cg_solve_batch(plan(L), dev(s), dev(b), x, rtol=rtol, mode=fc.FC_MODE_MIXED, precond=True)
+        assert rc == fc.FC_OK
+        xb = host(x)
+        assert np.all(xb[0] == 0.0) and rs[0]["refinements"] == 1 and rs[0]["iters"] == 0
+        assert rs[0]["zero_start"] == 0 and rs[0]["fp64_products"] == 1
+        for k in range(1, nb):
+            xa, ra = solve_alone(L, s[k], b[k], None, fc.FC_MODE_MIXED, True, rtol, x0=x0[k])
+            assert np.array_equal(xb[k], xa) and rs[k]["iters"] == ra["iters"]
+
+
+def test_groups_of_several_sizes():
+    """cg_solve_groups runs batches of three sizes concurrently: each group's
+    results are those of cg_solve_batch on the same plan."""
+    sizes = {20: 4, 37: 3, 64: 5}
+    groups, want = [], {}
+    for L, nb in sizes.items():
+        s, b, _ = problems(L, nb, 300 + L)
+        x = dev(np.zeros((nb, L * L)))
+        groups.append((plan(L), dev(s), dev(b), x, None))
+        xw = dev(np.zeros((nb, L * L)))
+        rc, rs = fc.cg_solve_batch(plan(L), dev(s), dev(b), xw, rtol=1e-9, mode=fc.FC_MODE_MIXED, precond=True,
+                                   x0_zero=True)
+        assert rc == fc.FC_OK
+        want[L] = (host(xw), rs)
+    rc, out = fc.cg_solve_groups(groups, rtol=1e-9, mode=fc.FC_MODE_MIXED, precond=True, x0_zero=True)
+    assert rc == fc.FC_OK
+    for (L, nb), g, rs in zip(sizes.items(), groups, out):
+        assert len(rs) == nb
+        assert np.array_equal(host(g[3]), want[L][0])
+        assert [r["iters"] for r in rs] == [r["iters"] for r in want[L][1]]
+        assert all(r["status"] == fc.FC_OK and r["true_rel_resid"] <= 1e-9 for r in rs)
+
+
+def test_zero_start_equals_explicit_zero():
+    """x0_zero takes P b as the first residual without a product; a start
+    from an explicit zero vector computes it by the FP64 product, whose
+    result is exactly P b as well (its norm summed in another order): the two
+    solves agree to the tolerance with the same work."""
+    L = 48
+    p = fc_inputs.problem(L, seed=4, b_kind="normal")
+    mask = (np.random.default_rng(1).random(L * L) >= 0.2).astype(np.uint8)
+    out = []
+    for x0_zero in (True, False):
+        x = dev(np.zeros(L * L))
+        r = fc.cg_solve(plan(L), dev(p["s"]), dev(p["b"]), x, mask=dev(mask, torch.uint8), rtol=1e-10,
+                        mode=fc.FC_MODE_MIXED, precond=True, x0_zero=x0_zero, warm_resid=False)
+        assert r["status"] == fc.FC_OK
+        assert r["zero_start"] == int(x0_zero) and r["fp64_products"] == r["refinements"] - int(x0_zero)
+        out.append((host(x), r["iters"], r["refinements"]))
+    assert rel2(out[0][0], out[1][0]) <= 1e-8
+    assert abs(out[0][1] - out[1][1]) <= 1 and out[0][2] == out[1][2]
+
+
+def test_invalid_batches():
+    L = 8
+    s = dev(np.ones(2 * L * L))
+    with pytest.raises(ValueError):
+        fc.cg_solve_batch(plan(L), s, s, dev(np.zeros(L * L + 1)))
+    with pytest.raises(fc.FcError):
+        fc.cg_solve_batch(plan(L), s, s, dev(np.zeros(2 * L * L)), mode=7)
+    x = dev(np.zeros(2 * L * L))
+    with pytest.raises(fc.FcError):  # one plan in two groups
+        fc.cg_solve_groups([(plan(L), s, s, x, None), (plan(L), s, s, x, None)])
+    p64 = fc.fftconv_plan_create(L, fc.FC_F64)
+    with pytest.raises(fc.FcError):  # mixed needs an FP32 side
+        fc.cg_solve_batch(p64, s, s, x, mode=fc.FC_MODE_MIXED)
