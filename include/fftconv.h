@@ -375,13 +375,18 @@ typedef struct cg_request {
  * device (the paper has no serving layer; this is the many-solve workload
  * around its Listing 2 solver).
  *   mem_budget_bytes  device memory the server may hold for plans and staging.
- *   max_slots         concurrent solves (worker slots, each with its own
- *                     non-blocking stream), 1..256.
+ *   max_slots         concurrent batched solves (worker slots, each with its
+ *                     own non-blocking stream), 1..256.
  *   stream            unused (each slot owns a stream).
  * A request is admitted when a slot is free and its plan fits the budget
- * (idle plans of other sizes are evicted if needed); plans stay resident and
- * are reused by later requests of the same L.  Work of different requests
- * overlaps on the device; each result depends only on its own inputs.
+ * (idle plans of other sizes are evicted if needed); the slot also takes the
+ * queued requests of the same L, mode and preconditioning (up to 64, each
+ * reserving its share of the plan's batch workspace within the budget) and
+ * runs them as one cg_solve_batch launch with each request's own tolerance,
+ * from x = 0.  Plans stay resident and are reused by later requests of the
+ * same L.  Work of different slots overlaps on the device; each result
+ * depends only on its own inputs (it equals cg_solve_batch of that request
+ * alone on a plan of its size).
  */
 int cg_server_create(cg_server **sv, size_t mem_budget_bytes, int max_slots, fc_stream_t stream);
 
@@ -396,6 +401,9 @@ int cg_poll(cg_server *sv, uint64_t ticket, cg_result *r, int *done);
 
 /* Memory held now and at peak, queued requests, resident plans. */
 int cg_server_stats(cg_server *sv, size_t *used, size_t *peak, int *queued, int *plans);
+
+/* Batched solves run so far, the requests they held, the largest batch. */
+int cg_server_batches(cg_server *sv, long long *batches, long long *solves, int *max_batch);
 
 /* Stop the workers (running solves finish), free plans and buffers. */
 int cg_server_destroy(cg_server *sv);

@@ -126,6 +126,8 @@ def _load():
     lib.cg_batch_submit.argtypes = [vp, ctypes.POINTER(cg_request), ctypes.POINTER(ctypes.c_uint64)]
     lib.cg_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(cg_result), ctypes.POINTER(i)]
     lib.cg_server_stats.argtypes = [vp, ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(i), ctypes.POINTER(i)]
+    lib.cg_server_batches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                      ctypes.POINTER(i)]
     lib.cg_server_destroy.argtypes = [vp]
     return lib
 
@@ -484,6 +486,15 @@ def cg_server_stats(sv: Server) -> dict:
     if rc != FC_OK:
         raise FcError(rc, "cg_server_stats")
     return {"used": used.value, "peak": peak.value, "queued": q.value, "plans": pl.value}
+
+
+def cg_server_batches(sv: Server) -> dict:
+    """Batched solves the server ran, the requests they held, the largest batch."""
+    nb, ns, mx = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int()
+    rc = _lib.cg_server_batches(sv.handle, ctypes.byref(nb), ctypes.byref(ns), ctypes.byref(mx))
+    if rc != FC_OK:
+        raise FcError(rc, "cg_server_batches")
+    return {"batches": nb.value, "solves": ns.value, "max_batch": mx.value}
 
 
 def cg_server_destroy(sv: Server) -> None:

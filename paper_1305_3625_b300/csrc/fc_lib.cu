@@ -799,6 +799,7 @@ int dalloc(fftconv_plan* p, void** ptr, size_t bytes) {
 }
 
 void batch_free(fftconv_plan* p);
+size_t batch_bytes_of(const fftconv_plan* p);
 
 void plan_free(fftconv_plan* p) {
     if (!p) return;
@@ -1457,7 +1458,7 @@ extern "C" int fftconv_plan_info(const fftconv_plan* p, int* L, int* M, int* pre
     if (L) *L = p->L;
     if (M) *M = p->M;
     if (prec) *prec = p->prec;
-    if (bytes) *bytes = p->bytes;
+    if (bytes) *bytes = p->bytes + batch_bytes_of(p);
     return FC_OK;
 }
 
@@ -2356,6 +2357,8 @@ void batch_buffers_free(BatchWs* w) {
     w->bytes = 0;
 }
 
+size_t batch_bytes_of(const fftconv_plan* p) { return p->batch ? p->batch->bytes : 0; }
+
 void batch_free(fftconv_plan* p) {
     BatchWs* w = p->batch;
     if (!w) return;
@@ -2449,7 +2452,7 @@ int batch_reserve(fftconv_plan* p, int nb, bool mixed) {
 // Queue one batch on stream st: inputs in, the solve graph, x and the
 // states out.  The caller waits on st and then reads the states.
 int batch_enqueue(fftconv_plan* p, int nb, const double* s, const double* b, double* x, const uint8_t* mask,
-                  const cg_opts* o, cudaStream_t st) {
+                  const cg_opts* o, cudaStream_t st, const double* rtols = nullptr) {
     const int mode = o->mode;
     const bool mixed = mode == FC_MODE_MIXED, precond = o->precond != 0;
     int rc = batch_reserve(p, nb, mixed);
@@ -2474,7 +2477,10 @@ int batch_enqueue(fftconv_plan* p, int nb, const double* s, const double* b, dou
     const size_t nN = (size_t)nb * N;
     CgState h;
     init_state(o, &h);
-    for (int k = 0; k < nb; ++k) w->st_host[k] = h;
+    for (int k = 0; k < nb; ++k) {
+        w->st_host[k] = h;
+        if (rtols) w->st_host[k].rtol2 = rtols[k] * rtols[k];
+    }
     FC_CK(cudaMemcpyAsync(v.st, w->st_host, sizeof(CgState) * nb, cudaMemcpyHostToDevice, st));
     FC_CK(cudaMemcpyAsync(v.s64, s, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     FC_CK(cudaMemcpyAsync(v.b64, b, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
@@ -2533,6 +2539,22 @@ extern "C" int cg_solve_batch(fftconv_plan* p, int nb, const double* s, const do
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t st = (cudaStream_t)stream;
     rc = batch_enqueue(p, nb, s, b, x, mask, o, st);
+    if (rc) return rc;
+    FC_CK(wait_stream(p, st));
+    return batch_results(p, nb, r,
+                         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+}
+
+// The solve server's entry (fc_server.cu): cg_solve_batch with a tolerance
+// per problem (host array of nb values).
+int fc_batch_solve_rtols(fftconv_plan* p, int nb, const double* s, const double* b, double* x, const cg_opts* o,
+                         const double* rtols, cg_result* r, cudaStream_t st) {
+    int rc = batch_check(p, nb, s, b, x, o);
+    if (rc) return rc;
+    for (int k = 0; k < nb; ++k)
+        if (!(rtols[k] >= 0.0)) return FC_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    rc = batch_enqueue(p, nb, s, b, x, nullptr, o, st, rtols);
     if (rc) return rc;
     FC_CK(wait_stream(p, st));
     return batch_results(p, nb, r,

@@ -2,14 +2,18 @@
 //
 // Requests (L, mode, rtol, host s and b) are queued by cg_batch_submit and
 // admitted when a worker slot is free and the device-memory budget holds the
-// request's plan.  Each slot is a host thread with its own non-blocking CUDA
-// stream; slots run their solves concurrently, so requests that arrive while
-// others are on the GPU overlap with them.  Plans (spectrum, tables,
-// workspaces) stay resident and are reused by later requests of the same L;
-// idle plans of other sizes are evicted when the budget requires it.  Each
-// result is the same whether a request runs alone or in a mix: a solve's
-// arithmetic depends only on its own inputs and its plan (reductions run in a
-// fixed order inside each solve).
+// request's plan.  A slot that admits a request also takes the other queued
+// requests of the same size, mode and preconditioning (up to kMaxBatch, as
+// the budget allows) and runs them as one batched solve (cg_solve_batch's
+// graph: every pass over all of them at once, each with its own tolerance).
+// Each slot is a host thread with its own non-blocking CUDA stream; slots
+// run their batches concurrently, so requests that arrive while others are
+// on the GPU overlap with them.  Plans (spectrum, tables, workspaces) stay
+// resident and are reused by later requests of the same L; idle plans of
+// other sizes are evicted when the budget requires it.  Each result is the
+// same whether a request runs alone or in a mix: a problem's arithmetic in a
+// batched solve depends only on its own inputs and its plan's launch shapes
+// (reductions run in a fixed order inside each problem), not on the batch.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -26,7 +30,13 @@
 
 #include "../../include/fftconv.h"
 
+// cg_solve_batch with a tolerance per problem (fc_lib.cu).
+int fc_batch_solve_rtols(fftconv_plan* p, int nb, const double* s, const double* b, double* x, const cg_opts* o,
+                         const double* rtols, cg_result* r, cudaStream_t st);
+
 namespace {
+
+constexpr int kMaxBatch = 64;  // requests one slot takes into one batched solve
 
 double now_s() {
     using namespace std::chrono;
@@ -37,7 +47,8 @@ struct Req {
     uint64_t ticket = 0;
     cg_request rq{};
     std::vector<double> s, b;  // host copies taken at submit
-    size_t est = 0;            // device bytes the request's plan needs
+    size_t est = 0;            // device bytes reserved: its plan (if one must be made) and its
+                               // share of the plan's batch workspace
     int state = 0;             // 0 queued, 1 running, 2 done
     int rc = 0;
     cg_result res{};
@@ -51,6 +62,8 @@ struct Slot {
     double *ds = nullptr, *db = nullptr, *dx = nullptr;  // device staging
     double *hs = nullptr, *hb = nullptr, *hx = nullptr;  // pinned host staging
     long cap = 0;
+    std::vector<double> rtols;
+    std::vector<cg_result> res;
 };
 
 int padded_side(int L) {
@@ -70,11 +83,27 @@ size_t estimate_bytes(int L) {
     return b;
 }
 
+// Device bytes one problem adds to a plan's batch workspace in the given
+// mode (as cg_solve_batch allocates it: FP64 iterate, residual, b, s, mask,
+// FP64 intermediate, state and partial sums; the mode's inner vectors,
+// preconditioner spectrum and, mixed, the FP32 intermediate), plus staging.
+size_t batch_bytes(int L, int mode) {
+    const size_t N = (size_t)L * L, M = padded_side(L), Q = M / 2 + 1, zs = (M / 2) * (size_t)L;
+    size_t b = N * (4 * 8 + 1) + 16 * zs + 512 + 8 * 3 * ((size_t)L + 1);
+    if (mode == FC_MODE_MIXED)
+        b += N * 6 * 4 + 4 * Q * Q + 8 * zs;
+    else
+        b += N * 3 * 8 + 8 * Q * Q;
+    return b + 3 * 8 * N;  // the slot's device staging of s, b, x
+}
+
 }  // namespace
 
 struct cg_server {
     int dev = 0;
     size_t budget = 0, used = 0, peak = 0;
+    long long batches = 0, solves = 0;  // batched solves run and the requests they held
+    int max_batch = 0;
     int max_slots = 0;
     std::mutex mu;
     std::condition_variable cv;
@@ -92,35 +121,61 @@ namespace {
 // Pick the first queued request that can run now: an idle plan of its size
 // exists, or its plan fits the budget (possibly after evicting idle plans of
 // other sizes).  Called with the lock held.  Returns the request and the plan
-// to use (nullptr: create one) and the idle plans to destroy.
-Req* admit_locked(cg_server* sv, fftconv_plan** plan, std::vector<fftconv_plan*>& evict) {
+// to use (nullptr: create one) and the idle plans to destroy.  The request's
+// reservation (r->est) covers its plan when one is made and one problem of
+// the plan's batch workspace.
+Req* admit_one_locked(cg_server* sv, fftconv_plan** plan, std::vector<fftconv_plan*>& evict) {
     for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
         Req* r = *it;
         auto ip = sv->idle.find(r->rq.L);
-        if (ip != sv->idle.end()) {
-            *plan = ip->second;
-            sv->idle.erase(ip);
-            sv->queue.erase(it);
-            return r;
-        }
+        const bool have = ip != sv->idle.end();
+        const size_t need = have ? batch_bytes(r->rq.L, r->rq.mode) : r->est;
         size_t freeable = 0;
-        for (auto& kv : sv->idle) freeable += sv->plan_bytes[kv.second];
-        if (sv->used + r->est <= sv->budget || sv->used - freeable + r->est <= sv->budget) {
-            while (sv->used + r->est > sv->budget && !sv->idle.empty()) {
-                auto v = sv->idle.begin();
-                evict.push_back(v->second);
-                sv->used -= sv->plan_bytes[v->second];
-                sv->plan_bytes.erase(v->second);
-                sv->idle.erase(v);
-            }
-            sv->used += r->est;  // reserved until the plan exists
-            if (sv->used > sv->peak) sv->peak = sv->used;
-            *plan = nullptr;
-            sv->queue.erase(it);
-            return r;
+        for (auto& kv : sv->idle)
+            if (!have || kv.second != ip->second) freeable += sv->plan_bytes[kv.second];
+        if (sv->used + need > sv->budget && sv->used - freeable + need > sv->budget) continue;
+        fftconv_plan* keep = have ? ip->second : nullptr;
+        if (have) sv->idle.erase(ip);
+        while (sv->used + need > sv->budget && !sv->idle.empty()) {
+            auto v = sv->idle.begin();
+            evict.push_back(v->second);
+            sv->used -= sv->plan_bytes[v->second];
+            sv->plan_bytes.erase(v->second);
+            sv->idle.erase(v);
         }
+        r->est = need;  // reserved until the batch ends
+        sv->used += need;
+        if (sv->used > sv->peak) sv->peak = sv->used;
+        *plan = keep;
+        sv->queue.erase(it);
+        return r;
     }
     return nullptr;
+}
+
+// Admit a request (admit_one_locked) and the queued requests that can join
+// its batch: same L, mode and preconditioning, each reserving one problem's
+// share of the batch workspace while the budget holds it.
+bool admit_locked(cg_server* sv, std::vector<Req*>& batch, fftconv_plan** plan, std::vector<fftconv_plan*>& evict) {
+    batch.clear();
+    Req* r = admit_one_locked(sv, plan, evict);
+    if (!r) return false;
+    batch.push_back(r);
+    const size_t per = batch_bytes(r->rq.L, r->rq.mode);
+    for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)batch.size() < kMaxBatch;) {
+        Req* q = *it;
+        if (q->rq.L == r->rq.L && q->rq.mode == r->rq.mode && q->rq.precond == r->rq.precond &&
+            sv->used + per <= sv->budget) {
+            q->est = per;
+            sv->used += per;
+            batch.push_back(q);
+            it = sv->queue.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (sv->used > sv->peak) sv->peak = sv->used;
+    return true;
 }
 
 int ensure_staging(Slot* sl, long n) {
@@ -145,67 +200,84 @@ int ensure_staging(Slot* sl, long n) {
 
 void worker(cg_server* sv, Slot* sl) {
     cudaSetDevice(sv->dev);
+    std::vector<Req*> batch;
     for (;;) {
-        Req* r = nullptr;
         fftconv_plan* plan = nullptr;
         std::vector<fftconv_plan*> evict;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            sv->cv.wait(lk, [&] {
-                if (sv->stop) return true;
-                r = admit_locked(sv, &plan, evict);
-                return r != nullptr;
-            });
-            if (!r) return;  // stopping
-            r->state = 1;
-            r->t_start = now_s();
+            sv->cv.wait(lk, [&] { return sv->stop || admit_locked(sv, batch, &plan, evict); });
+            if (batch.empty()) return;  // stopping
+            const double t = now_s();
+            for (Req* q : batch) {
+                q->state = 1;
+                q->t_start = t;
+            }
+            sv->batches += 1;
+            sv->solves += (long long)batch.size();
+            if ((int)batch.size() > sv->max_batch) sv->max_batch = (int)batch.size();
         }
         for (fftconv_plan* e : evict) fftconv_plan_destroy(e);
-        const int L = r->rq.L;
+        Req* r = batch[0];
+        const int L = r->rq.L, nb = (int)batch.size();
         const long N = (long)L * L;
+        const bool created = plan == nullptr;
         int rc = FC_OK;
-        if (!plan) {
+        if (created) {
             rc = fftconv_plan_create(&plan, L, FC_F32 | FC_F64, nullptr);
             // many slot threads wait at once: let them sleep, not spin
             if (rc == FC_OK) rc = fftconv_plan_sync_mode(plan, 1);
-            std::lock_guard<std::mutex> lk(sv->mu);
-            sv->used -= r->est;
-            if (rc == FC_OK) {
-                size_t nb = 0;
-                fftconv_plan_info(plan, nullptr, nullptr, nullptr, &nb);
-                sv->plan_bytes[plan] = nb;
-                sv->used += nb;
-                if (sv->used > sv->peak) sv->peak = sv->used;
-            }
         }
-        if (rc == FC_OK) rc = ensure_staging(sl, N);
+        if (rc == FC_OK) rc = ensure_staging(sl, (long)nb * N);
+        sl->rtols.resize(nb);
+        sl->res.assign(nb, cg_result{});
         if (rc == FC_OK) {
-            memcpy(sl->hs, r->s.data(), sizeof(double) * N);
-            memcpy(sl->hb, r->b.data(), sizeof(double) * N);
-            cudaMemcpyAsync(sl->ds, sl->hs, sizeof(double) * N, cudaMemcpyHostToDevice, sl->stream);
-            cudaMemcpyAsync(sl->db, sl->hb, sizeof(double) * N, cudaMemcpyHostToDevice, sl->stream);
+            for (int k = 0; k < nb; ++k) {
+                memcpy(sl->hs + (size_t)k * N, batch[k]->s.data(), sizeof(double) * N);
+                memcpy(sl->hb + (size_t)k * N, batch[k]->b.data(), sizeof(double) * N);
+                sl->rtols[k] = batch[k]->rq.rtol;
+            }
+            cudaMemcpyAsync(sl->ds, sl->hs, sizeof(double) * N * nb, cudaMemcpyHostToDevice, sl->stream);
+            cudaMemcpyAsync(sl->db, sl->hb, sizeof(double) * N * nb, cudaMemcpyHostToDevice, sl->stream);
             cg_opts o{};
             o.rtol = r->rq.rtol;
             o.mode = r->rq.mode;
             o.x0_zero = 1;
             o.precond = r->rq.precond;
-            rc = cg_solve(plan, sl->ds, sl->db, sl->dx, nullptr, &o, &r->res, sl->stream);
+            rc = fc_batch_solve_rtols(plan, nb, sl->ds, sl->db, sl->dx, &o, sl->rtols.data(), sl->res.data(),
+                                      sl->stream);
             if (rc == FC_OK || rc == FC_ENOCONV || rc == FC_ENANINF) {
-                cudaMemcpyAsync(sl->hx, sl->dx, sizeof(double) * N, cudaMemcpyDeviceToHost, sl->stream);
+                rc = FC_OK;
+                cudaMemcpyAsync(sl->hx, sl->dx, sizeof(double) * N * nb, cudaMemcpyDeviceToHost, sl->stream);
                 if (cudaEventRecord(sl->done, sl->stream) != cudaSuccess || cudaEventSynchronize(sl->done) != cudaSuccess)
                     rc = FC_ECUDA;
-                if (r->rq.x) memcpy(r->rq.x, sl->hx, sizeof(double) * N);
+                for (int k = 0; k < nb && rc == FC_OK; ++k)
+                    if (batch[k]->rq.x) memcpy(batch[k]->rq.x, sl->hx + (size_t)k * N, sizeof(double) * N);
             }
         }
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            r->rc = rc;
-            r->res.status = rc;
-            r->t_done = now_s();
-            r->res.latency_s = r->t_done - r->t_submit;
-            r->res.run_s = r->t_done - r->t_start;
-            r->state = 2;
-            if (plan) sv->idle.emplace(L, plan);
+            const double t = now_s();
+            for (int k = 0; k < nb; ++k) {
+                Req* q = batch[k];
+                sv->used -= q->est;  // reservations end; the plan's bytes are counted below
+                q->res = sl->res[k];
+                q->rc = rc != FC_OK ? rc : q->res.status;
+                q->res.status = q->rc;
+                q->t_done = t;
+                q->res.latency_s = q->t_done - q->t_submit;
+                q->res.run_s = q->t_done - q->t_start;
+                q->state = 2;
+            }
+            if (plan) {
+                size_t nbytes = 0;
+                fftconv_plan_info(plan, nullptr, nullptr, nullptr, &nbytes);
+                size_t& held = sv->plan_bytes[plan];  // 0 for a plan made here
+                sv->used += nbytes - held;
+                held = nbytes;
+                if (sv->used > sv->peak) sv->peak = sv->used;
+                sv->idle.emplace(L, plan);
+            }
         }
         sv->cv.notify_all();
     }
@@ -245,7 +317,7 @@ extern "C" int cg_batch_submit(cg_server* sv, const cg_request* rq, uint64_t* ti
     if (!sv || !rq || !ticket || !rq->s || !rq->b || rq->L < 1 || rq->L > 4096 || !(rq->rtol >= 0) ||
         (rq->mode != FC_MODE_F64 && rq->mode != FC_MODE_MIXED))
         return FC_EINVAL;
-    const size_t est = estimate_bytes(rq->L);
+    const size_t est = estimate_bytes(rq->L) + batch_bytes(rq->L, rq->mode);
     if (est > sv->budget) return FC_EBUDGET;
     Req* r = new (std::nothrow) Req();
     if (!r) return FC_ENOMEM;
@@ -285,6 +357,15 @@ extern "C" int cg_poll(cg_server* sv, uint64_t ticket, cg_result* res, int* done
         delete r;
         return rc == FC_ENOCONV || rc == FC_ENANINF ? FC_OK : rc;
     }
+    return FC_OK;
+}
+
+extern "C" int cg_server_batches(cg_server* sv, long long* batches, long long* solves, int* max_batch) {
+    if (!sv) return FC_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (batches) *batches = sv->batches;
+    if (solves) *solves = sv->solves;
+    if (max_batch) *max_batch = sv->max_batch;
     return FC_OK;
 }
 

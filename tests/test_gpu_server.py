@@ -1,5 +1,6 @@
 """The continuous-batching solve server (cg_server_*): results in a mix equal
-the same requests solved alone, budget admission, polling."""
+the same requests solved alone, requests of one size run as batches, budget
+admission, polling."""
 import time
 
 import numpy as np
@@ -13,11 +14,13 @@ from gpu_util import dev, host
 pytestmark = pytest.mark.gpu
 
 
-def alone(L, s, b, rtol, mode):
+def alone(L, s, b, rtol, mode, precond=False):
+    """The request solved by itself: the server's batched solve with one
+    problem, on a fresh plan of its size."""
     plan = fc.fftconv_plan_create(L)
     x = dev(np.zeros(L * L))
-    r = fc.cg_solve(plan, dev(s), dev(b), x, rtol=rtol, mode=mode, x0_zero=True)
-    return host(x), r
+    rc, rs = fc.cg_solve_batch(plan, dev(s), dev(b), x, rtol=rtol, mode=mode, x0_zero=True, precond=precond)
+    return host(x), rs[0]
 
 
 def wait_all(sv, tickets, timeout=120.0):
@@ -56,6 +59,32 @@ def test_mix_equals_alone():
     sv.close()
 
 
+def test_same_size_requests_run_as_batches():
+    """A burst of requests of one size with mixed tolerances: one slot takes
+    them into batched solves, each result bitwise the request alone."""
+    L = 48
+    reqs = []
+    for k in range(20):
+        p = fc_inputs.problem(L, seed=900 + k, b_kind="normal")
+        reqs.append((p["s"], p["b"], (1e-6, 1e-8, 1e-10)[k % 3]))
+    sv = fc.cg_server_create(4 << 30, max_slots=1)
+    # occupy the slot so that the burst queues up behind it
+    big = fc_inputs.problem(256, seed=1, b_kind="normal")
+    first = fc.cg_batch_submit(sv, 256, big["s"], big["b"], rtol=1e-10, mode=1, precond=True)
+    outs = [np.zeros(L * L) for _ in reqs]
+    tickets = [fc.cg_batch_submit(sv, L, s, b, x_out=o, rtol=tol, mode=1, precond=True)
+               for (s, b, tol), o in zip(reqs, outs)]
+    res = wait_all(sv, [first] + tickets)
+    st = fc.cg_server_batches(sv)
+    assert st["solves"] == 21 and st["max_batch"] > 1 and st["batches"] < 21
+    for (s, b, tol), o, t in zip(reqs, outs, tickets):
+        xa, ra = alone(L, s, b, tol, 1, precond=True)
+        r = res[t]
+        assert r["status"] == fc.FC_OK and r["true_rel_resid"] <= tol
+        assert r["iters"] == ra["iters"] and np.array_equal(o, xa)
+    sv.close()
+
+
 def test_budget_admission_and_eviction():
     L1, L2 = 64, 128
     p1, p2 = fc_inputs.problem(L1, seed=1), fc_inputs.problem(L2, seed=2)
@@ -83,21 +112,25 @@ def test_budget_admission_and_eviction():
     sv.close()
 
 
-def test_many_small_requests_overlap():
-    """Throughput with several slots exceeds one slot on many small solves."""
+def test_many_small_requests_batch():
+    """24 small requests through one slot run as batched solves and finish
+    sooner than the same solves one at a time on one plan."""
     L = 64
     probs = [fc_inputs.problem(L, seed=500 + k, b_kind="normal") for k in range(24)]
-
-    def run(slots):
-        sv = fc.cg_server_create(4 << 30, max_slots=slots)
-        warm = fc.cg_batch_submit(sv, L, probs[0]["s"], probs[0]["b"], rtol=1e-8)
-        wait_all(sv, [warm])
-        t0 = time.perf_counter()
-        ts = [fc.cg_batch_submit(sv, L, p["s"], p["b"], rtol=1e-8) for p in probs]
-        wait_all(sv, ts)
-        dt = time.perf_counter() - t0
-        sv.close()
-        return dt
-
-    t1, t8 = run(1), run(8)
-    assert t8 < t1
+    sv = fc.cg_server_create(4 << 30, max_slots=1)
+    wait_all(sv, [fc.cg_batch_submit(sv, L, p["s"], p["b"], rtol=1e-8) for p in probs])  # plan, workspace
+    t0 = time.perf_counter()
+    wait_all(sv, [fc.cg_batch_submit(sv, L, p["s"], p["b"], rtol=1e-8) for p in probs])
+    t_server = time.perf_counter() - t0
+    assert fc.cg_server_batches(sv)["max_batch"] > 1
+    sv.close()
+    plan = fc.fftconv_plan_create(L)
+    inputs = [(dev(p["s"]), dev(p["b"])) for p in probs]
+    x = dev(np.zeros(L * L))
+    fc.cg_solve(plan, *inputs[0], x, rtol=1e-8, mode=1, x0_zero=True)  # graph built
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s, b in inputs:
+        fc.cg_solve(plan, s, b, x, rtol=1e-8, mode=1, x0_zero=True)
+    t_alone = time.perf_counter() - t0
+    assert t_server < t_alone
