@@ -237,9 +237,11 @@ int cg_solve(fftconv_plan *p, const double *s, const double *b, double *x, const
  * Every pass of the operator (Section 3) runs over all nb problems at once,
  * so small systems fill the GPU.  Each problem keeps its own state and step
  * decisions; a problem that has converged skips the remaining passes and the
- * loops run until the last problem finishes.  Problem k's result is the one
- * cg_solve gives with the same launch shapes (pass C takes the thread-load
- * shape where the plan chose the TMA-staged one).
+ * loops run until the last problem finishes.  Batched launches use the
+ * standard launch shape of each pass (cg_tune shapes 1, 1, 1), whatever the
+ * plan's tuner chose for single solves, so problem k's result is the one
+ * cg_solve gives on a plan with those shapes (and the per-pass graph loop),
+ * independent of nb and of the other problems.
  *   nb    1 .. 65535 problems.
  *   s, b  device, nb*L*L doubles: problem k at offset k*L*L.
  *   x     device, nb*L*L doubles: in = starts (unless o->x0_zero), out = solutions.

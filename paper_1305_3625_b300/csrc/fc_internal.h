@@ -68,14 +68,21 @@ __device__ __forceinline__ bool gate_closed(const CgState* st, int gate) {
            ((gate & GATE_IDLE) && st->idle);
 }
 
-// Per-problem strides of a batched launch (elements; 0 with one problem).
-// The kernels add them as index offsets (problem blockIdx.y), so a pointer
-// argument keeps its meaning as a mode flag when null.
+// Per-problem strides of a batched launch (elements).  The batched kernels
+// add them as index offsets (problem blockIdx.y), so a pointer argument
+// keeps its meaning as a mode flag when null.  They travel in a second kernel
+// parameter: widening the pass argument blocks themselves changed the
+// register allocation of the single-problem kernels (spills in the
+// 64-register shapes).
 struct BatchStride {
     long n;     // L*L vectors (x, r, p, q, z, s, b, mask)
     long z;     // complex elements of the intermediate
     long q;     // spectrum quarter (0: one spectrum shared by all problems)
     long part;  // doubles of partial sums
+};
+struct BatchArgs {
+    int gate;   // GATE_* bits
+    BatchStride bs;
 };
 
 // Pass A modes: plain input; CG update (x, r, p) + transform p; FP64 iterate
@@ -101,8 +108,6 @@ struct RowFwdArgs {
     double* part;                // per-block partial sums
     cpx<T>* Z;                   // L x M intermediate
     const cpx<T>* tw;            // exp(-2 pi i m/M), m < M
-    int gate;                    // GATE_* bits (batched solves; 0: none)
-    BatchStride bs;              // problem blockIdx.y: vectors at + y*bs.n, Z at + y*bs.z, ...
 };
 
 template <typename T>
@@ -113,7 +118,6 @@ struct ColArgs {
     const cpx<T>* tw;
     const CgState* st;           // with gate: the state whose fields may skip the pass
     int gate;                    // GATE_* bits (GATE_WARM: the residual was updated, no product)
-    BatchStride bs;
 };
 
 template <typename T>
@@ -133,8 +137,6 @@ struct RowInvArgs {
     unsigned long long h_outer, h_inner;  // graph conditional handles (0: none)
     const cpx<T>* Z;
     const cpx<T>* tw;
-    int gate;                    // GATE_* bits (batched solves; 0: none)
-    BatchStride bs;
 };
 
 // Decide the CG step after the product q = A p of one iteration of Listing 2.

@@ -549,6 +549,7 @@ struct Variants {
     KVP pers[6];
     int n_pers = 0;
     KV rows_full, cols_full;  // FP64 only: spectrum set-up
+    KV rfwd_b, colc_b, rinv_b;  // batched forms (blockIdx.y = problem) of the standard shapes
 };
 
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -573,6 +574,16 @@ void add_rinv_tma(Variants& v) {
     if constexpr (M / 16 >= 32 && tma_smem_bytes(M) <= 200 * 1024) {
         if (v.n_rinv < Variants::kMax) v.rinv[v.n_rinv++] = KV{(const void*)k_rinv_tma<M, 16>, M / 16, 1, 16, tma_smem_bytes(M), 1};
     }
+}
+
+// The batched forms of the standard shapes (the first registered of each
+// pass): batched solves launch these, whatever the plan's tuner chose.
+template <typename T, int M, int ER, int RB, int EC, int CB>
+void add_batched(Variants& v) {
+    constexpr bool DR = use_db<T, M, RB>(), DC = use_db<T, M, CB>();
+    v.rfwd_b = KV{(const void*)k_rfwd_b<T, M, ER, RB, 1, DR>, RB * (M / ER), RB, ER, pass_smem<T, M, RB, DR>()};
+    v.rinv_b = KV{(const void*)k_rinv_b<T, M, ER, RB, 1, DR>, RB * (M / ER), RB, ER, pass_smem<T, M, RB, DR>()};
+    v.colc_b = KV{(const void*)k_colc_b<T, M, EC, CB, 1, DC>, CB * (M / EC), CB, EC, pass_smem<T, M, CB, DC>()};
 }
 
 template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
@@ -610,12 +621,15 @@ void make_variants(Variants& v) {
         if constexpr (M <= 16) {
             add_row<T, M, M, 64>(v);
             add_col<T, M, M, clampi(64, 1, H)>(v);
+            add_batched<T, M, M, 64, M, clampi(64, 1, H)>(v);
         } else if constexpr (M <= 128) {
             constexpr int G = M / 16;
             add_row<T, M, 16, clampi(128 / G, 1, 128)>(v);
             add_col<T, M, 16, clampi(256 / G, 1, H)>(v);
+            add_batched<T, M, 16, clampi(128 / G, 1, 128), 16, clampi(256 / G, 1, H)>(v);
         } else {
             constexpr int G16 = M / 16, G8 = M / 8, G4 = M / 4;
+            add_batched<T, M, 16, clampi(256 / G16, 1, 64), 16, clampi(128 / G16, 1, H)>(v);
             add_row<T, M, 16, clampi(256 / G16, 1, 64)>(v);
             add_row<T, M, 16, clampi(512 / G16, 1, 64)>(v);
             add_row<T, M, 8, clampi(256 / G8, 1, 64)>(v);
@@ -655,6 +669,7 @@ void make_variants(Variants& v) {
         constexpr int CB = clampi(256 / G, 1, H);
         add_row<T, M, E, RB>(v);
         add_col<T, M, E, CB>(v);
+        add_batched<T, M, E, RB, E, CB>(v);
         constexpr int CBF = clampi(256 / G, 1, M);
         v.rows_full = KV{(const void*)k_rows_full<M, E, RB>, RB * G, RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<double>)};
         v.cols_full = KV{(const void*)k_cols_full<M, E, CBF>, CBF * G, CBF, E, (size_t)CBF * seg_len(M) * sizeof(cpx<double>)};
@@ -702,6 +717,9 @@ int set_smem_attrs(const Variants& v) {
                 rc = set_cuda_err(cudaGetLastError(), "cudaFuncSetAttribute(persistent)");
     if (!rc) rc = set_smem_attr(v.rows_full);
     if (!rc) rc = set_smem_attr(v.cols_full);
+    if (!rc) rc = set_smem_attr(v.rfwd_b);
+    if (!rc) rc = set_smem_attr(v.colc_b);
+    if (!rc) rc = set_smem_attr(v.rinv_b);
     return rc;
 }
 
@@ -1762,16 +1780,33 @@ struct SolveView {
     cpx<T>* Z() const {
         return (cpx<T>*)(sizeof(T) == 4 ? Z32 : Z64);
     }
-    int gate_inner() const { return batched ? GATE_IDLE : 0; }
-    int gate_outer() const { return batched ? GATE_FINISHED : 0; }
-    // the kernel spectrum is one for all problems; the preconditioner's is per problem
-    BatchStride kernel_spectrum() const {
-        BatchStride b = bs;
-        b.q = 0;
+    // batched launches' second argument: the inner passes skip idle
+    // problems, the true-residual passes finished ones; the kernel spectrum
+    // is one for all problems, the preconditioner's is per problem
+    BatchArgs inner(bool shared_spectrum = false) const {
+        BatchArgs b{GATE_IDLE, bs};
+        if (shared_spectrum) b.bs.q = 0;
+        return b;
+    }
+    BatchArgs outer() const {
+        BatchArgs b{GATE_FINISHED, bs};
+        b.bs.q = 0;
         return b;
     }
     dim3 grid(int gx) const { return dim3((unsigned)gx, (unsigned)nb); }
 };
+
+// A pass node following prev (nullptr: the first node of a body): its
+// arguments, and for batched solves the batch argument bb.
+template <typename A>
+cudaGraphNode_t pass_node(GraphBuilder& gb, cudaGraph_t g, cudaGraphNode_t prev, const KV& k, dim3 grid,
+                          const SolveView& V, const A& args, const BatchArgs& bb) {
+    if (V.batched)
+        return prev ? gb.pass(g, prev, k.f, grid, k.threads, k.smem, args, bb)
+                    : gb.kernel(g, nullptr, 0, k.f, grid, k.threads, k.smem, args, bb);
+    return prev ? gb.pass(g, prev, k.f, grid, k.threads, k.smem, args)
+                : gb.kernel(g, nullptr, 0, k.f, grid, k.threads, k.smem, args);
+}
 
 SolveView plan_view(fftconv_plan* p) {
     SolveView v;
@@ -1785,28 +1820,24 @@ SolveView plan_view(fftconv_plan* p) {
     return v;
 }
 
-// Pass C's launch shape: the tuned one, except that batched solves take the
-// thread-load shape instead of the TMA-staged one (whose tensor map and
-// persistent grid describe one problem).
-const KV& rinv_shape(const PrecRes& R, bool batched) {
-    if (!batched || !R.rinv().tma) return R.rinv();
-    for (int k = 0; k < R.v.n_rinv; ++k)
-        if (!R.v.rinv[k].tma) return R.v.rinv[k];
-    return R.rinv();  // not reached: every size carries thread-load shapes
-}
+// The launch shapes of a solve graph: the tuned ones, or for batched solves
+// the batched forms of the standard shapes.
+const KV& rfwd_shape(const PrecRes& R, bool batched) { return batched ? R.v.rfwd_b : R.rfwd(); }
+const KV& colc_shape(const PrecRes& R, bool batched) { return batched ? R.v.colc_b : R.colc(); }
+const KV& rinv_shape(const PrecRes& R, bool batched) { return batched ? R.v.rinv_b : R.rinv(); }
 
 // Pass C as a graph node following prev (the TMA-staged shape gets its
 // tensor-map arguments).
 template <typename T>
 cudaGraphNode_t graph_rinv(GraphBuilder& gb, cudaGraph_t g, cudaGraphNode_t prev, fftconv_plan* p, PrecRes& R,
-                           const KV& kc, const SolveView& V, const RowInvArgs<T>& c) {
+                           const KV& kc, const SolveView& V, const RowInvArgs<T>& c, const BatchArgs& bb) {
     if constexpr (sizeof(T) == 4) {
         if (kc.tma) {
             const RowInvTma P = tma_args(p, R, c);
             return gb.pass(g, prev, kc.f, dim3(R.tma_grid), kc.threads, kc.smem, P);
         }
     }
-    return gb.pass(g, prev, kc.f, V.grid(row_grid(p, kc)), kc.threads, kc.smem, c);
+    return pass_node(gb, g, prev, kc, V.grid(row_grid(p, kc)), V, c, bb);
 }
 
 // After the deciding pass of a batched loop body: the loop control node.
@@ -1824,7 +1855,7 @@ void batch_ctl_node(GraphBuilder& gb, cudaGraph_t g, cudaGraphNode_t prev, const
 template <typename T>
 void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, const SolveView& V, T* cx,
                     T* cr, T* cp, T* cq, const T* s, const double* r64_start, cudaGraphConditionalHandle h_inner) {
-    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = rinv_shape(R, V.batched);
+    const KV &ka = rfwd_shape(R, V.batched), &kb = colc_shape(R, V.batched), &kc = rinv_shape(R, V.batched);
     RowFwdArgs<T> a{};
     a.L = p->L;
     a.mode = RF_CG;
@@ -1837,12 +1868,9 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     a.part = V.part;
     a.Z = V.Z<T>();
     a.tw = (const cpx<T>*)R.tws(ka.E);
-    a.gate = V.gate_inner();
-    a.bs = V.bs;
-    cudaGraphNode_t nA = gb.kernel(body, nullptr, 0, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a);
-    ColArgs<T> b{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, V.gate_inner(),
-                 V.kernel_spectrum()};
-    cudaGraphNode_t nB = gb.pass(body, nA, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b);
+    cudaGraphNode_t nA = pass_node(gb, body, nullptr, ka, V.grid(row_grid(p, ka)), V, a, V.inner());
+    ColArgs<T> b{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, 0};
+    cudaGraphNode_t nB = pass_node(gb, body, nA, kb, V.grid(col_grid(p, kb)), V, b, V.inner(true));
     RowInvArgs<T> c{};
     c.L = p->L;
     c.mode = RI_CG;
@@ -1856,9 +1884,7 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     c.h_inner = V.batched ? 0 : h_inner;
     c.Z = V.Z<T>();
     c.tw = (const cpx<T>*)R.tws(kc.E);
-    c.gate = V.gate_inner();
-    c.bs = V.bs;
-    cudaGraphNode_t nC = graph_rinv<T>(gb, body, nB, p, R, kc, V, c);
+    cudaGraphNode_t nC = graph_rinv<T>(gb, body, nB, p, R, kc, V, c, V.inner());
     if (V.batched) batch_ctl_node(gb, body, nC, V, 0, h_inner, nullptr);
 }
 
@@ -1869,8 +1895,7 @@ template <typename T>
 void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, const SolveView& V, T* cx,
                         T* cr, T* cp, T* cq, T* cz, const T* s, const T* pq, const double* r64_start,
                         cudaGraphConditionalHandle h_inner) {
-    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = rinv_shape(R, V.batched);
-    const int gi = V.gate_inner();
+    const KV &ka = rfwd_shape(R, V.batched), &kb = colc_shape(R, V.batched), &kc = rinv_shape(R, V.batched);
     RowFwdArgs<T> a1{};
     a1.L = p->L;
     a1.mode = RF_PCG_R;
@@ -1883,11 +1908,9 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a1.part = V.part;
     a1.Z = V.Z<T>();
     a1.tw = (const cpx<T>*)R.tws(ka.E);
-    a1.gate = gi;
-    a1.bs = V.bs;
-    cudaGraphNode_t n1 = gb.kernel(body, nullptr, 0, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a1);
-    ColArgs<T> b1{p->L, V.Z<T>(), pq, (const cpx<T>*)R.tws(kb.E), V.st, gi, V.bs};
-    cudaGraphNode_t n2 = gb.pass(body, n1, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b1);
+    cudaGraphNode_t n1 = pass_node(gb, body, nullptr, ka, V.grid(row_grid(p, ka)), V, a1, V.inner());
+    ColArgs<T> b1{p->L, V.Z<T>(), pq, (const cpx<T>*)R.tws(kb.E), V.st, 0};
+    cudaGraphNode_t n2 = pass_node(gb, body, n1, kb, V.grid(col_grid(p, kb)), V, b1, V.inner());
     RowInvArgs<T> c1{};
     c1.L = p->L;
     c1.mode = RI_PCG_Z;
@@ -1898,9 +1921,7 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c1.part = V.part;
     c1.Z = V.Z<T>();
     c1.tw = (const cpx<T>*)R.tws(kc.E);
-    c1.gate = gi;
-    c1.bs = V.bs;
-    cudaGraphNode_t n3 = graph_rinv<T>(gb, body, n2, p, R, kc, V, c1);
+    cudaGraphNode_t n3 = graph_rinv<T>(gb, body, n2, p, R, kc, V, c1, V.inner());
     RowFwdArgs<T> a2{};
     a2.L = p->L;
     a2.mode = RF_PCG_P;
@@ -1911,11 +1932,9 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a2.part = V.part;
     a2.Z = V.Z<T>();
     a2.tw = (const cpx<T>*)R.tws(ka.E);
-    a2.gate = gi;
-    a2.bs = V.bs;
-    cudaGraphNode_t n4 = gb.pass(body, n3, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a2);
-    ColArgs<T> b2{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, gi, V.kernel_spectrum()};
-    cudaGraphNode_t n5 = gb.pass(body, n4, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b2);
+    cudaGraphNode_t n4 = pass_node(gb, body, n3, ka, V.grid(row_grid(p, ka)), V, a2, V.inner());
+    ColArgs<T> b2{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, 0};
+    cudaGraphNode_t n5 = pass_node(gb, body, n4, kb, V.grid(col_grid(p, kb)), V, b2, V.inner(true));
     RowInvArgs<T> c2{};
     c2.L = p->L;
     c2.mode = RI_CG;
@@ -1929,9 +1948,7 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c2.h_inner = V.batched ? 0 : h_inner;
     c2.Z = V.Z<T>();
     c2.tw = (const cpx<T>*)R.tws(kc.E);
-    c2.gate = gi;
-    c2.bs = V.bs;
-    cudaGraphNode_t n6 = graph_rinv<T>(gb, body, n5, p, R, kc, V, c2);
+    cudaGraphNode_t n6 = graph_rinv<T>(gb, body, n5, p, R, kc, V, c2, V.inner());
     if (V.batched) batch_ctl_node(gb, body, n6, V, 0, h_inner, nullptr);
 }
 
@@ -1997,7 +2014,8 @@ int build_graph_with(fftconv_plan* p, const SolveView& V, int mode, bool precond
         if (e != cudaSuccess) gb.rc = set_cuda_err(e, "cudaGraphConditionalHandleCreate(inner)");
     }
     if (!gb.rc) {
-        const KV &ka = p->p64.rfwd(), &kb = p->p64.colc(), &kc = p->p64.rinv();
+        const KV &ka = rfwd_shape(p->p64, V.batched), &kb = colc_shape(p->p64, V.batched),
+                 &kc = rinv_shape(p->p64, V.batched);
         RowFwdArgs<double> a{};
         a.L = p->L;
         a.mode = RF_XUPD;
@@ -2008,13 +2026,11 @@ int build_graph_with(fftconv_plan* p, const SolveView& V, int mode, bool precond
         a.part = V.part;
         a.Z = V.Z<double>();
         a.tw = (const cpx<double>*)p->p64.tws(ka.E);
-        a.gate = V.gate_outer();
-        a.bs = V.bs;
         // the mask is applied to x in the same pass (x = 0 off the active set)
-        cudaGraphNode_t nA = gb.kernel(outer, nullptr, 0, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a);
+        cudaGraphNode_t nA = pass_node(gb, outer, nullptr, ka, V.grid(row_grid(p, ka)), V, a, V.outer());
         ColArgs<double> b{p->L, V.Z<double>(), (const double*)p->p64.Gq, (const cpx<double>*)p->p64.tws(kb.E), V.st,
-                          GATE_WARM | V.gate_outer(), V.kernel_spectrum()};
-        cudaGraphNode_t nB = gb.pass(outer, nA, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b);
+                          GATE_WARM};
+        cudaGraphNode_t nB = pass_node(gb, outer, nA, kb, V.grid(col_grid(p, kb)), V, b, V.outer());
         RowInvArgs<double> c{};
         c.L = p->L;
         c.mode = RI_RESID;
@@ -2029,9 +2045,7 @@ int build_graph_with(fftconv_plan* p, const SolveView& V, int mode, bool precond
         c.h_inner = V.batched ? 0 : h_inner;
         c.Z = V.Z<double>();
         c.tw = (const cpx<double>*)p->p64.tws(kc.E);
-        c.gate = V.gate_outer();
-        c.bs = V.bs;
-        cudaGraphNode_t nC = gb.pass(outer, nB, kc.f, V.grid(row_grid(p, kc)), kc.threads, kc.smem, c);
+        cudaGraphNode_t nC = pass_node(gb, outer, nB, kc, V.grid(row_grid(p, kc)), V, c, V.outer());
         if (V.batched) batch_ctl_node(gb, outer, nC, V, h_outer, h_inner, &nC);
         cudaGraphNode_t nInner = nullptr;
         cudaGraph_t inner = gb.while_node(outer, &nC, 1, h_inner, &nInner);

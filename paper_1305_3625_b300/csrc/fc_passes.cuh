@@ -420,40 +420,58 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
     }
 }
 
-// MINB: blocks per SM the register allocation must allow; DB: double-buffered
-// exchanges (default: when they fit, see use_db).
-template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
-__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a) {
-    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
-    extern __shared__ __align__(16) unsigned char smraw[];
-    CgState* const st = a.st + blockIdx.y;  // problem blockIdx.y of a batched launch
-    pdl_enter();
-    if (a.gate && gate_closed(st, a.gate)) return;
-    if (a.mode == RF_XUPD && st->warm) return;  // residual already updated: no product
-    const AScal<T> sc = ascal_from_state(a, st);
-    T acc = 0, acc_rp = 0;
-    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp,
-                               (size_t)blockIdx.y * a.bs.n, (size_t)blockIdx.y * a.bs.z);
-    pdl_leave();
-    // partial sums in the pass's precision (FP32: two-float combination,
-    // FP64: FP64), totals in FP64
-    double* const part = a.part + blockIdx.y * a.bs.part;
-    if (a.mode == RF_CG) {
+// Pass A's grid sums: partials in the pass's precision (FP32: two-float
+// combination, FP64: FP64), totals in FP64, written by the last block.
+template <typename T>
+__device__ __forceinline__ void rfwd_sums(int mode, double* part, CgState* st, T acc, T acc_rp) {
+    if (mode == RF_CG) {
         T pv[2] = {acc, acc_rp};
         double tot[2];
         if (grid_sum_last<2>(pv, part, &st->cntA, tot) && threadIdx.x == 0) {
             st->rr = tot[0];
             st->rp = tot[1];
         }
-    } else if (a.mode == RF_PCG_R) {
+    } else if (mode == RF_PCG_R) {
         T pv[1] = {acc};
         double tot[1];
         if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rr = tot[0];
-    } else if (a.mode == RF_PCG_P) {
+    } else if (mode == RF_PCG_P) {
         T pv[1] = {acc_rp};
         double tot[1];
         if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rp = tot[0];
     }
+}
+
+// MINB: blocks per SM the register allocation must allow; DB: double-buffered
+// exchanges (default: when they fit, see use_db).
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
+    if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
+    const AScal<T> sc = ascal_from_state(a, a.st);
+    T acc = 0, acc_rp = 0;
+    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
+    pdl_leave();
+    rfwd_sums(a.mode, a.part, a.st, acc, acc_rp);
+}
+
+// The batched form: problem blockIdx.y at the strides of bb, gated.
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_b(const RowFwdArgs<T> a, const BatchArgs bb) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CgState* const st = a.st + blockIdx.y;
+    pdl_enter();
+    if (bb.gate && gate_closed(st, bb.gate)) return;
+    if (a.mode == RF_XUPD && st->warm) return;
+    const AScal<T> sc = ascal_from_state(a, st);
+    T acc = 0, acc_rp = 0;
+    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp,
+                               (size_t)blockIdx.y * bb.bs.n, (size_t)blockIdx.y * bb.bs.z);
+    pdl_leave();
+    rfwd_sums(a.mode, a.part + blockIdx.y * bb.bs.part, st, acc, acc_rp);
 }
 
 // ------------------------------------------------------------ pass B ----
@@ -531,9 +549,18 @@ template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M,
 __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
-    if (a.gate && gate_closed(a.st + blockIdx.y, a.gate)) return;
-    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * a.bs.z,
-                               (size_t)blockIdx.y * a.bs.q);
+    if (a.gate && gate_closed(a.st, a.gate)) return;
+    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    pdl_leave();
+}
+
+template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
+__global__ void __launch_bounds__(CB*(M / E), MINB) k_colc_b(const ColArgs<T> a, const BatchArgs bb) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
+    if ((a.gate | bb.gate) && gate_closed(a.st + blockIdx.y, a.gate | bb.gate)) return;
+    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * bb.bs.z,
+                               (size_t)blockIdx.y * bb.bs.q);
     pdl_leave();
 }
 
@@ -656,26 +683,10 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
                             v, s0, s1, s2);
 }
 
-template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
-__global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a) {
-    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
-    extern __shared__ __align__(16) unsigned char smraw[];
-    CgState* const st = a.st + blockIdx.y;  // problem blockIdx.y of a batched launch
-    pdl_enter();
-    if (a.gate && gate_closed(st, a.gate)) return;
-    T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
-    // warm residual: r64 and its sums (rr64, bb) are already in place, and
-    // block 0 alone hands them to the decision
-    const bool warm = a.mode == RI_RESID && st->warm;
-    if (!warm) {
-        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2,
-                                   (size_t)blockIdx.y * a.bs.n, (size_t)blockIdx.y * a.bs.z);
-    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-        s0 = (T)st->rr64;
-        s1 = (T)st->bb;
-    }
-    pdl_leave();
-    double* const part = a.part + blockIdx.y * a.bs.part;
+// Pass C's grid sums and step decisions (last block).  warm (RI_RESID): the
+// residual and its sums were updated in place, and block 0 alone hands them on.
+template <typename T>
+__device__ __forceinline__ void rinv_sums(const RowInvArgs<T>& a, double* part, CgState* st, T s0, T s1, T s2) {
     if (a.mode == RI_CG) {
         T pv[3] = {s0, s1, s2};
         double tot[3];
@@ -692,6 +703,46 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a
         double tot[1];
         if (grid_sum_last<1>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(st, tot[0]);
     }
+}
+
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
+    T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
+    // warm residual: r64 and its sums (rr64, bb) are already in place, and
+    // block 0 alone hands them to the decision
+    const bool warm = a.mode == RI_RESID && a.st->warm;
+    if (!warm) {
+        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s0 = (T)a.st->rr64;
+        s1 = (T)a.st->bb;
+    }
+    pdl_leave();
+    rinv_sums(a, a.part, a.st, s0, s1, s2);
+}
+
+// The batched form: problem blockIdx.y at the strides of bb, gated.
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv_b(const RowInvArgs<T> a, const BatchArgs bb) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    CgState* const st = a.st + blockIdx.y;
+    pdl_enter();
+    if (bb.gate && gate_closed(st, bb.gate)) return;
+    T s0 = 0, s1 = 0, s2 = 0;
+    const bool warm = a.mode == RI_RESID && st->warm;
+    if (!warm) {
+        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2,
+                                   (size_t)blockIdx.y * bb.bs.n, (size_t)blockIdx.y * bb.bs.z);
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+        s0 = (T)st->rr64;
+        s1 = (T)st->bb;
+    }
+    pdl_leave();
+    rinv_sums(a, a.part + blockIdx.y * bb.bs.part, st, s0, s1, s2);
 }
 
 }  // namespace fc
