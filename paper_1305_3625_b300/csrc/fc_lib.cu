@@ -2209,10 +2209,10 @@ int init_state(const cg_opts* o, CgState* h) {
     h->inner_rtol2 = irt * irt;
     {
         // the fraction of the outer target at which an inner run may stop
-        // early (FC_INNER_GOAL, default 0.5; 0 turns it off)
+        // early (FC_INNER_GOAL, default 0.85; 0 turns it off)
         static const double goal = [] {
             const char* e = getenv("FC_INNER_GOAL");
-            const double v = e ? atof(e) : 0.5;
+            const double v = e ? atof(e) : 0.85;
             return v > 0.0 && v < 1.0 ? v : 0.0;
         }();
         h->inner_goal2 = goal * goal;
