@@ -458,12 +458,12 @@ def run_ours(args, world, rank, local, pg):
         if breqs:
             # the same 256 requests once untimed (plans, batch workspaces and
             # staging made), then timed
-            drain([fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True)
-                   for Lk, pk in breqs])
+            drain([fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True,
+                                      borrow=True) for Lk, pk in breqs])
             bs0 = fc.cg_server_batches(sv)
             t0 = time.perf_counter()
-            tk = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True)
-                  for Lk, pk in breqs]
+            tk = [fc.cg_batch_submit(sv, Lk, pk["s"], pk["b"], rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True,
+                                     borrow=True) for Lk, pk in breqs]
             res = drain(tk)
             dt = time.perf_counter() - t0
             assert all(r["status"] == fc.FC_OK for r in res.values())
@@ -485,7 +485,7 @@ def run_ours(args, world, rank, local, pg):
             for timed in (False, True):
                 c0 = time.perf_counter()
                 drain([fc.cg_batch_submit(sv, rq["L"], probs[rq["k"]]["s"], probs[rq["k"]]["b"], rtol=rq["tol"],
-                                          mode=fc.FC_MODE_MIXED, precond=True) for rq in base[:ncap]])
+                                          mode=fc.FC_MODE_MIXED, precond=True, borrow=True) for rq in base[:ncap]])
                 cap = ncap / (time.perf_counter() - c0)
             b0 = fc.cg_server_batches(sv)
             stream_ = fc_inputs.request_stream(args.serve_requests, seed=777, rate_per_s=0.7 * cap)
@@ -496,7 +496,7 @@ def run_ours(args, world, rank, local, pg):
                     time.sleep(0.0001)
                 pk = probs[rq["k"]]
                 tickets.append(fc.cg_batch_submit(sv, rq["L"], pk["s"], pk["b"], rtol=rq["tol"],
-                                                  mode=fc.FC_MODE_MIXED, precond=True))
+                                                  mode=fc.FC_MODE_MIXED, precond=True, borrow=True))
             res = drain(tickets)
             dt = time.perf_counter() - t0
             lat = sorted(r["latency_s"] * 1e3 for r in res.values())

@@ -359,7 +359,8 @@ int fc_masked_step_static(int64_t N, const double *t, uint8_t *mask, double *x, 
 /* ------------------------------------------------------------- serving -- */
 
 /* One solve request.  Host pointers: s and b (L*L doubles) are copied at
- * submit; x (L*L doubles) receives the solution before cg_poll reports done. */
+ * submit (or read when the request runs, with FC_REQ_BORROW); x (L*L
+ * doubles) receives the solution before cg_poll reports done. */
 typedef struct cg_request {
     int L;           /* 1..4096                                              */
     int mode;        /* FC_MODE_F64 or FC_MODE_MIXED                         */
@@ -369,8 +370,12 @@ typedef struct cg_request {
     double *x;       /* host, receives the solution (may be NULL)            */
     uint64_t tag;    /* caller's tag                                         */
     int precond;     /* 1: Fourier-preconditioned CG (see cg_opts.precond)   */
-    int reserved;
+    int flags;       /* FC_REQ_BORROW: s and b are not copied at submit; the
+                        caller keeps them valid and unchanged until cg_poll
+                        reports the request done (0: copied at submit)     */
 } cg_request;
+
+#define FC_REQ_BORROW 1
 
 /*
  * cg_server_create -- a continuous-batching solve server on the current
@@ -386,7 +391,8 @@ typedef struct cg_request {
  * reserving its share of the plan's batch workspace within the budget) and
  * runs them as one cg_solve_batch launch with each request's own tolerance,
  * from x = 0.  Plans stay resident and are reused by later requests of the
- * same L.  Work of different slots overlaps on the device; each result
+ * same L; there is one plan per size, so a request whose size is being
+ * solved waits and joins that plan's next batch.  Work of different slots overlaps on the device; each result
  * depends only on its own inputs (it equals cg_solve_batch of that request
  * alone on a plan of its size).
  */

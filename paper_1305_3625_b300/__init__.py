@@ -31,6 +31,7 @@ FC_GREEN_POINT = 0
 FC_GREEN_CELL = 1
 FC_MODE_F64 = 0
 FC_MODE_MIXED = 1
+FC_REQ_BORROW = 1
 
 STATUS_NAMES = {0: "FC_OK", -1: "FC_EINVAL", -2: "FC_ENOMEM", -3: "FC_EBUDGET", -4: "FC_ENOCONV",
                 -5: "FC_ENANINF", -6: "FC_ETIMEOUT", -7: "FC_ECUDA", -8: "FC_ENOTFOUND"}
@@ -88,7 +89,7 @@ class fc_run_result(ctypes.Structure):
 class cg_request(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("mode", ctypes.c_int), ("rtol", ctypes.c_double),
                 ("s", ctypes.c_void_p), ("b", ctypes.c_void_p), ("x", ctypes.c_void_p),
-                ("tag", ctypes.c_uint64), ("precond", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("tag", ctypes.c_uint64), ("precond", ctypes.c_int), ("flags", ctypes.c_int)]
 
 
 LIB_PATH = _build.LIB
@@ -442,9 +443,12 @@ def cg_server_create(mem_budget_bytes: int, max_slots: int = 16) -> Server:
 
 
 def cg_batch_submit(sv: Server, L: int, s, b, x_out=None, rtol: float = 1e-8, mode: int = FC_MODE_MIXED,
-                    tag: int = 0, precond: bool = False) -> int:
+                    tag: int = 0, precond: bool = False, borrow: bool = False) -> int:
     """Queue one solve (host float64 arrays of L*L); x_out (float64, L*L,
-    C-contiguous numpy array) receives the solution.  Returns the ticket."""
+    C-contiguous numpy array) receives the solution.  borrow: the server
+    reads s and b when the request runs instead of copying them at submit
+    (this wrapper keeps them alive until the request is polled done; the
+    caller must not change them meanwhile).  Returns the ticket."""
     import numpy as np
     n = int(L) * int(L)
     s = np.ascontiguousarray(s, dtype=np.float64)
@@ -455,12 +459,12 @@ def cg_batch_submit(sv: Server, L: int, s, b, x_out=None, rtol: float = 1e-8, mo
         raise ValueError("x_out must be a contiguous float64 array of L*L values")
     rq = cg_request(L=int(L), mode=int(mode), rtol=float(rtol), s=s.ctypes.data, b=b.ctypes.data,
                     x=x_out.ctypes.data if x_out is not None else None, tag=int(tag),
-                    precond=int(bool(precond)), reserved=0)
+                    precond=int(bool(precond)), flags=FC_REQ_BORROW if borrow else 0)
     t = ctypes.c_uint64()
     rc = _lib.cg_batch_submit(sv.handle, ctypes.byref(rq), ctypes.byref(t))
     if rc != FC_OK:
         raise FcError(rc, "cg_batch_submit")
-    sv._keep[t.value] = x_out
+    sv._keep[t.value] = (x_out, s, b) if borrow else x_out
     return t.value
 
 

@@ -2337,10 +2337,19 @@ struct BatchWs {
     bool has64 = false;   // FP64 inner vectors (FP64-mode batches) allocated
     bool has32 = false;   // FP32 inner vectors (mixed batches) allocated
     SolveView v;
-    CgState* st_host = nullptr;  // pinned, cap states
-    cudaGraph_t graph[4] = {};
-    cudaGraphExec_t gexec[4] = {};
-    int g_nb[4] = {};
+    CgState* st_host = nullptr;  // pinned, st_cap states
+    int st_cap = 0;
+    // instantiated solve graphs by (mode index, problems launched), least
+    // recently used evicted
+    struct Graph {
+        int gi = -1, nb = 0;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        unsigned long long used = 0;
+    };
+    static constexpr int kGraphs = 16;
+    Graph graphs[kGraphs];
+    unsigned long long tick = 0;
     cudaStream_t stream = nullptr;  // own stream: groups of cg_solve_groups run concurrently
     cudaEvent_t ev = nullptr;
     size_t bytes = 0;
@@ -2350,21 +2359,19 @@ struct BatchWs {
 namespace {
 
 void batch_graphs_free(BatchWs* w) {
-    for (int m = 0; m < 4; ++m) {
-        if (w->gexec[m]) cudaGraphExecDestroy(w->gexec[m]);
-        if (w->graph[m]) cudaGraphDestroy(w->graph[m]);
-        w->gexec[m] = nullptr;
-        w->graph[m] = nullptr;
-        w->g_nb[m] = 0;
+    for (auto& g : w->graphs) {
+        if (g.ex) cudaGraphExecDestroy(g.ex);
+        if (g.g) cudaGraphDestroy(g.g);
+        g = BatchWs::Graph{};
     }
 }
 
-void batch_buffers_free(BatchWs* w) {
+// Buffers back to the stream-ordered pool on st (every earlier batch on this
+// workspace has finished: the calls wait for their batches).
+void batch_buffers_free(BatchWs* w, cudaStream_t st) {
     batch_graphs_free(w);
-    for (void* q : w->blocks) cudaFree(q);
+    for (void* q : w->blocks) cudaFreeAsync(q, st);
     w->blocks.clear();
-    if (w->st_host) cudaFreeHost(w->st_host);
-    w->st_host = nullptr;
     w->v = SolveView{};
     w->cap = 0;
     w->has64 = w->has32 = false;
@@ -2376,7 +2383,9 @@ size_t batch_bytes_of(const fftconv_plan* p) { return p->batch ? p->batch->bytes
 void batch_free(fftconv_plan* p) {
     BatchWs* w = p->batch;
     if (!w) return;
-    batch_buffers_free(w);
+    batch_buffers_free(w, w->stream);
+    cudaStreamSynchronize(w->stream);
+    if (w->st_host) cudaFreeHost(w->st_host);
     if (w->ev) cudaEventDestroy(w->ev);
     if (w->stream) cudaStreamDestroy(w->stream);
     delete w;
@@ -2384,11 +2393,11 @@ void batch_free(fftconv_plan* p) {
 }
 
 template <typename P>
-int balloc(BatchWs* w, P** ptr, size_t bytes) {
+int balloc(BatchWs* w, P** ptr, size_t bytes, cudaStream_t st) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = cudaMallocAsync(&q, bytes, st);
     if (e != cudaSuccess) {
-        set_cuda_err(e, "cudaMalloc(batch)");
+        set_cuda_err(e, "cudaMallocAsync(batch)");
         return FC_ENOMEM;
     }
     w->blocks.push_back(q);
@@ -2397,9 +2406,19 @@ int balloc(BatchWs* w, P** ptr, size_t bytes) {
     return FC_OK;
 }
 
-// Buffers for nb problems in the given mode (grown, never shrunk; graphs
-// are rebuilt after a re-allocation).
-int batch_reserve(fftconv_plan* p, int nb, bool mixed) {
+// Problems a padded batch of nb launches: the next of 1, 2, 3, 4, 6, 8, 12,
+// 16, 24, 32, 48, 64, ... (at most 1.5 nb), so that the server's batches of
+// varying size reuse a few instantiated graphs.
+int batch_bucket(int nb) {
+    int b = 1;
+    while (b < nb) b = (b & (b - 1)) ? (b / 3) * 4 : (b >= 2 ? b + b / 2 : b + 1);
+    return b;
+}
+
+// Buffers for nb problems in the given mode on stream st (grown, never
+// shrunk; stream-ordered, so growing stalls no other stream; the graphs are
+// rebuilt after a re-allocation).
+int batch_reserve(fftconv_plan* p, int nb, bool mixed, cudaStream_t st) {
     if (!p->batch) {
         p->batch = new (std::nothrow) BatchWs();
         if (!p->batch) return FC_ENOMEM;
@@ -2407,12 +2426,20 @@ int batch_reserve(fftconv_plan* p, int nb, bool mixed) {
         FC_CK(cudaEventCreateWithFlags(&p->batch->ev, cudaEventDisableTiming));
     }
     BatchWs* w = p->batch;
+    if (w->st_cap < nb) {
+        const int n = nb > 64 ? nb : 64;
+        if (w->st_host) cudaFreeHost(w->st_host);
+        w->st_host = nullptr;
+        w->st_cap = 0;
+        if (cudaMallocHost(&w->st_host, sizeof(CgState) * n) != cudaSuccess)
+            return set_cuda_err(cudaGetLastError(), "cudaMallocHost(batch states)");
+        w->st_cap = n;
+    }
     const bool need64 = !mixed, need32 = mixed;
     if (w->cap >= nb && (!need64 || w->has64) && (!need32 || w->has32)) return FC_OK;
     const int cap = nb > w->cap ? nb : w->cap;
     const bool h64 = w->has64 || need64, h32 = w->has32 || need32;
-    cudaDeviceSynchronize();  // no graph of this workspace may still run
-    batch_buffers_free(w);
+    batch_buffers_free(w, st);
     const long N = p->N, Q = p->M / 2 + 1, QQ = Q * Q;
     const long zs = (long)(p->M / 2) * p->L;
     const long ps = 3 * (long)(p->L + 1);
@@ -2423,7 +2450,7 @@ int batch_reserve(fftconv_plan* p, int nb, bool mixed) {
     v.bs = BatchStride{N, zs, QQ, ps};
     int rc = FC_OK;
     auto A = [&](auto** ptr, size_t bytes) {
-        if (!rc) rc = balloc(w, ptr, bytes);
+        if (!rc) rc = balloc(w, ptr, bytes, st);
     };
     A(&v.x64, 8 * n * N);
     A(&v.r64, 8 * n * N);
@@ -2449,12 +2476,10 @@ int batch_reserve(fftconv_plan* p, int nb, bool mixed) {
         A(&v.pq32, 4 * n * QQ);
         A(&v.Z32, 8 * n * zs);
     }
-    if (!rc && cudaMallocHost(&w->st_host, sizeof(CgState) * n) != cudaSuccess)
-        rc = set_cuda_err(cudaGetLastError(), "cudaMallocHost(batch states)");
-    if (!rc && cudaMemset(v.st, 0, sizeof(CgState) * n) != cudaSuccess)
-        rc = set_cuda_err(cudaGetLastError(), "cudaMemset(batch states)");
+    if (!rc && cudaMemsetAsync(v.st, 0, sizeof(CgState) * n, st) != cudaSuccess)
+        rc = set_cuda_err(cudaGetLastError(), "cudaMemsetAsync(batch states)");
     if (rc) {
-        batch_buffers_free(w);
+        batch_buffers_free(w, st);
         return rc;
     }
     w->cap = cap;
@@ -2463,39 +2488,61 @@ int batch_reserve(fftconv_plan* p, int nb, bool mixed) {
     return FC_OK;
 }
 
+// The instantiated solve graph for (mode index gi, nbg problems), built on
+// first use.
+int batch_graph(fftconv_plan* p, int gi, int nbg, cudaGraphExec_t* ex) {
+    BatchWs* w = p->batch;
+    BatchWs::Graph* slot = nullptr;
+    for (auto& g : w->graphs)
+        if (g.ex && g.gi == gi && g.nb == nbg) slot = &g;
+    if (!slot) {
+        for (auto& g : w->graphs)
+            if (!slot || !g.ex || (slot->ex && g.used < slot->used)) slot = &g;
+        if (slot->ex) cudaGraphExecDestroy(slot->ex);
+        if (slot->g) cudaGraphDestroy(slot->g);
+        *slot = BatchWs::Graph{};
+        SolveView V = w->v;
+        V.nb = nbg;
+        int rc = build_graph_view(p, V, gi & 1, (gi & 2) != 0, &slot->g, &slot->ex);
+        if (rc) return rc;
+        slot->gi = gi;
+        slot->nb = nbg;
+    }
+    slot->used = ++w->tick;
+    *ex = slot->ex;
+    return FC_OK;
+}
+
 // Queue one batch on stream st: inputs in, the solve graph, x and the
-// states out.  The caller waits on st and then reads the states.
+// states out.  The caller waits on st and then reads the states.  pad: the
+// graph runs a bucket of problems (batch_bucket), the ones past nb finished
+// from the start (their blocks return at entry).
 int batch_enqueue(fftconv_plan* p, int nb, const double* s, const double* b, double* x, const uint8_t* mask,
-                  const cg_opts* o, cudaStream_t st, const double* rtols = nullptr) {
+                  const cg_opts* o, cudaStream_t st, const double* rtols = nullptr, bool pad = false) {
     const int mode = o->mode;
     const bool mixed = mode == FC_MODE_MIXED, precond = o->precond != 0;
-    int rc = batch_reserve(p, nb, mixed);
+    const int nbg = pad ? batch_bucket(nb) : nb;
+    int rc = batch_reserve(p, nbg, mixed, st);
     if (rc) return rc;
     BatchWs* w = p->batch;
-    const int gi = mode + 2 * (precond ? 1 : 0);
-    if (w->gexec[gi] && w->g_nb[gi] != nb) {
-        cudaGraphExecDestroy(w->gexec[gi]);
-        cudaGraphDestroy(w->graph[gi]);
-        w->gexec[gi] = nullptr;
-        w->graph[gi] = nullptr;
-    }
-    if (!w->gexec[gi]) {
-        SolveView V = w->v;
-        V.nb = nb;
-        rc = build_graph_view(p, V, mode, precond, &w->graph[gi], &w->gexec[gi]);
-        if (rc) return rc;
-        w->g_nb[gi] = nb;
-    }
+    cudaGraphExec_t ex = nullptr;
+    rc = batch_graph(p, mode + 2 * (precond ? 1 : 0), nbg, &ex);
+    if (rc) return rc;
     const SolveView& v = w->v;
     const long N = p->N;
     const size_t nN = (size_t)nb * N;
     CgState h;
     init_state(o, &h);
-    for (int k = 0; k < nb; ++k) {
+    for (int k = 0; k < nbg; ++k) {
         w->st_host[k] = h;
-        if (rtols) w->st_host[k].rtol2 = rtols[k] * rtols[k];
+        if (rtols && k < nb) w->st_host[k].rtol2 = rtols[k] * rtols[k];
+        if (k >= nb) {  // padding: nothing to do
+            w->st_host[k].finished = 1;
+            w->st_host[k].idle = 1;
+            w->st_host[k].status = FC_OK;
+        }
     }
-    FC_CK(cudaMemcpyAsync(v.st, w->st_host, sizeof(CgState) * nb, cudaMemcpyHostToDevice, st));
+    FC_CK(cudaMemcpyAsync(v.st, w->st_host, sizeof(CgState) * nbg, cudaMemcpyHostToDevice, st));
     FC_CK(cudaMemcpyAsync(v.s64, s, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     FC_CK(cudaMemcpyAsync(v.b64, b, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     if (mask) {
@@ -2511,7 +2558,7 @@ int batch_enqueue(fftconv_plan* p, int nb, const double* s, const double* b, dou
     } else {
         FC_CK(cudaMemcpyAsync(v.x64, x, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     }
-    FC_CK(cudaGraphLaunch(w->gexec[gi], st));
+    FC_CK(cudaGraphLaunch(ex, st));
     FC_CK(cudaMemcpyAsync(x, v.x64, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     FC_CK(cudaMemcpyAsync(w->st_host, v.st, sizeof(CgState) * nb, cudaMemcpyDeviceToHost, st));
     return FC_OK;
@@ -2568,7 +2615,7 @@ int fc_batch_solve_rtols(fftconv_plan* p, int nb, const double* s, const double*
     for (int k = 0; k < nb; ++k)
         if (!(rtols[k] >= 0.0)) return FC_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
-    rc = batch_enqueue(p, nb, s, b, x, nullptr, o, st, rtols);
+    rc = batch_enqueue(p, nb, s, b, x, nullptr, o, st, rtols, true);
     if (rc) return rc;
     FC_CK(wait_stream(p, st));
     return batch_results(p, nb, r,
@@ -2591,7 +2638,8 @@ extern "C" int cg_solve_groups(int ngroups, const cg_batch_group* g, const cg_op
     cudaStream_t st = (cudaStream_t)stream;
     // fork: every group on its plan's own stream after the caller's work
     for (int i = 0; i < ngroups; ++i) {
-        int rc = batch_reserve(g[i].plan, g[i].nb, o->mode == FC_MODE_MIXED);
+        fftconv_plan* gp = g[i].plan;
+        int rc = batch_reserve(gp, g[i].nb, o->mode == FC_MODE_MIXED, gp->batch ? gp->batch->stream : st);
         if (rc) return rc;
     }
     cudaEvent_t fork = g[0].plan->batch->ev;

@@ -9,13 +9,15 @@
 // Each slot is a host thread with its own non-blocking CUDA stream; slots
 // run their batches concurrently, so requests that arrive while others are
 // on the GPU overlap with them.  Plans (spectrum, tables, workspaces) stay
-// resident and are reused by later requests of the same L; idle plans of
-// other sizes are evicted when the budget requires it.  Each result is the
+// resident and are reused by later requests of the same L (one plan per
+// size: a request whose size is being solved waits and joins the next batch);
+// idle plans of other sizes are evicted when the budget requires it.  Each result is the
 // same whether a request runs alone or in a mix: a problem's arithmetic in a
 // batched solve depends only on its own inputs and its plan's launch shapes
 // (reductions run in a fixed order inside each problem), not on the batch.
 #include <cuda_runtime.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -38,6 +40,16 @@ namespace {
 
 constexpr int kMaxBatch = 64;  // requests one slot takes into one batched solve
 
+// FC_SERVER_TRACE=1: one line per batched solve on stderr (size, plan made or
+// kept, and the wall time of set-up, input copies, solve and output copies).
+bool trace_on() {
+    static const bool on = [] {
+        const char* e = getenv("FC_SERVER_TRACE");
+        return e && strcmp(e, "0");
+    }();
+    return on;
+}
+
 double now_s() {
     using namespace std::chrono;
     return duration<double>(steady_clock::now().time_since_epoch()).count();
@@ -46,7 +58,9 @@ double now_s() {
 struct Req {
     uint64_t ticket = 0;
     cg_request rq{};
-    std::vector<double> s, b;  // host copies taken at submit
+    std::vector<double> s, b;  // host copies taken at submit (empty with FC_REQ_BORROW)
+    const double* sp() const { return s.empty() ? rq.s : s.data(); }
+    const double* bp() const { return b.empty() ? rq.b : b.data(); }
     size_t est = 0;            // device bytes reserved: its plan (if one must be made) and its
                                // share of the plan's batch workspace
     int state = 0;             // 0 queued, 1 running, 2 done
@@ -59,8 +73,7 @@ struct Slot {
     std::thread th;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;  // blocking-sync event: a waiting slot thread sleeps
-    double *ds = nullptr, *db = nullptr, *dx = nullptr;  // device staging
-    double *hs = nullptr, *hb = nullptr, *hx = nullptr;  // pinned host staging
+    double *ds = nullptr, *db = nullptr, *dx = nullptr;  // device staging (stream-ordered)
     long cap = 0;
     std::vector<double> rtols;
     std::vector<cg_result> res;
@@ -111,6 +124,7 @@ struct cg_server {
     std::unordered_map<uint64_t, Req*> reqs;
     std::multimap<int, fftconv_plan*> idle;      // idle plans by L
     std::map<fftconv_plan*, size_t> plan_bytes;  // every plan held
+    std::map<int, int> plans_of;                 // plans held (idle, busy or being made) per L
     uint64_t next_ticket = 1;
     bool stop = false;
     std::vector<Slot*> slots;
@@ -129,6 +143,9 @@ Req* admit_one_locked(cg_server* sv, fftconv_plan** plan, std::vector<fftconv_pl
         Req* r = *it;
         auto ip = sv->idle.find(r->rq.L);
         const bool have = ip != sv->idle.end();
+        // a plan of this size exists but is busy: the request waits for it
+        // (and joins its next batch) rather than making a second plan
+        if (!have && sv->plans_of[r->rq.L] > 0) continue;
         const size_t need = have ? batch_bytes(r->rq.L, r->rq.mode) : r->est;
         size_t freeable = 0;
         for (auto& kv : sv->idle)
@@ -141,8 +158,10 @@ Req* admit_one_locked(cg_server* sv, fftconv_plan** plan, std::vector<fftconv_pl
             evict.push_back(v->second);
             sv->used -= sv->plan_bytes[v->second];
             sv->plan_bytes.erase(v->second);
+            sv->plans_of[v->first] -= 1;
             sv->idle.erase(v);
         }
+        if (!have) sv->plans_of[r->rq.L] += 1;  // the plan this slot will make
         r->est = need;  // reserved until the batch ends
         sv->used += need;
         if (sv->used > sv->peak) sv->peak = sv->used;
@@ -178,23 +197,27 @@ bool admit_locked(cg_server* sv, std::vector<Req*>& batch, fftconv_plan** plan, 
     return true;
 }
 
+// Device staging for n doubles per vector, grown geometrically with
+// stream-ordered allocations (no device-wide synchronisation while other
+// slots run).  There is no pinned host staging: allocating pinned memory
+// takes a driver lock for a long time (measured: 100-250 ms per growth,
+// stalling every slot), so the copies go straight from and to the
+// requests' own host arrays.
 int ensure_staging(Slot* sl, long n) {
     if (n <= sl->cap) return FC_OK;
-    cudaStreamSynchronize(sl->stream);
-    cudaFree(sl->ds);
-    cudaFree(sl->db);
-    cudaFree(sl->dx);
-    cudaFreeHost(sl->hs);
-    cudaFreeHost(sl->hb);
-    cudaFreeHost(sl->hx);
-    sl->ds = sl->db = sl->dx = sl->hs = sl->hb = sl->hx = nullptr;
+    long cap = sl->cap > 0 ? sl->cap : n;
+    while (cap < n) cap *= 2;
+    cudaFreeAsync(sl->ds, sl->stream);
+    cudaFreeAsync(sl->db, sl->stream);
+    cudaFreeAsync(sl->dx, sl->stream);
+    sl->ds = sl->db = sl->dx = nullptr;
     sl->cap = 0;
-    const size_t bytes = sizeof(double) * (size_t)n;
-    if (cudaMalloc(&sl->ds, bytes) != cudaSuccess || cudaMalloc(&sl->db, bytes) != cudaSuccess ||
-        cudaMalloc(&sl->dx, bytes) != cudaSuccess || cudaMallocHost(&sl->hs, bytes) != cudaSuccess ||
-        cudaMallocHost(&sl->hb, bytes) != cudaSuccess || cudaMallocHost(&sl->hx, bytes) != cudaSuccess)
+    const size_t bytes = sizeof(double) * (size_t)cap;
+    if (cudaMallocAsync((void**)&sl->ds, bytes, sl->stream) != cudaSuccess ||
+        cudaMallocAsync((void**)&sl->db, bytes, sl->stream) != cudaSuccess ||
+        cudaMallocAsync((void**)&sl->dx, bytes, sl->stream) != cudaSuccess)
         return FC_ENOMEM;
-    sl->cap = n;
+    sl->cap = cap;
     return FC_OK;
 }
 
@@ -231,14 +254,20 @@ void worker(cg_server* sv, Slot* sl) {
         if (rc == FC_OK) rc = ensure_staging(sl, (long)nb * N);
         sl->rtols.resize(nb);
         sl->res.assign(nb, cg_result{});
+        const double t_in = now_s();
         if (rc == FC_OK) {
-            for (int k = 0; k < nb; ++k) {
-                memcpy(sl->hs + (size_t)k * N, batch[k]->s.data(), sizeof(double) * N);
-                memcpy(sl->hb + (size_t)k * N, batch[k]->b.data(), sizeof(double) * N);
+            for (int k = 0; k < nb && rc == FC_OK; ++k) {
                 sl->rtols[k] = batch[k]->rq.rtol;
+                if (cudaMemcpyAsync(sl->ds + (size_t)k * N, batch[k]->sp(), sizeof(double) * N,
+                                    cudaMemcpyHostToDevice, sl->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(sl->db + (size_t)k * N, batch[k]->bp(), sizeof(double) * N,
+                                    cudaMemcpyHostToDevice, sl->stream) != cudaSuccess)
+                    rc = FC_ECUDA;
             }
-            cudaMemcpyAsync(sl->ds, sl->hs, sizeof(double) * N * nb, cudaMemcpyHostToDevice, sl->stream);
-            cudaMemcpyAsync(sl->db, sl->hb, sizeof(double) * N * nb, cudaMemcpyHostToDevice, sl->stream);
+        }
+        const double t_solve = now_s();
+        double t_out = t_solve;
+        if (rc == FC_OK) {
             cg_opts o{};
             o.rtol = r->rq.rtol;
             o.mode = r->rq.mode;
@@ -246,14 +275,24 @@ void worker(cg_server* sv, Slot* sl) {
             o.precond = r->rq.precond;
             rc = fc_batch_solve_rtols(plan, nb, sl->ds, sl->db, sl->dx, &o, sl->rtols.data(), sl->res.data(),
                                       sl->stream);
+            t_out = now_s();
             if (rc == FC_OK || rc == FC_ENOCONV || rc == FC_ENANINF) {
                 rc = FC_OK;
-                cudaMemcpyAsync(sl->hx, sl->dx, sizeof(double) * N * nb, cudaMemcpyDeviceToHost, sl->stream);
-                if (cudaEventRecord(sl->done, sl->stream) != cudaSuccess || cudaEventSynchronize(sl->done) != cudaSuccess)
-                    rc = FC_ECUDA;
                 for (int k = 0; k < nb && rc == FC_OK; ++k)
-                    if (batch[k]->rq.x) memcpy(batch[k]->rq.x, sl->hx + (size_t)k * N, sizeof(double) * N);
+                    if (batch[k]->rq.x &&
+                        cudaMemcpyAsync(batch[k]->rq.x, sl->dx + (size_t)k * N, sizeof(double) * N,
+                                        cudaMemcpyDeviceToHost, sl->stream) != cudaSuccess)
+                        rc = FC_ECUDA;
+                if (rc == FC_OK && (cudaEventRecord(sl->done, sl->stream) != cudaSuccess ||
+                                    cudaEventSynchronize(sl->done) != cudaSuccess))
+                    rc = FC_ECUDA;
             }
+        }
+        if (trace_on()) {
+            const double t_end = now_s();
+            fprintf(stderr, "[fftconv server] L=%d nb=%d plan=%s set-up %.2f ms, inputs %.2f ms, solve %.2f ms, "
+                    "outputs %.2f ms\n", L, nb, created ? "new" : "kept", (t_in - batch[0]->t_start) * 1e3,
+                    (t_solve - t_in) * 1e3, (t_out - t_solve) * 1e3, (t_end - t_out) * 1e3);
         }
         {
             std::lock_guard<std::mutex> lk(sv->mu);
@@ -269,6 +308,7 @@ void worker(cg_server* sv, Slot* sl) {
                 q->res.run_s = q->t_done - q->t_start;
                 q->state = 2;
             }
+            if (!plan && created) sv->plans_of[L] -= 1;  // the plan could not be made
             if (plan) {
                 size_t nbytes = 0;
                 fftconv_plan_info(plan, nullptr, nullptr, nullptr, &nbytes);
@@ -315,7 +355,7 @@ extern "C" int cg_server_create(cg_server** out, size_t mem_budget_bytes, int ma
 
 extern "C" int cg_batch_submit(cg_server* sv, const cg_request* rq, uint64_t* ticket) {
     if (!sv || !rq || !ticket || !rq->s || !rq->b || rq->L < 1 || rq->L > 4096 || !(rq->rtol >= 0) ||
-        (rq->mode != FC_MODE_F64 && rq->mode != FC_MODE_MIXED))
+        (rq->mode != FC_MODE_F64 && rq->mode != FC_MODE_MIXED) || (rq->flags & ~FC_REQ_BORROW))
         return FC_EINVAL;
     const size_t est = estimate_bytes(rq->L) + batch_bytes(rq->L, rq->mode);
     if (est > sv->budget) return FC_EBUDGET;
@@ -323,8 +363,10 @@ extern "C" int cg_batch_submit(cg_server* sv, const cg_request* rq, uint64_t* ti
     if (!r) return FC_ENOMEM;
     const size_t N = (size_t)rq->L * rq->L;
     try {
-        r->s.assign(rq->s, rq->s + N);
-        r->b.assign(rq->b, rq->b + N);
+        if (!(rq->flags & FC_REQ_BORROW)) {
+            r->s.assign(rq->s, rq->s + N);
+            r->b.assign(rq->b, rq->b + N);
+        }
     } catch (...) {
         delete r;
         return FC_ENOMEM;
@@ -391,13 +433,13 @@ extern "C" int cg_server_destroy(cg_server* sv) {
     for (auto& kv : sv->plan_bytes) fftconv_plan_destroy(kv.first);
     for (Slot* sl : sv->slots) {
         if (sl->stream) cudaStreamSynchronize(sl->stream);
-        cudaFree(sl->ds);
-        cudaFree(sl->db);
-        cudaFree(sl->dx);
-        cudaFreeHost(sl->hs);
-        cudaFreeHost(sl->hb);
-        cudaFreeHost(sl->hx);
-        if (sl->stream) cudaStreamDestroy(sl->stream);
+        if (sl->stream) {
+            cudaFreeAsync(sl->ds, sl->stream);
+            cudaFreeAsync(sl->db, sl->stream);
+            cudaFreeAsync(sl->dx, sl->stream);
+            cudaStreamSynchronize(sl->stream);
+            cudaStreamDestroy(sl->stream);
+        }
         if (sl->done) cudaEventDestroy(sl->done);
         delete sl;
     }

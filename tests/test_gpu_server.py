@@ -85,6 +85,23 @@ def test_same_size_requests_run_as_batches():
     sv.close()
 
 
+def test_borrowed_inputs():
+    """FC_REQ_BORROW: s and b are read when the request runs, not copied at
+    submit; the results are bitwise those of copied requests."""
+    L = 40
+    probs = [fc_inputs.problem(L, seed=70 + k, b_kind="normal") for k in range(6)]
+    sv = fc.cg_server_create(4 << 30, max_slots=2)
+    outs = {False: [np.zeros(L * L) for _ in probs], True: [np.zeros(L * L) for _ in probs]}
+    for borrow in (False, True):
+        ts = [fc.cg_batch_submit(sv, L, p["s"], p["b"], x_out=o, rtol=1e-9, mode=1, precond=True, borrow=borrow)
+              for p, o in zip(probs, outs[borrow])]
+        res = wait_all(sv, ts)
+        assert all(r["status"] == fc.FC_OK for r in res.values())
+    for a, b in zip(outs[False], outs[True]):
+        assert np.array_equal(a, b)
+    sv.close()
+
+
 def test_budget_admission_and_eviction():
     L1, L2 = 64, 128
     p1, p2 = fc_inputs.problem(L1, seed=1), fc_inputs.problem(L2, seed=2)
