@@ -430,6 +430,14 @@ def run_ours(args, world, rank, local, pg):
         allr = [r for g in res for r in g]
         assert all(r["status"] == fc.FC_OK and r["true_rel_resid"] <= 1e-8 for r in allr)
         dt = statistics.median(times)
+        # each size's batch alone (one cg_solve_batch call), for the split of the time
+        per_size = {}
+        for gp, gs, gb, gx, _ in groups:
+            gx.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fc.cg_solve_batch(gp, gs, gb, gx, **kw)
+            per_size[str(gp.L)] = round(1e3 * (time.perf_counter() - t0), 2)
         # plain FP64 CG one solve at a time on a sample of the same requests
         # (every 8th), each from x = 0 to the same tolerance
         f64_plans, f64_t, f64_n = {}, 0.0, 0
@@ -451,6 +459,7 @@ def run_ours(args, world, rank, local, pg):
                    "rtol": 1e-8, "mode": "mixed, Fourier-preconditioned, x0 = 0",
                    "launch": "cg_solve_groups: one batched solve graph per size, the sizes concurrent",
                    "seconds": round(dt, 4), "seconds_runs": [round(t, 4) for t in times],
+                   "ms_each_size_alone": per_size,
                    "solves_per_s": round(len(allr) / dt, 1),
                    "iters_mean": round(statistics.mean(r["iters"] for r in allr), 1),
                    "fp64_products_mean": round(statistics.mean(r["fp64_products"] for r in allr), 2),
