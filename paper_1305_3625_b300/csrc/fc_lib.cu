@@ -2648,18 +2648,19 @@ extern "C" int cg_solve_groups(int ngroups, const cg_batch_group* g, const cg_op
         BatchWs* w = g[i].plan->batch;
         FC_CK(cudaStreamWaitEvent(w->stream, fork, 0));
     }
-    for (int i = 0; i < ngroups; ++i) {
+    int rc = FC_OK;
+    for (int i = 0; i < ngroups && rc == FC_OK; ++i) {
         BatchWs* w = g[i].plan->batch;
-        int rc = batch_enqueue(g[i].plan, g[i].nb, g[i].s, g[i].b, g[i].x, g[i].mask, o, w->stream);
-        if (rc) return rc;
+        rc = batch_enqueue(g[i].plan, g[i].nb, g[i].s, g[i].b, g[i].x, g[i].mask, o, w->stream);
     }
-    // join
+    // join (also after a failed enqueue: no group's work outlives the call)
     for (int i = 0; i < ngroups; ++i) {
         BatchWs* w = g[i].plan->batch;
-        FC_CK(cudaEventRecord(w->ev, w->stream));
-        FC_CK(cudaStreamWaitEvent(st, w->ev, 0));
+        if (cudaEventRecord(w->ev, w->stream) != cudaSuccess || cudaStreamWaitEvent(st, w->ev, 0) != cudaSuccess)
+            cudaStreamSynchronize(w->stream);
     }
     FC_CK(wait_stream(g[0].plan, st));
+    if (rc) return rc;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int status = FC_OK;
     for (int i = 0; i < ngroups; ++i) {
