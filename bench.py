@@ -597,6 +597,45 @@ def run_ours(args, world, rank, local, pg):
                 if fr["steps_done"] else None}
         del fs, fb, ft, fmask, fx
 
+    # an ensemble of breaking runs (fc_fracture_run_batch): independent
+    # samples of the model in lockstep, against one run at a time
+    ensemble = None
+    if args.ensemble_runs > 0 and args.frac_steps > 0:
+        Le, ne, se = 128, args.ensemble_runs, 50
+        pe = [fc_inputs.problem(Le, seed=3000 + k, with_t=True, t_gradient=FRAC_GRADIENT) for k in range(ne)]
+        st_ = lambda key: torch.tensor(np.stack([q[key] for q in pe]), device=dev)
+        es, eb, et = st_("s"), st_("b"), st_("t")
+        eplan = fc.fftconv_plan_create(Le, fc.FC_F32 | fc.FC_F64)
+        kw = dict(rtol=RTOL, mode=fc.FC_MODE_MIXED, precond=True)
+
+        def ens_run():
+            em = torch.ones(ne * Le * Le, device=dev, dtype=torch.uint8)
+            ex_ = torch.zeros(ne * Le * Le, device=dev, dtype=torch.float64)
+            er = torch.empty(ne * se, device=dev, dtype=torch.int64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc_, rr = fc.fc_fracture_run_batch(eplan, es, eb, et, em, ex_, se, er, **kw)
+            return time.perf_counter() - t0, rc_, rr
+
+        ens_run()  # graphs and workspaces made
+        et_s, erc, err_ = ens_run()
+        assert erc == fc.FC_OK
+        # one run at a time, on the first runs of the same ensemble
+        n1, t1 = min(4, ne), 0.0
+        for k in range(n1):
+            m1 = torch.ones(Le * Le, device=dev, dtype=torch.uint8)
+            x1 = torch.zeros(Le * Le, device=dev, dtype=torch.float64)
+            r1 = torch.empty(se, device=dev, dtype=torch.int64)
+            fr1 = fc.fc_fracture_run(eplan, es[k], eb[k], et[k], m1, x1, se, r1, **kw)
+            t1 += fr1["seconds"]
+        ensemble = {"runs": ne, "L": Le, "steps_per_run": se, "t_gradient": FRAC_GRADIENT,
+                    "mode": "mixed, Fourier-preconditioned", "seconds": round(et_s, 4),
+                    "removal_steps_per_s": round(sum(r["steps_done"] for r in err_) / et_s, 1),
+                    "iters_per_step": round(sum(r["iters"] for r in err_) / max(sum(r["steps_done"] for r in err_), 1), 2),
+                    "one_run_at_a_time_steps_per_s": round(n1 * se / t1, 1),
+                    "vs_one_at_a_time": round(sum(r["steps_done"] for r in err_) / et_s / (n1 * se / t1), 1)}
+        del eplan
+
     # aggregate over ranks: units summed, slowest rank's time
     value, tot_ms, _ = aggregate_rate(args.steps, sum(ms_mixed), pg, dev)
 
@@ -656,6 +695,7 @@ def run_ours(args, world, rank, local, pg):
             "matvec_L4096": big,
             "large_loop_L4096": large_loop,
             "batched": batched,
+            "fracture_ensemble": ensemble,
             "batched_server": batched_server,
             "serving": serving,
             "roofline": {"bound": "hbm", "kernel": "fftconv_apply FP32 (3 passes), L=1024",
@@ -720,6 +760,7 @@ def main():
     ap.add_argument("--big", type=int, default=1)
     ap.add_argument("--big-steps", type=int, default=200, dest="big_steps")
     ap.add_argument("--frac-steps", type=int, default=100, dest="frac_steps")
+    ap.add_argument("--ensemble-runs", type=int, default=64, dest="ensemble_runs")
     ap.add_argument("--batch-solves", type=int, default=256, dest="batch_solves")
     ap.add_argument("--serve-requests", type=int, default=600, dest="serve_requests")
     ap.add_argument("--serve-f64", type=int, default=160, dest="serve_f64",

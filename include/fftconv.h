@@ -334,6 +334,29 @@ int fc_fracture_run(fftconv_plan *p, const double *s, const double *b, const dou
                     fc_run_result *res, fc_stream_t stream);
 
 /*
+ * fc_fracture_run_batch -- nb independent breaking runs of the plan's size
+ * (an ensemble of samples, Section 2's model with its own s, b, t each) in
+ * lockstep: every step is one batched solve of all runs that are still going
+ * (cg_solve_batch's graph, warm-started from each run's last solution, every
+ * first residual an FP64 product) and one batched removal.  A run stops when
+ * no active fibre is left or its solve does not converge; from then on its
+ * entries are -1 and its mask and x stay as they were.  The whole run stops
+ * when every run has stopped or after `steps` steps.
+ *   s, b, t   device, nb*L*L doubles (run k at offset k*L*L).
+ *   mask, x   device, nb*L*L bytes / doubles, updated in place.
+ *   removed   device, nb*steps int64: run k's index removed at step j at
+ *             k*steps + j (-1: none).
+ *   ratio     device, nb*steps doubles (same layout), or NULL: max |x|/t.
+ *   res       host, nb results, or NULL (seconds: the whole call).
+ * Blocks until the run ends (one host synchronisation per step).  Returns
+ * FC_OK when every run ended without a failed solve, else the first failing
+ * status.  Errors: FC_EINVAL, FC_ENOMEM, FC_ECUDA.
+ */
+int fc_fracture_run_batch(fftconv_plan *p, int nb, const double *s, const double *b, const double *t,
+                          uint8_t *mask, double *x, int steps, const cg_opts *o, int64_t *removed,
+                          double *ratio, fc_run_result *res, fc_stream_t stream);
+
+/*
  * fc_masked_step_static -- the same breaking step as fc_masked_step, for
  * callers that cannot allocate device memory at the point of the call: a
  * process whose device memory is entirely reserved by another allocator (a

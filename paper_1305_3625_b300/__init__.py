@@ -122,6 +122,8 @@ def _load():
     lib.fftconv_plan_sync_mode.argtypes = [vp, i]
     lib.fc_fracture_run.argtypes = [vp, vp, vp, vp, vp, vp, i, ctypes.POINTER(cg_opts), vp, vp,
                                     ctypes.POINTER(fc_run_result), vp]
+    lib.fc_fracture_run_batch.argtypes = [vp, i, vp, vp, vp, vp, vp, i, ctypes.POINTER(cg_opts), vp, vp,
+                                          ctypes.POINTER(fc_run_result), vp]
     lib.fc_masked_step_static.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp]
     lib.cg_server_create.argtypes = [ctypes.POINTER(vp), sz, i, vp]
     lib.cg_batch_submit.argtypes = [vp, ctypes.POINTER(cg_request), ctypes.POINTER(ctypes.c_uint64)]
@@ -366,6 +368,31 @@ def fc_fracture_run(plan: Plan, s, b, t, mask, x, steps: int, removed, ratio=Non
     if rc in (FC_EINVAL, FC_ECUDA, FC_ENOMEM):
         raise FcError(rc, "fc_fracture_run")
     return r.as_dict()
+
+
+def fc_fracture_run_batch(plan: Plan, s, b, t, mask, x, steps: int, removed, ratio=None, rtol: float = 1e-10,
+                          mode: int = FC_MODE_F64, precond: bool = False, inner_rtol: float = 0.0,
+                          max_iter: int = 0, stream=None):
+    """nb breaking runs in lockstep: s, b, t, x (float64) and mask (uint8) hold
+    nb*L*L elements (run k at offset k*L*L); removed (int64) and ratio
+    (float64, optional) nb*steps (run k's step j at k*steps + j).  Returns
+    (rc, list of nb run-result dicts)."""
+    n = plan.L * plan.L
+    if not isinstance(x, torch.Tensor) or x.numel() % n or x.numel() == 0:
+        raise ValueError(f"x must hold a positive multiple of {n} elements")
+    nb = x.numel() // n
+    o = cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode), inner_rtol=float(inner_rtol),
+                precond=int(bool(precond)))
+    rs = (fc_run_result * nb)()
+    rc = _lib.fc_fracture_run_batch(plan.handle, nb, _ptr(s, torch.float64, nb * n, "s"),
+                                    _ptr(b, torch.float64, nb * n, "b"), _ptr(t, torch.float64, nb * n, "t"),
+                                    _ptr(mask, torch.uint8, nb * n, "mask"), _ptr(x, torch.float64, nb * n, "x"),
+                                    int(steps), ctypes.byref(o),
+                                    _ptr(removed, torch.int64, nb * int(steps), "removed"),
+                                    _ptr(ratio, torch.float64, nb * int(steps), "ratio"), rs, _stream(stream))
+    if rc in (FC_EINVAL, FC_ECUDA, FC_ENOMEM):
+        raise FcError(rc, "fc_fracture_run_batch")
+    return rc, [r.as_dict() for r in rs]
 
 
 def fftconv_plan_info(plan: Plan) -> dict:

@@ -436,9 +436,28 @@ __device__ __forceinline__ void am_block_reduce(double* sv, long long* si) {
 // to the lowest index), then mask[i*] = 0 and x[i*] = 0.  Each block reduces
 // its sites; the last block to finish reduces the per-block winners.  The
 // order is total, so the result does not depend on the reduction order.
+// Problem blockIdx.y of a batch: fields at stride N, its result at stride
+// rstride, its own winners and counter; with st, a problem whose state holds
+// a status other than FC_OK (its solve failed, or it sits the step out)
+// removes nothing and reports -1.
 __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, uint8_t* mask, double* x,
                                                        int64_t* removed, double* ratio, double* pv,
-                                                       long long* pi, ArgmaxCtl* ctl) {
+                                                       long long* pi, ArgmaxCtl* ctl, long rstride = 0,
+                                                       const CgState* st = nullptr) {
+    if (st && st[blockIdx.y].status != FC_OK) {  // the same in every block of the problem
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            removed[(long)blockIdx.y * rstride] = -1;
+            if (ratio) ratio[(long)blockIdx.y * rstride] = -1.0;
+        }
+        return;
+    }
+    const long yo = (long)blockIdx.y * N;
+    t += yo, mask += yo, x += yo;
+    removed += (long)blockIdx.y * rstride;
+    if (ratio) ratio += (long)blockIdx.y * rstride;
+    pv += (long)blockIdx.y * gridDim.x;
+    pi += (long)blockIdx.y * gridDim.x;
+    ctl += blockIdx.y;
     __shared__ double sv[256];
     __shared__ long long si[256];
     __shared__ bool is_last;
@@ -2354,6 +2373,11 @@ struct BatchWs {
     cudaEvent_t ev = nullptr;
     size_t bytes = 0;
     std::vector<void*> blocks;
+    // batched breaking steps: per-problem argmax winners and counters
+    double* am_v = nullptr;
+    long long* am_i = nullptr;
+    ArgmaxCtl* am_ctl = nullptr;
+    int am_cap = 0;
 };
 
 namespace {
@@ -2376,6 +2400,10 @@ void batch_buffers_free(BatchWs* w, cudaStream_t st) {
     w->cap = 0;
     w->has64 = w->has32 = false;
     w->bytes = 0;
+    w->am_v = nullptr;
+    w->am_i = nullptr;
+    w->am_ctl = nullptr;
+    w->am_cap = 0;
 }
 
 size_t batch_bytes_of(const fftconv_plan* p) { return p->batch ? p->batch->bytes : 0; }
@@ -2666,6 +2694,131 @@ extern "C" int cg_solve_groups(int ngroups, const cg_batch_group* g, const cg_op
     for (int i = 0; i < ngroups; ++i) {
         const int si = batch_results(g[i].plan, g[i].nb, g[i].r, secs);
         if (status == FC_OK) status = si;
+    }
+    return status;
+}
+
+// fc_fracture_run_batch: nb independent breaking runs of the plan's size in
+// lockstep.  The fields stay in the batch workspace for the whole run; each
+// step is one batched solve (warm-started from the last solution, first
+// residual by product) and one batched removal.
+extern "C" int fc_fracture_run_batch(fftconv_plan* p, int nb, const double* s, const double* b, const double* t,
+                                     uint8_t* mask, double* x, int steps, const cg_opts* o, int64_t* removed,
+                                     double* ratio, fc_run_result* res, fc_stream_t stream) {
+    if (!t || !mask || !removed || steps < 0) return FC_EINVAL;
+    cg_opts def{};
+    def.rtol = 1e-10;
+    def.mode = FC_MODE_F64;
+    if (!o) o = &def;
+    int rc = batch_check(p, nb, s, b, x, o);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const auto t0 = std::chrono::steady_clock::now();
+    const bool mixed = o->mode == FC_MODE_MIXED, precond = o->precond != 0;
+    rc = batch_reserve(p, nb, mixed, st);
+    if (rc) return rc;
+    BatchWs* w = p->batch;
+    if (w->am_cap < nb) {
+        rc = balloc(w, &w->am_v, sizeof(double) * (size_t)nb * p->am_grid, st);
+        if (!rc) rc = balloc(w, &w->am_i, sizeof(long long) * (size_t)nb * p->am_grid, st);
+        if (!rc) rc = balloc(w, &w->am_ctl, sizeof(ArgmaxCtl) * (size_t)nb, st);
+        if (rc) return rc;
+        FC_CK(cudaMemsetAsync(w->am_ctl, 0, sizeof(ArgmaxCtl) * (size_t)nb, st));
+        w->am_cap = nb;
+    }
+    cudaGraphExec_t ex = nullptr;
+    rc = batch_graph(p, o->mode + 2 * (precond ? 1 : 0), nb, &ex);
+    if (rc) return rc;
+    const SolveView& v = w->v;
+    const long N = p->N;
+    const size_t nN = (size_t)nb * N;
+    FC_CK(cudaMemcpyAsync(v.s64, s, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(v.b64, b, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(v.x64, x, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(v.mask, mask, nN, cudaMemcpyDeviceToDevice, st));
+    std::vector<fc_run_result> acc((size_t)nb);
+    std::vector<int> alive((size_t)nb, 1);
+    for (auto& a : acc) a.status = FC_OK;
+    CgState h;
+    init_state(o, &h);
+    int64_t* rm_host = nullptr;
+    FC_CK(cudaMallocHost(&rm_host, sizeof(int64_t) * (size_t)nb));
+    int step = 0;
+    for (; step < steps && rc == FC_OK; ++step) {
+        for (int k = 0; k < nb; ++k) {
+            w->st_host[k] = h;
+            if (!alive[k]) {  // nothing left to solve: the problem sits out (and removes nothing)
+                w->st_host[k].finished = 1;
+                w->st_host[k].idle = 1;
+                w->st_host[k].status = FC_ENOCONV;
+            }
+        }
+        if (cudaMemcpyAsync(v.st, w->st_host, sizeof(CgState) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaGraphLaunch(ex, st) != cudaSuccess ||
+            cudaMemcpyAsync(w->st_host, v.st, sizeof(CgState) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(solve)");
+            break;
+        }
+        k_masked_argmax<<<dim3(p->am_grid, nb), 256, 0, st>>>(N, t, v.mask, v.x64, removed + step,
+                                                              ratio ? ratio + step : nullptr, w->am_v, w->am_i,
+                                                              w->am_ctl, steps, v.st);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpy2DAsync(rm_host, sizeof(int64_t), removed + step, sizeof(int64_t) * steps, sizeof(int64_t), nb,
+                              cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            wait_stream(p, st) != cudaSuccess) {
+            rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(step)");
+            break;
+        }
+        int any = 0;
+        for (int k = 0; k < nb; ++k) {
+            if (!alive[k]) continue;
+            const CgState& f = w->st_host[k];
+            cg_result r{};
+            fill_result(f, &r);
+            acc[k].iters += r.iters;
+            acc[k].fp64_products += r.fp64_products;
+            if (f.status != FC_OK) {
+                acc[k].status = f.status;
+                alive[k] = 0;
+            } else if (rm_host[k] < 0) {
+                alive[k] = 0;  // no active fibre left
+            } else {
+                acc[k].steps_done = step + 1;
+            }
+            any |= alive[k];
+        }
+        if (!any) {
+            ++step;
+            break;
+        }
+    }
+    // steps not run: nothing removed (index -1, ratio -1)
+    if (rc == FC_OK && step < steps) {
+        const std::vector<int64_t> none((size_t)(steps - step), -1);
+        const std::vector<double> noratio((size_t)(steps - step), -1.0);
+        for (int k = 0; k < nb && rc == FC_OK; ++k) {
+            if (cudaMemcpyAsync(removed + (size_t)k * steps + step, none.data(), sizeof(int64_t) * (steps - step),
+                                cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                (ratio && cudaMemcpyAsync(ratio + (size_t)k * steps + step, noratio.data(),
+                                          sizeof(double) * (steps - step), cudaMemcpyHostToDevice, st) != cudaSuccess))
+                rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(tail)");
+        }
+        if (rc == FC_OK && cudaStreamSynchronize(st) != cudaSuccess)
+            rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(tail)");
+    }
+    if (rc == FC_OK) {
+        FC_CK(cudaMemcpyAsync(x, v.x64, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
+        FC_CK(cudaMemcpyAsync(mask, v.mask, nN, cudaMemcpyDeviceToDevice, st));
+        FC_CK(wait_stream(p, st));
+    }
+    cudaFreeHost(rm_host);
+    if (rc) return rc;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    int status = FC_OK;
+    for (int k = 0; k < nb; ++k) {
+        acc[k].seconds = secs;
+        if (res) res[k] = acc[k];
+        if (status == FC_OK && acc[k].status != FC_OK) status = acc[k].status;
     }
     return status;
 }

@@ -88,3 +88,52 @@ def test_run_stops_when_nothing_is_left():
     assert sorted(rem[:4].tolist()) == [0, 1, 2, 3] and rem[4] == -1
     assert rat[4] == -1.0 and np.all(rat[:4] > 0)
     assert not mask.any()
+
+
+def test_batched_runs_match_oracle_loops():
+    """Three independent FP64 runs in one fc_fracture_run_batch: each breaks
+    the oracle's fibres in the oracle's order with its load ratios, the
+    problem sizes' smallest (L = 5) running out of fibres mid-run."""
+    L, nb, steps = 5, 3, 30
+    ps = [fc_inputs.problem(L, seed=20 + k, with_t=True, t_gradient=1.0 + k) for k in range(nb)]
+    pl = fc.fftconv_plan_create(L, fc.FC_F32 | fc.FC_F64)
+    st = lambda key: dev(np.stack([q[key] for q in ps]))
+    mask = dev(np.ones((nb, L * L)), torch.uint8)
+    x = dev(np.zeros((nb, L * L)))
+    removed = torch.full((nb * steps,), -2, device="cuda", dtype=torch.int64)
+    ratio = torch.zeros(nb * steps, device="cuda", dtype=torch.float64)
+    rc, rs = fc.fc_fracture_run_batch(pl, st("s"), st("b"), st("t"), mask, x, steps, removed, ratio,
+                                      rtol=1e-12, mode=fc.FC_MODE_F64)
+    assert rc == fc.FC_OK
+    rem, rat, mk = host(removed).reshape(nb, steps), host(ratio).reshape(nb, steps), host(mask).reshape(nb, -1)
+    for k, q in enumerate(ps):
+        assert rs[k]["status"] == fc.FC_OK and rs[k]["steps_done"] == L * L
+        want = oracle.masked_loop(L, q["s"], q["b"], q["t"], L * L, rtol=1e-13)
+        assert np.array_equal(rem[k, :L * L], want["picks"])
+        assert np.allclose(rat[k, :L * L], want["ratios"], rtol=1e-9, atol=0)
+        assert np.all(rem[k, L * L:] == -1) and np.all(rat[k, L * L:] == -1.0)
+        assert not mk[k].any()
+
+
+@pytest.mark.parametrize("mode,precond", [(fc.FC_MODE_F64, False), (fc.FC_MODE_MIXED, True)])
+def test_batched_runs_match_single_runs(mode, precond):
+    """Four runs at L = 24 (different gradients): the same picks as each run
+    alone through fc_fracture_run, ratios within the solve tolerance."""
+    L, nb, steps = 24, 4, 12
+    rtol = 1e-12 if mode == fc.FC_MODE_F64 else 1e-10
+    ps = [fc_inputs.problem(L, seed=40 + k, with_t=True, t_gradient=0.5 * k) for k in range(nb)]
+    pl = fc.fftconv_plan_create(L, fc.FC_F32 | fc.FC_F64)
+    st = lambda key: dev(np.stack([q[key] for q in ps]))
+    mask = dev(np.ones((nb, L * L)), torch.uint8)
+    x = dev(np.zeros((nb, L * L)))
+    removed = torch.empty(nb * steps, device="cuda", dtype=torch.int64)
+    ratio = torch.empty(nb * steps, device="cuda", dtype=torch.float64)
+    rc, rs = fc.fc_fracture_run_batch(pl, st("s"), st("b"), st("t"), mask, x, steps, removed, ratio, rtol=rtol,
+                                      mode=mode, precond=precond)
+    assert rc == fc.FC_OK and all(r["steps_done"] == steps for r in rs)
+    rem, rat = host(removed).reshape(nb, steps), host(ratio).reshape(nb, steps)
+    for k, q in enumerate(ps):
+        _, r1, rem1, rat1, mask1, x1 = run_gpu(L, q, steps, mode, rtol, precond=precond)
+        assert np.array_equal(rem[k], rem1)
+        assert np.allclose(rat[k], rat1, rtol=1e-6 if mode == fc.FC_MODE_MIXED else 1e-9, atol=0)
+        assert np.array_equal(host(mask).reshape(nb, -1)[k], mask1)
