@@ -337,8 +337,11 @@ int fc_fracture_run(fftconv_plan *p, const double *s, const double *b, const dou
  * fc_fracture_run_batch -- nb independent breaking runs of the plan's size
  * (an ensemble of samples, Section 2's model with its own s, b, t each) in
  * lockstep: every step is one batched solve of all runs that are still going
- * (cg_solve_batch's graph, warm-started from each run's last solution, every
- * first residual an FP64 product) and one batched removal.  A run stops when
+ * (cg_solve_batch's graph, warm-started from each run's last solution) and
+ * one batched removal.  After the first step each run's first true residual
+ * is its last final FP64 residual updated for the one removal (r_i += x_k
+ * G(r_i - r_k) on the remaining sites; cg_opts.warm_resid = -1 recomputes
+ * it); the residual that certifies each solve is always an FP64 product.  A run stops when
  * no active fibre is left or its solve does not converge; from then on its
  * entries are -1 and its mask and x stay as they were.  The whole run stops
  * when every run has stopped or after `steps` steps.

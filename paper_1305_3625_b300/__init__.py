@@ -372,7 +372,7 @@ def fc_fracture_run(plan: Plan, s, b, t, mask, x, steps: int, removed, ratio=Non
 
 def fc_fracture_run_batch(plan: Plan, s, b, t, mask, x, steps: int, removed, ratio=None, rtol: float = 1e-10,
                           mode: int = FC_MODE_F64, precond: bool = False, inner_rtol: float = 0.0,
-                          max_iter: int = 0, stream=None):
+                          max_iter: int = 0, warm_resid: bool = True, stream=None):
     """nb breaking runs in lockstep: s, b, t, x (float64) and mask (uint8) hold
     nb*L*L elements (run k at offset k*L*L); removed (int64) and ratio
     (float64, optional) nb*steps (run k's step j at k*steps + j).  Returns
@@ -382,7 +382,7 @@ def fc_fracture_run_batch(plan: Plan, s, b, t, mask, x, steps: int, removed, rat
         raise ValueError(f"x must hold a positive multiple of {n} elements")
     nb = x.numel() // n
     o = cg_opts(rtol=float(rtol), max_iter=int(max_iter), mode=int(mode), inner_rtol=float(inner_rtol),
-                precond=int(bool(precond)))
+                precond=int(bool(precond)), warm_resid=0 if warm_resid else -1)
     rs = (fc_run_result * nb)()
     rc = _lib.fc_fracture_run_batch(plan.handle, nb, _ptr(s, torch.float64, nb * n, "s"),
                                     _ptr(b, torch.float64, nb * n, "b"), _ptr(t, torch.float64, nb * n, "t"),

@@ -284,6 +284,43 @@ __global__ void __launch_bounds__(256) k_zero_start(long N, const double* b, con
     }
 }
 
+// Residual update after one removal per problem (batched breaking runs,
+// problem blockIdx.y): the previous solve's final residual r = P (b - A x)
+// becomes P' (b - A P' x) = P' (r + x_k A e_k), i.e. r_i += x_k G(r_i - r_k)
+// on the sites still active and 0 at the removed site k, with |r|^2 and the
+// new |P' b|^2 handed to the next solve's first refinement decision (warm).
+// A problem without a removal (k < 0) is left to recompute its residual.
+__global__ void __launch_bounds__(256) k_warm_resid_batch(long N, int L, const double* gt, const uint8_t* mask,
+                                                          const double* b64, double* r64, double* part, long bpart,
+                                                          CgState* st, const long long* kidx, const double* kx) {
+    const long long k = kidx[blockIdx.y];
+    if (k < 0) return;  // the same in every block of the problem
+    const long o = (long)blockIdx.y * N;
+    mask += o, b64 += o, r64 += o;
+    part += blockIdx.y * bpart;
+    st += blockIdx.y;
+    const double xk = kx[blockIdx.y];
+    const int ky = (int)(k / L), kxx = (int)(k % L);
+    double v[2] = {0.0, 0.0}, tot[2];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        double r = 0.0;
+        if (mask[i]) {
+            const int iy = (int)(i / L), ix = (int)(i % L);
+            r = r64[i] + xk * __ldg(gt + (size_t)abs(iy - ky) * L + abs(ix - kxx));
+            const double bv = b64[i];
+            v[1] += bv * bv;
+        }
+        r64[i] = r;
+        v[0] += r * r;
+    }
+    if (grid_sum_last<2>(v, part, &st->cntC, tot) && threadIdx.x == 0) {
+        st->rr64 = tot[0];
+        st->bb = tot[1];
+        st->warm = 1;
+        st->warm_used = 1;
+    }
+}
+
 // Loop control of a batched solve (one node after the deciding pass): the
 // outer loop runs while any problem is unfinished, the inner loop while any
 // problem has an inner run open.  A finished problem is idle.
@@ -443,11 +480,13 @@ __device__ __forceinline__ void am_block_reduce(double* sv, long long* si) {
 __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, uint8_t* mask, double* x,
                                                        int64_t* removed, double* ratio, double* pv,
                                                        long long* pi, ArgmaxCtl* ctl, long rstride = 0,
-                                                       const CgState* st = nullptr) {
+                                                       const CgState* st = nullptr, long long* kidx = nullptr,
+                                                       double* kx = nullptr) {
     if (st && st[blockIdx.y].status != FC_OK) {  // the same in every block of the problem
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             removed[(long)blockIdx.y * rstride] = -1;
             if (ratio) ratio[(long)blockIdx.y * rstride] = -1.0;
+            if (kidx) kidx[blockIdx.y] = -1;
         }
         return;
     }
@@ -500,6 +539,10 @@ __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, 
         const long long gi = si[0];
         *removed = gi;
         if (ratio) *ratio = sv[0];  // max |x|/t (-1 with no active site)
+        if (kidx) {  // batched runs: the removal, for the next solve's residual update
+            kidx[blockIdx.y] = gi;
+            kx[blockIdx.y] = gi >= 0 ? x[gi] : 0.0;
+        }
         if (gi >= 0) {
             mask[gi] = 0;
             x[gi] = 0.0;
@@ -2377,6 +2420,8 @@ struct BatchWs {
     double* am_v = nullptr;
     long long* am_i = nullptr;
     ArgmaxCtl* am_ctl = nullptr;
+    long long* rm_idx = nullptr;  // per problem: the site removed last and its x before removal
+    double* rm_x = nullptr;
     int am_cap = 0;
 };
 
@@ -2403,6 +2448,8 @@ void batch_buffers_free(BatchWs* w, cudaStream_t st) {
     w->am_v = nullptr;
     w->am_i = nullptr;
     w->am_ctl = nullptr;
+    w->rm_idx = nullptr;
+    w->rm_x = nullptr;
     w->am_cap = 0;
 }
 
@@ -2722,6 +2769,8 @@ extern "C" int fc_fracture_run_batch(fftconv_plan* p, int nb, const double* s, c
         rc = balloc(w, &w->am_v, sizeof(double) * (size_t)nb * p->am_grid, st);
         if (!rc) rc = balloc(w, &w->am_i, sizeof(long long) * (size_t)nb * p->am_grid, st);
         if (!rc) rc = balloc(w, &w->am_ctl, sizeof(ArgmaxCtl) * (size_t)nb, st);
+        if (!rc) rc = balloc(w, &w->rm_idx, sizeof(long long) * (size_t)nb, st);
+        if (!rc) rc = balloc(w, &w->rm_x, sizeof(double) * (size_t)nb, st);
         if (rc) return rc;
         FC_CK(cudaMemsetAsync(w->am_ctl, 0, sizeof(ArgmaxCtl) * (size_t)nb, st));
         w->am_cap = nb;
@@ -2741,6 +2790,9 @@ extern "C" int fc_fracture_run_batch(fftconv_plan* p, int nb, const double* s, c
     for (auto& a : acc) a.status = FC_OK;
     CgState h;
     init_state(o, &h);
+    // after the first step each solve's first residual is updated from the
+    // last one (the removal is the only change), unless turned off
+    const bool warm = o->warm_resid == 0 && p->gtab != nullptr;
     int64_t* rm_host = nullptr;
     FC_CK(cudaMallocHost(&rm_host, sizeof(int64_t) * (size_t)nb));
     int step = 0;
@@ -2753,15 +2805,29 @@ extern "C" int fc_fracture_run_batch(fftconv_plan* p, int nb, const double* s, c
                 w->st_host[k].status = FC_ENOCONV;
             }
         }
-        if (cudaMemcpyAsync(v.st, w->st_host, sizeof(CgState) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-            cudaGraphLaunch(ex, st) != cudaSuccess ||
+        if (cudaMemcpyAsync(v.st, w->st_host, sizeof(CgState) * nb, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(states)");
+            break;
+        }
+        if (step > 0 && warm) {
+            // the first residual of this solve from the last one and the removal
+            int gw = grid_1d(N, 256);
+            if (gw > p->L + 1) gw = p->L + 1;  // two partial sums per block in 3 (L+1) doubles per problem
+            k_warm_resid_batch<<<dim3(gw, nb), 256, 0, st>>>(N, p->L, p->gtab, v.mask, v.b64, v.r64, v.part,
+                                                             v.bs.part, v.st, w->rm_idx, w->rm_x);
+            if (cudaGetLastError() != cudaSuccess) {
+                rc = set_cuda_err(cudaGetLastError(), "k_warm_resid_batch");
+                break;
+            }
+        }
+        if (cudaGraphLaunch(ex, st) != cudaSuccess ||
             cudaMemcpyAsync(w->st_host, v.st, sizeof(CgState) * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
             rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(solve)");
             break;
         }
         k_masked_argmax<<<dim3(p->am_grid, nb), 256, 0, st>>>(N, t, v.mask, v.x64, removed + step,
                                                               ratio ? ratio + step : nullptr, w->am_v, w->am_i,
-                                                              w->am_ctl, steps, v.st);
+                                                              w->am_ctl, steps, v.st, w->rm_idx, w->rm_x);
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpy2DAsync(rm_host, sizeof(int64_t), removed + step, sizeof(int64_t) * steps, sizeof(int64_t), nb,
                               cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -2777,6 +2843,7 @@ extern "C" int fc_fracture_run_batch(fftconv_plan* p, int nb, const double* s, c
             fill_result(f, &r);
             acc[k].iters += r.iters;
             acc[k].fp64_products += r.fp64_products;
+            acc[k].resid_updated += r.resid_updated;
             if (f.status != FC_OK) {
                 acc[k].status = f.status;
                 alive[k] = 0;

@@ -108,6 +108,7 @@ def test_batched_runs_match_oracle_loops():
     rem, rat, mk = host(removed).reshape(nb, steps), host(ratio).reshape(nb, steps), host(mask).reshape(nb, -1)
     for k, q in enumerate(ps):
         assert rs[k]["status"] == fc.FC_OK and rs[k]["steps_done"] == L * L
+        assert rs[k]["resid_updated"] >= L * L - 1  # every solve after the first
         want = oracle.masked_loop(L, q["s"], q["b"], q["t"], L * L, rtol=1e-13)
         assert np.array_equal(rem[k, :L * L], want["picks"])
         assert np.allclose(rat[k, :L * L], want["ratios"], rtol=1e-9, atol=0)
@@ -115,10 +116,13 @@ def test_batched_runs_match_oracle_loops():
         assert not mk[k].any()
 
 
+@pytest.mark.parametrize("warm", [True, False])
 @pytest.mark.parametrize("mode,precond", [(fc.FC_MODE_F64, False), (fc.FC_MODE_MIXED, True)])
-def test_batched_runs_match_single_runs(mode, precond):
-    """Four runs at L = 24 (different gradients): the same picks as each run
-    alone through fc_fracture_run, ratios within the solve tolerance."""
+def test_batched_runs_match_single_runs(mode, precond, warm):
+    """Four runs at L = 24 (different gradients), with and without the
+    residual update after each removal: the same picks as each run alone
+    through fc_fracture_run, ratios within the solve tolerance, one FP64
+    product fewer per step with the update."""
     L, nb, steps = 24, 4, 12
     rtol = 1e-12 if mode == fc.FC_MODE_F64 else 1e-10
     ps = [fc_inputs.problem(L, seed=40 + k, with_t=True, t_gradient=0.5 * k) for k in range(nb)]
@@ -129,8 +133,10 @@ def test_batched_runs_match_single_runs(mode, precond):
     removed = torch.empty(nb * steps, device="cuda", dtype=torch.int64)
     ratio = torch.empty(nb * steps, device="cuda", dtype=torch.float64)
     rc, rs = fc.fc_fracture_run_batch(pl, st("s"), st("b"), st("t"), mask, x, steps, removed, ratio, rtol=rtol,
-                                      mode=mode, precond=precond)
+                                      mode=mode, precond=precond, warm_resid=warm)
     assert rc == fc.FC_OK and all(r["steps_done"] == steps for r in rs)
+    for r in rs:
+        assert r["resid_updated"] == (steps - 1 if warm else 0)
     rem, rat = host(removed).reshape(nb, steps), host(ratio).reshape(nb, steps)
     for k, q in enumerate(ps):
         _, r1, rem1, rat1, mask1, x1 = run_gpu(L, q, steps, mode, rtol, precond=precond)
