@@ -392,9 +392,9 @@ def run_ours(args, world, rank, local, pg):
                            "snapshot during the next step; x and mask stay on the device"}
 
     # batched workload: 256 independent mixed solves, L ~ U{64,128,256,512},
-    # b ~ N(0,1), rtol 1e-8, from x = 0: one cg_solve_groups call (each size a
-    # batched graph on its plan's stream, the four running concurrently); the
-    # same requests through the solve server as a second figure
+    # b ~ N(0,1), rtol 1e-8, from x = 0: one cg_solve_groups call (one graph,
+    # each size's batched solve a parallel branch of it); the same requests
+    # through the solve server as a second figure
     batched = None
     batched_server = None
     serving = None
@@ -457,7 +457,7 @@ def run_ours(args, world, rank, local, pg):
         batched = {"solves": len(allr), "L": "U{64,128,256,512}", "groups": {str(g[0].L): int(g[3].shape[0])
                                                                           for g in groups},
                    "rtol": 1e-8, "mode": "mixed, Fourier-preconditioned, x0 = 0",
-                   "launch": "cg_solve_groups: one batched solve graph per size, the sizes concurrent",
+                   "launch": "cg_solve_groups: one graph launch, a batched solve per size as parallel branches",
                    "seconds": round(dt, 4), "seconds_runs": [round(t, 4) for t in times],
                    "ms_each_size_alone": per_size,
                    "solves_per_s": round(len(allr) / dt, 1),

@@ -272,11 +272,14 @@ typedef struct cg_batch_group {
 } cg_batch_group;
 
 /*
- * cg_solve_groups -- batches of several sizes at once: each group is a
- * cg_solve_batch on its own plan, launched on the plan's own stream after
- * the work already queued on stream (fork), and stream waits for all of them
- * (join), so the groups' graphs run concurrently on the device.  Each group
- * needs a distinct plan.  Blocks the host thread until every group ends.
+ * cg_solve_groups -- batches of several sizes at once, in one CUDA graph
+ * launch on stream: each group is a cg_solve_batch on its own plan, and the
+ * graph holds each group's solve as a parallel branch (its own loops and
+ * conditions), so the sizes run concurrently on the device.  The graph is
+ * cached by the groups' workspaces, sizes and mode.  (Where such a graph
+ * cannot be made, each group's graph runs on its plan's own stream, forked
+ * from and joined to stream.)  Each group needs a distinct plan.  Blocks the
+ * host thread until every group ends.
  * Returns FC_OK when every problem converged, otherwise the first other
  * status; errors: FC_EINVAL (bad group, repeated plan), FC_ENOMEM, FC_ECUDA.
  */

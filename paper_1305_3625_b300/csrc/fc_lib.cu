@@ -15,6 +15,7 @@
 #include <sys/stat.h>
 
 #include <chrono>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -2014,26 +2015,17 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     if (V.batched) batch_ctl_node(gb, body, n6, V, 0, h_inner, nullptr);
 }
 
-// Build the solve graph for one mode on the buffers of V:
-//   [prologue] -> while(outer) { A64 (fold correction, mask, FFT x) -> B64 ->
-//                                C64 (true residual, decide) ->
-//                                while(inner) { A -> B -> C } -> final }
-// (batched: a loop control node after C64 and after each inner body).
-int build_graph_with(fftconv_plan* p, const SolveView& V, int mode, bool precond, bool pdl, cudaGraph_t* gout,
-                     cudaGraphExec_t* eout) {
+// Add one solve (prologue, outer loop) to graph g as a branch with no
+// dependencies: its own conditional handles, its own buffers V.
+int add_solve_nodes(fftconv_plan* p, const SolveView& V, int mode, bool precond, bool pdl, cudaGraph_t g) {
     GraphBuilder gb;
     gb.pdl = pdl;
-    cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle h_outer = 0, h_inner = 0;
     cudaGraphNode_t nPro = nullptr, nOuter = nullptr;
     const long N = p->N;
     const bool mixed = mode == FC_MODE_MIXED;
-    FC_CK(cudaGraphCreate(&g, 0));
     cudaError_t e = cudaGraphConditionalHandleCreate(&h_outer, g, 1, cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) {
-        cudaGraphDestroy(g);
-        return set_cuda_err(e, "cudaGraphConditionalHandleCreate");
-    }
+    if (e != cudaSuccess) return set_cuda_err(e, "cudaGraphConditionalHandleCreate");
     int ndeps = 0;
     if (mixed) {
         // FP32 copy of the diagonal for the inner products (all problems)
@@ -2137,12 +2129,25 @@ int build_graph_with(fftconv_plan* p, const SolveView& V, int mode, bool precond
                       fx, fp);
         }
     }
-    if (gb.rc) {
+    return gb.rc;
+}
+
+// Build the solve graph for one mode on the buffers of V:
+//   [prologue] -> while(outer) { A64 (fold correction, mask, FFT x) -> B64 ->
+//                                C64 (true residual, decide) ->
+//                                while(inner) { A -> B -> C } -> final }
+// (batched: a loop control node after C64 and after each inner body).
+int build_graph_with(fftconv_plan* p, const SolveView& V, int mode, bool precond, bool pdl, cudaGraph_t* gout,
+                     cudaGraphExec_t* eout) {
+    cudaGraph_t g = nullptr;
+    FC_CK(cudaGraphCreate(&g, 0));
+    int rc = add_solve_nodes(p, V, mode, precond, pdl, g);
+    if (rc) {
         cudaGraphDestroy(g);
-        return gb.rc;
+        return rc;
     }
     cudaGraphExec_t ex = nullptr;
-    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
         return set_cuda_err(e, "cudaGraphInstantiate");
@@ -2423,6 +2428,7 @@ struct BatchWs {
     long long* rm_idx = nullptr;  // per problem: the site removed last and its x before removal
     double* rm_x = nullptr;
     int am_cap = 0;
+    unsigned long long gen = 0;  // unique per allocation of the buffers (keys of combined graphs)
 };
 
 namespace {
@@ -2557,9 +2563,11 @@ int batch_reserve(fftconv_plan* p, int nb, bool mixed, cudaStream_t st) {
         batch_buffers_free(w, st);
         return rc;
     }
+    static std::atomic<unsigned long long> next_gen{1};
     w->cap = cap;
     w->has64 = h64;
     w->has32 = h32;
+    w->gen = next_gen++;
     return FC_OK;
 }
 
@@ -2588,6 +2596,10 @@ int batch_graph(fftconv_plan* p, int gi, int nbg, cudaGraphExec_t* ex) {
     return FC_OK;
 }
 
+int batch_stage_in(fftconv_plan* p, int nb, int nbg, const double* s, const double* b, const double* x,
+                   const uint8_t* mask, const cg_opts* o, cudaStream_t st, const double* rtols);
+int batch_stage_out(fftconv_plan* p, int nb, double* x, cudaStream_t st);
+
 // Queue one batch on stream st: inputs in, the solve graph, x and the
 // states out.  The caller waits on st and then reads the states.  pad: the
 // graph runs a bucket of problems (batch_bucket), the ones past nb finished
@@ -2599,10 +2611,20 @@ int batch_enqueue(fftconv_plan* p, int nb, const double* s, const double* b, dou
     const int nbg = pad ? batch_bucket(nb) : nb;
     int rc = batch_reserve(p, nbg, mixed, st);
     if (rc) return rc;
-    BatchWs* w = p->batch;
     cudaGraphExec_t ex = nullptr;
     rc = batch_graph(p, mode + 2 * (precond ? 1 : 0), nbg, &ex);
     if (rc) return rc;
+    rc = batch_stage_in(p, nb, nbg, s, b, x, mask, o, st, rtols);
+    if (rc) return rc;
+    FC_CK(cudaGraphLaunch(ex, st));
+    return batch_stage_out(p, nb, x, st);
+}
+
+// A batch's inputs into the workspace on st: states (the problems past nb
+// finished from the start), s, b, the mask, and x or the zero start.
+int batch_stage_in(fftconv_plan* p, int nb, int nbg, const double* s, const double* b, const double* x,
+                   const uint8_t* mask, const cg_opts* o, cudaStream_t st, const double* rtols) {
+    BatchWs* w = p->batch;
     const SolveView& v = w->v;
     const long N = p->N;
     const size_t nN = (size_t)nb * N;
@@ -2633,9 +2655,14 @@ int batch_enqueue(fftconv_plan* p, int nb, const double* s, const double* b, dou
     } else {
         FC_CK(cudaMemcpyAsync(v.x64, x, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
     }
-    FC_CK(cudaGraphLaunch(ex, st));
-    FC_CK(cudaMemcpyAsync(x, v.x64, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
-    FC_CK(cudaMemcpyAsync(w->st_host, v.st, sizeof(CgState) * nb, cudaMemcpyDeviceToHost, st));
+    return FC_OK;
+}
+
+// A finished batch's solutions and states out of the workspace on st.
+int batch_stage_out(fftconv_plan* p, int nb, double* x, cudaStream_t st) {
+    BatchWs* w = p->batch;
+    FC_CK(cudaMemcpyAsync(x, w->v.x64, sizeof(double) * (size_t)nb * p->N, cudaMemcpyDeviceToDevice, st));
+    FC_CK(cudaMemcpyAsync(w->st_host, w->v.st, sizeof(CgState) * nb, cudaMemcpyDeviceToHost, st));
     return FC_OK;
 }
 
@@ -2697,6 +2724,74 @@ int fc_batch_solve_rtols(fftconv_plan* p, int nb, const double* s, const double*
                          std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
 }
 
+namespace {
+
+// One graph holding every group's batched solve as a parallel branch (one
+// launch for all sizes), cached by the groups' workspace generations (unique
+// per allocation, so a graph never outlives the buffers it names in use),
+// batch sizes and mode; least recently used of four evicted.
+struct GroupsGraph {
+    std::vector<unsigned long long> gens;
+    std::vector<int> nbs;
+    int gi = -1;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    unsigned long long used = 0;
+};
+std::mutex g_groups_mu;
+GroupsGraph g_groups[4];
+unsigned long long g_groups_tick = 0;
+
+// The combined graph for these groups (call with g_groups_mu held).
+int groups_graph(int ngroups, const cg_batch_group* g, int mode, bool precond, cudaGraphExec_t* ex) {
+    const int gi = mode + 2 * (precond ? 1 : 0);
+    std::vector<unsigned long long> gens;
+    std::vector<int> nbs;
+    for (int i = 0; i < ngroups; ++i) {
+        gens.push_back(g[i].plan->batch->gen);
+        nbs.push_back(g[i].nb);
+    }
+    GroupsGraph* slot = nullptr;
+    for (auto& c : g_groups)
+        if (c.ex && c.gi == gi && c.gens == gens && c.nbs == nbs) slot = &c;
+    if (!slot) {
+        for (auto& c : g_groups)
+            if (!slot || !c.ex || (slot->ex && c.used < slot->used)) slot = &c;
+        if (slot->ex) cudaGraphExecDestroy(slot->ex);
+        if (slot->g) cudaGraphDestroy(slot->g);
+        *slot = GroupsGraph{};
+        int rc = FC_ECUDA;
+        for (int pdl = pdl_on() ? 1 : 0; pdl >= 0 && rc != FC_OK; --pdl) {
+            cudaGraph_t gr = nullptr;
+            FC_CK(cudaGraphCreate(&gr, 0));
+            rc = FC_OK;
+            for (int i = 0; i < ngroups && rc == FC_OK; ++i) {
+                SolveView V = g[i].plan->batch->v;
+                V.nb = g[i].nb;
+                rc = add_solve_nodes(g[i].plan, V, mode, precond, pdl != 0, gr);
+            }
+            cudaGraphExec_t e = nullptr;
+            if (rc == FC_OK && cudaGraphInstantiate(&e, gr, 0) != cudaSuccess)
+                rc = set_cuda_err(cudaGetLastError(), "cudaGraphInstantiate(groups)");
+            if (rc == FC_OK) {
+                slot->g = gr;
+                slot->ex = e;
+            } else {
+                cudaGraphDestroy(gr);
+            }
+        }
+        if (rc) return rc;
+        slot->gens = gens;
+        slot->nbs = nbs;
+        slot->gi = gi;
+    }
+    slot->used = ++g_groups_tick;
+    *ex = slot->ex;
+    return FC_OK;
+}
+
+}  // namespace
+
 extern "C" int cg_solve_groups(int ngroups, const cg_batch_group* g, const cg_opts* o, fc_stream_t stream) {
     if (ngroups < 1 || !g) return FC_EINVAL;
     cg_opts def{};
@@ -2713,10 +2808,34 @@ extern "C" int cg_solve_groups(int ngroups, const cg_batch_group* g, const cg_op
     cudaStream_t st = (cudaStream_t)stream;
     // fork: every group on its plan's own stream after the caller's work
     for (int i = 0; i < ngroups; ++i) {
-        fftconv_plan* gp = g[i].plan;
-        int rc = batch_reserve(gp, g[i].nb, o->mode == FC_MODE_MIXED, gp->batch ? gp->batch->stream : st);
+        int rc = batch_reserve(g[i].plan, g[i].nb, o->mode == FC_MODE_MIXED, st);
         if (rc) return rc;
     }
+    {
+        // one graph for all groups: inputs in, one launch, outputs out, all on st
+        std::unique_lock<std::mutex> lk(g_groups_mu);
+        cudaGraphExec_t ex = nullptr;
+        if (groups_graph(ngroups, g, o->mode, o->precond != 0, &ex) == FC_OK) {
+            int rc = FC_OK;
+            for (int i = 0; i < ngroups && rc == FC_OK; ++i)
+                rc = batch_stage_in(g[i].plan, g[i].nb, g[i].nb, g[i].s, g[i].b, g[i].x, g[i].mask, o, st, nullptr);
+            if (rc == FC_OK && cudaGraphLaunch(ex, st) != cudaSuccess)
+                rc = set_cuda_err(cudaGetLastError(), "cudaGraphLaunch(groups)");
+            lk.unlock();
+            for (int i = 0; i < ngroups && rc == FC_OK; ++i) rc = batch_stage_out(g[i].plan, g[i].nb, g[i].x, st);
+            FC_CK(wait_stream(g[0].plan, st));
+            if (rc) return rc;
+            const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            int status = FC_OK;
+            for (int i = 0; i < ngroups; ++i) {
+                const int si = batch_results(g[i].plan, g[i].nb, g[i].r, secs);
+                if (status == FC_OK) status = si;
+            }
+            return status;
+        }
+    }
+    // no combined graph could be made: each group's graph on its plan's
+    // stream, forked from and joined to st
     cudaEvent_t fork = g[0].plan->batch->ev;
     FC_CK(cudaEventRecord(fork, st));
     for (int i = 0; i < ngroups; ++i) {
