@@ -420,8 +420,8 @@ typedef struct cg_request {
  * reserving its share of the plan's batch workspace within the budget) and
  * runs them as one cg_solve_batch launch with each request's own tolerance,
  * from x = 0.  Plans stay resident and are reused by later requests of the
- * same L; there is one plan per size, so a request whose size is being
- * solved waits and joins that plan's next batch.  Work of different slots overlaps on the device; each result
+ * same L; a size holds at most two plans, so a request whose size's plans
+ * are both busy waits and joins the next batch.  Work of different slots overlaps on the device; each result
  * depends only on its own inputs (it equals cg_solve_batch of that request
  * alone on a plan of its size).
  */

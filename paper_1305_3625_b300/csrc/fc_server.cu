@@ -9,8 +9,9 @@
 // Each slot is a host thread with its own non-blocking CUDA stream; slots
 // run their batches concurrently, so requests that arrive while others are
 // on the GPU overlap with them.  Plans (spectrum, tables, workspaces) stay
-// resident and are reused by later requests of the same L (one plan per
-// size: a request whose size is being solved waits and joins the next batch);
+// resident and are reused by later requests of the same L (at most two plans
+// per size: a request whose size's plans are all busy waits and joins the
+// next batch);
 // idle plans of other sizes are evicted when the budget requires it.  Each result is the
 // same whether a request runs alone or in a mix: a problem's arithmetic in a
 // batched solve depends only on its own inputs and its plan's launch shapes
@@ -39,6 +40,7 @@ int fc_batch_solve_rtols(fftconv_plan* p, int nb, const double* s, const double*
 namespace {
 
 constexpr int kMaxBatch = 64;  // requests one slot takes into one batched solve
+constexpr int kPlansPerSize = 2;  // plans one size may hold (busy ones included)
 
 // FC_SERVER_TRACE=1: one line per batched solve on stderr (size, plan made or
 // kept, and the wall time of set-up, input copies, solve and output copies).
@@ -143,9 +145,9 @@ Req* admit_one_locked(cg_server* sv, fftconv_plan** plan, std::vector<fftconv_pl
         Req* r = *it;
         auto ip = sv->idle.find(r->rq.L);
         const bool have = ip != sv->idle.end();
-        // a plan of this size exists but is busy: the request waits for it
-        // (and joins its next batch) rather than making a second plan
-        if (!have && sv->plans_of[r->rq.L] > 0) continue;
+        // every plan this size may hold is busy: the request waits for one
+        // (and joins its next batch) rather than making another
+        if (!have && sv->plans_of[r->rq.L] >= kPlansPerSize) continue;
         const size_t need = have ? batch_bytes(r->rq.L, r->rq.mode) : r->est;
         size_t freeable = 0;
         for (auto& kv : sv->idle)
