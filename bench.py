@@ -618,7 +618,9 @@ def run_ours(args, world, rank, local, pg):
             return time.perf_counter() - t0, rc_, rr
 
         ens_run()  # graphs and workspaces made
+        torch.cuda.nvtx.range_push("ensemble")
         et_s, erc, err_ = ens_run()
+        torch.cuda.nvtx.range_pop()
         assert erc == fc.FC_OK
         # one run at a time, on the first runs of the same ensemble
         n1, t1 = min(4, ne), 0.0
