@@ -42,8 +42,7 @@ import numpy as np  # noqa: E402
 L_BENCH = 1024
 RTOL = 1e-10
 # DRAM bytes (read + write) of the three FP32 passes of one L = 1024 apply, summed over the
-# passes of one ncu capture (cold cache per launch; the writes stay in L2):
-# profiles/fft_passes_f32_L1024.md
+# passes of one ncu capture (cold cache per launch; the writes stay in L2)
 MATVEC_TRAFFIC_L1024 = 25.39e6
 FRAC_GRADIENT = 2.0  # thresholds xi + 2 (iy + 1/2)/L in the fracture-run section
 METRIC = "CG matvec GB/s vs HBM peak; solves/sec + p50/p99 latency, mixed vs FP64 plain"

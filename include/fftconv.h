@@ -11,7 +11,7 @@
  *   L x L grid, G(r) = 1/(pi r) for r > 0 and G(0) = 4 ln(1 + sqrt 2)/pi
  *   (Eq. 1c with a = 1 and (1 - nu^2)/E = 1).
  *
- *   C is applied as in Section 3 (Eq. 3, Listing 3): zero-pad x to the M x M
+ *   C is applied as in Section 3 (Eq. 3, Listing 4): zero-pad x to the M x M
  *   grid (M = smallest power of two >= 2L), forward 2D FFT, multiply by the
  *   precomputed kernel spectrum, inverse 2D FFT, keep the [0, L)^2 corner.
  *   The solve is unpreconditioned conjugate gradients (Listing 2).
@@ -140,7 +140,7 @@ const char *fc_last_error(void);
 
 /*
  * fftconv_plan_create -- set up C for an L x L grid (Section 3: the transform
- * of G is static and computed at initialisation, Listing 3).
+ * of G is static and computed at initialisation, Listing 4).
  *   p     out: new plan (host pointer to a handle).
  *   L     1 <= L <= 4096.  M = smallest power of two >= 2L.
  *   prec  FC_F32, FC_F64 or FC_F32|FC_F64 (the mixed solve needs both).
@@ -194,7 +194,7 @@ int fftconv_plan_shapes(const fftconv_plan *p, int prec, int n_shapes[3], int ch
 int fftconv_plan_solver(const fftconv_plan *p, int prec, int *n, int *chosen, int *threads, int *grid);
 
 /*
- * fftconv_apply -- y = C x (Listing 3: cpyComplex, FFT, elementMult, inverse
+ * fftconv_apply -- y = C x (Listing 4: cpyComplex, FFT, elementMult, inverse
  * FFT, cpyReal), three kernel passes on stream.
  *   x, y  device pointers to L*L values (float for an FC_F32 apply, double
  *         for FC_F64); x and y must not overlap.

@@ -307,7 +307,7 @@ int orc_fft2(int M, double *re, double *im, int sign)
 }
 
 /* Kernel spectrum FFT2(k) / M^2 (Listing 3's normalisation folded in once; the
- * transform of G is computed at set-up, Listing 3 comment).  re and im are
+ * transform of G is computed at set-up, Listing 4 comment).  re and im are
  * M x M. */
 int orc_spectrum(int L, double *re, double *im)
 {
@@ -362,7 +362,7 @@ static int conv_init(orc_conv *c, int L)
     return 0;
 }
 
-/* y = C x through the Fourier route of Listing 3: copy x into a zero complex
+/* y = C x through the Fourier route of Listing 4: copy x into a zero complex
  * grid, forward 2D transform, multiply by the kernel spectrum, inverse 2D
  * transform, keep the real part of the [0, L)^2 corner. */
 static int conv_apply(orc_conv *c, const double *x, double *y)

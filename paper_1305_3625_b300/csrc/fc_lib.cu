@@ -22,6 +22,7 @@
 
 #include "fc_persist.cuh"
 #include "fc_tma.cuh"
+#include "fc_variants.h"
 
 using namespace fc;
 
@@ -131,40 +132,6 @@ __global__ void k_kernel_table(int L, int M, const double* gt, cpx<double>* K) {
     bool okx = jx < L || jx > M - L, oky = jy < L || jy > M - L;
     int ax = jx < L ? jx : M - jx, ay = jy < L ? jy : M - jy;
     K[idx] = cpx<double>{(okx && oky) ? gt[(size_t)ay * L + ax] : 0.0, 0.0};
-}
-
-// Unpruned forward FFT of every row of an M x M grid (spectrum set-up only).
-template <int M, int E, int RB>
-__global__ void __launch_bounds__(RB*(M / E)) k_rows_full(cpx<double>* K, const cpx<double>* tw) {
-    using C = cpx<double>;
-    constexpr int G = M / E;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
-    const int j = threadIdx.x % G, c = threadIdx.x / G, row = blockIdx.x * RB + c;
-    const bool ok = row < M;
-    C v[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = ok ? K[(size_t)row * M + j + e * G] : C{0, 0};
-    fft_stages<double, M, E, false, false, 0>(v, j, sm + c * seg_len(M), sm + c * seg_len(M), tw);
-    if (ok)
-#pragma unroll
-        for (int e = 0; e < E; ++e) K[(size_t)row * M + j + e * G] = v[e];
-}
-
-// Unpruned forward FFT of every column of an M x M grid.
-template <int M, int E, int CB>
-__global__ void __launch_bounds__(CB*(M / E)) k_cols_full(cpx<double>* K, const cpx<double>* tw) {
-    using C = cpx<double>;
-    constexpr int G = M / E;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
-    const int c = threadIdx.x % CB, j = threadIdx.x / CB, col = blockIdx.x * CB + c;
-    C v[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = K[(size_t)(j + e * G) * M + col];
-    fft_stages<double, M, E, false, false, 0>(v, j, sm + c * seg_len(M), sm + c * seg_len(M), tw);
-#pragma unroll
-    for (int e = 0; e < E; ++e) K[(size_t)(j + e * G) * M + col] = v[e];
 }
 
 __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
@@ -585,180 +552,18 @@ __global__ void __launch_bounds__(512) k_front(int L, const uint8_t* mask, int32
         damage_end[ix] = de;
     }
 }
-
-// ------------------------------------------------------- dispatch tables --
-
-// One compiled launch shape of a pass: E values per thread (stage radix) and
-// `per` row pairs (passes A, C) or columns (pass B) per block.
-struct KV {
-    const void* f = nullptr;
-    int threads = 0, per = 0, E = 0;
-    size_t smem = 0;
-    int tma = 0;  // 1: TMA-staged persistent pass C (k_rinv_tma; needs the plan's tensor map)
-};
-
-// One compiled persistent inner-CG kernel: pass A/C shape (EA, RB) and
-// pass B shape (EB, CB) with the same block size.
-struct KVP {
-    const void* f = nullptr;
-    int threads = 0, EA = 0, RB = 0, EB = 0, CB = 0;
-    size_t smem = 0;
-};
-
-struct Variants {
-    static constexpr int kMax = 12;  // compiled shapes per pass and size (at most)
-    KV rfwd[kMax], colc[kMax], rinv[kMax];
-    int n_rfwd = 0, n_colc = 0, n_rinv = 0;
-    KVP pers[6];
-    int n_pers = 0;
-    KV rows_full, cols_full;  // FP64 only: spectrum set-up
-    KV rfwd_b, colc_b, rinv_b;  // batched forms (blockIdx.y = problem) of the standard shapes
-};
-
-constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
-
-template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
-void add_row(Variants& v) {
-    if constexpr (RB * (M / E) <= 1024 && pass_smem<T, M, RB, DB>() <= 200 * 1024) {
-        KV f{(const void*)k_rfwd<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
-        KV i{(const void*)k_rinv<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
-        for (int k = 0; k < v.n_rfwd; ++k)
-            if (v.rfwd[k].f == f.f) return;
-        if (v.n_rfwd >= Variants::kMax || v.n_rinv >= Variants::kMax) return;
-        v.rfwd[v.n_rfwd++] = f;
-        v.rinv[v.n_rinv++] = i;
-    }
-}
-
-// TMA-staged pass C (FP32): one row pair per loop iteration, M/16 threads.
-template <int M>
-void add_rinv_tma(Variants& v) {
-    // whole warps per block (the block reductions shuffle across full warps)
-    if constexpr (M / 16 >= 32 && tma_smem_bytes(M) <= 200 * 1024) {
-        if (v.n_rinv < Variants::kMax) v.rinv[v.n_rinv++] = KV{(const void*)k_rinv_tma<M, 16>, M / 16, 1, 16, tma_smem_bytes(M), 1};
-    }
-}
-
-// The batched forms of the standard shapes (the first registered of each
-// pass): batched solves launch these, whatever the plan's tuner chose.
-template <typename T, int M, int ER, int RB, int EC, int CB>
-void add_batched(Variants& v) {
-    constexpr bool DR = use_db<T, M, RB>(), DC = use_db<T, M, CB>();
-    v.rfwd_b = KV{(const void*)k_rfwd_b<T, M, ER, RB, 1, DR>, RB * (M / ER), RB, ER, pass_smem<T, M, RB, DR>()};
-    v.rinv_b = KV{(const void*)k_rinv_b<T, M, ER, RB, 1, DR>, RB * (M / ER), RB, ER, pass_smem<T, M, RB, DR>()};
-    v.colc_b = KV{(const void*)k_colc_b<T, M, EC, CB, 1, DC>, CB * (M / EC), CB, EC, pass_smem<T, M, CB, DC>()};
-}
-
-template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
-void add_col(Variants& v) {
-    if constexpr (CB * (M / E) <= 1024 && pass_smem<T, M, CB, DB>() <= 200 * 1024) {
-        KV c{(const void*)k_colc<T, M, E, CB, MINB, DB>, CB * (M / E), CB, E, pass_smem<T, M, CB, DB>()};
-        for (int k = 0; k < v.n_colc; ++k)
-            if (v.colc[k].f == c.f) return;
-        if (v.n_colc < Variants::kMax) v.colc[v.n_colc++] = c;
-    }
-}
-
-template <typename T, int M, int EA, int EB, int NT>
-void add_pers(Variants& v) {
-    constexpr int GA = EA <= M ? M / EA : 1, GB = EB <= M ? M / EB : 1;
-    constexpr int RB = NT / GA, CB = NT / GB;
-    constexpr size_t SA = pass_smem<T, M, (RB > 0 ? RB : 1)>(), SB = pass_smem<T, M, (CB > 0 ? CB : 1)>();
-    constexpr size_t SM = SA > SB ? SA : SB;
-    if constexpr (M >= 64 && EA <= M && EB <= M && RB >= 1 && CB >= 1 && RB * GA == NT && CB * GB == NT &&
-                  CB <= M / 2 && NT <= 1024 && NT % 32 == 0 && SM <= 200 * 1024) {
-        if (v.n_pers < 6)
-            v.pers[v.n_pers++] = KVP{(const void*)k_cg_persist<T, M, EA, RB, EB, CB>, NT, EA, RB, EB, CB, SM};
-    }
-}
-
-// Launch shapes compiled for each (precision, M).  FP32 sizes from 256 up
-// carry seven to nine shapes per pass for the autotuner: E = 16, 8 or 4 with
-// one or more rows or columns per block, single-buffered 64-register shapes
-// (more resident blocks), 1024-thread row blocks, and the TMA-staged pass C.
-// FP64 (ALU-bound on this part) carries one.
-template <typename T, int M>
-void make_variants(Variants& v) {
-    constexpr int H = M / 2;
-    if constexpr (sizeof(T) == 4) {
-        if constexpr (M <= 16) {
-            add_row<T, M, M, 64>(v);
-            add_col<T, M, M, clampi(64, 1, H)>(v);
-            add_batched<T, M, M, 64, M, clampi(64, 1, H)>(v);
-        } else if constexpr (M <= 128) {
-            constexpr int G = M / 16;
-            add_row<T, M, 16, clampi(128 / G, 1, 128)>(v);
-            add_col<T, M, 16, clampi(256 / G, 1, H)>(v);
-            add_batched<T, M, 16, clampi(128 / G, 1, 128), 16, clampi(256 / G, 1, H)>(v);
-        } else {
-            constexpr int G16 = M / 16, G8 = M / 8, G4 = M / 4;
-            add_batched<T, M, 16, clampi(256 / G16, 1, 64), 16, clampi(128 / G16, 1, H)>(v);
-            add_row<T, M, 16, clampi(256 / G16, 1, 64)>(v);
-            add_row<T, M, 16, clampi(512 / G16, 1, 64)>(v);
-            add_row<T, M, 8, clampi(256 / G8, 1, 64)>(v);
-            add_row<T, M, 8, clampi(512 / G8, 1, 64)>(v);
-            add_row<T, M, 4, clampi(512 / G4, 1, 64)>(v);
-            add_col<T, M, 16, clampi(128 / G16, 1, H)>(v);
-            add_col<T, M, 16, clampi(256 / G16, 1, H)>(v);
-            add_col<T, M, 8, clampi(256 / G8, 1, H)>(v);
-            add_col<T, M, 8, clampi(512 / G8, 1, H)>(v);
-            add_col<T, M, 4, clampi(512 / G4, 1, H)>(v);
-            // single-buffered, at most 64 registers: more resident blocks
-            // (a one-wave grid where the default shapes need 1.15 waves)
-            constexpr int C1 = clampi(128 / G16, 1, H), C2 = clampi(256 / G16, 1, H);
-            constexpr int R1 = clampi(128 / G16, 1, 64), R2 = clampi(256 / G16, 1, 64);
-            add_col<T, M, 16, C1, clampi(65536 / (C1 * G16 * 64), 1, 16), false>(v);
-            add_col<T, M, 16, C2, clampi(65536 / (C2 * G16 * 64), 1, 16), false>(v);
-            // the same with a 72-register cap (fewer spills, one block fewer per SM)
-            constexpr int MB72 = clampi(65536 / (C1 * G16 * 72), 1, 16);
-            if constexpr (MB72 > 1) add_col<T, M, 16, C1, MB72, false>(v);
-            add_row<T, M, 16, R1, clampi(65536 / (R1 * G16 * 64), 1, 16), false>(v);
-            add_row<T, M, 16, R2, clampi(65536 / (R2 * G16 * 64), 1, 16), false>(v);
-            // 1024-thread row blocks: more rows per block make the column-major
-            // intermediate's row segments longer (full 32-byte sectors at M = 8192)
-            add_row<T, M, 16, clampi(1024 / G16, 1, 64), 1, false>(v);
-            add_rinv_tma<M>(v);
-        }
-        add_pers<T, M, 16, 16, (M * M / 32 < 256 ? M * M / 32 : 256)>(v);
-        add_pers<T, M, 16, 8, 256>(v);
-        add_pers<T, M, 8, 8, 256>(v);
-        add_pers<T, M, 16, 16, 512>(v);
-        add_pers<T, M, 8, 8, 512>(v);
-        add_pers<T, M, 8, 8, 1024>(v);
-    } else {
-        constexpr int E = M <= 8 ? M : (M <= 2048 ? 8 : 16);
-        constexpr int G = M / E;
-        constexpr int RB = M <= 8 ? 64 : clampi(256 / G, 1, 128);
-        constexpr int CB = clampi(256 / G, 1, H);
-        add_row<T, M, E, RB>(v);
-        add_col<T, M, E, CB>(v);
-        add_batched<T, M, E, RB, E, CB>(v);
-        constexpr int CBF = clampi(256 / G, 1, M);
-        v.rows_full = KV{(const void*)k_rows_full<M, E, RB>, RB * G, RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<double>)};
-        v.cols_full = KV{(const void*)k_cols_full<M, E, CBF>, CBF * G, CBF, E, (size_t)CBF * seg_len(M) * sizeof(cpx<double>)};
-        add_pers<T, M, E, E, (M / E) * 4 <= 256 ? (M / E) * 4 : (M / E)>(v);
-        add_pers<T, M, E, E, 256>(v);
-    }
-}
-
 template <typename T>
 bool get_variants(int M, Variants* v) {
     *v = Variants{};
+    const bool f64 = sizeof(T) == 8;
     switch (M) {
-        case 2: make_variants<T, 2>(*v); return true;
-        case 4: make_variants<T, 4>(*v); return true;
-        case 8: make_variants<T, 8>(*v); return true;
-        case 16: make_variants<T, 16>(*v); return true;
-        case 32: make_variants<T, 32>(*v); return true;
-        case 64: make_variants<T, 64>(*v); return true;
-        case 128: make_variants<T, 128>(*v); return true;
-        case 256: make_variants<T, 256>(*v); return true;
-        case 512: make_variants<T, 512>(*v); return true;
-        case 1024: make_variants<T, 1024>(*v); return true;
-        case 2048: make_variants<T, 2048>(*v); return true;
-        case 4096: make_variants<T, 4096>(*v); return true;
-        case 8192: make_variants<T, 8192>(*v); return true;
-        default: return false;
+        case 256: variants_256(f64, v); return true;
+        case 512: variants_512(f64, v); return true;
+        case 1024: variants_1024(f64, v); return true;
+        case 2048: variants_2048(f64, v); return true;
+        case 4096: variants_4096(f64, v); return true;
+        case 8192: variants_8192(f64, v); return true;
+        default: return variants_small(M, f64, v);
     }
 }
 

@@ -1,5 +1,5 @@
 // The three HBM passes of one application of the coupling operator C
-// (Listing 3's cpyComplex -> forward 2D FFT -> elementMult -> inverse 2D FFT
+// (Listing 4's cpyComplex -> forward 2D FFT -> elementMult -> inverse 2D FFT
 // -> cpyReal, Section 3) on the zero-padded M x M grid, with the CG vector
 // work of Listing 2 fused into the first and last pass.
 //

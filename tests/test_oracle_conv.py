@@ -8,7 +8,7 @@ import oracle
 
 @pytest.mark.parametrize("L", [1, 2, 3, 5, 8, 16, 33, 48])
 def test_fft_route_matches_direct_sum(L):
-    """Two independent algorithms: the padded-FFT route of Listing 3 vs the sum of Eq. 1b."""
+    """Two independent algorithms: the padded-FFT route of Listing 4 vs the sum of Eq. 1b."""
     rng = np.random.default_rng(L)
     x = rng.standard_normal(L * L)
     yd = oracle.conv_direct(L, x)
