@@ -141,24 +141,45 @@ def aggregate_rate(units: float, local_ms: float, pg=None, device="cpu"):
 
 # ---------------------------------------------------------------- oracle --
 
-def oracle_iteration_time(L, budget_s):
-    """Seconds per CG iteration of the plain FP64 oracle at size L, from a
-    bounded run of its CG (cold start, capped iterations)."""
-    import fc_inputs
-    import oracle
-    p = fc_inputs.problem(L, seed=0, with_t=True)
-    oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=1)  # compile / page in
-    t0 = time.perf_counter()
-    _, _, it1, _ = oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=1)
-    one = time.perf_counter() - t0
-    k = max(2, min(200, int(budget_s / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    _, _, itk, _ = oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=k)
-    tk = time.perf_counter() - t0
-    # a solve = setup + iterations; separate the two from the 1- and k-iteration runs
-    per_it = max((tk - one) / max(itk - it1, 1), 1e-9)
-    setup = max(one - per_it * it1, 0.0)
-    return per_it, setup, itk, tk + one
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+class OracleLoop:
+    """The breaking loop of the bench workload run by the FP64 CPU oracle as
+    it stands: each step a warm-started masked CG solve (Listing 2, plain
+    FP64, first residual computed) to the bench's tolerance, then the
+    removal of argmax |x|/t.  The first step starts from x = 0."""
+
+    def __init__(self, L, seed):
+        import fc_inputs
+        self.L = L
+        p = fc_inputs.problem(L, seed=seed, with_t=True)
+        self.s, self.b, self.t = p["s"], p["b"], p["t"]
+        self.x = np.zeros(L * L)
+        self.mask = np.ones(L * L, dtype=np.uint8)
+        self.steps = 0
+
+    def step(self):
+        import oracle
+        t0 = time.perf_counter()
+        x, rc, it, rel = oracle.cg(self.L, self.s, self.b, x0=self.x, mask=self.mask, rtol=RTOL)
+        if rc != 0 or rel > RTOL:
+            raise RuntimeError(f"oracle solve failed: rc={rc} rel={rel}")
+        k, _ = oracle.argmax_ratio(x, self.t, self.mask)
+        if k >= 0:
+            self.mask[k] = 0
+            x[k] = 0.0
+        self.x = x
+        self.steps += 1
+        return time.perf_counter() - t0, it
 
 
 # ------------------------------------------------------------------ ours --
@@ -650,8 +671,15 @@ def run_ours(args, world, rank, local, pg):
         iters = [r["iters"] for r in res_mixed]
         iters64 = [r["iters"] for r in res_f64]
         f64_rate = k64 / (sum(ms_f64) * 1e-3)
-        per_it_cpu, setup_cpu, it_cpu, cpu_s = oracle_iteration_time(L, args.cpu_budget)
-        cpu_solve_s = setup_cpu + per_it_cpu * statistics.mean(iters64)
+        # the oracle on the host cores: whole steps of the same loop (the cold
+        # first step, then timed warm-started steps while the budget lasts)
+        cpu = OracleLoop(L, seed=rank)
+        cold_s, cold_it = cpu.step()
+        cpu_times, cpu_its = [], []
+        while not cpu_times or (sum(cpu_times) < args.cpu_budget and len(cpu_times) < 5):
+            dt_, it_ = cpu.step()
+            cpu_times.append(dt_)
+            cpu_its.append(it_)
         out = {
             "metric": METRIC,
             "value": round(value, 3),
@@ -703,11 +731,14 @@ def run_ours(args, world, rank, local, pg):
                          "achieved": round(mv_gbs, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(mv_gbs / peak, 3), "traffic": args.traffic,
                          "peak_kind": peak_kind},
-            "cpu_baseline": {"value": round(1.0 / cpu_solve_s, 5), "unit": "solves/s",
-                             "cores": int(os.environ.get("OMP_NUM_THREADS", "1")), "kind": "oracle",
-                             "sample": (f"oracle FP64 CG at L={L}: {it_cpu} iterations timed "
-                                        f"({cpu_s:.1f} s), scaled by the FP64 path's "
-                                        f"{statistics.mean(iters64):.1f} iterations per solve")},
+            "cpu_baseline": {"value": round(len(cpu_times) / sum(cpu_times), 5), "unit": "solves/s",
+                             "cores": int(os.environ.get("OMP_NUM_THREADS", "1")), "cpu_model": cpu_model(),
+                             "kind": "oracle",
+                             "sample": (f"whole steps of the same breaking loop at L={L} by the FP64 oracle "
+                                        f"(plain CG to rtol {RTOL:g}, warm-started, + removal): steps 2-"
+                                        f"{1 + len(cpu_times)} timed ({sum(cpu_times):.1f} s, "
+                                        f"{statistics.mean(cpu_its):.0f} iterations each) after the cold "
+                                        f"first step ({cold_s:.1f} s, {cold_it} iterations)")},
             "e2e": e2e,
             "fracture_run": frac,
             "gpu_launches": sum(launches(r, fc.FC_MODE_MIXED) for r in res_mixed),
@@ -718,35 +749,39 @@ def run_ours(args, world, rank, local, pg):
 
 
 def run_reference(args, world, rank):
-    """The oracle, as it stands, on the host cores: each step is a bounded
-    sample (a few CG iterations of the L = 1024 solve) scaled to solves/s."""
+    """The oracle, as it stands, on the host cores: W untimed and K timed
+    whole steps of the bench's breaking loop (each a warm-started FP64 CG
+    solve to rtol 1e-10 plus the removal; the first warm-up step is the cold
+    solve from x = 0).  Rank 0 alone runs it."""
     if rank != 0:
         return None
-    import fc_inputs
-    import oracle
     L = L_BENCH
-    p = fc_inputs.problem(L, seed=0, with_t=True)
-    iters_per_solve = args.ref_iters
-    ms = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        _, _, it, _ = oracle.cg(L, p["s"], p["b"], rtol=1e-30, maxit=args.ref_sample_iters)
-        dt = time.perf_counter() - t0
-        if k >= args.warmup:
-            ms.append(dt * 1e3 * iters_per_solve / max(it, 1))
+    loop = OracleLoop(L, seed=0)
+    for _ in range(args.warmup):
+        loop.step()
+    ms, its = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dt, it = loop.step()
+        ms.append(dt * 1e3)
+        its.append(it)
+    wall = time.perf_counter() - t0
     value = len(ms) / (sum(ms) * 1e-3)
     cores = int(os.environ.get("OMP_NUM_THREADS", "1"))
-    sample = (f"per step: oracle FP64 CG at L={L}, {args.ref_sample_iters} iterations from x=0, "
-              f"scaled to {iters_per_solve} iterations per solve")
+    sample = (f"{args.steps} whole steps of the breaking loop at L={L} after {args.warmup} warm-up steps: "
+              f"warm-started oracle FP64 CG (Listing 2) to rtol {RTOL:g} + removal, "
+              f"{statistics.mean(its):.1f} iterations per solve")
     return {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(statistics.mean(ms), 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L, "rtol": RTOL, "mode": "oracle FP64 CG (CPU)"},
+            "config": {"workload": WORKLOAD, "L": L, "rtol": RTOL, "mode": "oracle FP64 CG (CPU), plain"},
+            "p50_ms": round(statistics.median(ms), 3),
             "cpu_baseline": {"value": round(value, 6), "unit": "solves/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+                    "d2h_bytes_per_step": 0},
+            "wall_s_timed_region": round(wall, 3)}
 
 
 def main():
@@ -757,7 +792,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--f64-steps", type=int, default=6, dest="f64_steps")
     ap.add_argument("--e2e-steps", type=int, default=30, dest="e2e_steps")
-    ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget")
+    ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget",
+                    help="seconds of timed warm oracle steps in the cpu_baseline leg (at least one step)")
     ap.add_argument("--big", type=int, default=1)
     ap.add_argument("--big-steps", type=int, default=200, dest="big_steps")
     ap.add_argument("--frac-steps", type=int, default=100, dest="frac_steps")
@@ -769,15 +805,15 @@ def main():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--traffic", type=float, default=MATVEC_TRAFFIC_L1024,
                     help="ncu dram bytes per matvec from a capture of the current kernels")
-    ap.add_argument("--ref-sample-iters", type=int, default=3, dest="ref_sample_iters")
-    ap.add_argument("--ref-iters", type=int, default=60, dest="ref_iters",
-                    help="CG iterations per warm-started solve used to scale the reference")
     args = ap.parse_args()
-    world, rank, local, pg = dist_setup(args)
     if args.impl == "reference":
-        out = run_reference(args, world, rank)
-    else:
-        out = run_ours(args, world, rank, local, pg)
+        # the oracle on rank 0's host cores; other ranks have no work
+        out = run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    world, rank, local, pg = dist_setup(args)
+    out = run_ours(args, world, rank, local, pg)
     if out is not None:
         print(json.dumps(out), flush=True)
     if pg:

@@ -208,6 +208,24 @@ int fftconv_apply(fftconv_plan *p, const void *x, void *y, fc_stream_t stream);
 int fftconv_apply_prec(fftconv_plan *p, int prec, const void *x, void *y, fc_stream_t stream);
 
 /*
+ * fftconv_cg_product -- one CG product of Listing 2 exactly as the solver's
+ * passes form it (Section 3's Fourier route with the fused epilogue):
+ * q = C p + s p, and the pass's grid sums of p.q, r.q and q.q, the dot
+ * products the CG step takes its step length and residual norm from.
+ *   p, r, s  device pointers to L*L values of the precision prec (FC_F32
+ *            or FC_F64): direction, residual and diagonal; q: output.
+ *   dots     host pointer to 3 doubles receiving p.q, r.q, q.q.
+ * In FC_F32 every thread accumulates its products as an exact-product
+ * two-float sum (Dot2) and the block and grid combine the pairs in
+ * two-float arithmetic; in FC_F64 the sums are FP64.  Uses the plan's
+ * intermediate and partial-sum buffers (not its solve state), so it must not
+ * run concurrently with another call on the same plan.  Synchronous (waits
+ * for stream).  Errors: FC_EINVAL, FC_ECUDA, FC_ENOMEM.
+ */
+int fftconv_cg_product(fftconv_plan *p, int prec, const void *pvec, const void *rvec, const void *s, void *q,
+                       double dots[3], fc_stream_t stream);
+
+/*
  * cg_solve -- solve P (C + S) P x = P b by CG (Listing 2), P the projection
  * on active fibres (mask), x = 0 off the active set.
  *   s     device, L*L doubles: diagonal s_i > 0 (compliance 1/k_i, Eq. 1a).
@@ -444,6 +462,52 @@ int cg_server_batches(cg_server *sv, long long *batches, long long *solves, int 
 
 /* Stop the workers (running solves finish), free plans and buffers. */
 int cg_server_destroy(cg_server *sv);
+
+/* ------------------------------------------------------------------------
+ * Memory accounting, workspace guards and failure injection.  The paper has
+ * no counterpart of these: they serve memory budgets and the tests of the
+ * library's own error paths.
+ * ---------------------------------------------------------------------- */
+
+/* Device memory the library holds through its own allocations (plans,
+ * batch workspaces, server staging, temporaries), measured at each
+ * allocation and free: *live_bytes now, *peak_bytes the high-water mark
+ * since the last reset, *live_allocs the live device and pinned-host
+ * allocations.  reset_peak != 0 restarts the high-water mark at the live
+ * value after reading it.  Any pointer may be NULL.  Host only, thread-safe. */
+int fc_mem_stats(size_t *live_bytes, size_t *peak_bytes, long long *live_allocs, int reset_peak);
+
+/* Every device buffer of a plan (and of its batch workspace) sits between
+ * two 256-byte guard bands filled with a fixed byte at allocation.  This
+ * checks them all on the device and sets *damaged to the number of bands
+ * that no longer hold it (0: no kernel wrote outside its buffers).  Call it
+ * with no work on the plan in flight; it waits for its own check only.
+ * Errors: FC_EINVAL, FC_ENOMEM, FC_ECUDA. */
+int fftconv_plan_check_guards(fftconv_plan *p, int *damaged);
+
+/* Failure injection for tests.  Nothing here faults or hangs the GPU.
+ *   FC_INJECT_ALLOC    (p ignored, may be NULL): value n > 0 makes the n-th
+ *                      device or pinned-host allocation of the library from
+ *                      now fail as if the memory were exhausted (once; the
+ *                      call that made it returns FC_ENOMEM and frees what it
+ *                      had allocated); 0 turns it off.  Process-wide.
+ *   FC_INJECT_BARRIER  value > 0: in the plan's next solves the persistent
+ *                      inner-CG kernel's last block leaves before its first
+ *                      grid-barrier arrival, so the other blocks' bounded
+ *                      waits, limited to `value` polls, run out and the
+ *                      solve returns FC_ETIMEOUT; 0 turns it off.
+ *   FC_INJECT_TMA      value > 0: in the plan's next solves and applies the
+ *                      TMA-staged pass C issues no copy for each block's
+ *                      first row pair, so its bounded mbarrier waits
+ *                      (`value` polls) run out and a solve returns
+ *                      FC_ETIMEOUT; 0 turns it off.
+ * The plan hooks are written into the plan's solve state at once (a
+ * synchronous copy) and copied into every later solve's state.
+ * Errors: FC_EINVAL, FC_ECUDA. */
+#define FC_INJECT_ALLOC 1
+#define FC_INJECT_BARRIER 2
+#define FC_INJECT_TMA 3
+int fc_debug_inject(fftconv_plan *p, int kind, long long value);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,9 @@ FC_GREEN_CELL = 1
 FC_MODE_F64 = 0
 FC_MODE_MIXED = 1
 FC_REQ_BORROW = 1
+FC_INJECT_ALLOC = 1
+FC_INJECT_BARRIER = 2
+FC_INJECT_TMA = 3
 
 STATUS_NAMES = {0: "FC_OK", -1: "FC_EINVAL", -2: "FC_ENOMEM", -3: "FC_EBUDGET", -4: "FC_ENOCONV",
                 -5: "FC_ENANINF", -6: "FC_ETIMEOUT", -7: "FC_ECUDA", -8: "FC_ENOTFOUND"}
@@ -114,6 +117,7 @@ def _load():
                                       ctypes.POINTER(sz)]
     lib.fftconv_apply.argtypes = [vp, vp, vp, vp]
     lib.fftconv_apply_prec.argtypes = [vp, i, vp, vp, vp]
+    lib.fftconv_cg_product.argtypes = [vp, i, vp, vp, vp, vp, ctypes.POINTER(d), vp]
     lib.cg_solve.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
     lib.cg_solve_batch.argtypes = [vp, i, vp, vp, vp, vp, ctypes.POINTER(cg_opts), ctypes.POINTER(cg_result), vp]
     lib.cg_solve_groups.argtypes = [i, ctypes.POINTER(cg_batch_group), ctypes.POINTER(cg_opts), vp]
@@ -132,6 +136,9 @@ def _load():
     lib.cg_server_batches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(i)]
     lib.cg_server_destroy.argtypes = [vp]
+    lib.fc_mem_stats.argtypes = [ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_longlong), i]
+    lib.fftconv_plan_check_guards.argtypes = [vp, ctypes.POINTER(i)]
+    lib.fc_debug_inject.argtypes = [vp, i, ctypes.c_longlong]
     return lib
 
 
@@ -242,6 +249,18 @@ def fftconv_apply_prec(plan: Plan, prec: int, x, y, stream=None) -> None:
 def fftconv_apply(plan: Plan, x, y, stream=None) -> None:
     prec = FC_F32 if x.dtype == torch.float32 else FC_F64
     fftconv_apply_prec(plan, prec, x, y, stream)
+
+
+def fftconv_cg_product(plan: Plan, prec: int, p, r, s, q, stream=None):
+    """q = C p + s p as the CG passes form it; returns their (p.q, r.q, q.q)."""
+    dt = torch.float32 if prec == FC_F32 else torch.float64
+    n = plan.L * plan.L
+    dots = (ctypes.c_double * 3)()
+    rc = _lib.fftconv_cg_product(plan.handle, int(prec), _ptr(p, dt, n, "p"), _ptr(r, dt, n, "r"),
+                                 _ptr(s, dt, n, "s"), _ptr(q, dt, n, "q"), dots, _stream(stream))
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_cg_product")
+    return tuple(dots)
 
 
 def _opts(rtol, mode, max_iter=0, refine_every=0, max_refine=0, inner_rtol=0.0, x0_zero=False, precond=False,
@@ -530,3 +549,28 @@ def cg_server_batches(sv: Server) -> dict:
 
 def cg_server_destroy(sv: Server) -> None:
     sv.close()
+
+
+def fc_mem_stats(reset_peak: bool = False) -> dict:
+    """The library's own device memory: live and peak bytes, live allocations."""
+    live, peak, n = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_longlong()
+    rc = _lib.fc_mem_stats(ctypes.byref(live), ctypes.byref(peak), ctypes.byref(n), int(bool(reset_peak)))
+    if rc != FC_OK:
+        raise FcError(rc, "fc_mem_stats")
+    return {"live_bytes": live.value, "peak_bytes": peak.value, "live_allocs": n.value}
+
+
+def fftconv_plan_check_guards(plan: Plan) -> int:
+    """Guard bands around the plan's buffers that were overwritten (0: none)."""
+    d = ctypes.c_int()
+    rc = _lib.fftconv_plan_check_guards(plan.handle, ctypes.byref(d))
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_plan_check_guards")
+    return d.value
+
+
+def fc_debug_inject(plan, kind: int, value: int) -> None:
+    """Test hooks (FC_INJECT_ALLOC with plan None, FC_INJECT_BARRIER, FC_INJECT_TMA)."""
+    rc = _lib.fc_debug_inject(plan.handle if plan is not None else None, int(kind), int(value))
+    if rc != FC_OK:
+        raise FcError(rc, "fc_debug_inject")

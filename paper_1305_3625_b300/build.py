@@ -19,7 +19,7 @@ OBJDIR = os.path.join(HERE, "_build")
 SOURCES = ["fc_lib.cu", "fc_server.cu", "fc_var_small.cu", "fc_var_256.cu", "fc_var_512.cu", "fc_var_1024.cu",
            "fc_var_2048.cu", "fc_var_4096.cu", "fc_var_8192.cu"]
 HEADERS = ["fc_fft.cuh", "fc_passes.cuh", "fc_internal.h", "fc_persist.cuh", "fc_tma.cuh", "fc_variants.h",
-           "fc_variants.cuh"]
+           "fc_variants.cuh", "fc_alloc.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

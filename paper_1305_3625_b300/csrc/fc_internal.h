@@ -51,6 +51,12 @@ struct CgState {
     int idle;            // 1: no inner run is in progress (batched solves: the inner passes skip
                          // this problem)
     unsigned cntA, cntC;  // last-block counters of passes A and C
+    double pq, rq, qq;    // grid sums of the last CG product's pass C (p.q, r.q, q.q)
+    // test hooks (fc_debug_inject): 1 = the persistent kernel's last block
+    // leaves before its first grid-barrier arrival, 2 = the TMA pass C issues
+    // no copy for each block's first row pair; dbg_limit: polls a bounded
+    // wait takes before it gives up (0: the default)
+    unsigned dbg_skip, dbg_limit;
 };
 
 // Largest number of changed iterate entries the residual update takes.
@@ -148,6 +154,9 @@ struct RowInvArgs {
 __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq, double qq,
                                                unsigned long long h_inner) {
     const double rr = st->rr;
+    st->pq = pq;
+    st->rq = rq;
+    st->qq = qq;
     double alpha = st->rp / pq;
     double rrn = rr - 2.0 * alpha * rq + alpha * alpha * qq;
     if (rrn < 0.0) rrn = 0.0;

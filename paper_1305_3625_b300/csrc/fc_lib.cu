@@ -8,6 +8,7 @@
 // residual and refinement; inner: CG iterations), so the host launches once
 // per solve and reads one status block at the end.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -18,8 +19,10 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
+#include "fc_alloc.h"
 #include "fc_persist.cuh"
 #include "fc_tma.cuh"
 #include "fc_variants.h"
@@ -40,6 +43,80 @@ int set_cuda_err(cudaError_t e, const char* what) {
         cudaError_t e_ = (call);                           \
         if (e_ != cudaSuccess) return set_cuda_err(e_, #call); \
     } while (0)
+
+}  // namespace
+
+// ------------------------------------------------------------ allocations --
+//
+// Every device and pinned allocation of the library goes through these
+// wrappers: they count the live allocations and bytes (fc_mem_stats) and honour
+// the allocation-failure injection of fc_debug_inject (FC_INJECT_ALLOC), so
+// that tests can fail any allocation of a set-up on the host and check that
+// the error path returns FC_ENOMEM and frees what it had made.
+
+namespace fc {
+
+static std::atomic<long long> g_fail_countdown{0};  // n > 0: the n-th allocation from now fails
+static std::mutex g_alloc_mu;
+static std::unordered_map<void*, size_t> g_live;  // live allocations and their bytes
+static size_t g_live_dev_bytes = 0, g_peak_dev_bytes = 0;
+
+static bool inject_failure() {
+    long long c = g_fail_countdown.load();
+    while (c > 0) {
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+
+static void note_alloc(void* ptr, size_t bytes, bool device) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_live[ptr] = device ? bytes : 0;
+    if (device) {
+        g_live_dev_bytes += bytes;
+        if (g_live_dev_bytes > g_peak_dev_bytes) g_peak_dev_bytes = g_live_dev_bytes;
+    }
+}
+
+static void note_free(void* ptr) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    auto it = g_live.find(ptr);
+    if (it == g_live.end()) return;
+    g_live_dev_bytes -= it->second;
+    g_live.erase(it);
+}
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+    if (inject_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) note_alloc(*ptr, bytes, true);
+    return e;
+}
+cudaError_t dev_malloc_async(void** ptr, size_t bytes, cudaStream_t s) {
+    if (inject_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(ptr, bytes, s);
+    if (e == cudaSuccess) note_alloc(*ptr, bytes, true);
+    return e;
+}
+cudaError_t host_malloc(void** ptr, size_t bytes) {
+    if (inject_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocHost(ptr, bytes);
+    if (e == cudaSuccess) note_alloc(*ptr, bytes, false);
+    return e;
+}
+void dev_free(void* ptr) {
+    if (ptr && cudaFree(ptr) == cudaSuccess) note_free(ptr);
+}
+void dev_free_async(void* ptr, cudaStream_t s) {
+    if (ptr && cudaFreeAsync(ptr, s) == cudaSuccess) note_free(ptr);
+}
+void host_free(void* ptr) {
+    if (ptr && cudaFreeHost(ptr) == cudaSuccess) note_free(ptr);
+}
+
+}  // namespace fc
+
+namespace {
 
 // ------------------------------------------------------- utility kernels --
 
@@ -603,6 +680,16 @@ int grid_1d(long n, int threads) {
 
 // ------------------------------------------------------------------ plan --
 
+// A device buffer between two guard bands of kGuard bytes of kGuardByte:
+// [base, base + kGuard) and [base + kGuard + bytes, base + 2 kGuard + bytes);
+// the user's bytes start at base + kGuard (256-byte aligned, as cudaMalloc's).
+struct GuardedAlloc {
+    void* base;
+    size_t bytes;
+};
+constexpr size_t kGuard = 256;
+constexpr unsigned char kGuardByte = 0xC5;
+
 struct PrecRes {
     bool on = false;
     Variants v;
@@ -670,18 +757,48 @@ struct fftconv_plan {
     bool blocking = false;       // waits block the host thread (event with blocking sync)
     cudaEvent_t ev_wait = nullptr;
     struct BatchWs* batch = nullptr;  // batched solves (cg_solve_batch), made on first use
+    // every device buffer of the plan, each between two guard bands
+    // (fftconv_plan_check_guards), and the set-up stream that fills them
+    std::vector<GuardedAlloc> allocs;
+    cudaStream_t setup = nullptr;
+    // test hooks (fc_debug_inject): copied into each solve's state
+    unsigned dbg_skip = 0, dbg_limit = 0;
 };
 
 namespace {
 
+// Fill the two guard bands of a guarded buffer on stream s.
+int fill_guards(const GuardedAlloc& a, cudaStream_t s) {
+    unsigned char* b = (unsigned char*)a.base;
+    FC_CK(cudaMemsetAsync(b, kGuardByte, kGuard, s));
+    FC_CK(cudaMemsetAsync(b + kGuard + a.bytes, kGuardByte, kGuard, s));
+    return FC_OK;
+}
+
+// A plan buffer of bytes (guarded; set-up only: the guards are filled on the
+// plan's set-up stream).
 int dalloc(fftconv_plan* p, void** ptr, size_t bytes) {
-    cudaError_t e = cudaMalloc(ptr, bytes);
+    void* base = nullptr;
+    cudaError_t e = dev_malloc(&base, bytes + 2 * kGuard);
     if (e != cudaSuccess) {
         set_cuda_err(e, "cudaMalloc");
         return FC_ENOMEM;
     }
+    p->allocs.push_back(GuardedAlloc{base, bytes});
+    *ptr = (unsigned char*)base + kGuard;
     p->bytes += bytes;
-    return FC_OK;
+    return fill_guards(p->allocs.back(), p->setup);
+}
+
+// Free one plan buffer made by dalloc.
+void dfree(fftconv_plan* p, void* ptr) {
+    for (size_t k = 0; k < p->allocs.size(); ++k)
+        if ((unsigned char*)p->allocs[k].base + kGuard == ptr) {
+            dev_free(p->allocs[k].base);
+            p->bytes -= p->allocs[k].bytes;
+            p->allocs.erase(p->allocs.begin() + (long)k);
+            return;
+        }
 }
 
 void batch_free(fftconv_plan* p);
@@ -694,18 +811,10 @@ void plan_free(fftconv_plan* p) {
         if (p->gexec[m]) cudaGraphExecDestroy(p->gexec[m]);
         if (p->graph[m]) cudaGraphDestroy(p->graph[m]);
     }
-    void* ptrs[] = {p->p32.Z, p->p32.Gq, p->p64.Z, p->p64.tw, p->p64.Gq, p->x64, p->r64,
-                    p->p64v, p->q64, p->b64, p->s64, p->mask, p->d32, p->r32, p->p32v, p->q32, p->s32,
-                    p->st, p->part, p->partA, p->partC, p->pctl, p->am_v, p->am_i, p->am_ctl,
-                    p->z64, p->pq64, p->z32, p->pq32, p->gtab, p->widx, p->wdx};
-    for (void* q : ptrs)
-        if (q) cudaFree(q);
-    for (int i = 0; i < 5; ++i) {
-        if (p->p32.twst[i]) cudaFree(p->p32.twst[i]);
-        if (p->p64.twst[i]) cudaFree(p->p64.twst[i]);
-    }
-    if (p->st_host) cudaFreeHost(p->st_host);
-    if (p->rm_host) cudaFreeHost(p->rm_host);
+    for (const GuardedAlloc& a : p->allocs) dev_free(a.base);
+    p->allocs.clear();
+    host_free(p->st_host);
+    host_free(p->rm_host);
     if (p->ev_wait) cudaEventDestroy(p->ev_wait);
     delete p;
 }
@@ -992,8 +1101,8 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     int rc = FC_OK;
     const size_t zbytes = sizeof(cpx<T>) * (size_t)(p->M / 2) * p->L;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocAsync((void**)&x, sizeof(T) * p->N, s) != cudaSuccess ||
-        cudaMallocAsync((void**)&y, sizeof(T) * p->N, s) != cudaSuccess ||
+        dev_malloc_async((void**)&x, sizeof(T) * p->N, s) != cudaSuccess ||
+        dev_malloc_async((void**)&y, sizeof(T) * p->N, s) != cudaSuccess ||
         cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
         cudaMemsetAsync(x, 0, sizeof(T) * p->N, s) != cudaSuccess || cudaMemsetAsync(R.Z, 0, zbytes, s) != cudaSuccess) {
         rc = set_cuda_err(cudaGetLastError(), "autotune set-up");
@@ -1023,8 +1132,8 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (s) {
-        if (x) cudaFreeAsync(x, s);
-        if (y) cudaFreeAsync(y, s);
+        dev_free_async(x, s);
+        dev_free_async(y, s);
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
@@ -1173,6 +1282,7 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
     } while (0)
     FC_TRYC(cudaGetDevice(&p->dev));
     FC_TRYC(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    p->setup = cs;
     // both precisions need FP64 set-up: the spectrum is built in FP64
     p->p64.on = true;
     p->p32.on = (prec & FC_F32) != 0;
@@ -1186,13 +1296,18 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
     FC_TRY(dalloc(p, &p->p64.Gq, sizeof(double) * (size_t)Q * Q));
     if (p->p32.on) FC_TRY(dalloc(p, &p->p32.Gq, sizeof(float) * (size_t)Q * Q));
     // spectrum: kernel table -> unpruned FP64 2D FFT -> quarter / M^2
-    e = cudaMallocAsync((void**)&K, sizeof(cpx<double>) * (size_t)M * M, cs);
+    e = dev_malloc_async((void**)&K, sizeof(cpx<double>) * (size_t)M * M, cs);
     if (e != cudaSuccess) {
         rc = FC_ENOMEM;
         set_cuda_err(e, "cudaMallocAsync(spectrum grid)");
         goto fail;
     }
-    FC_TRYC(cudaMallocAsync((void**)&maxes, 2 * sizeof(double), cs));
+    e = dev_malloc_async((void**)&maxes, 2 * sizeof(double), cs);
+    if (e != cudaSuccess) {
+        rc = FC_ENOMEM;
+        set_cuda_err(e, "cudaMallocAsync(spectrum maxima)");
+        goto fail;
+    }
     FC_TRYC(cudaMemsetAsync(maxes, 0, 2 * sizeof(double), cs));
     k_twiddles<<<(M + 255) / 256, 256, 0, cs>>>(M, (cpx<double>*)p->p64.tw, nullptr);
     FC_TRYC(cudaGetLastError());
@@ -1208,7 +1323,12 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
     if (prec & FC_F64) {
         FC_TRY(dalloc(p, (void**)&p->gtab, sizeof(double) * N));
     } else {
-        FC_TRYC(cudaMallocAsync((void**)&gt_tmp, sizeof(double) * N, cs));
+        e = dev_malloc_async((void**)&gt_tmp, sizeof(double) * N, cs);
+        if (e != cudaSuccess) {
+            rc = FC_ENOMEM;
+            set_cuda_err(e, "cudaMallocAsync(offset table)");
+            goto fail;
+        }
     }
     {
         double* gt = (prec & FC_F64) ? p->gtab : gt_tmp;
@@ -1230,13 +1350,11 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
         FC_TRYC(cudaGetLastError());
         FC_TRYC(cudaMemcpyAsync(hmax, maxes, sizeof(hmax), cudaMemcpyDeviceToHost, cs));
     }
-    FC_TRYC(cudaFreeAsync(K, cs));
+    dev_free_async(K, cs);
     K = nullptr;
-    if (gt_tmp) {
-        FC_TRYC(cudaFreeAsync(gt_tmp, cs));
-        gt_tmp = nullptr;
-    }
-    FC_TRYC(cudaFreeAsync(maxes, cs));
+    dev_free_async(gt_tmp, cs);
+    gt_tmp = nullptr;
+    dev_free_async(maxes, cs);
     maxes = nullptr;
     FC_TRYC(cudaStreamSynchronize(cs));
     if (!(hmax[0] <= 1e-12 * hmax[1])) {
@@ -1288,19 +1406,23 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
     if (!(prec & FC_F64)) {
         // FP32-only plan: drop the FP64 tables once the FP32 ones exist
         FC_TRYC(cudaStreamSynchronize(cs));
-        cudaFree(p->p64.tw);
-        cudaFree(p->p64.Gq);
-        p->bytes -= sizeof(cpx<double>) * M + sizeof(double) * (size_t)Q * Q;
+        dfree(p, p->p64.tw);
+        dfree(p, p->p64.Gq);
         p->p64.tw = p->p64.Gq = nullptr;
         for (int i = 0; i < 5; ++i)
             if (p->p64.twst[i]) {
-                cudaFree(p->p64.twst[i]);
+                dfree(p, p->p64.twst[i]);
                 p->p64.twst[i] = nullptr;
             }
         p->p64.on = false;
     }
-    FC_TRYC(cudaMallocHost(&p->st_host, sizeof(CgState)));
-    FC_TRYC(cudaMallocHost(&p->rm_host, sizeof(int64_t)));
+    e = host_malloc((void**)&p->st_host, sizeof(CgState));
+    if (e == cudaSuccess) e = host_malloc((void**)&p->rm_host, sizeof(int64_t));
+    if (e != cudaSuccess) {
+        rc = FC_ENOMEM;
+        set_cuda_err(e, "cudaMallocHost");
+        goto fail;
+    }
     FC_TRYC(cudaStreamSynchronize(cs));
     if (prec & FC_F64) FC_TRY(autotune<double>(p, p->p64, tune));
     if (p->p32.on) FC_TRY(autotune<float>(p, p->p32, tune));
@@ -1316,17 +1438,18 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
                                             verbose));
     }
     cudaStreamDestroy(cs);
+    p->setup = nullptr;
     *out = p;
     return FC_OK;
 fail:
     if (cs) {
-        if (K) cudaFreeAsync(K, cs);
-        if (maxes) cudaFreeAsync(maxes, cs);
-        if (gt_tmp) cudaFreeAsync(gt_tmp, cs);
+        dev_free_async(K, cs);
+        dev_free_async(maxes, cs);
+        dev_free_async(gt_tmp, cs);
         cudaStreamSynchronize(cs);
-        cudaStreamDestroy(cs);
     }
     plan_free(p);
+    if (cs) cudaStreamDestroy(cs);
     return rc;
 #undef FC_TRY
 #undef FC_TRYC
@@ -1418,6 +1541,77 @@ extern "C" int fftconv_apply_prec(fftconv_plan* p, int prec, const void* x, void
 extern "C" int fftconv_apply(fftconv_plan* p, const void* x, void* y, fc_stream_t stream) {
     if (!p) return FC_EINVAL;
     return fftconv_apply_prec(p, (p->prec & FC_F32) ? FC_F32 : FC_F64, x, y, stream);
+}
+
+namespace {
+
+// One CG product of Listing 2 as the solver's passes compute it: q = C p + s p
+// with the pass-C sums p.q, r.q, q.q, on a state of its own.
+template <typename T>
+int cg_product_t(fftconv_plan* p, PrecRes& R, const T* pv, const T* rv, const T* sv, T* qv, double dots[3],
+                 cudaStream_t s) {
+    CgState* st = nullptr;
+    if (dev_malloc_async((void**)&st, sizeof(CgState), s) != cudaSuccess) {
+        set_cuda_err(cudaErrorMemoryAllocation, "cudaMallocAsync(state)");
+        return FC_ENOMEM;
+    }
+    int rc = FC_OK;
+    if (cudaMemsetAsync(st, 0, sizeof(CgState), s) != cudaSuccess) rc = set_cuda_err(cudaGetLastError(), "memset");
+    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+    if (!rc) {
+        RowFwdArgs<T> a{};
+        a.L = p->L;
+        a.mode = RF_PLAIN;
+        a.x = pv;
+        a.st = st;
+        a.part = p->part;
+        a.Z = (cpx<T>*)R.Z;
+        a.tw = (const cpx<T>*)R.tws(ka.E);
+        rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, s, a);
+    }
+    if (!rc) {
+        ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
+        rc = launch_dep(kb.f, col_grid(p, kb), kb.threads, kb.smem, s, b);
+    }
+    if (!rc) {
+        RowInvArgs<T> c{};
+        c.L = p->L;
+        c.mode = RI_CG;
+        c.s = sv;
+        c.cp = pv;
+        c.cr = rv;
+        c.cq = qv;
+        c.st = st;
+        c.part = p->part;
+        c.Z = (const cpx<T>*)R.Z;
+        c.tw = (const cpx<T>*)R.tws(kc.E);
+        rc = launch_rinv<T>(p, R, kc, c, s, true);
+    }
+    CgState h;
+    if (!rc && cudaMemcpyAsync(&h, st, sizeof(CgState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = set_cuda_err(cudaGetLastError(), "cudaMemcpyAsync(state)");
+    dev_free_async(st, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = set_cuda_err(cudaGetLastError(), "cg product");
+    if (!rc) {
+        dots[0] = h.pq;
+        dots[1] = h.rq;
+        dots[2] = h.qq;
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int fftconv_cg_product(fftconv_plan* p, int prec, const void* pvec, const void* rvec, const void* s,
+                                  void* q, double dots[3], fc_stream_t stream) {
+    if (!p || !pvec || !rvec || !s || !q || !dots || !(prec == FC_F32 || prec == FC_F64)) return FC_EINVAL;
+    PrecRes& R = prec == FC_F32 ? p->p32 : p->p64;
+    if (!R.on) return FC_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == FC_F32)
+        return cg_product_t<float>(p, R, (const float*)pvec, (const float*)rvec, (const float*)s, (float*)q, dots, st);
+    return cg_product_t<double>(p, R, (const double*)pvec, (const double*)rvec, (const double*)s, (double*)q, dots,
+                                st);
 }
 
 // ------------------------------------------------- persistent inner CG --
@@ -2126,6 +2320,8 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     }
     CgState h;
     init_state(o, &h);
+    h.dbg_skip = p->dbg_skip;
+    h.dbg_limit = p->dbg_limit;
     *p->st_host = h;
     FC_CK(cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st));
     // inputs into the plan's buffers (the graph is built on them); after a
@@ -2225,7 +2421,7 @@ struct BatchWs {
     cudaStream_t stream = nullptr;  // own stream: groups of cg_solve_groups run concurrently
     cudaEvent_t ev = nullptr;
     size_t bytes = 0;
-    std::vector<void*> blocks;
+    std::vector<GuardedAlloc> blocks;  // each between two guard bands
     // batched breaking steps: per-problem argmax winners and counters
     double* am_v = nullptr;
     long long* am_i = nullptr;
@@ -2250,7 +2446,7 @@ void batch_graphs_free(BatchWs* w) {
 // workspace has finished: the calls wait for their batches).
 void batch_buffers_free(BatchWs* w, cudaStream_t st) {
     batch_graphs_free(w);
-    for (void* q : w->blocks) cudaFreeAsync(q, st);
+    for (const GuardedAlloc& a : w->blocks) dev_free_async(a.base, st);
     w->blocks.clear();
     w->v = SolveView{};
     w->cap = 0;
@@ -2271,7 +2467,7 @@ void batch_free(fftconv_plan* p) {
     if (!w) return;
     batch_buffers_free(w, w->stream);
     cudaStreamSynchronize(w->stream);
-    if (w->st_host) cudaFreeHost(w->st_host);
+    host_free(w->st_host);
     if (w->ev) cudaEventDestroy(w->ev);
     if (w->stream) cudaStreamDestroy(w->stream);
     delete w;
@@ -2281,15 +2477,15 @@ void batch_free(fftconv_plan* p) {
 template <typename P>
 int balloc(BatchWs* w, P** ptr, size_t bytes, cudaStream_t st) {
     void* q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, bytes, st);
+    cudaError_t e = dev_malloc_async(&q, bytes + 2 * kGuard, st);
     if (e != cudaSuccess) {
         set_cuda_err(e, "cudaMallocAsync(batch)");
         return FC_ENOMEM;
     }
-    w->blocks.push_back(q);
+    w->blocks.push_back(GuardedAlloc{q, bytes});
     w->bytes += bytes;
-    *ptr = (P*)q;
-    return FC_OK;
+    *ptr = (P*)((unsigned char*)q + kGuard);
+    return fill_guards(w->blocks.back(), st);
 }
 
 // Problems a padded batch of nb launches: the next of 1, 2, 3, 4, 6, 8, 12,
@@ -2314,11 +2510,13 @@ int batch_reserve(fftconv_plan* p, int nb, bool mixed, cudaStream_t st) {
     BatchWs* w = p->batch;
     if (w->st_cap < nb) {
         const int n = nb > 64 ? nb : 64;
-        if (w->st_host) cudaFreeHost(w->st_host);
+        host_free(w->st_host);
         w->st_host = nullptr;
         w->st_cap = 0;
-        if (cudaMallocHost(&w->st_host, sizeof(CgState) * n) != cudaSuccess)
-            return set_cuda_err(cudaGetLastError(), "cudaMallocHost(batch states)");
+        if (host_malloc((void**)&w->st_host, sizeof(CgState) * n) != cudaSuccess) {
+            set_cuda_err(cudaErrorMemoryAllocation, "cudaMallocHost(batch states)");
+            return FC_ENOMEM;
+        }
         w->st_cap = n;
     }
     const bool need64 = !mixed, need32 = mixed;
@@ -2718,7 +2916,10 @@ extern "C" int fc_fracture_run_batch(fftconv_plan* p, int nb, const double* s, c
     // last one (the removal is the only change), unless turned off
     const bool warm = o->warm_resid == 0 && p->gtab != nullptr;
     int64_t* rm_host = nullptr;
-    FC_CK(cudaMallocHost(&rm_host, sizeof(int64_t) * (size_t)nb));
+    if (host_malloc((void**)&rm_host, sizeof(int64_t) * (size_t)nb) != cudaSuccess) {
+        set_cuda_err(cudaErrorMemoryAllocation, "cudaMallocHost(removed indices)");
+        return FC_ENOMEM;
+    }
     int step = 0;
     for (; step < steps && rc == FC_OK; ++step) {
         for (int k = 0; k < nb; ++k) {
@@ -2798,11 +2999,12 @@ extern "C" int fc_fracture_run_batch(fftconv_plan* p, int nb, const double* s, c
             rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(tail)");
     }
     if (rc == FC_OK) {
-        FC_CK(cudaMemcpyAsync(x, v.x64, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st));
-        FC_CK(cudaMemcpyAsync(mask, v.mask, nN, cudaMemcpyDeviceToDevice, st));
-        FC_CK(wait_stream(p, st));
+        if (cudaMemcpyAsync(x, v.x64, sizeof(double) * nN, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(mask, v.mask, nN, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            wait_stream(p, st) != cudaSuccess)
+            rc = set_cuda_err(cudaGetLastError(), "fc_fracture_run_batch(results)");
     }
-    cudaFreeHost(rm_host);
+    host_free(rm_host);
     if (rc) return rc;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int status = FC_OK;
@@ -2921,4 +3123,93 @@ extern "C" int fc_masked_step_static(int64_t N, const double* t, uint8_t* mask, 
     k_masked_argmax<<<grid, 256, 0, s>>>((long)N, t, mask, x, removed, nullptr, pv, pi, ctl);
     FC_CK(cudaGetLastError());
     return FC_OK;
+}
+
+// ------------------------------------------------ memory and test hooks --
+
+extern "C" int fc_mem_stats(size_t* live_bytes, size_t* peak_bytes, long long* live_allocs, int reset_peak) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (live_bytes) *live_bytes = g_live_dev_bytes;
+    if (peak_bytes) *peak_bytes = g_peak_dev_bytes;
+    if (live_allocs) *live_allocs = (long long)g_live.size();
+    if (reset_peak) g_peak_dev_bytes = g_live_dev_bytes;
+    return FC_OK;
+}
+
+extern "C" int fc_debug_inject(fftconv_plan* p, int kind, long long value) {
+    if (value < 0) return FC_EINVAL;
+    switch (kind) {
+        case FC_INJECT_ALLOC:
+            g_fail_countdown.store(value);
+            return FC_OK;
+        case FC_INJECT_BARRIER:
+        case FC_INJECT_TMA:
+            if (!p || value > 0xffffffffLL) return FC_EINVAL;
+            p->dbg_skip = value ? (kind == FC_INJECT_BARRIER ? 1u : 2u) : 0u;
+            p->dbg_limit = (unsigned)value;
+            {
+                // the plan's state now as well (applies read it; solves copy it in)
+                const unsigned v[2] = {p->dbg_skip, p->dbg_limit};
+                static_assert(offsetof(CgState, dbg_limit) == offsetof(CgState, dbg_skip) + sizeof(unsigned),
+                              "adjacent hook fields");
+                FC_CK(cudaMemcpy((char*)p->st + offsetof(CgState, dbg_skip), v, sizeof(v), cudaMemcpyHostToDevice));
+            }
+            return FC_OK;
+        default:
+            return FC_EINVAL;
+    }
+}
+
+namespace {
+
+// Guard bands of a plan's buffers: block b checks band b (kGuard bytes, one
+// per thread) and counts it once if any byte differs from kGuardByte.
+__global__ void __launch_bounds__(256) k_check_guards(const unsigned char* const* bands, unsigned* damaged) {
+    const unsigned char* g = bands[blockIdx.x];
+    const int bad = g[threadIdx.x] != kGuardByte;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicAdd(damaged, 1u);
+}
+
+}  // namespace
+
+extern "C" int fftconv_plan_check_guards(fftconv_plan* p, int* damaged) {
+    if (!p || !damaged) return FC_EINVAL;
+    *damaged = 0;
+    std::vector<const unsigned char*> bands;
+    auto add = [&](const GuardedAlloc& a) {
+        const unsigned char* b = (const unsigned char*)a.base;
+        bands.push_back(b);
+        bands.push_back(b + kGuard + a.bytes);
+    };
+    for (const GuardedAlloc& a : p->allocs) add(a);
+    if (p->batch)
+        for (const GuardedAlloc& a : p->batch->blocks) add(a);
+    if (bands.empty()) return FC_OK;
+    static_assert(kGuard == 256, "one thread per guard byte");
+    cudaStream_t s = nullptr;
+    void* dev = nullptr;
+    const size_t pbytes = sizeof(void*) * bands.size();
+    FC_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    int rc = FC_OK;
+    unsigned h = 0;
+    if (dev_malloc_async(&dev, pbytes + sizeof(unsigned), s) != cudaSuccess) {
+        set_cuda_err(cudaErrorMemoryAllocation, "cudaMallocAsync(guard list)");
+        rc = FC_ENOMEM;
+    } else {
+        unsigned* cnt = (unsigned*)((unsigned char*)dev + pbytes);
+        if (cudaMemcpyAsync(dev, bands.data(), pbytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemsetAsync(cnt, 0, sizeof(unsigned), s) != cudaSuccess)
+            rc = set_cuda_err(cudaGetLastError(), "guard check set-up");
+        if (!rc) {
+            k_check_guards<<<(unsigned)bands.size(), 256, 0, s>>>((const unsigned char* const*)dev, cnt);
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(&h, cnt, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+                rc = set_cuda_err(cudaGetLastError(), "guard check");
+        }
+        dev_free_async(dev, s);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess && !rc) rc = set_cuda_err(cudaGetLastError(), "guard check");
+    cudaStreamDestroy(s);
+    if (!rc) *damaged = (int)h;
+    return rc;
 }

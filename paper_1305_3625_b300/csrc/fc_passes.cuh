@@ -163,6 +163,40 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h, float l) {
     lo = __fsub_rn(err, __fsub_rn(hi, sum));
 }
 
+// Per-thread accumulator of a pass's dot products.  FP64 passes: an FP64
+// sum.  FP32 passes: Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26, 2005): each product a*b is split
+// exactly into its rounded value and its rounding error (one fma), the
+// rounded values are summed with TwoSum, and both kinds of error collect in
+// lo.  hi + lo is as accurate as the sum taken in twice the working
+// precision and rounded, plus an error of order (n u)^2 of the sum of
+// |a_i b_i| (n <= 16 products per thread), so the FP32 vectors' dot products
+// reach the accuracy of FP64 accumulation without FP64 arithmetic.
+template <typename T>
+struct Acc {
+    T v = 0;
+    __device__ __forceinline__ void prod(T a, T b) { v += a * b; }
+    __device__ __forceinline__ void set(T x) { v = x; }
+    __device__ __forceinline__ double value() const { return (double)v; }
+};
+template <>
+struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);
+        float s, t;
+        two_sum(hi, p, s, t);
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(t, e));
+    }
+    __device__ __forceinline__ void set(float x) {
+        hi = x;
+        lo = 0.f;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // Sum NV two-float values over the block (fixed order: warp tree, then warp
 // 0 over the warp sums).  Result valid in thread 0.  Whole warps only.
 template <int NV>
@@ -197,19 +231,20 @@ __device__ __forceinline__ void block_sum_ff(float (&hi)[NV], float (&lo)[NV], f
     }
 }
 
-// grid_sum_last for FP32 partials: the per-block sums are published as
-// two-float pairs (part holds NV float2 per block, the room of NV doubles)
-// and the last block's warp 0 adds them in block order the same way.  tot:
-// the FP64 totals, valid in thread 0 of the last block.
+// grid_sum_last for FP32 partials (each thread's Dot2 pair): the per-block
+// sums are published as two-float pairs (part holds NV float2 per block, the
+// room of NV doubles) and the last block's warp 0 adds them in block order
+// the same way.  tot: the FP64 totals, valid in thread 0 of the last block.
 template <int NV>
-__device__ __forceinline__ bool grid_sum_last(float (&v)[NV], double* part, unsigned* cnt, double (&tot)[NV]) {
+__device__ __forceinline__ bool grid_sum_last(const Acc<float> (&v)[NV], double* part, unsigned* cnt,
+                                              double (&tot)[NV]) {
     __shared__ float2 scratch[32][NV];
     __shared__ bool is_last;
     float hi[NV], lo[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        hi[k] = v[k];
-        lo[k] = 0.f;
+        hi[k] = v[k].hi;
+        lo[k] = v[k].lo;
     }
     block_sum_ff<NV>(hi, lo, scratch);
     float2* pf = reinterpret_cast<float2*>(part);
@@ -248,6 +283,16 @@ __device__ __forceinline__ bool grid_sum_last(float (&v)[NV], double* part, unsi
     return true;
 }
 
+// grid_sum_last for FP64 partials held in accumulators.
+template <int NV>
+__device__ __forceinline__ bool grid_sum_last(const Acc<double> (&a)[NV], double* part, unsigned* cnt,
+                                              double (&tot)[NV]) {
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = a[k].v;
+    return grid_sum_last<NV>(v, part, cnt, tot);
+}
+
 // --------------------------------------------------- per-element input ---
 
 // Block-uniform scalars of a pass-A unit (the CG step of the last product,
@@ -273,8 +318,8 @@ __device__ __forceinline__ T pass_a_value(int mode, const T* __restrict__ xin, T
                                           T* __restrict__ cr, T* __restrict__ cp, const T* __restrict__ cq,
                                           const T* __restrict__ cz, const double* __restrict__ r64,
                                           double* __restrict__ x64, const float* __restrict__ d32,
-                                          const uint8_t* __restrict__ mask, size_t i, const AScal<T>& sc, T& acc,
-                                          T& acc_rp) {
+                                          const uint8_t* __restrict__ mask, size_t i, const AScal<T>& sc,
+                                          Acc<T>& acc, Acc<T>& acc_rp) {
     if (mode == RF_PLAIN) return xin[i];
     if (mode == RF_XUPD) {
         double xv = x64[i];
@@ -299,14 +344,14 @@ __device__ __forceinline__ T pass_a_value(int mode, const T* __restrict__ xin, T
             r = cr[i] - sc.alpha * cq[i];
             cr[i] = r;
         }
-        acc += r * r;
+        acc.prod(r, r);
         return r;
     }
     if (mode == RF_PCG_P) {  // PCG: p = z + beta p; transform p
         const T z = cz[i];
         const T p = sc.first ? z : z + sc.beta * cp[i];
         cp[i] = p;
-        acc_rp += cr[i] * p;
+        acc_rp.prod(cr[i], p);
         return p;
     }
     T r, p;
@@ -327,8 +372,8 @@ __device__ __forceinline__ T pass_a_value(int mode, const T* __restrict__ xin, T
         p = r + sc.beta * p;
     }
     cp[i] = p;
-    acc += r * r;
-    acc_rp += r * p;
+    acc.prod(r, r);
+    acc_rp.prod(r, p);
     return p;
 }
 
@@ -341,7 +386,7 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
                                               const T* __restrict__ cz, const double* __restrict__ r64,
                                               double* __restrict__ x64, const float* __restrict__ d32,
                                               const uint8_t* __restrict__ mask, const AScal<T>& sc, int j, int r0,
-                                              int L, size_t vo, cpx<T> (&v)[E], T& acc, T& acc_rp) {
+                                              int L, size_t vo, cpx<T> (&v)[E], Acc<T>& acc, Acc<T>& acc_rp) {
     constexpr int G = M / E;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -380,8 +425,8 @@ __device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a, con
 // memory in use: the caller synchronises before the block reuses it.  vo, zo:
 // the problem's offsets in the vectors and the intermediate.
 template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
-__device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm, T& acc,
-                                          T& acc_rp, size_t vo = 0, size_t zo = 0) {
+__device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm,
+                                          Acc<T>& acc, Acc<T>& acc_rp, size_t vo = 0, size_t zo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;  // shared elements per pair
@@ -423,20 +468,21 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
 // Pass A's grid sums: partials in the pass's precision (FP32: two-float
 // combination, FP64: FP64), totals in FP64, written by the last block.
 template <typename T>
-__device__ __forceinline__ void rfwd_sums(int mode, double* part, CgState* st, T acc, T acc_rp) {
+__device__ __forceinline__ void rfwd_sums(int mode, double* part, CgState* st, const Acc<T>& acc,
+                                          const Acc<T>& acc_rp) {
     if (mode == RF_CG) {
-        T pv[2] = {acc, acc_rp};
+        const Acc<T> pv[2] = {acc, acc_rp};
         double tot[2];
         if (grid_sum_last<2>(pv, part, &st->cntA, tot) && threadIdx.x == 0) {
             st->rr = tot[0];
             st->rp = tot[1];
         }
     } else if (mode == RF_PCG_R) {
-        T pv[1] = {acc};
+        const Acc<T> pv[1] = {acc};
         double tot[1];
         if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rr = tot[0];
     } else if (mode == RF_PCG_P) {
-        T pv[1] = {acc_rp};
+        const Acc<T> pv[1] = {acc_rp};
         double tot[1];
         if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rp = tot[0];
     }
@@ -451,7 +497,7 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a
     pdl_enter();
     if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
     const AScal<T> sc = ascal_from_state(a, a.st);
-    T acc = 0, acc_rp = 0;
+    Acc<T> acc, acc_rp;
     rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
     pdl_leave();
     rfwd_sums(a.mode, a.part, a.st, acc, acc_rp);
@@ -467,7 +513,7 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_b(const RowFwdArgs<T>
     if (bb.gate && gate_closed(st, bb.gate)) return;
     if (a.mode == RF_XUPD && st->warm) return;
     const AScal<T> sc = ascal_from_state(a, st);
-    T acc = 0, acc_rp = 0;
+    Acc<T> acc, acc_rp;
     rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp,
                                (size_t)blockIdx.y * bb.bs.n, (size_t)blockIdx.y * bb.bs.z);
     pdl_leave();
@@ -576,7 +622,7 @@ __device__ __forceinline__ void pass_c_value(int mode, T* __restrict__ y, const 
                                              T* __restrict__ cz, const uint8_t* __restrict__ mask,
                                              const double* __restrict__ x64, const double* __restrict__ b64,
                                              const double* __restrict__ s64, double* __restrict__ r64, size_t i,
-                                             T yv, T& s0, T& s1, T& s2) {
+                                             T yv, Acc<T>& s0, Acc<T>& s1, Acc<T>& s2) {
     const bool act = mask == nullptr || mask[i] != 0;
     if (mode == RI_PLAIN) {
         y[i] = yv;
@@ -584,20 +630,20 @@ __device__ __forceinline__ void pass_c_value(int mode, T* __restrict__ y, const 
         const T p = cp[i];
         const T q = act ? yv + s[i] * p : (T)0;
         cq[i] = q;
-        s0 += p * q;
-        s1 += cr[i] * q;
-        s2 += q * q;
+        s0.prod(p, q);
+        s1.prod(cr[i], q);
+        s2.prod(q, q);
     } else if (mode == RI_PCG_Z) {
         const T z = act ? yv : (T)0;
         cz[i] = z;
-        s0 += cr[i] * z;
+        s0.prod(cr[i], z);
     } else {  // RI_RESID (T = double)
         const double xv = x64[i];
         const double bv = act ? b64[i] : 0.0;
         const double r = act ? bv - ((double)yv + s64[i] * xv) : 0.0;
         r64[i] = r;
-        s0 += (T)(r * r);
-        s1 += (T)(bv * bv);
+        s0.prod((T)r, (T)r);
+        s1.prod((T)bv, (T)bv);
     }
 }
 
@@ -610,7 +656,7 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
                                                const uint8_t* __restrict__ mask, const double* __restrict__ x64,
                                                const double* __restrict__ b64, const double* __restrict__ s64,
                                                double* __restrict__ r64, int j, int r0, int L, size_t vo,
-                                               const cpx<T> (&v)[E], T& s0, T& s1, T& s2) {
+                                               const cpx<T> (&v)[E], Acc<T>& s0, Acc<T>& s1, Acc<T>& s2) {
     constexpr int G = M / E;
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
@@ -629,8 +675,8 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
 // One unit of pass C: RB row pairs starting at pair unit*RB.  Adds this
 // thread's partial sums to s0, s1, s2.  vo, zo: the problem's offsets.
 template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
-__device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, T& s0, T& s1, T& s2,
-                                          size_t vo = 0, size_t zo = 0) {
+__device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, Acc<T>& s0, Acc<T>& s1,
+                                          Acc<T>& s2, size_t vo = 0, size_t zo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;
@@ -686,20 +732,21 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
 // Pass C's grid sums and step decisions (last block).  warm (RI_RESID): the
 // residual and its sums were updated in place, and block 0 alone hands them on.
 template <typename T>
-__device__ __forceinline__ void rinv_sums(const RowInvArgs<T>& a, double* part, CgState* st, T s0, T s1, T s2) {
+__device__ __forceinline__ void rinv_sums(const RowInvArgs<T>& a, double* part, CgState* st, const Acc<T>& s0,
+                                          const Acc<T>& s1, const Acc<T>& s2) {
     if (a.mode == RI_CG) {
-        T pv[3] = {s0, s1, s2};
+        const Acc<T> pv[3] = {s0, s1, s2};
         double tot[3];
         if (grid_sum_last<3>(pv, part, &st->cntC, tot) && threadIdx.x == 0)
             cg_step_decide(st, tot[0], tot[1], tot[2], a.h_inner);
     } else if (a.mode == RI_RESID) {
-        double pv[2] = {(double)s0, (double)s1}, tot[2];
+        double pv[2] = {s0.value(), s1.value()}, tot[2];
         if (grid_sum_last<2>(pv, part, &st->cntC, tot) && threadIdx.x == 0) {
             refine_decide(st, tot[0], tot[1], a.h_outer, a.h_inner);
             st->warm = 0;  // every block has read it: later cycles recompute the residual
         }
     } else if (a.mode == RI_PCG_Z) {
-        T pv[1] = {s0};
+        const Acc<T> pv[1] = {s0};
         double tot[1];
         if (grid_sum_last<1>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(st, tot[0]);
     }
@@ -710,15 +757,15 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a
     static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
-    T s0 = 0, s1 = 0, s2 = 0;  // short per-thread runs, summed in FP64 below
+    Acc<T> s0, s1, s2;  // short per-thread runs (FP64, or Dot2 pairs in FP32)
     // warm residual: r64 and its sums (rr64, bb) are already in place, and
     // block 0 alone hands them to the decision
     const bool warm = a.mode == RI_RESID && a.st->warm;
     if (!warm) {
         rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-        s0 = (T)a.st->rr64;
-        s1 = (T)a.st->bb;
+        s0.set((T)a.st->rr64);
+        s1.set((T)a.st->bb);
     }
     pdl_leave();
     rinv_sums(a, a.part, a.st, s0, s1, s2);
@@ -732,14 +779,14 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv_b(const RowInvArgs<T>
     CgState* const st = a.st + blockIdx.y;
     pdl_enter();
     if (bb.gate && gate_closed(st, bb.gate)) return;
-    T s0 = 0, s1 = 0, s2 = 0;
+    Acc<T> s0, s1, s2;
     const bool warm = a.mode == RI_RESID && st->warm;
     if (!warm) {
         rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2,
                                    (size_t)blockIdx.y * bb.bs.n, (size_t)blockIdx.y * bb.bs.z);
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-        s0 = (T)st->rr64;
-        s1 = (T)st->bb;
+        s0.set((T)st->rr64);
+        s1.set((T)st->bb);
     }
     pdl_leave();
     rinv_sums(a, a.part + blockIdx.y * bb.bs.part, st, s0, s1, s2);

@@ -21,9 +21,10 @@ struct PersistCtl {
 };
 
 // Grid-wide barrier of a cooperative launch (all blocks resident).  The wait
-// is bounded: after 2^24 polls (about two seconds) it sets ctl->err and
-// returns.  Returns false in every thread once an error is flagged.
-__device__ __forceinline__ bool grid_barrier(PersistCtl* ctl) {
+// is bounded: after `limit` polls (2^24 by default, about two seconds) it
+// sets ctl->err and returns.  Returns false in every thread once an error is
+// flagged.
+__device__ __forceinline__ bool grid_barrier(PersistCtl* ctl, unsigned limit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -38,7 +39,7 @@ __device__ __forceinline__ bool grid_barrier(PersistCtl* ctl) {
         } else {
             unsigned polls = 0;
             while (*vgen == gen) {
-                if (++polls > (1u << 24)) {
+                if (++polls > limit) {
                     atomicExch(&ctl->err, 1);
                     break;
                 }
@@ -73,16 +74,17 @@ __device__ __forceinline__ void sum_partials(const double* part, double (&tot)[N
 }
 
 // Publish this block's NV partial sums in slot blockIdx.x of part: FP32
-// partials as two-float pairs (two_sum / ff_add), FP64 ones as doubles.
-// scratch: the block's shared [32][NV] doubles (reused as float2 pairs).
+// partials (each thread's Dot2 pair) as two-float pairs (two_sum / ff_add),
+// FP64 ones as doubles.  scratch: the block's shared [32][NV] doubles
+// (reused as float2 pairs).
 template <int NV, typename T>
-__device__ __forceinline__ void publish_partials(const T (&v)[NV], double* part, double (*scratch)[NV]) {
+__device__ __forceinline__ void publish_partials(const Acc<T> (&v)[NV], double* part, double (*scratch)[NV]) {
     if constexpr (sizeof(T) == 4) {
         float hi[NV], lo[NV];
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            hi[k] = v[k];
-            lo[k] = 0.f;
+            hi[k] = v[k].hi;
+            lo[k] = v[k].lo;
         }
         block_sum_ff<NV>(hi, lo, reinterpret_cast<float2(*)[NV]>(scratch));
         if (threadIdx.x == 0)
@@ -92,7 +94,7 @@ __device__ __forceinline__ void publish_partials(const T (&v)[NV], double* part,
     } else {
         double d[NV];
 #pragma unroll
-        for (int k = 0; k < NV; ++k) d[k] = v[k];
+        for (int k = 0; k < NV; ++k) d[k] = v[k].value();
         block_sum<NV>(d, scratch);
         if (threadIdx.x == 0)
 #pragma unroll
@@ -150,6 +152,9 @@ __global__ void __launch_bounds__(RB*(M / EA)) k_cg_persist(PersistArgs<T> P) {
     __shared__ double bcast[3];
     CgState* st = P.A.st;
     if (st->finished) return;  // the outer loop has stopped: no inner run
+    const unsigned limit = st->dbg_limit ? st->dbg_limit : (1u << 24);
+    // test hook: the last block never arrives, the others' waits run out
+    const bool leave = st->dbg_skip == 1 && gridDim.x > 1 && blockIdx.x == gridDim.x - 1;
 
     // the inner-run state, kept identical in every block
     int first = st->first;
@@ -166,16 +171,17 @@ __global__ void __launch_bounds__(RB*(M / EA)) k_cg_persist(PersistArgs<T> P) {
     while (true) {
         // phase A: CG update + pair-packed row FFTs, partial r.r and r.p
         const AScal<T> sc{first, (T)alpha, (T)beta, (T)(first ? bcarry : 0.0), inv_sigma, 0.0};
-        T acc = 0, acc_rp = 0;
+        Acc<T> acc, acc_rp;
         for (int u = blockIdx.x; u < P.nA; u += gridDim.x) {
             rfwd_unit<T, M, EA, RB>(P.A, sc, u, sm, acc, acc_rp);
             __syncthreads();
         }
         {
-            const T pv[2] = {acc, acc_rp};
+            const Acc<T> pv[2] = {acc, acc_rp};
             publish_partials<2, T>(pv, P.partA, reinterpret_cast<double(*)[2]>(scratch));
         }
-        if (!(ok = grid_barrier(P.ctl))) break;
+        if (leave) return;
+        if (!(ok = grid_barrier(P.ctl, limit))) break;
         {
             double tot[2];
             total_partials<2, T>(P.partA, tot, reinterpret_cast<double(*)[2]>(scratch), bcast);
@@ -187,18 +193,18 @@ __global__ void __launch_bounds__(RB*(M / EA)) k_cg_persist(PersistArgs<T> P) {
             colc_unit<T, M, EB, CB>(P.B, u, sm);
             __syncthreads();
         }
-        if (!(ok = grid_barrier(P.ctl))) break;
+        if (!(ok = grid_barrier(P.ctl, limit))) break;
         // phase C: inverse row FFTs, q = P (C p + s p), partial p.q, r.q, q.q
-        T s0 = 0, s1 = 0, s2 = 0;
+        Acc<T> s0, s1, s2;
         for (int u = blockIdx.x; u < P.nA; u += gridDim.x) {
             rinv_unit<T, M, EA, RB>(P.C, u, sm, s0, s1, s2);
             __syncthreads();
         }
         {
-            const T pv[3] = {s0, s1, s2};
+            const Acc<T> pv[3] = {s0, s1, s2};
             publish_partials<3, T>(pv, P.partC, scratch);
         }
-        if (!(ok = grid_barrier(P.ctl))) break;
+        if (!(ok = grid_barrier(P.ctl, limit))) break;
         double tot[3];
         total_partials<3, T>(P.partC, tot, scratch, bcast);
         // the step decision of cg_step_decide, taken identically in every block

@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "../../include/fftconv.h"
+#include "fc_alloc.h"
 
 // cg_solve_batch with a tolerance per problem (fc_lib.cu).
 int fc_batch_solve_rtols(fftconv_plan* p, int nb, const double* s, const double* b, double* x, const cg_opts* o,
@@ -209,15 +210,15 @@ int ensure_staging(Slot* sl, long n) {
     if (n <= sl->cap) return FC_OK;
     long cap = sl->cap > 0 ? sl->cap : n;
     while (cap < n) cap *= 2;
-    cudaFreeAsync(sl->ds, sl->stream);
-    cudaFreeAsync(sl->db, sl->stream);
-    cudaFreeAsync(sl->dx, sl->stream);
+    fc::dev_free_async(sl->ds, sl->stream);
+    fc::dev_free_async(sl->db, sl->stream);
+    fc::dev_free_async(sl->dx, sl->stream);
     sl->ds = sl->db = sl->dx = nullptr;
     sl->cap = 0;
     const size_t bytes = sizeof(double) * (size_t)cap;
-    if (cudaMallocAsync((void**)&sl->ds, bytes, sl->stream) != cudaSuccess ||
-        cudaMallocAsync((void**)&sl->db, bytes, sl->stream) != cudaSuccess ||
-        cudaMallocAsync((void**)&sl->dx, bytes, sl->stream) != cudaSuccess)
+    if (fc::dev_malloc_async((void**)&sl->ds, bytes, sl->stream) != cudaSuccess ||
+        fc::dev_malloc_async((void**)&sl->db, bytes, sl->stream) != cudaSuccess ||
+        fc::dev_malloc_async((void**)&sl->dx, bytes, sl->stream) != cudaSuccess)
         return FC_ENOMEM;
     sl->cap = cap;
     return FC_OK;
@@ -436,9 +437,9 @@ extern "C" int cg_server_destroy(cg_server* sv) {
     for (Slot* sl : sv->slots) {
         if (sl->stream) cudaStreamSynchronize(sl->stream);
         if (sl->stream) {
-            cudaFreeAsync(sl->ds, sl->stream);
-            cudaFreeAsync(sl->db, sl->stream);
-            cudaFreeAsync(sl->dx, sl->stream);
+            fc::dev_free_async(sl->ds, sl->stream);
+            fc::dev_free_async(sl->db, sl->stream);
+            fc::dev_free_async(sl->dx, sl->stream);
             cudaStreamSynchronize(sl->stream);
             cudaStreamDestroy(sl->stream);
         }

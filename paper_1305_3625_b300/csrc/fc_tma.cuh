@@ -54,10 +54,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 }
 
 // Wait for the phase with the given parity to complete; gives up after
-// 2^20 polls (each try_wait may itself suspend the thread briefly: well over
-// the microseconds a staged copy takes, well under a second) and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-    for (unsigned i = 0; i < (1u << 20); ++i)
+// `limit` polls (2^20 by default; each try_wait may itself suspend the
+// thread briefly: well over the microseconds a staged copy takes, well under
+// a second) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned limit) {
+    for (unsigned i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -113,6 +114,9 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
     const int j = threadIdx.x;
     const int L = a.L;
     pdl_enter();
+    const unsigned limit = a.st->dbg_limit ? a.st->dbg_limit : (1u << 20);
+    // test hook: no copy for the block's first row pair, its waits run out
+    const bool skip_first = a.st->dbg_skip == 2;
     if (j == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -127,11 +131,11 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
             tma_load_2d(reinterpret_cast<unsigned char*>(buf[b]) + (size_t)k * BK * 16, &P.map, 4 * unit, k * BK,
                         &bar[b]);
     };
-    float s0 = 0, s1 = 0, s2 = 0;
+    Acc<float> s0, s1, s2;
     unsigned ph0 = 0, ph1 = 0;
     bool pending[2] = {false, false};
     int u = blockIdx.x;
-    if (j == 0 && u < P.units) issue(u, 0);
+    if (j == 0 && u < P.units && !skip_first) issue(u, 0);
     pending[0] = u < P.units;
     bool ok = true;
     for (int it = 0; u < P.units; ++it, u += gridDim.x) {
@@ -140,13 +144,13 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
         if (j == 0 && nu < P.units) issue(nu, cur ^ 1);
         pending[cur ^ 1] = nu < P.units;
         unsigned& ph = cur ? ph1 : ph0;
-        if (j == 0) s_ok = mbar_wait_bounded(&bar[cur], ph);
+        if (j == 0) s_ok = mbar_wait_bounded(&bar[cur], ph, limit);
         __syncthreads();
         if (!s_ok) {
             ok = false;
             break;
         }
-        mbar_wait_bounded(&bar[cur], ph);  // completes at once; acquires the staged data in this thread
+        mbar_wait_bounded(&bar[cur], ph, limit);  // completes at once; acquires the staged data in this thread
         ph ^= 1u;
         pending[cur] = false;
         const C* stg = buf[cur];
@@ -186,16 +190,16 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
         // (bounded) before the block's shared memory is released
         atomicExch(&a.st->tma_err, 1);
         for (int b = 0; b < 2; ++b)
-            if (pending[b]) mbar_wait_bounded(&bar[b], b ? ph1 : ph0);
+            if (pending[b]) mbar_wait_bounded(&bar[b], b ? ph1 : ph0, limit);
     }
     pdl_leave();  // every block still joins the grid reduction below
     if (a.mode == RI_CG) {
-        float pv[3] = {s0, s1, s2};
+        const Acc<float> pv[3] = {s0, s1, s2};
         double tot[3];
         if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
             cg_step_decide(a.st, tot[0], tot[1], tot[2], a.h_inner);
     } else if (a.mode == RI_PCG_Z) {
-        float pv[1] = {s0};
+        const Acc<float> pv[1] = {s0};
         double tot[1];
         if (grid_sum_last<1>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(a.st, tot[0]);
     }

@@ -44,3 +44,51 @@ def conv_rel_bound(u, M):
 
 def conv_err(y, ref):
     return float(np.linalg.norm(y - ref)) / float(np.linalg.norm(ref))
+
+
+def conv_max_bound(u, M):
+    """Max-norm error allowed for y = C x, relative to max |y|:
+    max_i |y_hat_i - y_i| <= u levels max_i |y_i|.
+
+    The roundings of the FFT round trip spread over all outputs like
+    independent noise of rms about u sqrt(levels) rms(y) (the normwise bound
+    above adds them up); the largest of N such entries is about
+    sqrt(2 ln N) of them, rms(y) <= max |y|, and
+    sqrt(max(2 ln N, 1)) sqrt(levels) <= levels on every grid L <= 4096
+    with M the padded side (e.g. 5.5 x 7.1 = 39 <= 50 at L = 2048).  Against max |y|
+    instead of ||y||_2 the bound is about sqrt(N) times tighter per entry,
+    so it fails an error confined to a few outputs (a row pair, the packed
+    column 0, a tile edge) that the 2-norm bound would let through."""
+    return u * conv_levels(M)
+
+
+def conv_max_err(y, ref):
+    return float(np.max(np.abs(y - ref))) / float(np.max(np.abs(ref)))
+
+
+def direct_sum_allowance(L, x, u=U64):
+    """Rounding error allowed to the oracle's direct sum of Eq. 1b itself at
+    every output (naive recursive summation of N = L^2 products in FP64):
+    each addition errs by at most u times the running sum, which is at most
+    (C|x|)_i = sum_j G_ij |x_j| (G >= 0); N such errors of random sign add up
+    to about sqrt(N) of them, and 4 sqrt(N) u (C|x|)_i covers the largest of
+    the outputs.  C|x| comes from the same direct sum."""
+    import oracle
+    return 4.0 * math.sqrt(L * L) * u * oracle.conv_direct(L, np.abs(np.asarray(x, dtype=np.float64)))
+
+
+def check_conv(y, ref, u, M, what, ref_abs=0.0):
+    """Both bounds: the 2-norm one of conv_rel_bound and the max-norm one of
+    conv_max_bound; ref_abs (a scalar or one value per output) is the
+    reference's own rounding error, allowed on top of the max-norm bound."""
+    e = conv_err(y, ref)
+    bound = conv_rel_bound(u, M)
+    em = conv_max_err(y, ref)
+    mbound = conv_max_bound(u, M)
+    ymax = float(np.max(np.abs(ref)))
+    excess = float(np.max(np.abs(y - ref) - ref_abs)) / ymax
+    print(f"{what}: rel err {e:.3e} (bound {bound:.3e}, {e / bound:.3f}), "
+          f"max err {em:.3e} (less the reference's allowance {excess:.3e}; bound {mbound:.3e}, "
+          f"{excess / mbound:.3f})")
+    assert e <= bound, (what, e, bound)
+    assert excess <= mbound, (what, excess, mbound)

@@ -178,3 +178,72 @@ def test_invalid_batches():
     p64 = fc.fftconv_plan_create(L, fc.FC_F64)
     with pytest.raises(fc.FcError):  # mixed needs an FP32 side
         fc.cg_solve_batch(p64, s, s, x, mode=fc.FC_MODE_MIXED)
+
+
+_oracle_x = {}
+
+
+def oracle_solution(L, seed0, k, s, b, mask):
+    """The oracle's FP64 CG (Listing 2) to a relative residual of 1e-13,
+    cached per problem (the batched modes below share the problems)."""
+    key = (L, seed0, k)
+    if key not in _oracle_x:
+        x, rc, _, rel = oracle.cg(L, s, b, mask=mask, rtol=1e-13)
+        assert rc == 0 and rel <= 1e-13
+        _oracle_x[key] = x
+    return _oracle_x[key]
+
+
+@pytest.mark.parametrize("mode,precond", [(fc.FC_MODE_F64, True), (fc.FC_MODE_MIXED, True),
+                                          (fc.FC_MODE_MIXED, False)])
+@pytest.mark.parametrize("L", [256, 512])
+def test_batch_config3_sizes_against_oracle(L, mode, precond):
+    """The batched workload's sizes (M = 512, 1024): three problems per batch,
+    one unmasked and two with 10 and 30 percent of the sites removed, each
+    bitwise the problem solved alone and within the solution-error targets
+    of the oracle's solve (1e-10 FP64, 1e-6 mixed; the solver's residual
+    tolerance is set below target / kappa, kappa ~ 0.8 L)."""
+    nb, seed0 = 3, 5000 + L
+    s, b, mask = problems(L, nb, seed0, masked=True, broken=[0.0, 0.1, 0.3])
+    rtol = 1e-13 if mode == fc.FC_MODE_F64 else 2e-9
+    x = dev(np.zeros((nb, L * L)))
+    rc, rs = fc.cg_solve_batch(plan(L), dev(s), dev(b), x, mask=dev(mask, torch.uint8), rtol=rtol, mode=mode,
+                               precond=precond, x0_zero=True)
+    assert rc == fc.FC_OK
+    xb = host(x)
+    target = 1e-10 if mode == fc.FC_MODE_F64 else 1e-6
+    for k in range(nb):
+        assert rs[k]["status"] == fc.FC_OK and rs[k]["true_rel_resid"] <= rtol
+        xa, ra = solve_alone(L, s[k], b[k], mask[k], mode, precond, rtol)
+        assert np.array_equal(xb[k], xa) and rs[k]["iters"] == ra["iters"]
+        want = oracle_solution(L, seed0, k, s[k], b[k], mask[k])
+        err = rel2(xb[k], want)
+        print(f"L={L} mode={mode} precond={precond} problem {k}: rel err {err:.3e}, {rs[k]['iters']} iterations")
+        assert err <= target
+        assert np.all(xb[k][mask[k] == 0] == 0.0)
+
+
+@pytest.mark.parametrize("L", [1024, 2048])
+def test_batch_server_sizes_oracle_residual(L):
+    """The largest sizes the solve server batches (M = 2048, 4096): each
+    problem's residual P (b - (C + S) x) recomputed by the oracle's FP64
+    operator is within the tolerance, which bounds the solution error by
+    |r| / lambda_min with lambda_min >= lambda_min(C) + min(s) > 1; and each
+    problem is bitwise the problem solved alone."""
+    nb, seed0 = 2, 7000 + L
+    s, b, mask = problems(L, nb, seed0, masked=True, broken=[0.0, 0.2])
+    rtol = 1e-8
+    x = dev(np.zeros((nb, L * L)))
+    rc, rs = fc.cg_solve_batch(plan(L), dev(s), dev(b), x, mask=dev(mask, torch.uint8), rtol=rtol,
+                               mode=fc.FC_MODE_MIXED, precond=True, x0_zero=True)
+    assert rc == fc.FC_OK
+    xb = host(x)
+    for k in range(nb):
+        assert rs[k]["status"] == fc.FC_OK
+        pb = np.where(mask[k] != 0, b[k], 0.0)
+        r = pb - oracle.apply_A(L, s[k], xb[k], mask[k])
+        rel = float(np.linalg.norm(r) / np.linalg.norm(pb))
+        print(f"L={L} problem {k}: oracle residual {rel:.3e} (solver {rs[k]['true_rel_resid']:.3e})")
+        assert rel <= 1.01 * rtol
+        xa, ra = solve_alone(L, s[k], b[k], mask[k], fc.FC_MODE_MIXED, True, rtol)
+        assert np.array_equal(xb[k], xa) and rs[k]["iters"] == ra["iters"]

@@ -294,3 +294,35 @@ def test_every_pass_shape_solves(L):
         x = dev(np.zeros(L * L))
         r = fc.cg_solve(pl, dev(p["s"]), dev(p["b"]), x, rtol=1e-8, mode=fc.FC_MODE_MIXED, precond=True)
         assert r["status"] == fc.FC_OK and r["true_rel_resid"] <= 1e-8, (L, shapes, r)
+
+
+@pytest.mark.parametrize("L", [100, 1024])
+def test_product_dot_products_fp64_grade(L):
+    """The FP32 passes' dot products p.q, r.q, q.q against exact sums of the
+    same FP32 vectors' products (math.fsum of the FP64 products, which are
+    exact for FP32 factors).  Each thread's Dot2 pair and the two-float block
+    and grid combination keep the error at the order of (16 u)^2 and
+    2^-44 per combining level of sum |a_i b_i|: 1e-11 of it is allowed,
+    against about 1e-6 for plain FP32 partial sums of 16 products."""
+    import math
+    plan = fc.fftconv_plan_create(L, fc.FC_F32 | fc.FC_F64)
+    rng = np.random.default_rng(L)
+    pv = dev(rng.standard_normal(L * L), torch.float32)
+    rv = dev(rng.standard_normal(L * L), torch.float32)
+    sv = dev(rng.uniform(0.5, 1.5, L * L), torch.float32)
+    q = torch.empty_like(pv)
+    got = fc.fftconv_cg_product(plan, fc.FC_F32, pv, rv, sv, q)
+    ph, rh, qh = (host(t).astype(np.float64) for t in (pv, rv, q))
+    for name, a, b, g in (("p.q", ph, qh, got[0]), ("r.q", rh, qh, got[1]), ("q.q", qh, qh, got[2])):
+        terms = a * b
+        exact = math.fsum(terms)
+        scale = math.fsum(np.abs(terms))
+        print(f"L={L} {name}: {g:.17g} exact {exact:.17g}, error {abs(g - exact) / scale:.2e} of sum |terms|")
+        assert abs(g - exact) <= 1e-11 * scale, (name, g, exact)
+    # FP64 passes: FP64 sums of the FP64 vectors' products
+    p64, r64, s64 = (dev(host(t).astype(np.float64)) for t in (pv, rv, sv))
+    q64 = torch.empty_like(p64)
+    got64 = fc.fftconv_cg_product(plan, fc.FC_F64, p64, r64, s64, q64)
+    qh64 = host(q64)
+    for a, b, g in ((ph, qh64, got64[0]), (rh, qh64, got64[1]), (qh64, qh64, got64[2])):
+        assert abs(g - math.fsum(a * b)) <= 1e-12 * math.fsum(np.abs(a * b))

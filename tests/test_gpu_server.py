@@ -8,6 +8,7 @@ import pytest
 import torch
 
 import fc_inputs
+import oracle
 import paper_1305_3625_b300 as fc
 from gpu_util import dev, host
 
@@ -131,14 +132,18 @@ def test_budget_admission_and_eviction():
 
 def test_many_small_requests_batch():
     """24 small requests through one slot run as batched solves and finish
-    sooner than the same solves one at a time on one plan."""
+    sooner than the same solves one at a time on one plan (medians of three
+    repeats of each, so that one slow sample on a shared GPU decides
+    nothing)."""
     L = 64
     probs = [fc_inputs.problem(L, seed=500 + k, b_kind="normal") for k in range(24)]
     sv = fc.cg_server_create(4 << 30, max_slots=1)
     wait_all(sv, [fc.cg_batch_submit(sv, L, p["s"], p["b"], rtol=1e-8) for p in probs])  # plan, workspace
-    t0 = time.perf_counter()
-    wait_all(sv, [fc.cg_batch_submit(sv, L, p["s"], p["b"], rtol=1e-8) for p in probs])
-    t_server = time.perf_counter() - t0
+    t_server = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        wait_all(sv, [fc.cg_batch_submit(sv, L, p["s"], p["b"], rtol=1e-8) for p in probs])
+        t_server.append(time.perf_counter() - t0)
     assert fc.cg_server_batches(sv)["max_batch"] > 1
     sv.close()
     plan = fc.fftconv_plan_create(L)
@@ -146,8 +151,42 @@ def test_many_small_requests_batch():
     x = dev(np.zeros(L * L))
     fc.cg_solve(plan, *inputs[0], x, rtol=1e-8, mode=1, x0_zero=True)  # graph built
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for s, b in inputs:
-        fc.cg_solve(plan, s, b, x, rtol=1e-8, mode=1, x0_zero=True)
-    t_alone = time.perf_counter() - t0
-    assert t_server < t_alone
+    t_alone = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        for s, b in inputs:
+            fc.cg_solve(plan, s, b, x, rtol=1e-8, mode=1, x0_zero=True)
+        t_alone.append(time.perf_counter() - t0)
+    assert sorted(t_server)[1] < sorted(t_alone)[1]
+
+
+def test_config4_sizes_against_oracle():
+    """Requests of the serving mix's sizes, L = 32, 1024 and 2048 (their
+    batched plans at M = 64, 2048, 4096), with tolerances 1e-6 and 1e-8,
+    through a server with several slots: each result's residual
+    b - (C + S) x recomputed by the oracle's FP64 operator is within the
+    request's tolerance, and the large ones are bitwise the request solved
+    alone."""
+    spec = [(32, 1e-6), (1024, 1e-8), (2048, 1e-6), (32, 1e-8), (1024, 1e-6), (2048, 1e-8), (32, 1e-8),
+            (1024, 1e-8)]
+    reqs = []
+    for k, (L, tol) in enumerate(spec):
+        p = fc_inputs.problem(L, seed=4400 + k, b_kind="normal")
+        reqs.append((L, tol, p["s"], p["b"]))
+    sv = fc.cg_server_create(24 << 30, max_slots=4)
+    outs = [np.zeros(L * L) for (L, *_rest) in reqs]
+    tickets = [fc.cg_batch_submit(sv, L, s, b, x_out=o, rtol=tol, mode=fc.FC_MODE_MIXED, precond=True)
+               for (L, tol, s, b), o in zip(reqs, outs)]
+    res = wait_all(sv, tickets, timeout=300.0)
+    sv.close()
+    for (L, tol, s, b), o, t in zip(reqs, outs, tickets):
+        r = res[t]
+        assert r["status"] == fc.FC_OK and r["true_rel_resid"] <= tol
+        rr = b - oracle.apply_A(L, s, o)
+        rel = float(np.linalg.norm(rr) / np.linalg.norm(b))
+        print(f"L={L} tol={tol:g}: oracle residual {rel:.3e}, {r['iters']} iterations")
+        assert rel <= 1.01 * tol
+    for k in (1, 2):
+        L, tol, s, b = reqs[k]
+        xa, ra = alone(L, s, b, tol, fc.FC_MODE_MIXED, precond=True)
+        assert np.array_equal(outs[k], xa) and res[tickets[k]]["iters"] == ra["iters"]
