@@ -16,8 +16,8 @@ struct cpx;
 // exactly one pass and read by later passes only, so no kernel reads a field
 // that another block of the same kernel may be writing.
 struct CgState {
-    double rr;           // r.r of the current inner residual (pass A, direct sum)
-    double rp;           // r.p of the current residual and direction (pass A)
+    double rr;           // r.r of the current inner residual (pass C's direct sum)
+    double rp;           // r.p of the current residual and direction (pass C)
     double alpha, beta;  // CG step length and direction update of the last product
     double tol2;         // inner stop: recursive r.r <= tol2
     double sigma;        // norm of the true residual the inner run started from
@@ -145,19 +145,25 @@ struct RowInvArgs {
     const cpx<T>* tw;
 };
 
-// Decide the CG step after the product q = A p of one iteration of Listing 2.
-// alpha = r.p / p.q, the exact minimiser along p (equal to r.r / p.q in exact
-// CG, where r is orthogonal to the previous direction, and still right after
-// a true-residual replacement); the new residual norm
-// |r - alpha q|^2 = rr - 2 alpha rq + alpha^2 qq gives beta = |r'|^2 / |r|^2
-// without a second pass over the vectors.
-__device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq, double qq,
-                                               unsigned long long h_inner) {
-    const double rr = st->rr;
+// Decide the CG step after the product q = A p of one iteration of Listing 2,
+// from pass C's sums: p.q, r.q, q.q and r.r, r.p of the residual and
+// direction pass A formed.  alpha = r.p / p.q, the exact minimiser along p
+// (equal to r.r / p.q in exact CG, where r is orthogonal to the previous
+// direction, and still right after a true-residual replacement); the new
+// residual norm |r - alpha q|^2 = rr - 2 alpha rq + alpha^2 qq gives
+// beta = |r'|^2 / |r|^2 without a second pass over the vectors.  The sums are
+// Dot2-accurate (errors of order 1e-15 of sum |a_i b_i|), so the cancellation
+// in |r'|^2 costs at most about 4e-15 rr / |r'|^2 of relative accuracy, far
+// below what a stopping test certified by an FP64 true residual needs.
+__device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq, double qq, double rr_now,
+                                               double rp_now, unsigned long long h_inner) {
+    st->rr = rr_now;
+    st->rp = rp_now;
+    const double rr = rr_now;
     st->pq = pq;
     st->rq = rq;
     st->qq = qq;
-    double alpha = st->rp / pq;
+    double alpha = rp_now / pq;
     double rrn = rr - 2.0 * alpha * rq + alpha * alpha * qq;
     if (rrn < 0.0) rrn = 0.0;
     int d = 0;

@@ -1399,7 +1399,7 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
         FC_TRY(dalloc(p, (void**)&p->am_ctl, sizeof(ArgmaxCtl)));
         FC_TRYC(cudaMemsetAsync(p->am_ctl, 0, sizeof(ArgmaxCtl), cs));
         FC_TRY(dalloc(p, (void**)&p->partA, sizeof(double) * 2 * kMaxPersistGrid));
-        FC_TRY(dalloc(p, (void**)&p->partC, sizeof(double) * 3 * kMaxPersistGrid));
+        FC_TRY(dalloc(p, (void**)&p->partC, sizeof(double) * 5 * kMaxPersistGrid));
         FC_TRY(dalloc(p, (void**)&p->pctl, sizeof(PersistCtl)));
         FC_TRYC(cudaMemsetAsync(p->pctl, 0, sizeof(PersistCtl), cs));
     }

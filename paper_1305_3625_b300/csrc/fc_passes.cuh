@@ -304,101 +304,138 @@ struct AScal {
     double inv_sigma, sig;
 };
 
-// The value pass A transforms at flat index i (row-major L x L): the plain
-// input, the CG update of Listing 2 (x += a p, r -= a q, p = r + b p; on the
-// first pass of a run p = r, or p = r + b' p_old when the direction is kept
-// across a true-residual replacement), or the FP64 iterate with the
-// folded-in correction of the last inner run (masked).  acc collects r.r.
-// The arrays are restrict-qualified parameters here and in pass_a_inputs:
-// they never overlap, so the compiler may issue the loads of all of a
-// thread's elements before the first store, instead of one element's memory
-// round trip after another.
-template <typename T>
-__device__ __forceinline__ T pass_a_value(int mode, const T* __restrict__ xin, T* __restrict__ cx,
-                                          T* __restrict__ cr, T* __restrict__ cp, const T* __restrict__ cq,
-                                          const T* __restrict__ cz, const double* __restrict__ r64,
-                                          double* __restrict__ x64, const float* __restrict__ d32,
-                                          const uint8_t* __restrict__ mask, size_t i, const AScal<T>& sc,
-                                          Acc<T>& acc, Acc<T>& acc_rp) {
-    if (mode == RF_PLAIN) return xin[i];
-    if (mode == RF_XUPD) {
-        double xv = x64[i];
-        if (d32 && sc.sig != 0.0) xv += sc.sig * (double)d32[i];
-        if (mask && !mask[i]) xv = 0.0;
-        x64[i] = xv;
-        return (T)xv;
-    }
-    if (mode == RF_PCG_R) {  // PCG: x += alpha p, r -= alpha q; transform r
-        T r;
-        if (sc.first) {
-            if (r64) {
-                r = (T)(r64[i] * sc.inv_sigma);
-                cr[i] = r;
-                cx[i] = 0;
-            } else {
-                r = cr[i];
-            }
-        } else {
-            const T p = cp[i];
-            cx[i] = cx[i] + sc.alpha * p;
-            r = cr[i] - sc.alpha * cq[i];
-            cr[i] = r;
-        }
-        acc.prod(r, r);
-        return r;
-    }
-    if (mode == RF_PCG_P) {  // PCG: p = z + beta p; transform p
-        const T z = cz[i];
-        const T p = sc.first ? z : z + sc.beta * cp[i];
-        cp[i] = p;
-        acc_rp.prod(cr[i], p);
-        return p;
-    }
-    T r, p;
-    if (sc.first) {
-        if (r64) {
-            r = (T)(r64[i] * sc.inv_sigma);
-            cr[i] = r;
-            cx[i] = 0;
-        } else {
-            r = cr[i];
-        }
-        p = sc.bcarry != (T)0 ? r + sc.bcarry * cp[i] : r;
-    } else {
-        p = cp[i];
-        cx[i] = cx[i] + sc.alpha * p;
-        r = cr[i] - sc.alpha * cq[i];
-        cr[i] = r;
-        p = r + sc.beta * p;
-    }
-    cp[i] = p;
-    acc.prod(r, r);
-    acc_rp.prod(r, p);
-    return p;
-}
-
-// Pass A's inputs of one thread: elements j + e*G (e < E/2, the rest is the
-// zero padding) of rows r0 and r0 + 1, packed as v[e] = row r0 + i row r0+1.
-// vo: the problem's offset in the vectors (batched launches).
+// Pass A's inputs of one thread: elements n = j + e*G (e < E/2; the rest is
+// the zero padding) of rows r0 and r0 + 1, packed as v[e] = row r0 + i row
+// r0+1.  The value transformed at each element is the plain input, the CG
+// update of Listing 2 (x += a p, r -= a q, p = r + b p; on the first pass of
+// a run p = r, or p = r + b' p_old when the direction is kept across a
+// true-residual replacement), the PCG halves (x, r update and transform r;
+// p = z + b p and transform p), or the FP64 iterate with the folded-in
+// correction of the last inner run (masked).  The dot products of the new r
+// and p are taken by pass C, which reads both again.  Each row's operands
+// are all loaded before the first is used, so a thread waits for one memory
+// round trip per row instead of one per element.  vo: the problem's offset
+// in the vectors (batched launches).
 template <typename T, int M, int E>
 __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xin, T* __restrict__ cx,
                                               T* __restrict__ cr, T* __restrict__ cp, const T* __restrict__ cq,
                                               const T* __restrict__ cz, const double* __restrict__ r64,
                                               double* __restrict__ x64, const float* __restrict__ d32,
                                               const uint8_t* __restrict__ mask, const AScal<T>& sc, int j, int r0,
-                                              int L, size_t vo, cpx<T> (&v)[E], Acc<T>& acc, Acc<T>& acc_rp) {
-    constexpr int G = M / E;
+                                              int L, size_t vo, cpx<T> (&v)[E]) {
+    constexpr int G = M / E, H = E / 2;  // n >= M/2 >= L for e >= E/2
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        v[e] = cpx<T>{0, 0};
-        const int n = j + e * G;
-        if (e < E / 2 && n < L) {  // n >= M/2 >= L for e >= E/2: the zero padding
-            if (r0 < L)
-                v[e].x = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask, vo + (size_t)r0 * L + n, sc,
-                                      acc, acc_rp);
-            if (r0 + 1 < L)
-                v[e].y = pass_a_value(mode, xin, cx, cr, cp, cq, cz, r64, x64, d32, mask,
-                                      vo + (size_t)(r0 + 1) * L + n, sc, acc, acc_rp);
+    for (int e = 0; e < E; ++e) v[e] = cpx<T>{0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (r0 + h >= L) continue;
+        const size_t b = vo + (size_t)(r0 + h) * L + j;
+        bool ok[H];
+#pragma unroll
+        for (int e = 0; e < H; ++e) ok[e] = j + e * G < L;
+        T val[H];
+#pragma unroll
+        for (int e = 0; e < H; ++e) val[e] = 0;
+        if (mode == RF_PLAIN) {
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) val[e] = xin[b + e * G];
+        } else if (mode == RF_XUPD) {
+            double xv[H];
+            float dv[H];
+            uint8_t mv[H];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    xv[e] = x64[b + e * G];
+                    dv[e] = d32 ? d32[b + e * G] : 0.f;
+                    mv[e] = mask ? mask[b + e * G] : (uint8_t)1;
+                }
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    double t = xv[e];
+                    if (d32 && sc.sig != 0.0) t += sc.sig * (double)dv[e];
+                    if (!mv[e]) t = 0.0;
+                    x64[b + e * G] = t;
+                    val[e] = (T)t;
+                }
+        } else if (sc.first && mode != RF_PCG_P) {  // a run starts: r from the true residual (or as kept)
+            if (r64) {
+                double rv[H];
+#pragma unroll
+                for (int e = 0; e < H; ++e)
+                    if (ok[e]) rv[e] = r64[b + e * G];
+#pragma unroll
+                for (int e = 0; e < H; ++e)
+                    if (ok[e]) {
+                        val[e] = (T)(rv[e] * sc.inv_sigma);
+                        cr[b + e * G] = val[e];
+                        cx[b + e * G] = 0;
+                    }
+            } else {
+#pragma unroll
+                for (int e = 0; e < H; ++e)
+                    if (ok[e]) val[e] = cr[b + e * G];
+            }
+            if (mode == RF_CG) {  // p = r, or r + b' p_old when the direction is kept
+                if (sc.bcarry != (T)0) {
+                    T pv[H];
+#pragma unroll
+                    for (int e = 0; e < H; ++e)
+                        if (ok[e]) pv[e] = cp[b + e * G];
+#pragma unroll
+                    for (int e = 0; e < H; ++e)
+                        if (ok[e]) val[e] = val[e] + sc.bcarry * pv[e];
+                }
+#pragma unroll
+                for (int e = 0; e < H; ++e)
+                    if (ok[e]) cp[b + e * G] = val[e];
+            }
+        } else if (mode == RF_PCG_P) {  // p = z + beta p
+            T zv[H], pv[H];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    zv[e] = cz[b + e * G];
+                    pv[e] = sc.first ? (T)0 : cp[b + e * G];
+                }
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    val[e] = sc.first ? zv[e] : zv[e] + sc.beta * pv[e];
+                    cp[b + e * G] = val[e];
+                }
+        } else {  // RF_CG, RF_PCG_R: x += alpha p, r -= alpha q (and p = r + beta p)
+            T pv[H], xv[H], rv[H], qv[H];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    pv[e] = cp[b + e * G];
+                    xv[e] = cx[b + e * G];
+                    rv[e] = cr[b + e * G];
+                    qv[e] = cq[b + e * G];
+                }
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    const T r = rv[e] - sc.alpha * qv[e];
+                    cx[b + e * G] = xv[e] + sc.alpha * pv[e];
+                    cr[b + e * G] = r;
+                    if (mode == RF_CG) {
+                        val[e] = r + sc.beta * pv[e];
+                        cp[b + e * G] = val[e];
+                    } else {
+                        val[e] = r;
+                    }
+                }
+        }
+#pragma unroll
+        for (int e = 0; e < H; ++e) {
+            if (h == 0)
+                v[e].x = val[e];
+            else
+                v[e].y = val[e];
         }
     }
 }
@@ -421,12 +458,12 @@ __device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a, con
 }
 
 // One unit of pass A: RB row pairs starting at pair unit*RB, G = M/E threads
-// per pair.  Adds this thread's r.r and r.p to acc, acc_rp.  Leaves shared
-// memory in use: the caller synchronises before the block reuses it.  vo, zo:
-// the problem's offsets in the vectors and the intermediate.
+// per pair.  Leaves shared memory in use: the caller synchronises before the
+// block reuses it.  vo, zo: the problem's offsets in the vectors and the
+// intermediate.
 template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
 __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm,
-                                          Acc<T>& acc, Acc<T>& acc_rp, size_t vo = 0, size_t zo = 0) {
+                                          size_t vo = 0, size_t zo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;  // shared elements per pair
@@ -436,8 +473,7 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
     const int r0 = (unit * RB + pl) * 2;
 
     C v[E];
-    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, L, vo, v,
-                           acc, acc_rp);
+    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, L, vo, v);
     C* g0 = sm + pl * GS;
     fft_stages<T, M, E, false, DB, 0>(v, j, g0, g0 + SEG, a.tw);
     C* wp = g0 + NB * SEG + spad(j);
@@ -465,29 +501,6 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
     }
 }
 
-// Pass A's grid sums: partials in the pass's precision (FP32: two-float
-// combination, FP64: FP64), totals in FP64, written by the last block.
-template <typename T>
-__device__ __forceinline__ void rfwd_sums(int mode, double* part, CgState* st, const Acc<T>& acc,
-                                          const Acc<T>& acc_rp) {
-    if (mode == RF_CG) {
-        const Acc<T> pv[2] = {acc, acc_rp};
-        double tot[2];
-        if (grid_sum_last<2>(pv, part, &st->cntA, tot) && threadIdx.x == 0) {
-            st->rr = tot[0];
-            st->rp = tot[1];
-        }
-    } else if (mode == RF_PCG_R) {
-        const Acc<T> pv[1] = {acc};
-        double tot[1];
-        if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rr = tot[0];
-    } else if (mode == RF_PCG_P) {
-        const Acc<T> pv[1] = {acc_rp};
-        double tot[1];
-        if (grid_sum_last<1>(pv, part, &st->cntA, tot) && threadIdx.x == 0) st->rp = tot[0];
-    }
-}
-
 // MINB: blocks per SM the register allocation must allow; DB: double-buffered
 // exchanges (default: when they fit, see use_db).
 template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
@@ -497,10 +510,8 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a
     pdl_enter();
     if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
     const AScal<T> sc = ascal_from_state(a, a.st);
-    Acc<T> acc, acc_rp;
-    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp);
+    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
     pdl_leave();
-    rfwd_sums(a.mode, a.part, a.st, acc, acc_rp);
 }
 
 // The batched form: problem blockIdx.y at the strides of bb, gated.
@@ -513,11 +524,9 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_b(const RowFwdArgs<T>
     if (bb.gate && gate_closed(st, bb.gate)) return;
     if (a.mode == RF_XUPD && st->warm) return;
     const AScal<T> sc = ascal_from_state(a, st);
-    Acc<T> acc, acc_rp;
-    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), acc, acc_rp,
-                               (size_t)blockIdx.y * bb.bs.n, (size_t)blockIdx.y * bb.bs.z);
+    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * bb.bs.n,
+                               (size_t)blockIdx.y * bb.bs.z);
     pdl_leave();
-    rfwd_sums(a.mode, a.part + blockIdx.y * bb.bs.part, st, acc, acc_rp);
 }
 
 // ------------------------------------------------------------ pass B ----
@@ -612,43 +621,14 @@ __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc_b(const ColArgs<T> a,
 
 // ------------------------------------------------------------ pass C ----
 
-// The epilogue of pass C at flat index i for the transformed value yv: the
-// plain output, the CG product q = P (C p + s p) with its dot products, the
-// preconditioned residual z, or the FP64 true residual r = P (b - C x - s x).
-// Restrict-qualified arrays, as for pass A.
-template <typename T>
-__device__ __forceinline__ void pass_c_value(int mode, T* __restrict__ y, const T* __restrict__ s,
-                                             const T* __restrict__ cp, const T* __restrict__ cr, T* __restrict__ cq,
-                                             T* __restrict__ cz, const uint8_t* __restrict__ mask,
-                                             const double* __restrict__ x64, const double* __restrict__ b64,
-                                             const double* __restrict__ s64, double* __restrict__ r64, size_t i,
-                                             T yv, Acc<T>& s0, Acc<T>& s1, Acc<T>& s2) {
-    const bool act = mask == nullptr || mask[i] != 0;
-    if (mode == RI_PLAIN) {
-        y[i] = yv;
-    } else if (mode == RI_CG) {
-        const T p = cp[i];
-        const T q = act ? yv + s[i] * p : (T)0;
-        cq[i] = q;
-        s0.prod(p, q);
-        s1.prod(cr[i], q);
-        s2.prod(q, q);
-    } else if (mode == RI_PCG_Z) {
-        const T z = act ? yv : (T)0;
-        cz[i] = z;
-        s0.prod(cr[i], z);
-    } else {  // RI_RESID (T = double)
-        const double xv = x64[i];
-        const double bv = act ? b64[i] : 0.0;
-        const double r = act ? bv - ((double)yv + s64[i] * xv) : 0.0;
-        r64[i] = r;
-        s0.prod((T)r, (T)r);
-        s1.prod((T)bv, (T)bv);
-    }
-}
-
-// Pass C's outputs of one thread: elements j + e*G < L (e < E/2, the crop)
-// of rows r0 (v[e].x) and r0 + 1 (v[e].y); vo: the problem's vector offset.
+// Pass C's outputs of one thread: elements n = j + e*G < L (e < E/2, the
+// crop) of rows r0 (v[e].x) and r0 + 1 (v[e].y), through the epilogue of the
+// mode: the plain output; the CG product q = P (C p + s p) with the dot
+// products the CG step takes (s0..s4: p.q, r.q, q.q and, of the r and p pass
+// A formed, r.r and r.p); the preconditioned residual z (s0: r.z); or the
+// FP64 true residual r = P (b - C x - s x) (s0: r.r, s1: (P b).(P b)).  Each
+// row's operands are all loaded before the first is used.  vo: the
+// problem's vector offset.
 template <typename T, int M, int E>
 __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, const T* __restrict__ s,
                                                const T* __restrict__ cp, const T* __restrict__ cr,
@@ -656,27 +636,92 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
                                                const uint8_t* __restrict__ mask, const double* __restrict__ x64,
                                                const double* __restrict__ b64, const double* __restrict__ s64,
                                                double* __restrict__ r64, int j, int r0, int L, size_t vo,
-                                               const cpx<T> (&v)[E], Acc<T>& s0, Acc<T>& s1, Acc<T>& s2) {
-    constexpr int G = M / E;
+                                               const cpx<T> (&v)[E], Acc<T>& s0, Acc<T>& s1, Acc<T>& s2,
+                                               Acc<T>& s3, Acc<T>& s4) {
+    constexpr int G = M / E, H = E / 2;
 #pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-        const int n = j + e * G;
-        if (n < L) {
-            if (r0 < L)
-                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, vo + (size_t)r0 * L + n, v[e].x, s0,
-                             s1, s2);
-            if (r0 + 1 < L)
-                pass_c_value(mode, y, s, cp, cr, cq, cz, mask, x64, b64, s64, r64, vo + (size_t)(r0 + 1) * L + n,
-                             v[e].y, s0, s1, s2);
+    for (int h = 0; h < 2; ++h) {
+        if (r0 + h >= L) continue;
+        const size_t b = vo + (size_t)(r0 + h) * L + j;
+        bool ok[H];
+        T yv[H];
+        uint8_t act[H];
+#pragma unroll
+        for (int e = 0; e < H; ++e) {
+            ok[e] = j + e * G < L;
+            yv[e] = h == 0 ? v[e].x : v[e].y;
+            act[e] = 1;
+        }
+        if (mode == RI_PLAIN) {
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) y[b + e * G] = yv[e];
+            continue;
+        }
+        if (mask) {
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) act[e] = mask[b + e * G];
+        }
+        if (mode == RI_CG) {
+            T pv[H], rv[H], sv[H];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    pv[e] = cp[b + e * G];
+                    rv[e] = cr[b + e * G];
+                    sv[e] = s[b + e * G];
+                }
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    const T q = act[e] ? yv[e] + sv[e] * pv[e] : (T)0;
+                    cq[b + e * G] = q;
+                    s0.prod(pv[e], q);
+                    s1.prod(rv[e], q);
+                    s2.prod(q, q);
+                    s3.prod(rv[e], rv[e]);
+                    s4.prod(rv[e], pv[e]);
+                }
+        } else if (mode == RI_PCG_Z) {
+            T rv[H];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) rv[e] = cr[b + e * G];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    const T z = act[e] ? yv[e] : (T)0;
+                    cz[b + e * G] = z;
+                    s0.prod(rv[e], z);
+                }
+        } else {  // RI_RESID (T = double)
+            double xv[H], bv[H], sv[H];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    xv[e] = x64[b + e * G];
+                    bv[e] = b64[b + e * G];
+                    sv[e] = s64[b + e * G];
+                }
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    const double bb = act[e] ? bv[e] : 0.0;
+                    const double r = act[e] ? bb - ((double)yv[e] + sv[e] * xv[e]) : 0.0;
+                    r64[b + e * G] = r;
+                    s0.prod((T)r, (T)r);
+                    s1.prod((T)bb, (T)bb);
+                }
         }
     }
 }
 
 // One unit of pass C: RB row pairs starting at pair unit*RB.  Adds this
-// thread's partial sums to s0, s1, s2.  vo, zo: the problem's offsets.
+// thread's partial sums to s0 .. s4.  vo, zo: the problem's offsets.
 template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
 __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, Acc<T>& s0, Acc<T>& s1,
-                                          Acc<T>& s2, size_t vo = 0, size_t zo = 0) {
+                                          Acc<T>& s2, Acc<T>& s3, Acc<T>& s4, size_t vo = 0, size_t zo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;
@@ -726,19 +771,19 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
     // with two buffers the first exchange writes buffer 1 while buffer 0 is still being read
     fft_stages<T, M, E, true, DB, DB ? 1 : 0>(v, j, g0, g0 + SEG, a.tw);
     pass_c_outputs<T, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j, r0, L, vo,
-                            v, s0, s1, s2);
+                            v, s0, s1, s2, s3, s4);
 }
 
 // Pass C's grid sums and step decisions (last block).  warm (RI_RESID): the
 // residual and its sums were updated in place, and block 0 alone hands them on.
 template <typename T>
 __device__ __forceinline__ void rinv_sums(const RowInvArgs<T>& a, double* part, CgState* st, const Acc<T>& s0,
-                                          const Acc<T>& s1, const Acc<T>& s2) {
+                                          const Acc<T>& s1, const Acc<T>& s2, const Acc<T>& s3, const Acc<T>& s4) {
     if (a.mode == RI_CG) {
-        const Acc<T> pv[3] = {s0, s1, s2};
-        double tot[3];
-        if (grid_sum_last<3>(pv, part, &st->cntC, tot) && threadIdx.x == 0)
-            cg_step_decide(st, tot[0], tot[1], tot[2], a.h_inner);
+        const Acc<T> pv[5] = {s0, s1, s2, s3, s4};
+        double tot[5];
+        if (grid_sum_last<5>(pv, part, &st->cntC, tot) && threadIdx.x == 0)
+            cg_step_decide(st, tot[0], tot[1], tot[2], tot[3], tot[4], a.h_inner);
     } else if (a.mode == RI_RESID) {
         double pv[2] = {s0.value(), s1.value()}, tot[2];
         if (grid_sum_last<2>(pv, part, &st->cntC, tot) && threadIdx.x == 0) {
@@ -757,18 +802,18 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a
     static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
-    Acc<T> s0, s1, s2;  // short per-thread runs (FP64, or Dot2 pairs in FP32)
+    Acc<T> s0, s1, s2, s3, s4;  // short per-thread runs (FP64, or Dot2 pairs in FP32)
     // warm residual: r64 and its sums (rr64, bb) are already in place, and
     // block 0 alone hands them to the decision
     const bool warm = a.mode == RI_RESID && a.st->warm;
     if (!warm) {
-        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2);
+        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2, s3, s4);
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
         s0.set((T)a.st->rr64);
         s1.set((T)a.st->bb);
     }
     pdl_leave();
-    rinv_sums(a, a.part, a.st, s0, s1, s2);
+    rinv_sums(a, a.part, a.st, s0, s1, s2, s3, s4);
 }
 
 // The batched form: problem blockIdx.y at the strides of bb, gated.
@@ -779,17 +824,17 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv_b(const RowInvArgs<T>
     CgState* const st = a.st + blockIdx.y;
     pdl_enter();
     if (bb.gate && gate_closed(st, bb.gate)) return;
-    Acc<T> s0, s1, s2;
+    Acc<T> s0, s1, s2, s3, s4;
     const bool warm = a.mode == RI_RESID && st->warm;
     if (!warm) {
-        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2,
+        rinv_unit<T, M, E, RB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2, s3, s4,
                                    (size_t)blockIdx.y * bb.bs.n, (size_t)blockIdx.y * bb.bs.z);
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
         s0.set((T)st->rr64);
         s1.set((T)st->bb);
     }
     pdl_leave();
-    rinv_sums(a, a.part + blockIdx.y * bb.bs.part, st, s0, s1, s2);
+    rinv_sums(a, a.part + blockIdx.y * bb.bs.part, st, s0, s1, s2, s3, s4);
 }
 
 }  // namespace fc

@@ -137,8 +137,8 @@ struct PersistArgs {
     ColArgs<T> B;
     RowInvArgs<T> C;
     int nA, nB;          // units of passes A and C (row pairs / RB) and B (columns / CB)
-    double* partA;       // [gridDim][2]
-    double* partC;       // [gridDim][3]
+    double* partA;       // unused (pass A takes no sums)
+    double* partC;       // [gridDim][5]
     PersistCtl* ctl;
     long N;              // L*L, for the final x += alpha p
 };
@@ -148,8 +148,8 @@ __global__ void __launch_bounds__(RB*(M / EA)) k_cg_persist(PersistArgs<T> P) {
     static_assert(RB * (M / EA) == CB * (M / EB), "phases must use the whole block");
     extern __shared__ __align__(16) unsigned char smraw[];
     cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
-    __shared__ double scratch[32][3];
-    __shared__ double bcast[3];
+    __shared__ double scratch[32][5];
+    __shared__ double bcast[5];
     CgState* st = P.A.st;
     if (st->finished) return;  // the outer loop has stopped: no inner run
     const unsigned limit = st->dbg_limit ? st->dbg_limit : (1u << 24);
@@ -169,46 +169,38 @@ __global__ void __launch_bounds__(RB*(M / EA)) k_cg_persist(PersistArgs<T> P) {
     bool ok = true;
 
     while (true) {
-        // phase A: CG update + pair-packed row FFTs, partial r.r and r.p
+        // phase A: CG update + pair-packed row FFTs
         const AScal<T> sc{first, (T)alpha, (T)beta, (T)(first ? bcarry : 0.0), inv_sigma, 0.0};
-        Acc<T> acc, acc_rp;
         for (int u = blockIdx.x; u < P.nA; u += gridDim.x) {
-            rfwd_unit<T, M, EA, RB>(P.A, sc, u, sm, acc, acc_rp);
+            rfwd_unit<T, M, EA, RB>(P.A, sc, u, sm);
             __syncthreads();
-        }
-        {
-            const Acc<T> pv[2] = {acc, acc_rp};
-            publish_partials<2, T>(pv, P.partA, reinterpret_cast<double(*)[2]>(scratch));
         }
         if (leave) return;
         if (!(ok = grid_barrier(P.ctl, limit))) break;
-        {
-            double tot[2];
-            total_partials<2, T>(P.partA, tot, reinterpret_cast<double(*)[2]>(scratch), bcast);
-            rr = tot[0];
-            rp = tot[1];
-        }
         // phase B: column FFT x spectrum x inverse
         for (int u = blockIdx.x; u < P.nB; u += gridDim.x) {
             colc_unit<T, M, EB, CB>(P.B, u, sm);
             __syncthreads();
         }
         if (!(ok = grid_barrier(P.ctl, limit))) break;
-        // phase C: inverse row FFTs, q = P (C p + s p), partial p.q, r.q, q.q
-        Acc<T> s0, s1, s2;
+        // phase C: inverse row FFTs, q = P (C p + s p), partial p.q, r.q, q.q,
+        // r.r, r.p
+        Acc<T> s0, s1, s2, s3, s4;
         for (int u = blockIdx.x; u < P.nA; u += gridDim.x) {
-            rinv_unit<T, M, EA, RB>(P.C, u, sm, s0, s1, s2);
+            rinv_unit<T, M, EA, RB>(P.C, u, sm, s0, s1, s2, s3, s4);
             __syncthreads();
         }
         {
-            const Acc<T> pv[3] = {s0, s1, s2};
-            publish_partials<3, T>(pv, P.partC, scratch);
+            const Acc<T> pv[5] = {s0, s1, s2, s3, s4};
+            publish_partials<5, T>(pv, P.partC, scratch);
         }
         if (!(ok = grid_barrier(P.ctl, limit))) break;
-        double tot[3];
-        total_partials<3, T>(P.partC, tot, scratch, bcast);
+        double tot[5];
+        total_partials<5, T>(P.partC, tot, scratch, bcast);
         // the step decision of cg_step_decide, taken identically in every block
         const double pq = tot[0], rq = tot[1], qq = tot[2];
+        rr = tot[3];
+        rp = tot[4];
         alpha = rp / pq;
         double rrn = rr - 2.0 * alpha * rq + alpha * alpha * qq;
         if (rrn < 0.0) rrn = 0.0;

@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
             tma_load_2d(reinterpret_cast<unsigned char*>(buf[b]) + (size_t)k * BK * 16, &P.map, 4 * unit, k * BK,
                         &bar[b]);
     };
-    Acc<float> s0, s1, s2;
+    Acc<float> s0, s1, s2, s3, s4;
     unsigned ph0 = 0, ph1 = 0;
     bool pending[2] = {false, false};
     int u = blockIdx.x;
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
         __syncthreads();  // staged values consumed: the buffer becomes the exchange buffer
         fft_stages<float, M, E, true, false, 0>(v, j, buf[cur], buf[cur], a.tw);
         pass_c_outputs<float, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j,
-                                    2 * u, L, 0, v, s0, s1, s2);
+                                    2 * u, L, 0, v, s0, s1, s2, s3, s4);
         __syncthreads();  // exchanges done: the buffer may receive the copy issued next
     }
     if (!ok && j == 0) {
@@ -194,10 +194,10 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
     }
     pdl_leave();  // every block still joins the grid reduction below
     if (a.mode == RI_CG) {
-        const Acc<float> pv[3] = {s0, s1, s2};
-        double tot[3];
-        if (grid_sum_last<3>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
-            cg_step_decide(a.st, tot[0], tot[1], tot[2], a.h_inner);
+        const Acc<float> pv[5] = {s0, s1, s2, s3, s4};
+        double tot[5];
+        if (grid_sum_last<5>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
+            cg_step_decide(a.st, tot[0], tot[1], tot[2], tot[3], tot[4], a.h_inner);
     } else if (a.mode == RI_PCG_Z) {
         const Acc<float> pv[1] = {s0};
         double tot[1];
