@@ -193,6 +193,17 @@ int fftconv_plan_shapes(const fftconv_plan *p, int prec, int n_shapes[3], int ch
  * as one graph node per pass inside a device-side while loop.  Host only. */
 int fftconv_plan_solver(const fftconv_plan *p, int prec, int *n, int *chosen, int *threads, int *grid);
 
+/* The launch shapes of the plan's batched solves (cg_solve_batch and the
+ * calls built on it): per pass, the index into the same compiled-shape
+ * lists fftconv_plan_shapes counts, its radix and rows or columns per
+ * block; *tuned (may be NULL) = 1 once chosen.  FP32 shapes are timed on the
+ * first batched use of a mixed plan (the FFT passes of Section 3 run over
+ * all problems at once) and the fastest kept for every later batch, so a
+ * problem's result does not depend on the size of the batch it joins; a
+ * plan created with forced shapes uses those.  Host only. */
+int fftconv_plan_batch_shapes(const fftconv_plan *p, int prec, int chosen[3], int radix[3], int per_block[3],
+                              int *tuned);
+
 /*
  * fftconv_apply -- y = C x (Listing 4: cpyComplex, FFT, elementMult, inverse
  * FFT, cpyReal), three kernel passes on stream.

@@ -112,6 +112,7 @@ def _load():
     lib.fftconv_plan_shapes.argtypes = [vp, i, ip3, ip3, ip3, ip3]
     ipt = ctypes.POINTER(ctypes.c_int)
     lib.fftconv_plan_solver.argtypes = [vp, i, ipt, ipt, ipt, ipt]
+    lib.fftconv_plan_batch_shapes.argtypes = [vp, i, ip3, ip3, ip3, ipt]
     lib.fftconv_plan_destroy.argtypes = [vp]
     lib.fftconv_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(sz)]
@@ -443,6 +444,16 @@ def fftconv_plan_shapes(plan: Plan, prec: int) -> dict:
     if rc != FC_OK:
         raise FcError(rc, "fftconv_plan_shapes")
     return {"n_shapes": list(n), "chosen": list(ch), "radix": list(rad), "per_block": list(per)}
+
+
+def fftconv_plan_batch_shapes(plan: Plan, prec: int) -> dict:
+    """Launch shapes of the plan's batched solves (indices into the same lists)."""
+    ip3 = ctypes.c_int * 3
+    ch, rd, pb, tu = ip3(), ip3(), ip3(), ctypes.c_int()
+    rc = _lib.fftconv_plan_batch_shapes(plan.handle, int(prec), ch, rd, pb, ctypes.byref(tu))
+    if rc != FC_OK:
+        raise FcError(rc, "fftconv_plan_batch_shapes")
+    return {"chosen": list(ch), "radix": list(rd), "per_block": list(pb), "tuned": bool(tu.value)}
 
 
 def fftconv_plan_solver(plan: Plan, prec: int) -> dict:

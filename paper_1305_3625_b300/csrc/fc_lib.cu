@@ -662,9 +662,9 @@ int set_smem_attrs(const Variants& v) {
                 rc = set_cuda_err(cudaGetLastError(), "cudaFuncSetAttribute(persistent)");
     if (!rc) rc = set_smem_attr(v.rows_full);
     if (!rc) rc = set_smem_attr(v.cols_full);
-    if (!rc) rc = set_smem_attr(v.rfwd_b);
-    if (!rc) rc = set_smem_attr(v.colc_b);
-    if (!rc) rc = set_smem_attr(v.rinv_b);
+    for (int k = 0; k < v.n_rfwd && !rc; ++k) rc = set_smem_attr(v.rfwd_b[k]);
+    for (int k = 0; k < v.n_colc && !rc; ++k) rc = set_smem_attr(v.colc_b[k]);
+    for (int k = 0; k < v.n_rinv && !rc; ++k) rc = set_smem_attr(v.rinv_b[k]);
     return rc;
 }
 
@@ -694,6 +694,9 @@ struct PrecRes {
     bool on = false;
     Variants v;
     int sel[3] = {0, 0, 0};  // chosen shape of pass A, B, C
+    int sel_b[3] = {0, 0, 0};  // chosen batched twin of pass A, B, C (indices into the same lists)
+    bool tuned_b = false;      // sel_b decided (tuned on first batched use, or forced)
+    bool tune_off = false;     // the plan was made without timing (no_autotune, FC_AUTOTUNE=0)
     int sel_pers = -1;       // chosen persistent inner-CG kernel (-1: graph loop)
     int pers_grid = 0;       // its cooperative grid (resident blocks)
     void* Z = nullptr;       // cpx<T>[(M/2) * L], column-major half spectra
@@ -1082,6 +1085,10 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
             if (forced[kind] > n[kind]) return FC_EINVAL;
             if (kind == 2 && R.v.rinv[forced[kind] - 1].tma && !R.tma_ok) return FC_EINVAL;
             R.sel[kind] = forced[kind] - 1;
+            // batched solves take the same shape where it has a twin (not the TMA pass C)
+            const KV& tw = kind == 0 ? R.v.rfwd_b[R.sel[kind]] : (kind == 1 ? R.v.colc_b[R.sel[kind]]
+                                                                              : R.v.rinv_b[R.sel[kind]]);
+            R.sel_b[kind] = tw.f ? R.sel[kind] : 0;
             continue;
         }
         R.sel[kind] = 0;
@@ -1094,6 +1101,8 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
         else
             need[kind] = timing;
     }
+    if (forced[0] > 0 || forced[1] > 0 || forced[2] > 0 || n[0] <= 1) R.tuned_b = true;  // no batched tuning
+    R.tune_off = !timing;
     if (!need[0] && !need[1] && !need[2]) return FC_OK;
     T *x = nullptr, *y = nullptr;
     cudaStream_t s = nullptr;
@@ -1137,6 +1146,128 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
         cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     }
+    return rc;
+}
+
+}  // namespace
+
+namespace {
+
+// The batched twins of each pass, timed like the single-problem shapes
+// (plain modes, 2 warm-up and 5 timed launches) over nb problems at once,
+// nb = min(16, 64 MB of intermediate); the fastest is kept for every batched
+// solve of the plan, whatever its batch size, so that a problem's arithmetic
+// does not depend on the batch it joins.  Choices are cached like the
+// single-problem ones (keys "... rfwd_b ...").  Runs on the first batched use
+// of a mixed plan (FP64 carries one shape); FC_AUTOTUNE=0 keeps the standard
+// shapes.
+template <typename T>
+int autotune_batched(fftconv_plan* p, PrecRes& R) {
+    if (R.tuned_b) return FC_OK;
+    R.tuned_b = true;
+    R.sel_b[0] = R.sel_b[1] = R.sel_b[2] = 0;
+    const char* env = getenv("FC_AUTOTUNE");
+    const bool timing = !R.tune_off && !(env && !strcmp(env, "0"));
+    const char* venv = getenv("FC_TUNE_VERBOSE");
+    const bool verbose = venv && strcmp(venv, "0");
+    const KV* lists[3] = {R.v.rfwd_b, R.v.colc_b, R.v.rinv_b};
+    const int n[3] = {R.v.n_rfwd, R.v.n_colc, R.v.n_rinv};
+    const char* names[3] = {"rfwd_b", "colc_b", "rinv_b"};
+    char keys[3][96];
+    bool need[3] = {false, false, false};
+    for (int kind = 0; kind < 3; ++kind) {
+        if (n[kind] <= 1) continue;
+        snprintf(keys[kind], sizeof(keys[kind]), "%s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M, p->L,
+                 names[kind], n[kind]);
+        int idx = 0;
+        if (tune_lookup(keys[kind], &idx) && idx >= 0 && idx < n[kind] && lists[kind][idx].f)
+            R.sel_b[kind] = idx;
+        else
+            need[kind] = timing;
+    }
+    if (!need[0] && !need[1] && !need[2]) return FC_OK;
+    const long N = p->N, zs = (long)(p->M / 2) * p->L;
+    long nbt = (64L << 20) / (long)(zs * sizeof(cpx<T>));
+    if (nbt > 16) nbt = 16;
+    if (nbt < 1) nbt = 1;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    void* buf = nullptr;
+    const size_t bytes = sizeof(T) * 2 * (size_t)nbt * N + sizeof(cpx<T>) * (size_t)nbt * zs + sizeof(CgState) * nbt;
+    int rc = FC_OK;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        rc = set_cuda_err(cudaGetLastError(), "batched autotune set-up");
+    if (!rc && dev_malloc_async(&buf, bytes, s) != cudaSuccess) {
+        set_cuda_err(cudaErrorMemoryAllocation, "cudaMallocAsync(batched autotune)");
+        rc = FC_ENOMEM;
+    }
+    if (!rc && cudaMemsetAsync(buf, 0, bytes, s) != cudaSuccess)
+        rc = set_cuda_err(cudaGetLastError(), "batched autotune set-up");
+    T* x = (T*)buf;
+    T* y = x + nbt * N;
+    cpx<T>* Z = (cpx<T>*)(y + nbt * N);
+    CgState* st = (CgState*)(Z + nbt * zs);
+    const BatchArgs bb{0, BatchStride{N, zs, 0, 0}};
+    for (int kind = 0; kind < 3 && !rc; ++kind) {
+        if (!need[kind]) continue;
+        float best = 1e30f;
+        int bi = 0;
+        for (int k = 0; k < n[kind] && !rc; ++k) {
+            const KV& kv = lists[kind][k];
+            if (!kv.f) continue;
+            const cpx<T>* tw = (const cpx<T>*)R.tws(kv.E);
+            RowFwdArgs<T> a{};
+            a.L = p->L;
+            a.mode = RF_PLAIN;
+            a.x = x;
+            a.st = st;
+            a.Z = Z;
+            a.tw = tw;
+            ColArgs<T> b{p->L, Z, (const T*)R.Gq, tw, st, 0};
+            RowInvArgs<T> c{};
+            c.L = p->L;
+            c.mode = RI_PLAIN;
+            c.y = y;
+            c.st = st;
+            c.Z = Z;
+            c.tw = tw;
+            const int gx = kind == 1 ? col_grid(p, kv) : row_grid(p, kv);
+            void* a2[2] = {kind == 0 ? (void*)&a : (kind == 1 ? (void*)&b : (void*)&c), (void*)&bb};
+            auto go = [&]() -> int {
+                if (cudaLaunchKernel(kv.f, dim3(gx, (unsigned)nbt), dim3(kv.threads), a2, kv.smem, s) != cudaSuccess)
+                    return set_cuda_err(cudaGetLastError(), "batched autotune launch");
+                return FC_OK;
+            };
+            float ms = 0;
+            for (int w = 0; w < 2 && !rc; ++w) rc = go();
+            if (!rc && cudaEventRecord(e0, s) != cudaSuccess) rc = set_cuda_err(cudaGetLastError(), "event");
+            for (int w = 0; w < 5 && !rc; ++w) rc = go();
+            if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = set_cuda_err(cudaGetLastError(), "event");
+            if (rc) break;
+            ms /= 5.0f;
+            if (verbose)
+                fprintf(stderr, "[fftconv tune] %s shape %d (E=%d, per=%d, threads=%d) x%ld problems: %.3f us\n",
+                        keys[kind], k, kv.E, kv.per, kv.threads, nbt, ms * 1e3f);
+            if (ms < best) {
+                best = ms;
+                bi = k;
+            }
+        }
+        if (!rc) {
+            R.sel_b[kind] = bi;
+            tune_store(keys[kind], bi);
+        }
+    }
+    if (s) {
+        dev_free_async(buf, s);
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     return rc;
 }
 
@@ -1484,6 +1615,21 @@ extern "C" int fftconv_plan_shapes(const fftconv_plan* p, int prec, int n_shapes
         radix[i] = k3[i]->E;
         per_block[i] = k3[i]->per;
     }
+    return FC_OK;
+}
+
+extern "C" int fftconv_plan_batch_shapes(const fftconv_plan* p, int prec, int chosen[3], int radix[3],
+                                         int per_block[3], int* tuned) {
+    if (!p || !chosen || !radix || !per_block) return FC_EINVAL;
+    const PrecRes* R = prec == FC_F32 ? (p->p32.on ? &p->p32 : nullptr) : (prec == FC_F64 && p->p64.on ? &p->p64 : nullptr);
+    if (!R) return FC_EINVAL;
+    const KV* k3[3] = {&R->v.rfwd_b[R->sel_b[0]], &R->v.colc_b[R->sel_b[1]], &R->v.rinv_b[R->sel_b[2]]};
+    for (int i = 0; i < 3; ++i) {
+        chosen[i] = R->sel_b[i];
+        radix[i] = k3[i]->E;
+        per_block[i] = k3[i]->per;
+    }
+    if (tuned) *tuned = R->tuned_b ? 1 : 0;
     return FC_OK;
 }
 
@@ -1884,9 +2030,9 @@ SolveView plan_view(fftconv_plan* p) {
 
 // The launch shapes of a solve graph: the tuned ones, or for batched solves
 // the batched forms of the standard shapes.
-const KV& rfwd_shape(const PrecRes& R, bool batched) { return batched ? R.v.rfwd_b : R.rfwd(); }
-const KV& colc_shape(const PrecRes& R, bool batched) { return batched ? R.v.colc_b : R.colc(); }
-const KV& rinv_shape(const PrecRes& R, bool batched) { return batched ? R.v.rinv_b : R.rinv(); }
+const KV& rfwd_shape(const PrecRes& R, bool batched) { return batched ? R.v.rfwd_b[R.sel_b[0]] : R.rfwd(); }
+const KV& colc_shape(const PrecRes& R, bool batched) { return batched ? R.v.colc_b[R.sel_b[1]] : R.colc(); }
+const KV& rinv_shape(const PrecRes& R, bool batched) { return batched ? R.v.rinv_b[R.sel_b[2]] : R.rinv(); }
 
 // Pass C as a graph node following prev (the TMA-staged shape gets its
 // tensor-map arguments).
@@ -2501,6 +2647,10 @@ int batch_bucket(int nb) {
 // shrunk; stream-ordered, so growing stalls no other stream; the graphs are
 // rebuilt after a re-allocation).
 int batch_reserve(fftconv_plan* p, int nb, bool mixed, cudaStream_t st) {
+    if (mixed && p->p32.on && !p->p32.tuned_b) {
+        const int rc = autotune_batched<float>(p, p->p32);
+        if (rc) return rc;
+    }
     if (!p->batch) {
         p->batch = new (std::nothrow) BatchWs();
         if (!p->batch) return FC_ENOMEM;

@@ -122,16 +122,33 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, uns
     }
     __syncthreads();
     if (!is_last) return false;
-    // the grid's partials are added by warp 0 alone (strided runs, one warp tree)
+    // the grid's partials are added by warp 0 alone (strided runs, one warp
+    // tree); lane l adds blocks l, l + 32, l + 64, ... in that order, four
+    // blocks' values loaded at a time so that their L2 round trips overlap
     if (threadIdx.x < 32) {
         __threadfence();
+        double acc[NV];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+        const unsigned G = gridDim.x;
+        for (unsigned b0 = threadIdx.x; b0 < G; b0 += 128) {
+            double q[4][NV];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    q[u][k] = b0 + 32 * u < G ? __ldcg(part + (size_t)(b0 + 32 * u) * NV + k) : 0.0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    if (b0 + 32 * u < G) acc[k] += q[u][k];
+        }
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
-            double acc = 0.0;
-            for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) acc += __ldcg(part + (size_t)b * NV + k);
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-            tot[k] = acc;
+            for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+            tot[k] = acc[k];
         }
         if (threadIdx.x == 0) *cnt = 0u;
     }
@@ -259,14 +276,29 @@ __device__ __forceinline__ bool grid_sum_last(const Acc<float> (&v)[NV], double*
     if (!is_last) return false;
     if (threadIdx.x < 32) {
         __threadfence();
+        // lane l adds blocks l, l + 32, l + 64, ... in that order, four blocks'
+        // pairs loaded at a time so that their L2 round trips overlap
 #pragma unroll
         for (int k = 0; k < NV; ++k) {
             hi[k] = 0.f;
             lo[k] = 0.f;
-            for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) {
-                const float2 q = __ldcg(pf + (size_t)b * NV + k);
-                ff_add(hi[k], lo[k], q.x, q.y);
-            }
+        }
+        const unsigned G = gridDim.x;
+        for (unsigned b0 = threadIdx.x; b0 < G; b0 += 128) {
+            float2 q[4][NV];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    q[u][k] = b0 + 32 * u < G ? __ldcg(pf + (size_t)(b0 + 32 * u) * NV + k) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < NV; ++k)
+                    if (b0 + 32 * u < G) ff_add(hi[k], lo[k], q[u][k].x, q[u][k].y);
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
                 const float h = __shfl_down_sync(0xffffffffu, hi[k], off);

@@ -52,6 +52,9 @@ void add_row(Variants& v) {
         for (int k = 0; k < v.n_rfwd; ++k)
             if (v.rfwd[k].f == f.f) return;
         if (v.n_rfwd >= Variants::kMax || v.n_rinv >= Variants::kMax) return;
+        // the batched twins (same arithmetic, blockIdx.y = problem) at the same index
+        v.rfwd_b[v.n_rfwd] = KV{(const void*)k_rfwd_b<T, M, E, RB, MINB, DB>, f.threads, RB, E, f.smem};
+        v.rinv_b[v.n_rinv] = KV{(const void*)k_rinv_b<T, M, E, RB, MINB, DB>, i.threads, RB, E, i.smem};
         v.rfwd[v.n_rfwd++] = f;
         v.rinv[v.n_rinv++] = i;
     }
@@ -62,18 +65,9 @@ template <int M>
 void add_rinv_tma(Variants& v) {
     // whole warps per block (the block reductions shuffle across full warps)
     if constexpr (M / 16 >= 32 && tma_smem_bytes(M) <= 200 * 1024) {
+        // no batched twin: rinv_b at this index stays empty
         if (v.n_rinv < Variants::kMax) v.rinv[v.n_rinv++] = KV{(const void*)k_rinv_tma<M, 16>, M / 16, 1, 16, tma_smem_bytes(M), 1};
     }
-}
-
-// The batched forms of the standard shapes (the first registered of each
-// pass): batched solves launch these, whatever the plan's tuner chose.
-template <typename T, int M, int ER, int RB, int EC, int CB>
-void add_batched(Variants& v) {
-    constexpr bool DR = use_db<T, M, RB>(), DC = use_db<T, M, CB>();
-    v.rfwd_b = KV{(const void*)k_rfwd_b<T, M, ER, RB, 1, DR>, RB * (M / ER), RB, ER, pass_smem<T, M, RB, DR>()};
-    v.rinv_b = KV{(const void*)k_rinv_b<T, M, ER, RB, 1, DR>, RB * (M / ER), RB, ER, pass_smem<T, M, RB, DR>()};
-    v.colc_b = KV{(const void*)k_colc_b<T, M, EC, CB, 1, DC>, CB * (M / EC), CB, EC, pass_smem<T, M, CB, DC>()};
 }
 
 template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
@@ -82,7 +76,9 @@ void add_col(Variants& v) {
         KV c{(const void*)k_colc<T, M, E, CB, MINB, DB>, CB * (M / E), CB, E, pass_smem<T, M, CB, DB>()};
         for (int k = 0; k < v.n_colc; ++k)
             if (v.colc[k].f == c.f) return;
-        if (v.n_colc < Variants::kMax) v.colc[v.n_colc++] = c;
+        if (v.n_colc >= Variants::kMax) return;
+        v.colc_b[v.n_colc] = KV{(const void*)k_colc_b<T, M, E, CB, MINB, DB>, c.threads, CB, E, c.smem};
+        v.colc[v.n_colc++] = c;
     }
 }
 
@@ -111,15 +107,12 @@ void make_variants(Variants& v) {
         if constexpr (M <= 16) {
             add_row<T, M, M, 64>(v);
             add_col<T, M, M, clampi(64, 1, H)>(v);
-            add_batched<T, M, M, 64, M, clampi(64, 1, H)>(v);
         } else if constexpr (M <= 128) {
             constexpr int G = M / 16;
             add_row<T, M, 16, clampi(128 / G, 1, 128)>(v);
             add_col<T, M, 16, clampi(256 / G, 1, H)>(v);
-            add_batched<T, M, 16, clampi(128 / G, 1, 128), 16, clampi(256 / G, 1, H)>(v);
         } else {
             constexpr int G16 = M / 16, G8 = M / 8, G4 = M / 4;
-            add_batched<T, M, 16, clampi(256 / G16, 1, 64), 16, clampi(128 / G16, 1, H)>(v);
             add_row<T, M, 16, clampi(256 / G16, 1, 64)>(v);
             add_row<T, M, 16, clampi(512 / G16, 1, 64)>(v);
             add_row<T, M, 8, clampi(256 / G8, 1, 64)>(v);
@@ -159,7 +152,6 @@ void make_variants(Variants& v) {
         constexpr int CB = clampi(256 / G, 1, H);
         add_row<T, M, E, RB>(v);
         add_col<T, M, E, CB>(v);
-        add_batched<T, M, E, RB, E, CB>(v);
         constexpr int CBF = clampi(256 / G, 1, M);
         v.rows_full = KV{(const void*)k_rows_full<M, E, RB>, RB * G, RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<double>)};
         v.cols_full = KV{(const void*)k_cols_full<M, E, CBF>, CBF * G, CBF, E, (size_t)CBF * seg_len(M) * sizeof(cpx<double>)};

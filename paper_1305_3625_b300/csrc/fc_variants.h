@@ -32,7 +32,10 @@ struct Variants {
     KVP pers[6];
     int n_pers = 0;
     KV rows_full, cols_full;  // FP64 only: spectrum set-up
-    KV rfwd_b, colc_b, rinv_b;  // batched forms (blockIdx.y = problem) of the standard shapes
+    // the batched twins (blockIdx.y = problem, the same arithmetic per problem)
+    // of rfwd[k], colc[k], rinv[k]; an entry with f == nullptr has none (the
+    // TMA-staged pass C)
+    KV rfwd_b[kMax], colc_b[kMax], rinv_b[kMax];
 };
 
 // Fill v with the compiled shapes of size M in FP32 (f64 = false) or FP64;

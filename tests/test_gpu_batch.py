@@ -247,3 +247,63 @@ def test_batch_server_sizes_oracle_residual(L):
         assert rel <= 1.01 * rtol
         xa, ra = solve_alone(L, s[k], b[k], mask[k], fc.FC_MODE_MIXED, True, rtol)
         assert np.array_equal(xb[k], xa) and rs[k]["iters"] == ra["iters"]
+
+
+@pytest.mark.parametrize("L", [100, 512])
+def test_every_batched_shape_equals_alone(L):
+    """The batched twin of every compiled launch shape (the batched solves'
+    autotuner candidates): a batch of three problems equals the same problems
+    solved alone on that shape, bitwise, and meets the tolerance by the
+    oracle's residual.  (The TMA-staged pass C has no twin; a batch then runs
+    the standard pass C.)"""
+    probe = fc.fftconv_plan_create(L, fc.FC_F32, no_autotune=True)
+    n = fc.fftconv_plan_shapes(probe, fc.FC_F32)["n_shapes"]
+    probe.close()
+    nb, rtol = 3, 1e-9
+    s, b, mask = problems(L, nb, 900 + L, masked=True, broken=[0.0, 0.1, 0.3])
+    for k in range(max(n)):
+        shapes = tuple(min(k, n[i] - 1) for i in range(3))
+        pl = fc.fftconv_plan_create(L, shapes=shapes, persistent=-1)
+        bs = fc.fftconv_plan_batch_shapes(pl, fc.FC_F32)
+        assert bs["tuned"]
+        x = dev(np.zeros((nb, L * L)))
+        rc, rs = fc.cg_solve_batch(pl, dev(s), dev(b), x, mask=dev(mask, torch.uint8), rtol=rtol,
+                                   mode=fc.FC_MODE_MIXED, precond=True, x0_zero=True)
+        assert rc == fc.FC_OK
+        xb = host(x)
+        for j in range(nb):
+            pb = np.where(mask[j] != 0, b[j], 0.0)
+            r = pb - oracle.apply_A(L, s[j], xb[j], mask[j])
+            assert np.linalg.norm(r) <= 1.01 * rtol * np.linalg.norm(pb), (k, j)
+            if bs["chosen"] == list(shapes):
+                xa = dev(np.zeros(L * L))
+                ra = fc.cg_solve(pl, dev(s[j]), dev(b[j]), xa, mask=dev(mask[j], torch.uint8), rtol=rtol,
+                                 mode=fc.FC_MODE_MIXED, precond=True, x0_zero=True, warm_resid=False)
+                assert np.array_equal(xb[j], host(xa)) and rs[j]["iters"] == ra["iters"], (k, j)
+        pl.close()
+
+
+def test_tuned_batched_shapes_equal_alone():
+    """A plan's batched shapes, tuned on its first batched use, are kept for
+    every later batch whatever its size; a problem solved alone on those
+    shapes gives the batched result bitwise."""
+    L, rtol = 512, 1e-8
+    pl = fc.fftconv_plan_create(L)
+    s, b, _ = problems(L, 5, 1234)
+    x = dev(np.zeros((5, L * L)))
+    rc, rs = fc.cg_solve_batch(pl, dev(s), dev(b), x, rtol=rtol, mode=fc.FC_MODE_MIXED, precond=True, x0_zero=True)
+    assert rc == fc.FC_OK
+    bs = fc.fftconv_plan_batch_shapes(pl, fc.FC_F32)
+    assert bs["tuned"]
+    print(f"L={L} batched shapes {bs}")
+    x1 = dev(np.zeros((2, L * L)))
+    rc, rs1 = fc.cg_solve_batch(pl, dev(s[:2]), dev(b[:2]), x1, rtol=rtol, mode=fc.FC_MODE_MIXED, precond=True,
+                                x0_zero=True)
+    assert rc == fc.FC_OK and fc.fftconv_plan_batch_shapes(pl, fc.FC_F32) == bs
+    assert np.array_equal(host(x1), host(x)[:2])
+    alone = fc.fftconv_plan_create(L, shapes=tuple(bs["chosen"]), persistent=-1)
+    for j in range(2):
+        xa = dev(np.zeros(L * L))
+        fc.cg_solve(alone, dev(s[j]), dev(b[j]), xa, rtol=rtol, mode=fc.FC_MODE_MIXED, precond=True, x0_zero=True,
+                    warm_resid=False)
+        assert np.array_equal(host(xa), host(x)[j])
