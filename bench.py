@@ -182,6 +182,121 @@ class OracleLoop:
         return time.perf_counter() - t0, it
 
 
+# --------------------------------------------------------------- serving --
+
+def pct(v, q):
+    """q-quantile of the sorted list v (nearest rank)."""
+    return v[min(len(v) - 1, max(0, int(math.ceil(q * len(v))) - 1))]
+
+
+def serve_run(args, fc, fc_inputs, sv, drain, dev):
+    """The serving workload: requests of L = 2^round(U[5,11]) with tolerances
+    from {1e-6, 1e-8} (mixed, preconditioned), Poisson arrivals at 0.5, 0.7
+    and 0.9 of the closed-loop capacity measured on the same mix.  Each
+    request's s and b come from a pool of seeded problems of its size (16 per
+    size: bounded host memory); its size, tolerance and arrival are its own.
+    Also: the library's measured device high-water mark, plain FP64 CG and FP64
+    PCG one request at a time on the capacity run's requests, and the oracle's
+    residual of spot-checked results."""
+    import torch
+    import oracle
+    n = args.serve_requests
+    base = fc_inputs.request_stream(n, seed=777, rate_per_s=1.0)
+    pool = {}
+    for L in sorted({rq["L"] for rq in base}):
+        pool[L] = [fc_inputs.problem(L, seed=777_000 + 97 * L + j, b_kind="normal") for j in range(16)]
+
+    def prob(rq):
+        return pool[rq["L"]][rq["k"] % 16]
+
+    def submit(rq, x_out=None):
+        pk = prob(rq)
+        return fc.cg_batch_submit(sv, rq["L"], pk["s"], pk["b"], x_out=x_out, rtol=rq["tol"],
+                                  mode=fc.FC_MODE_MIXED, precond=True, borrow=True)
+
+    # the server's plans made ahead (two per size), then closed-loop capacity
+    # (all submitted at once; the first round, untimed, grows the batch
+    # workspaces and staging)
+    for L in sorted(pool):
+        fc.cg_server_reserve(sv, L, 2)
+    ncap = min(len(base), args.serve_f64)
+    mem0 = fc.fc_mem_stats(reset_peak=True)
+    for timed in (False, True):
+        c0 = time.perf_counter()
+        drain([submit(rq) for rq in base[:ncap]])
+        cap = ncap / (time.perf_counter() - c0)
+    rates = []
+    for rel in (0.5, 0.7, 0.9):
+        stream_ = fc_inputs.request_stream(n, seed=777, rate_per_s=rel * cap)
+        b0 = fc.cg_server_batches(sv)
+        t0 = time.perf_counter()
+        tickets = []
+        for rq in stream_:
+            while time.perf_counter() - t0 < rq["arrival_s"]:
+                time.sleep(0.0001)
+            tickets.append(submit(rq))
+        res = drain(tickets)
+        dt = time.perf_counter() - t0
+        assert all(r["status"] == fc.FC_OK for r in res.values())
+        lat = sorted(r["latency_s"] * 1e3 for r in res.values())
+        by_l = {}
+        for rq, tk in zip(stream_, tickets):
+            by_l.setdefault(rq["L"], []).append(res[tk]["latency_s"] * 1e3)
+        b1 = fc.cg_server_batches(sv)
+        nb = max(b1["batches"] - b0["batches"], 1)
+        rates.append({"rate_rel_capacity": rel, "rate_per_s": round(rel * cap, 1),
+                      "solves_per_s": round(len(stream_) / dt, 2),
+                      "p50_ms": round(pct(lat, 0.5), 3), "p99_ms": round(pct(lat, 0.99), 3),
+                      "mean_batch": round((b1["solves"] - b0["solves"]) / nb, 2),
+                      "p99_ms_by_L": {str(L): round(pct(sorted(v), 0.99), 2) for L, v in sorted(by_l.items())}})
+    mem1 = fc.fc_mem_stats()
+    st = fc.cg_server_stats(sv)
+    # one request at a time on exactly the requests of the capacity run: plain
+    # FP64 CG (Listing 2) and FP64 PCG, each from x = 0 to the request's tolerance
+    f64 = {}
+    for name, pre in (("f64_one_at_a_time", False), ("f64_pcg_one_at_a_time", True)):
+        t64, lat64, plans64 = 0.0, [], {}
+        for rq in base[:ncap]:
+            Lq = rq["L"]
+            if Lq not in plans64:
+                plans64[Lq] = fc.fftconv_plan_create(Lq, fc.FC_F64)
+            pk = prob(rq)
+            sd, bd = torch.tensor(pk["s"], device=dev), torch.tensor(pk["b"], device=dev)
+            xd = torch.zeros_like(sd)
+            torch.cuda.synchronize()
+            a0 = time.perf_counter()
+            fc.cg_solve(plans64[Lq], sd, bd, xd, rtol=rq["tol"], mode=fc.FC_MODE_F64, x0_zero=True, precond=pre)
+            xd.cpu()
+            a1 = time.perf_counter()
+            t64 += a1 - a0
+            lat64.append((a1 - a0) * 1e3)
+        f64[name] = {"requests": ncap, "solves_per_s": round(ncap / t64, 2),
+                     "p50_ms": round(pct(sorted(lat64), 0.5), 3),
+                     "mode": "plain FP64 CG (Listing 2)" if not pre else "FP64 PCG (same preconditioner)"}
+        del plans64
+    # spot checks: results of the first requests of the stream (closed loop,
+    # outside the timed runs) against the oracle's FP64 residual b - (C + S) x
+    nspot = min(args.serve_spot, len(base))
+    outs = [np.zeros(rq["L"] ** 2) for rq in base[:nspot]]
+    res = drain([submit(rq, o) for rq, o in zip(base[:nspot], outs)])
+    worst = 0.0
+    for rq, o in zip(base[:nspot], outs):
+        pk = prob(rq)
+        r = pk["b"] - oracle.apply_A(rq["L"], pk["s"], o)
+        worst = max(worst, float(np.linalg.norm(r) / np.linalg.norm(pk["b"])) / rq["tol"])
+    serving = {"requests_per_rate": n, "of_configuration": 20000,
+               "inputs": "16 seeded problems per size, reused by the stream's requests",
+               "capacity_per_s": round(cap, 1), "L": "2^round(U[5,11])", "tol": "{1e-6,1e-8}",
+               "slots": args.slots, "rates": rates,
+               "mem_peak_GB_measured": round((mem1["peak_bytes"] - mem0["live_bytes"]) / 1e9, 3),
+               "mem_peak_GB_reserved": round(st["peak"] / 1e9, 2), "budget_GB": 150,
+               "oracle_spot_checks": {"requests": nspot, "max_residual_over_tol": round(worst, 4)}}
+    serving.update(f64)
+    serving["capacity_vs_f64_one_at_a_time"] = round(cap / f64["f64_one_at_a_time"]["solves_per_s"], 2)
+    serving["capacity_vs_f64_pcg_one_at_a_time"] = round(cap / f64["f64_pcg_one_at_a_time"]["solves_per_s"], 2)
+    return serving
+
+
 # ------------------------------------------------------------------ ours --
 
 def run_ours(args, world, rank, local, pg):
@@ -458,22 +573,29 @@ def run_ours(args, world, rank, local, pg):
             t0 = time.perf_counter()
             fc.cg_solve_batch(gp, gs, gb, gx, **kw)
             per_size[str(gp.L)] = round(1e3 * (time.perf_counter() - t0), 2)
-        # plain FP64 CG one solve at a time on a sample of the same requests
-        # (every 8th), each from x = 0 to the same tolerance
-        f64_plans, f64_t, f64_n = {}, 0.0, 0
+        # FP64 one solve at a time on a sample of the same requests (every
+        # 8th), each from x = 0 to the same tolerance: plain CG (Listing 2) and
+        # CG with the same preconditioner
+        f64_plans, f64_t, f64p_t, f64_n = {}, 0.0, 0.0, 0
         for k in range(0, len(breqs), 8):
             Lk, pk = breqs[k]
             if Lk not in f64_plans:
                 f64_plans[Lk] = fc.fftconv_plan_create(Lk, fc.FC_F64)
             s_, b_ = (torch.tensor(pk[n_], dtype=torch.float64, device="cuda") for n_ in ("s", "b"))
-            x_ = torch.zeros_like(s_)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            r = fc.cg_solve(f64_plans[Lk], s_, b_, x_, rtol=1e-8, mode=fc.FC_MODE_F64, x0_zero=True)
-            f64_t += time.perf_counter() - t0
+            for pre in (False, True):
+                x_ = torch.zeros_like(s_)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = fc.cg_solve(f64_plans[Lk], s_, b_, x_, rtol=1e-8, mode=fc.FC_MODE_F64, x0_zero=True,
+                                precond=pre)
+                if pre:
+                    f64p_t += time.perf_counter() - t0
+                else:
+                    f64_t += time.perf_counter() - t0
+                assert r["status"] == fc.FC_OK
             f64_n += 1
-            assert r["status"] == fc.FC_OK
         f64_rate = f64_n / f64_t
+        f64p_rate = f64_n / f64p_t
         batched = {"solves": len(allr), "L": "U{64,128,256,512}", "groups": {str(g[0].L): int(g[3].shape[0])
                                                                           for g in groups},
                    "rtol": 1e-8, "mode": "mixed, Fourier-preconditioned, x0 = 0",
@@ -486,7 +608,10 @@ def run_ours(args, world, rank, local, pg):
                    "max_true_rel_resid": max(r["true_rel_resid"] for r in allr),
                    "f64_one_at_a_time": {"solves": f64_n, "solves_per_s": round(f64_rate, 1),
                                          "mode": "plain FP64 CG (Listing 2), x0 = 0"},
-                   "vs_f64_one_at_a_time": round(len(allr) / dt / f64_rate, 1)}
+                   "vs_f64_one_at_a_time": round(len(allr) / dt / f64_rate, 1),
+                   "f64_pcg_one_at_a_time": {"solves": f64_n, "solves_per_s": round(f64p_rate, 1),
+                                             "mode": "FP64 CG with the same preconditioner, x0 = 0"},
+                   "vs_f64_pcg_one_at_a_time": round(len(allr) / dt / f64p_rate, 1)}
         del groups, f64_plans
     if args.batch_solves > 0 or args.serve_requests > 0:
         sv = fc.cg_server_create(150 << 30, max_slots=args.slots)
@@ -524,68 +649,7 @@ def run_ours(args, world, rank, local, pg):
             bs1 = fc.cg_server_batches(sv)
             batched_server["batches"] = bs1["batches"] - bs0["batches"]
         if args.serve_requests > 0:
-            base = fc_inputs.request_stream(args.serve_requests, seed=777, rate_per_s=1.0)
-            probs = {}
-            for rq in base:
-                probs[rq["k"]] = fc_inputs.problem(rq["L"], seed=rq["seed"], b_kind="normal")
-            # closed-loop capacity on this mix (all submitted at once; the
-            # same requests once before, untimed, make the plans, batch
-            # workspaces and staging the run needs), then Poisson arrivals at
-            # 0.7 of it
-            ncap = min(len(base), args.serve_f64)
-            for timed in (False, True):
-                c0 = time.perf_counter()
-                drain([fc.cg_batch_submit(sv, rq["L"], probs[rq["k"]]["s"], probs[rq["k"]]["b"], rtol=rq["tol"],
-                                          mode=fc.FC_MODE_MIXED, precond=True, borrow=True) for rq in base[:ncap]])
-                cap = ncap / (time.perf_counter() - c0)
-            b0 = fc.cg_server_batches(sv)
-            stream_ = fc_inputs.request_stream(args.serve_requests, seed=777, rate_per_s=0.7 * cap)
-            t0 = time.perf_counter()
-            tickets = []
-            for rq in stream_:
-                while time.perf_counter() - t0 < rq["arrival_s"]:
-                    time.sleep(0.0001)
-                pk = probs[rq["k"]]
-                tickets.append(fc.cg_batch_submit(sv, rq["L"], pk["s"], pk["b"], rtol=rq["tol"],
-                                                  mode=fc.FC_MODE_MIXED, precond=True, borrow=True))
-            res = drain(tickets)
-            dt = time.perf_counter() - t0
-            lat = sorted(r["latency_s"] * 1e3 for r in res.values())
-            st = fc.cg_server_stats(sv)
-            b1 = fc.cg_server_batches(sv)
-            # plain one-at-a-time FP64 on exactly the requests of the capacity run
-            n64 = ncap
-            t64, lat64 = 0.0, []
-            plans64 = {}
-            for rq in base[:n64]:
-                Lq = rq["L"]
-                if Lq not in plans64:
-                    plans64[Lq] = fc.fftconv_plan_create(Lq, fc.FC_F64)
-                pk = probs[rq["k"]]
-                sd, bd = torch.tensor(pk["s"], device=dev), torch.tensor(pk["b"], device=dev)
-                xd = torch.zeros_like(sd)
-                torch.cuda.synchronize()
-                a0 = time.perf_counter()
-                fc.cg_solve(plans64[Lq], sd, bd, xd, rtol=rq["tol"], mode=fc.FC_MODE_F64, x0_zero=True)
-                xh = xd.cpu()
-                a1 = time.perf_counter()
-                t64 += a1 - a0
-                lat64.append((a1 - a0) * 1e3)
-            serving = {"requests": len(stream_), "capacity_per_s": round(cap, 1), "rate_per_s": round(0.7 * cap, 1),
-                       "L": "2^round(U[5,11])", "tol": "{1e-6,1e-8}", "slots": args.slots,
-                       "solves_per_s": round(len(stream_) / dt, 2),
-                       "p50_ms": round(lat[len(lat) // 2], 3),
-                       "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
-                       "mem_peak_GB": round(st["peak"] / 1e9, 2),
-                       "batches": b1["batches"] - b0["batches"],
-                       "mean_batch": round((b1["solves"] - b0["solves"]) / max(b1["batches"] - b0["batches"], 1), 2),
-                       "f64_one_at_a_time": {"requests": n64,
-                                             "solves_per_s": round(n64 / t64, 2) if t64 > 0 else None,
-                                             "p50_ms": round(sorted(lat64)[len(lat64) // 2], 3) if lat64 else None}}
-            if serving["f64_one_at_a_time"]["solves_per_s"]:
-                # same requests, same tolerances: closed-loop server capacity vs one-at-a-time FP64
-                serving["capacity_vs_f64_one_at_a_time"] = round(
-                    cap / serving["f64_one_at_a_time"]["solves_per_s"], 2)
+            serving = serve_run(args, fc, fc_inputs, sv, drain, dev)
         sv.close()
 
     # a fracture run under a threshold gradient (fc_fracture_run): the
@@ -665,9 +729,6 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0:
         srt = sorted(ms_mixed)
 
-        def pct(v, q):
-            return v[min(len(v) - 1, int(math.ceil(q * len(v))) - 1)]
-
         iters = [r["iters"] for r in res_mixed]
         iters64 = [r["iters"] for r in res_f64]
         f64_rate = k64 / (sum(ms_f64) * 1e-3)
@@ -708,6 +769,7 @@ def run_ours(args, world, rank, local, pg):
                           "p99_ms": round(max(ms_f64), 3),
                           "iters_per_solve": round(statistics.mean(iters64), 2)},
             "mixed_over_f64": round(value / world / f64_rate, 2),
+            "mixed_over_f64_pcg": round(value / world / (k64 / (sum(ms_f64p) * 1e-3)), 2),
             "f64_pcg": {"value": round(k64 / (sum(ms_f64p) * 1e-3), 3), "unit": "solves/s",
                         "iters_per_solve": round(statistics.mean(r["iters"] for r in res_f64p), 2)},
             "mixed_cg_no_precond": {"value": round(kmc / (sum(ms_mcg) * 1e-3), 3), "unit": "solves/s",
@@ -799,7 +861,10 @@ def main():
     ap.add_argument("--frac-steps", type=int, default=100, dest="frac_steps")
     ap.add_argument("--ensemble-runs", type=int, default=64, dest="ensemble_runs")
     ap.add_argument("--batch-solves", type=int, default=256, dest="batch_solves")
-    ap.add_argument("--serve-requests", type=int, default=600, dest="serve_requests")
+    ap.add_argument("--serve-requests", type=int, default=2000, dest="serve_requests",
+                    help="requests per arrival rate of the serving run (configuration: 20000)")
+    ap.add_argument("--serve-spot", type=int, default=200, dest="serve_spot",
+                    help="served results checked against the oracle's residual")
     ap.add_argument("--serve-f64", type=int, default=160, dest="serve_f64",
                     help="requests of the serving mix solved closed-loop and by one-at-a-time FP64")
     ap.add_argument("--slots", type=int, default=8)

@@ -193,16 +193,28 @@ int fftconv_plan_shapes(const fftconv_plan *p, int prec, int n_shapes[3], int ch
  * as one graph node per pass inside a device-side while loop.  Host only. */
 int fftconv_plan_solver(const fftconv_plan *p, int prec, int *n, int *chosen, int *threads, int *grid);
 
-/* The launch shapes of the plan's batched solves (cg_solve_batch and the
- * calls built on it): per pass, the index into the same compiled-shape
- * lists fftconv_plan_shapes counts, its radix and rows or columns per
- * block; *tuned (may be NULL) = 1 once chosen.  FP32 shapes are timed on the
- * first batched use of a mixed plan (the FFT passes of Section 3 run over
- * all problems at once) and the fastest kept for every later batch, so a
- * problem's result does not depend on the size of the batch it joins; a
- * plan created with forced shapes uses those.  Host only. */
-int fftconv_plan_batch_shapes(const fftconv_plan *p, int prec, int chosen[3], int radix[3], int per_block[3],
-                              int *tuned);
+/* The launch shapes of one of the plan's three uses of the passes of
+ * Section 3's Fourier route, per pass: the index into the compiled-shape
+ * lists that fftconv_plan_shapes counts, its radix and rows or columns per
+ * block.
+ *   FC_SHAPES_APPLY  fftconv_apply (timed in the plain modes at plan creation)
+ *   FC_SHAPES_SOLVE  the passes inside cg_solve's graphs (FP32 passes of a
+ *                    mixed plan timed again in the CG modes: the vector
+ *                    updates and dot products of Listing 2 fused in)
+ *   FC_SHAPES_BATCH  cg_solve_batch and the calls built on it: the batched
+ *                    twins (blockIdx.y = problem), FP32 ones timed in the CG
+ *                    modes on the first batched use of a mixed plan and kept
+ *                    for every later batch, so that a problem's result does
+ *                    not depend on the size of the batch it joins
+ * A plan created with forced shapes uses those everywhere (a batch keeps the
+ * standard pass C where the forced one, the TMA-staged pass, has no twin).
+ * *tuned (may be NULL) = 0 while the batched shapes are still to be chosen.
+ * Host only.  Errors: FC_EINVAL. */
+#define FC_SHAPES_APPLY 0
+#define FC_SHAPES_SOLVE 1
+#define FC_SHAPES_BATCH 2
+int fftconv_plan_shape_set(const fftconv_plan *p, int prec, int set, int chosen[3], int radix[3], int per_block[3],
+                           int *tuned);
 
 /*
  * fftconv_apply -- y = C x (Listing 4: cpyComplex, FFT, elementMult, inverse
@@ -455,6 +467,14 @@ typedef struct cg_request {
  * alone on a plan of its size).
  */
 int cg_server_create(cg_server **sv, size_t mem_budget_bytes, int max_slots, fc_stream_t stream);
+
+/* Make plans for size L ahead of requests, so that no request waits for a
+ * plan's set-up (spectrum, tables, autotuning: 20-90 ms): up to nplans idle
+ * plans (at most the server's plans per size, 2 unless
+ * FC_SERVER_PLANS_PER_SIZE says otherwise), each within the memory budget.
+ * Blocks the calling thread while the plans are made; requests keep running.
+ * Errors: FC_EINVAL, FC_EBUDGET (a plan does not fit), FC_ENOMEM, FC_ECUDA. */
+int cg_server_reserve(cg_server *sv, int L, int nplans);
 
 /* Queue a request; *ticket identifies it.  FC_EBUDGET if its plan can never
  * fit the budget, FC_EINVAL for bad arguments.  Returns at once. */

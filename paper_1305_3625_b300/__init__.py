@@ -32,6 +32,9 @@ FC_GREEN_CELL = 1
 FC_MODE_F64 = 0
 FC_MODE_MIXED = 1
 FC_REQ_BORROW = 1
+FC_SHAPES_APPLY = 0
+FC_SHAPES_SOLVE = 1
+FC_SHAPES_BATCH = 2
 FC_INJECT_ALLOC = 1
 FC_INJECT_BARRIER = 2
 FC_INJECT_TMA = 3
@@ -112,7 +115,7 @@ def _load():
     lib.fftconv_plan_shapes.argtypes = [vp, i, ip3, ip3, ip3, ip3]
     ipt = ctypes.POINTER(ctypes.c_int)
     lib.fftconv_plan_solver.argtypes = [vp, i, ipt, ipt, ipt, ipt]
-    lib.fftconv_plan_batch_shapes.argtypes = [vp, i, ip3, ip3, ip3, ipt]
+    lib.fftconv_plan_shape_set.argtypes = [vp, i, i, ip3, ip3, ip3, ipt]
     lib.fftconv_plan_destroy.argtypes = [vp]
     lib.fftconv_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i),
                                       ctypes.POINTER(sz)]
@@ -137,6 +140,7 @@ def _load():
     lib.cg_server_batches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                       ctypes.POINTER(i)]
     lib.cg_server_destroy.argtypes = [vp]
+    lib.cg_server_reserve.argtypes = [vp, i, i]
     lib.fc_mem_stats.argtypes = [ctypes.POINTER(sz), ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_longlong), i]
     lib.fftconv_plan_check_guards.argtypes = [vp, ctypes.POINTER(i)]
     lib.fc_debug_inject.argtypes = [vp, i, ctypes.c_longlong]
@@ -446,14 +450,18 @@ def fftconv_plan_shapes(plan: Plan, prec: int) -> dict:
     return {"n_shapes": list(n), "chosen": list(ch), "radix": list(rad), "per_block": list(per)}
 
 
-def fftconv_plan_batch_shapes(plan: Plan, prec: int) -> dict:
-    """Launch shapes of the plan's batched solves (indices into the same lists)."""
+def fftconv_plan_shape_set(plan: Plan, prec: int, which: int) -> dict:
+    """Launch shapes of FC_SHAPES_APPLY, FC_SHAPES_SOLVE or FC_SHAPES_BATCH."""
     ip3 = ctypes.c_int * 3
     ch, rd, pb, tu = ip3(), ip3(), ip3(), ctypes.c_int()
-    rc = _lib.fftconv_plan_batch_shapes(plan.handle, int(prec), ch, rd, pb, ctypes.byref(tu))
+    rc = _lib.fftconv_plan_shape_set(plan.handle, int(prec), int(which), ch, rd, pb, ctypes.byref(tu))
     if rc != FC_OK:
-        raise FcError(rc, "fftconv_plan_batch_shapes")
+        raise FcError(rc, "fftconv_plan_shape_set")
     return {"chosen": list(ch), "radix": list(rd), "per_block": list(pb), "tuned": bool(tu.value)}
+
+
+def fftconv_plan_batch_shapes(plan: Plan, prec: int) -> dict:
+    return fftconv_plan_shape_set(plan, prec, FC_SHAPES_BATCH)
 
 
 def fftconv_plan_solver(plan: Plan, prec: int) -> dict:
@@ -497,6 +505,13 @@ def cg_server_create(mem_budget_bytes: int, max_slots: int = 16) -> Server:
     if rc != FC_OK:
         raise FcError(rc, "cg_server_create")
     return Server(h)
+
+
+def cg_server_reserve(sv: Server, L: int, nplans: int = 2) -> None:
+    """Make up to nplans plans of size L before requests need them."""
+    rc = _lib.cg_server_reserve(sv.handle, int(L), int(nplans))
+    if rc != FC_OK:
+        raise FcError(rc, "cg_server_reserve")
 
 
 def cg_batch_submit(sv: Server, L: int, s, b, x_out=None, rtol: float = 1e-8, mode: int = FC_MODE_MIXED,

@@ -95,9 +95,10 @@ struct BatchArgs {
 // with the folded correction; PCG first half (x, r update, transform r);
 // PCG second half (p = z + beta p, transform p).
 enum { RF_PLAIN = 0, RF_CG = 1, RF_XUPD = 2, RF_PCG_R = 3, RF_PCG_P = 4 };
-// Pass C modes: plain output; CG product q; FP64 true residual; PCG
-// preconditioned residual z = P M^-1 r.
-enum { RI_PLAIN = 0, RI_CG = 1, RI_RESID = 2, RI_PCG_Z = 3 };
+// Pass C modes: plain output; CG product q (five sums); FP64 true residual;
+// PCG preconditioned residual z = P M^-1 r (sums r.z, r.r); PCG product q
+// (sum p.q).
+enum { RI_PLAIN = 0, RI_CG = 1, RI_RESID = 2, RI_PCG_Z = 3, RI_PQ = 4 };
 
 template <typename T>
 struct RowFwdArgs {
@@ -135,6 +136,7 @@ struct RowInvArgs {
     const T* cr;
     T* cq;                       // RI_CG: product q = P (C p + s p)
     T* cz;                       // RI_PCG_Z: preconditioned residual
+                                 // (RI_PQ: q = P (C p + s p) into cq, p.q only)
     const uint8_t* mask;         // 1 = active fibre (null: all active)
     const double *x64, *b64, *s64;
     double* r64;                 // RI_RESID: r = P (b - C x - s x)
@@ -185,12 +187,53 @@ __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq
     if (h_inner) cudaGraphSetConditional(h_inner, d == 0 ? 1u : 0u);
 }
 
-// PCG (Fourier preconditioner): after z = M^-1 r, beta = r.z / r_prev.z_prev
-// for the direction update of the next pass.
-__device__ __forceinline__ void pcg_z_decide(CgState* st, double rz) {
+// Preconditioned CG (Listing 2 with the Fourier preconditioner M), one
+// iteration as the inner loop body runs it: x += alpha p and r -= alpha q
+// (pass A; at the start of a run r from the true residual), z = M^-1 r
+// (passes B, C: pcg_zr_decide, which also takes the stopping test), p = z +
+// beta p (pass A), q = A p (passes B, C: pcg_alpha_decide).
+
+// After q = A p: alpha = r.z / p.q (the step of Hestenes and Stiefel with
+// the preconditioner).  A breakdown (p.q not positive, alpha not finite) or
+// the iteration cap ends the run after the next update of x and r: the
+// decision of the z pass that follows then stops the loop.
+__device__ __forceinline__ void pcg_alpha_decide(CgState* st, double pq) {
+    st->pq = pq;
+    double alpha = st->rz / pq;
+    int d = st->inner_done;
+    if (!(pq > 0.0) || !isfinite(alpha)) {
+        d = 3;
+        alpha = 0.0;
+    }
+    st->iter += 1;
+    st->cycle_iter += 1;
+    if (d == 0 && (st->iter >= st->max_iter || st->cycle_iter >= st->cycle_max)) d = 2;
+    if (st->tma_err) d = 4;
+    st->alpha = alpha;
+    st->first = 0;
+    st->inner_done = d;
+}
+
+// After z = M^-1 r of the updated residual: beta = r.z / r_prev.z_prev for
+// the next direction, and the stopping test on r.r itself (summed directly
+// from r, not from the recursion |r - alpha q|^2).  Sets the loop condition;
+// once the run has ended (idle) the rest of the body returns at entry.
+__device__ __forceinline__ void pcg_zr_decide(CgState* st, double rz, double rr, unsigned long long h_inner) {
+    st->rr = rr;
+    int d = st->inner_done;
+    if (d == 0) {
+        if (!isfinite(rz) || !isfinite(rr))
+            d = 3;
+        else if (rr <= st->tol2)
+            d = 1;
+    }
+    if (st->tma_err) d = 4;
     st->beta = (st->first || !(st->rz > 0.0)) ? 0.0 : rz / st->rz;
     st->rz_prev = st->rz;
     st->rz = rz;
+    st->inner_done = d;
+    st->idle = d != 0;
+    if (h_inner) cudaGraphSetConditional(h_inner, d == 0 ? 1u : 0u);
 }
 
 // Decide the outer loop after a true residual r = P (b - A x): stop when

@@ -499,18 +499,55 @@ struct ArgmaxCtl {
 // finish reduces the per-block winners in block order.
 // (value, index) order of the breaking rule: larger |x|/t first, then the
 // lower index; an index of -1 marks "no active site".
+// A positive double (its bits) as a float truncated to 24 significant bits,
+// by integer operations; 0 outside [2^-100, 2^101) (or for a number that is
+// not positive), where quotients of two such floats stay clear of the range
+// in which the fast FP32 division loses its 2-ulp bound.
+__device__ __forceinline__ float trunc_float(long long bits) {
+    const int e = (int)(bits >> 52);  // biased exponent (a set sign bit makes it negative)
+    if (e < 1023 - 100 || e > 1023 + 100) return 0.0f;
+    const unsigned fb = ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((bits >> 29) & 0x7fffff);
+    return __uint_as_float(fb);
+}
+
 __device__ __forceinline__ bool am_better(double ov, long long oi, double mv, long long mi) {
     return oi >= 0 && (mi < 0 || ov > mv || (ov == mv && oi < mi));
 }
 
-__device__ __forceinline__ void am_block_reduce(double* sv, long long* si) {
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s && am_better(sv[threadIdx.x + s], si[threadIdx.x + s], sv[threadIdx.x], si[threadIdx.x])) {
-            sv[threadIdx.x] = sv[threadIdx.x + s];
-            si[threadIdx.x] = si[threadIdx.x + s];
+// The best (value, index) of a block by the breaking rule's order: warp
+// shuffles, then warp 0 over the warps' winners (valid in thread 0).  The
+// order is total, so the winner does not depend on the reduction order.
+__device__ __forceinline__ void am_block_reduce(double& bv, long long& bi) {
+    __shared__ double sv[32];
+    __shared__ long long si[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (am_better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
         }
-        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        bv = lane < nw ? sv[lane] : -1.0;
+        bi = lane < nw ? si[lane] : -1;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+            const long long oi = __shfl_down_sync(0xffffffffu, bi, off);
+            if (am_better(ov, oi, bv, bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
     }
 }
 
@@ -542,25 +579,81 @@ __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, 
     pv += (long)blockIdx.y * gridDim.x;
     pi += (long)blockIdx.y * gridDim.x;
     ctl += blockIdx.y;
-    __shared__ double sv[256];
-    __shared__ long long si[256];
     __shared__ bool is_last;
     double bv = -1.0;
     long long bi = -1;
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-        if (!mask[i]) continue;
-        double v = fabs(x[i]) / t[i];
+    // The exact ratio |x|/t (IEEE FP64 division) decides, but a thread first
+    // ranks its sites by an FP32 estimate and divides exactly only for the
+    // sites whose estimate ends within the estimate's error band of its
+    // largest one (this part's FP64 unit is slow).  The estimate's operands
+    // are the doubles' exponents and leading 23 mantissa bits reassembled as
+    // floats by integer operations (a double-to-float conversion runs on the
+    // FP64 unit), so each is within 2^-23 below its double; with a 2-ulp
+    // division the estimate is within 6e-7 of the exact ratio.  The thread's
+    // best site therefore ends with an estimate within 1.2e-6 of the largest
+    // and is never dropped from the candidates (band 2e-6); sites with an
+    // operand outside [2^-100, 2^101), and candidates beyond the four a thread
+    // keeps, are divided at once.
+    constexpr float kBand = 2e-6f;
+    float emax = -1.0f;
+    float cest[4];
+    long cidx[4];
+    int nc = 0;
+    auto exact = [&](long i, double xa, double tv) {
+        const double v = xa / tv;
         if (am_better(v, i, bv, bi)) {
             bv = v;
             bi = i;
         }
+    };
+    const long stride = (long)gridDim.x * blockDim.x;
+    // four sites per round: their loads are issued together, one memory round
+    // trip per round instead of one per site
+    for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += 4 * stride) {
+        uint8_t mv[4];
+        double xv[4], tv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long i = i0 + u * stride;
+            const bool in = i < N;
+            mv[u] = in ? mask[i] : (uint8_t)0;
+            xv[u] = in ? x[i] : 0.0;
+            tv[u] = in ? t[i] : 1.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!mv[u]) continue;
+            const long i = i0 + u * stride;
+            const float xf = trunc_float(__double_as_longlong(xv[u]) & 0x7fffffffffffffffLL);
+            const float tf = trunc_float(__double_as_longlong(tv[u]));
+            if (!(xf > 0.0f && tf > 0.0f)) {
+                exact(i, fabs(xv[u]), tv[u]);
+                continue;
+            }
+            const float est = __fdividef(xf, tf);
+            if (est > emax * (1.0f + kBand)) {  // a new leader: the old candidates fall behind
+                emax = est;
+                nc = 0;
+            } else if (est < emax * (1.0f - kBand)) {
+                continue;
+            }
+            if (est > emax) emax = est;
+            if (nc < 4) {
+                cest[nc] = est;
+                cidx[nc] = i;
+                ++nc;
+            } else {
+                exact(i, fabs(xv[u]), tv[u]);
+            }
+        }
     }
-    sv[threadIdx.x] = bv;
-    si[threadIdx.x] = bi;
-    am_block_reduce(sv, si);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (c < nc && cest[c] >= emax * (1.0f - kBand)) exact(cidx[c], fabs(x[cidx[c]]), t[cidx[c]]);
+    am_block_reduce(bv, bi);
     if (threadIdx.x == 0) {
-        pv[blockIdx.x] = sv[0];
-        pi[blockIdx.x] = si[0];
+        pv[blockIdx.x] = bv;
+        pi[blockIdx.x] = bi;
         __threadfence();
         is_last = atomicAdd(&ctl->cnt, 1u) == gridDim.x - 1;
     }
@@ -577,13 +670,11 @@ __global__ void __launch_bounds__(256) k_masked_argmax(long N, const double* t, 
             bi = oi;
         }
     }
-    sv[threadIdx.x] = bv;
-    si[threadIdx.x] = bi;
-    am_block_reduce(sv, si);
+    am_block_reduce(bv, bi);
     if (threadIdx.x == 0) {
-        const long long gi = si[0];
+        const long long gi = bi;
         *removed = gi;
-        if (ratio) *ratio = sv[0];  // max |x|/t (-1 with no active site)
+        if (ratio) *ratio = bv;  // max |x|/t (-1 with no active site)
         if (kidx) {  // batched runs: the removal, for the next solve's residual update
             kidx[blockIdx.y] = gi;
             kx[blockIdx.y] = gi >= 0 ? x[gi] : 0.0;
@@ -693,7 +784,8 @@ constexpr unsigned char kGuardByte = 0xC5;
 struct PrecRes {
     bool on = false;
     Variants v;
-    int sel[3] = {0, 0, 0};  // chosen shape of pass A, B, C
+    int sel[3] = {0, 0, 0};  // chosen shape of pass A, B, C for fftconv_apply (plain passes)
+    int sel_cg[3] = {0, 0, 0};  // chosen shape of each pass inside solves (timed in the CG modes)
     int sel_b[3] = {0, 0, 0};  // chosen batched twin of pass A, B, C (indices into the same lists)
     bool tuned_b = false;      // sel_b decided (tuned on first batched use, or forced)
     bool tune_off = false;     // the plan was made without timing (no_autotune, FC_AUTOTUNE=0)
@@ -709,6 +801,9 @@ struct PrecRes {
     const KV& rfwd() const { return v.rfwd[sel[0]]; }
     const KV& colc() const { return v.colc[sel[1]]; }
     const KV& rinv() const { return v.rinv[sel[2]]; }
+    const KV& rfwd_cg() const { return v.rfwd[sel_cg[0]]; }
+    const KV& colc_cg() const { return v.colc[sel_cg[1]]; }
+    const KV& rinv_cg() const { return v.rinv[sel_cg[2]]; }
     const void* tws(int E) const { return twst[E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : 0]; }
     // every shape this precision may launch has its stage twiddle table
     bool tables_ok(int M) const {
@@ -1026,7 +1121,7 @@ void tune_store(const char* key, int idx) {
 // time one launch shape of one pass (kind 0: A, 1: B, 2: C), PLAIN mode
 template <typename T>
 int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStream_t s, cudaEvent_t e0,
-               cudaEvent_t e1, float* ms) {
+               cudaEvent_t e1, float* ms, T* const* cgv = nullptr) {
     const KV& kv = kind == 0 ? R.v.rfwd[k] : (kind == 1 ? R.v.colc[k] : R.v.rinv[k]);
     const cpx<T>* tw = (const cpx<T>*)R.tws(kv.E);
     RowFwdArgs<T> a{};
@@ -1043,6 +1138,22 @@ int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStr
     c.st = p->st;
     c.Z = (const cpx<T>*)R.Z;
     c.tw = tw;
+    if (cgv) {
+        // the solver's modes: pass A's CG update of x and r (x += a p, r -= a q),
+        // pass C's product q = C p + s p with its five sums
+        a.mode = RF_PCG_R;
+        a.cx = cgv[0];
+        a.cr = cgv[1];
+        a.cp = cgv[2];
+        a.cq = cgv[3];
+        a.st = p->st;
+        c.mode = RI_CG;
+        c.cr = cgv[1];
+        c.cp = cgv[2];
+        c.cq = cgv[3];
+        c.s = cgv[4];
+        c.part = p->part;
+    }
     if (kv.tma && !R.tma_ok) {  // no tensor map for this size: never chosen
         *ms = 1e30f;
         return FC_OK;
@@ -1078,13 +1189,14 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
     const char* venv = getenv("FC_TUNE_VERBOSE");
     const bool verbose = venv && strcmp(venv, "0");
     const char* names[3] = {"rfwd", "colc", "rinv"};
-    bool need[3] = {false, false, false};
-    char keys[3][96];
+    bool need[3] = {false, false, false}, need_cg[3] = {false, false, false};
+    char keys[3][96], keys_cg[3][96];
     for (int kind = 0; kind < 3; ++kind) {
         if (forced[kind] > 0) {
             if (forced[kind] > n[kind]) return FC_EINVAL;
             if (kind == 2 && R.v.rinv[forced[kind] - 1].tma && !R.tma_ok) return FC_EINVAL;
             R.sel[kind] = forced[kind] - 1;
+            R.sel_cg[kind] = forced[kind] - 1;
             // batched solves take the same shape where it has a twin (not the TMA pass C)
             const KV& tw = kind == 0 ? R.v.rfwd_b[R.sel[kind]] : (kind == 1 ? R.v.colc_b[R.sel[kind]]
                                                                               : R.v.rinv_b[R.sel[kind]]);
@@ -1092,6 +1204,7 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
             continue;
         }
         R.sel[kind] = 0;
+        R.sel_cg[kind] = 0;
         if (n[kind] <= 1) continue;
         snprintf(keys[kind], sizeof(keys[kind]), "%s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M,
                  p->L, names[kind], n[kind]);
@@ -1100,10 +1213,18 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
             R.sel[kind] = idx;
         else
             need[kind] = timing;
+        R.sel_cg[kind] = R.sel[kind];  // the column pass is the same in every mode
+        if (kind == 1 || sizeof(T) != 4 || !(p->prec & FC_F64)) continue;  // solves: FP32 passes of mixed plans
+        snprintf(keys_cg[kind], sizeof(keys_cg[kind]), "f32 M=%d L=%d %s_cg n=%d ", p->M, p->L, names[kind], n[kind]);
+        if (tune_lookup(keys_cg[kind], &idx) && idx >= 0 && idx < n[kind] &&
+            !(kind == 2 && R.v.rinv[idx].tma && !R.tma_ok))
+            R.sel_cg[kind] = idx;
+        else
+            need_cg[kind] = timing;
     }
     if (forced[0] > 0 || forced[1] > 0 || forced[2] > 0 || n[0] <= 1) R.tuned_b = true;  // no batched tuning
     R.tune_off = !timing;
-    if (!need[0] && !need[1] && !need[2]) return FC_OK;
+    if (!need[0] && !need[1] && !need[2] && !need_cg[0] && !need_cg[2]) return FC_OK;
     T *x = nullptr, *y = nullptr;
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -1138,6 +1259,35 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
             tune_store(keys[kind], bi);
         }
     }
+    R.sel_cg[1] = R.sel[1];
+    for (int kind = 0; kind < 3; kind += 2)
+        if (need[kind] && !need_cg[kind] && !(sizeof(T) == 4 && (p->prec & FC_F64))) R.sel_cg[kind] = R.sel[kind];
+    // inside solves passes A and C run in the CG modes (vector updates, five
+    // dot products): their shapes are timed again in those modes on the
+    // plan's FP32 vectors (zeroed; the plan's state, fresh, takes the steps)
+    for (int kind = 0; kind < 3 && !rc; ++kind) {
+        if (!need_cg[kind]) continue;
+        T* cgv[5] = {(T*)p->d32, (T*)p->r32, (T*)p->p32v, (T*)p->q32, (T*)p->s32};
+        for (int i = 0; i < 5 && !rc; ++i)
+            if (cudaMemsetAsync(cgv[i], 0, sizeof(T) * p->N, s) != cudaSuccess)
+                rc = set_cuda_err(cudaGetLastError(), "autotune set-up");
+        float best = 1e30f;
+        int bi = 0;
+        for (int k = 0; k < n[kind] && !rc; ++k) {
+            float ms = 0;
+            rc = time_shape<T>(p, R, kind, k, x, y, s, e0, e1, &ms, cgv);
+            if (!rc && verbose)
+                fprintf(stderr, "[fftconv tune] %s shape %d (CG mode): %.3f us\n", keys_cg[kind], k, ms * 1e3f);
+            if (!rc && ms < best) {
+                best = ms;
+                bi = k;
+            }
+        }
+        if (!rc) {
+            R.sel_cg[kind] = bi;
+            tune_store(keys_cg[kind], bi);
+        }
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (s) {
@@ -1154,7 +1304,7 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
 namespace {
 
 // The batched twins of each pass, timed like the single-problem shapes
-// (plain modes, 2 warm-up and 5 timed launches) over nb problems at once,
+// (in the solver's modes, 2 warm-up and 5 timed launches) over nb problems at once,
 // nb = min(16, 64 MB of intermediate); the fastest is kept for every batched
 // solve of the plan, whatever its batch size, so that a problem's arithmetic
 // does not depend on the batch it joins.  Choices are cached like the
@@ -1172,7 +1322,7 @@ int autotune_batched(fftconv_plan* p, PrecRes& R) {
     const bool verbose = venv && strcmp(venv, "0");
     const KV* lists[3] = {R.v.rfwd_b, R.v.colc_b, R.v.rinv_b};
     const int n[3] = {R.v.n_rfwd, R.v.n_colc, R.v.n_rinv};
-    const char* names[3] = {"rfwd_b", "colc_b", "rinv_b"};
+    const char* names[3] = {"rfwd_bcg", "colc_b", "rinv_bcg"};
     char keys[3][96];
     bool need[3] = {false, false, false};
     for (int kind = 0; kind < 3; ++kind) {
@@ -1186,14 +1336,17 @@ int autotune_batched(fftconv_plan* p, PrecRes& R) {
             need[kind] = timing;
     }
     if (!need[0] && !need[1] && !need[2]) return FC_OK;
-    const long N = p->N, zs = (long)(p->M / 2) * p->L;
+    const long N = p->N, zs = (long)(p->M / 2) * p->L, ps = 3 * (long)(p->L + 1);
     long nbt = (64L << 20) / (long)(zs * sizeof(cpx<T>));
     if (nbt > 16) nbt = 16;
     if (nbt < 1) nbt = 1;
     cudaStream_t s = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     void* buf = nullptr;
-    const size_t bytes = sizeof(T) * 2 * (size_t)nbt * N + sizeof(cpx<T>) * (size_t)nbt * zs + sizeof(CgState) * nbt;
+    // six vectors (x, r, p, q, s, output) per problem, the intermediate, the
+    // states and partial sums
+    const size_t bytes = sizeof(T) * 6 * (size_t)nbt * N + sizeof(cpx<T>) * (size_t)nbt * zs +
+                         sizeof(CgState) * nbt + sizeof(double) * (size_t)nbt * ps;
     int rc = FC_OK;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess)
@@ -1203,12 +1356,13 @@ int autotune_batched(fftconv_plan* p, PrecRes& R) {
         rc = FC_ENOMEM;
     }
     if (!rc && cudaMemsetAsync(buf, 0, bytes, s) != cudaSuccess)
-        rc = set_cuda_err(cudaGetLastError(), "batched autotune set-up");
-    T* x = (T*)buf;
-    T* y = x + nbt * N;
-    cpx<T>* Z = (cpx<T>*)(y + nbt * N);
+        rc = set_cuda_err(cudaGetLastError(), "batched autotune set-up");  // states: first = 0, alpha = 0
+    T* cv[6];
+    for (int i = 0; i < 6; ++i) cv[i] = (T*)buf + (size_t)i * nbt * N;
+    cpx<T>* Z = (cpx<T>*)(cv[5] + nbt * N);
     CgState* st = (CgState*)(Z + nbt * zs);
-    const BatchArgs bb{0, BatchStride{N, zs, 0, 0}};
+    double* part = (double*)(st + nbt);
+    const BatchArgs bb{0, BatchStride{N, zs, 0, ps}};
     for (int kind = 0; kind < 3 && !rc; ++kind) {
         if (!need[kind]) continue;
         float best = 1e30f;
@@ -1217,19 +1371,30 @@ int autotune_batched(fftconv_plan* p, PrecRes& R) {
             const KV& kv = lists[kind][k];
             if (!kv.f) continue;
             const cpx<T>* tw = (const cpx<T>*)R.tws(kv.E);
+            // the modes batched solves run: pass A's CG update of x and r, pass
+            // C's product with its five sums (zeroed vectors, fresh states)
             RowFwdArgs<T> a{};
             a.L = p->L;
-            a.mode = RF_PLAIN;
-            a.x = x;
+            a.mode = RF_PCG_R;
+            a.cx = cv[0];
+            a.cr = cv[1];
+            a.cp = cv[2];
+            a.cq = cv[3];
             a.st = st;
+            a.part = part;
             a.Z = Z;
             a.tw = tw;
             ColArgs<T> b{p->L, Z, (const T*)R.Gq, tw, st, 0};
             RowInvArgs<T> c{};
             c.L = p->L;
-            c.mode = RI_PLAIN;
-            c.y = y;
+            c.mode = RI_CG;
+            c.cr = cv[1];
+            c.cp = cv[2];
+            c.cq = cv[3];
+            c.s = cv[4];
+            c.y = cv[5];
             c.st = st;
+            c.part = part;
             c.Z = Z;
             c.tw = tw;
             const int gx = kind == 1 ? col_grid(p, kv) : row_grid(p, kv);
@@ -1524,7 +1689,9 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
     {
         int g = L;  // row passes never use more blocks than rows
         FC_TRY(dalloc(p, (void**)&p->part, sizeof(double) * 3 * (size_t)(g + 1)));
-        p->am_grid = grid_1d(N, 256);
+        // 16 sites per thread (the FP32 estimate then skips most exact divisions)
+        const long ag = (N + 4095) / 4096;
+        p->am_grid = ag < 1 ? 1 : (ag > 2 * 148 ? 2 * 148 : (int)ag);
         FC_TRY(dalloc(p, (void**)&p->am_v, sizeof(double) * p->am_grid));
         FC_TRY(dalloc(p, (void**)&p->am_i, sizeof(long long) * p->am_grid));
         FC_TRY(dalloc(p, (void**)&p->am_ctl, sizeof(ArgmaxCtl)));
@@ -1618,18 +1785,28 @@ extern "C" int fftconv_plan_shapes(const fftconv_plan* p, int prec, int n_shapes
     return FC_OK;
 }
 
-extern "C" int fftconv_plan_batch_shapes(const fftconv_plan* p, int prec, int chosen[3], int radix[3],
-                                         int per_block[3], int* tuned) {
-    if (!p || !chosen || !radix || !per_block) return FC_EINVAL;
+extern "C" int fftconv_plan_shape_set(const fftconv_plan* p, int prec, int set, int chosen[3], int radix[3],
+                                      int per_block[3], int* tuned) {
+    if (!p || !chosen || !radix || !per_block || set < FC_SHAPES_APPLY || set > FC_SHAPES_BATCH) return FC_EINVAL;
     const PrecRes* R = prec == FC_F32 ? (p->p32.on ? &p->p32 : nullptr) : (prec == FC_F64 && p->p64.on ? &p->p64 : nullptr);
     if (!R) return FC_EINVAL;
-    const KV* k3[3] = {&R->v.rfwd_b[R->sel_b[0]], &R->v.colc_b[R->sel_b[1]], &R->v.rinv_b[R->sel_b[2]]};
+    const int* sel = set == FC_SHAPES_APPLY ? R->sel : (set == FC_SHAPES_SOLVE ? R->sel_cg : R->sel_b);
+    const KV* k3[3];
+    if (set == FC_SHAPES_BATCH) {
+        k3[0] = &R->v.rfwd_b[sel[0]];
+        k3[1] = &R->v.colc_b[sel[1]];
+        k3[2] = &R->v.rinv_b[sel[2]];
+    } else {
+        k3[0] = &R->v.rfwd[sel[0]];
+        k3[1] = &R->v.colc[sel[1]];
+        k3[2] = &R->v.rinv[sel[2]];
+    }
     for (int i = 0; i < 3; ++i) {
-        chosen[i] = R->sel_b[i];
+        chosen[i] = sel[i];
         radix[i] = k3[i]->E;
         per_block[i] = k3[i]->per;
     }
-    if (tuned) *tuned = R->tuned_b ? 1 : 0;
+    if (tuned) *tuned = set == FC_SHAPES_BATCH ? (R->tuned_b ? 1 : 0) : 1;
     return FC_OK;
 }
 
@@ -1703,7 +1880,7 @@ int cg_product_t(fftconv_plan* p, PrecRes& R, const T* pv, const T* rv, const T*
     }
     int rc = FC_OK;
     if (cudaMemsetAsync(st, 0, sizeof(CgState), s) != cudaSuccess) rc = set_cuda_err(cudaGetLastError(), "memset");
-    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+    const KV &ka = R.rfwd_cg(), &kb = R.colc_cg(), &kc = R.rinv_cg();
     if (!rc) {
         RowFwdArgs<T> a{};
         a.L = p->L;
@@ -1949,17 +2126,19 @@ struct GraphBuilder {
         if (e != cudaSuccess) rc = set_cuda_err(e, "cudaGraphAddDependencies(programmatic)");
         return n;
     }
+    // A conditional node: WHILE (the body runs while the handle is non-zero)
+    // or, with once, IF (the body runs once if it is).
     cudaGraph_t while_node(cudaGraph_t g, const cudaGraphNode_t* deps, int ndeps, cudaGraphConditionalHandle h,
-                           cudaGraphNode_t* node) {
+                           cudaGraphNode_t* node, bool once = false) {
         if (rc) return nullptr;
         cudaGraphNodeParams np{};
         np.type = cudaGraphNodeTypeConditional;
         np.conditional.handle = h;
-        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.type = once ? cudaGraphCondTypeIf : cudaGraphCondTypeWhile;
         np.conditional.size = 1;
         cudaError_t e = cudaGraphAddNode(node, g, deps, nullptr, ndeps, &np);
         if (e != cudaSuccess) {
-            rc = set_cuda_err(e, "cudaGraphAddNode(while)");
+            rc = set_cuda_err(e, once ? "cudaGraphAddNode(if)" : "cudaGraphAddNode(while)");
             return nullptr;
         }
         return np.conditional.phGraph_out[0];
@@ -2030,9 +2209,9 @@ SolveView plan_view(fftconv_plan* p) {
 
 // The launch shapes of a solve graph: the tuned ones, or for batched solves
 // the batched forms of the standard shapes.
-const KV& rfwd_shape(const PrecRes& R, bool batched) { return batched ? R.v.rfwd_b[R.sel_b[0]] : R.rfwd(); }
-const KV& colc_shape(const PrecRes& R, bool batched) { return batched ? R.v.colc_b[R.sel_b[1]] : R.colc(); }
-const KV& rinv_shape(const PrecRes& R, bool batched) { return batched ? R.v.rinv_b[R.sel_b[2]] : R.rinv(); }
+const KV& rfwd_shape(const PrecRes& R, bool batched) { return batched ? R.v.rfwd_b[R.sel_b[0]] : R.rfwd_cg(); }
+const KV& colc_shape(const PrecRes& R, bool batched) { return batched ? R.v.colc_b[R.sel_b[1]] : R.colc_cg(); }
+const KV& rinv_shape(const PrecRes& R, bool batched) { return batched ? R.v.rinv_b[R.sel_b[2]] : R.rinv_cg(); }
 
 // Pass C as a graph node following prev (the TMA-staged shape gets its
 // tensor-map arguments).
@@ -2096,9 +2275,13 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     if (V.batched) batch_ctl_node(gb, body, nC, V, 0, h_inner, nullptr);
 }
 
-// Inner body of preconditioned CG: A1 (x, r update; transform r) -> B1 with
-// the preconditioner spectrum -> C1 (z = M^-1 r, r.z, beta) -> A2 (p = z +
-// beta p; transform p) -> B2 with the kernel spectrum -> C2 (q, step decision).
+// The inner loop body of preconditioned CG (pcg_zr_decide, pcg_alpha_decide):
+// A1 (x += alpha p, r -= alpha q, or at the start of a run r from the true
+// residual; transform r) -> B1 with the preconditioner spectrum -> C1
+// (z = M^-1 r, r.z and r.r: beta, the stopping test on r.r, the loop
+// condition) -> A2 (p = z + beta p; transform p) -> B2 with the kernel
+// spectrum -> C2 (q = A p, p.q: alpha).  Once C1 has ended the run, A2, B2
+// and C2 return at entry; x already holds the last update.
 template <typename T>
 void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, const SolveView& V, T* cx,
                         T* cr, T* cp, T* cq, T* cz, const T* s, const T* pq, const double* r64_start,
@@ -2127,9 +2310,11 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c1.mask = V.mask;
     c1.st = V.st;
     c1.part = V.part;
+    c1.h_inner = V.batched ? 0 : h_inner;
     c1.Z = V.Z<T>();
     c1.tw = (const cpx<T>*)R.tws(kc.E);
     cudaGraphNode_t n3 = graph_rinv<T>(gb, body, n2, p, R, kc, V, c1, V.inner());
+    if (V.batched) batch_ctl_node(gb, body, n3, V, 0, h_inner, &n3);
     RowFwdArgs<T> a2{};
     a2.L = p->L;
     a2.mode = RF_PCG_P;
@@ -2140,24 +2325,24 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a2.part = V.part;
     a2.Z = V.Z<T>();
     a2.tw = (const cpx<T>*)R.tws(ka.E);
-    cudaGraphNode_t n4 = pass_node(gb, body, n3, ka, V.grid(row_grid(p, ka)), V, a2, V.inner());
-    ColArgs<T> b2{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, 0};
+    cudaGraphNode_t n4 = V.batched ? gb.kernel(body, &n3, 1, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a2,
+                                               V.inner())
+                                   : pass_node(gb, body, n3, ka, V.grid(row_grid(p, ka)), V, a2, V.inner());
+    // the single-problem column pass returns at entry once the run has ended
+    ColArgs<T> b2{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, V.batched ? 0 : GATE_IDLE};
     cudaGraphNode_t n5 = pass_node(gb, body, n4, kb, V.grid(col_grid(p, kb)), V, b2, V.inner(true));
     RowInvArgs<T> c2{};
     c2.L = p->L;
-    c2.mode = RI_CG;
+    c2.mode = RI_PQ;
     c2.s = s;
     c2.cp = cp;
-    c2.cr = cr;
     c2.cq = cq;
     c2.mask = V.mask;
     c2.st = V.st;
     c2.part = V.part;
-    c2.h_inner = V.batched ? 0 : h_inner;
     c2.Z = V.Z<T>();
     c2.tw = (const cpx<T>*)R.tws(kc.E);
-    cudaGraphNode_t n6 = graph_rinv<T>(gb, body, n5, p, R, kc, V, c2, V.inner());
-    if (V.batched) batch_ctl_node(gb, body, n6, V, 0, h_inner, nullptr);
+    graph_rinv<T>(gb, body, n5, p, R, kc, V, c2, V.inner());
 }
 
 // Add one solve (prologue, outer loop) to graph g as a branch with no
@@ -2262,7 +2447,9 @@ int add_solve_nodes(fftconv_plan* p, const SolveView& V, int mode, bool precond,
                                        h_inner);
         }
         const CgState* cst = V.st;
-        if (mixed) {
+        if (precond) {
+            // the residual half updates x before each stopping test: nothing left to apply
+        } else if (mixed) {
             float* fx = V.d32;
             const float* fp = V.p32v;
             gb.kernel(outer, &nInner, 1, (const void*)k_cg_final<float>, V.grid(grid_1d(N, 256)), 256, 0, N, cst, fx,

@@ -541,6 +541,7 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
+    if (a.mode == RF_PCG_P && a.st->idle) return;  // PCG: the z pass ended the run
     const AScal<T> sc = ascal_from_state(a, a.st);
     rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
     pdl_leave();
@@ -657,8 +658,9 @@ __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc_b(const ColArgs<T> a,
 // crop) of rows r0 (v[e].x) and r0 + 1 (v[e].y), through the epilogue of the
 // mode: the plain output; the CG product q = P (C p + s p) with the dot
 // products the CG step takes (s0..s4: p.q, r.q, q.q and, of the r and p pass
-// A formed, r.r and r.p); the preconditioned residual z (s0: r.z); or the
-// FP64 true residual r = P (b - C x - s x) (s0: r.r, s1: (P b).(P b)).  Each
+// A formed, r.r and r.p); the PCG product q with p.q (s0); the
+// preconditioned residual z (s0: r.z, s1: r.r); or the FP64 true residual
+// r = P (b - C x - s x) (s0: r.r, s1: (P b).(P b)).  Each
 // row's operands are all loaded before the first is used.  vo: the
 // problem's vector offset.
 template <typename T, int M, int E>
@@ -715,6 +717,21 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
                     s3.prod(rv[e], rv[e]);
                     s4.prod(rv[e], pv[e]);
                 }
+        } else if (mode == RI_PQ) {
+            T pv[H], sv[H];
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    pv[e] = cp[b + e * G];
+                    sv[e] = s[b + e * G];
+                }
+#pragma unroll
+            for (int e = 0; e < H; ++e)
+                if (ok[e]) {
+                    const T q = act[e] ? yv[e] + sv[e] * pv[e] : (T)0;
+                    cq[b + e * G] = q;
+                    s0.prod(pv[e], q);
+                }
         } else if (mode == RI_PCG_Z) {
             T rv[H];
 #pragma unroll
@@ -726,6 +743,7 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
                     const T z = act[e] ? yv[e] : (T)0;
                     cz[b + e * G] = z;
                     s0.prod(rv[e], z);
+                    s1.prod(rv[e], rv[e]);
                 }
         } else {  // RI_RESID (T = double)
             double xv[H], bv[H], sv[H];
@@ -823,9 +841,13 @@ __device__ __forceinline__ void rinv_sums(const RowInvArgs<T>& a, double* part, 
             st->warm = 0;  // every block has read it: later cycles recompute the residual
         }
     } else if (a.mode == RI_PCG_Z) {
+        const Acc<T> pv[2] = {s0, s1};
+        double tot[2];
+        if (grid_sum_last<2>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_zr_decide(st, tot[0], tot[1], a.h_inner);
+    } else if (a.mode == RI_PQ) {
         const Acc<T> pv[1] = {s0};
         double tot[1];
-        if (grid_sum_last<1>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(st, tot[0]);
+        if (grid_sum_last<1>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_alpha_decide(st, tot[0]);
     }
 }
 
@@ -834,6 +856,7 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a
     static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
+    if (a.mode == RI_PQ && a.st->idle) return;  // PCG: the z pass ended the run
     Acc<T> s0, s1, s2, s3, s4;  // short per-thread runs (FP64, or Dot2 pairs in FP32)
     // warm residual: r64 and its sums (rr64, bb) are already in place, and
     // block 0 alone hands them to the decision

@@ -41,7 +41,20 @@ int fc_batch_solve_rtols(fftconv_plan* p, int nb, const double* s, const double*
 namespace {
 
 constexpr int kMaxBatch = 64;  // requests one slot takes into one batched solve
-constexpr int kPlansPerSize = 2;  // plans one size may hold (busy ones included)
+// Requests up to this size run on the slots' higher-priority streams: their
+// short passes are scheduled ahead of the long ones of large solves, so that
+// a small request is not held behind a large one sharing the GPU.
+constexpr int kSmallL = 256;
+
+// Plans one size may hold (busy ones included): 2, or FC_SERVER_PLANS_PER_SIZE.
+int plans_per_size() {
+    static const int n = [] {
+        const char* e = getenv("FC_SERVER_PLANS_PER_SIZE");
+        const int v = e ? atoi(e) : 0;
+        return v >= 1 && v <= 16 ? v : 2;
+    }();
+    return n;
+}
 
 // FC_SERVER_TRACE=1: one line per batched solve on stderr (size, plan made or
 // kept, and the wall time of set-up, input copies, solve and output copies).
@@ -74,7 +87,8 @@ struct Req {
 
 struct Slot {
     std::thread th;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;     // lower priority: requests of L > kSmallL (and staging growth)
+    cudaStream_t stream_hi = nullptr;  // higher priority: requests of L <= kSmallL
     cudaEvent_t done = nullptr;  // blocking-sync event: a waiting slot thread sleeps
     double *ds = nullptr, *db = nullptr, *dx = nullptr;  // device staging (stream-ordered)
     long cap = 0;
@@ -148,7 +162,7 @@ Req* admit_one_locked(cg_server* sv, fftconv_plan** plan, std::vector<fftconv_pl
         const bool have = ip != sv->idle.end();
         // every plan this size may hold is busy: the request waits for one
         // (and joins its next batch) rather than making another
-        if (!have && sv->plans_of[r->rq.L] >= kPlansPerSize) continue;
+        if (!have && sv->plans_of[r->rq.L] >= plans_per_size()) continue;
         const size_t need = have ? batch_bytes(r->rq.L, r->rq.mode) : r->est;
         size_t freeable = 0;
         for (auto& kv : sv->idle)
@@ -210,6 +224,9 @@ int ensure_staging(Slot* sl, long n) {
     if (n <= sl->cap) return FC_OK;
     long cap = sl->cap > 0 ? sl->cap : n;
     while (cap < n) cap *= 2;
+    // nothing of the slot's may still use the old buffers, on either stream
+    if (cudaStreamSynchronize(sl->stream_hi) != cudaSuccess || cudaStreamSynchronize(sl->stream) != cudaSuccess)
+        return FC_ECUDA;
     fc::dev_free_async(sl->ds, sl->stream);
     fc::dev_free_async(sl->db, sl->stream);
     fc::dev_free_async(sl->dx, sl->stream);
@@ -220,6 +237,8 @@ int ensure_staging(Slot* sl, long n) {
         fc::dev_malloc_async((void**)&sl->db, bytes, sl->stream) != cudaSuccess ||
         fc::dev_malloc_async((void**)&sl->dx, bytes, sl->stream) != cudaSuccess)
         return FC_ENOMEM;
+    // the buffers may be used on the slot's other stream: their allocation done
+    if (cudaStreamSynchronize(sl->stream) != cudaSuccess) return FC_ECUDA;
     sl->cap = cap;
     return FC_OK;
 }
@@ -246,6 +265,7 @@ void worker(cg_server* sv, Slot* sl) {
         for (fftconv_plan* e : evict) fftconv_plan_destroy(e);
         Req* r = batch[0];
         const int L = r->rq.L, nb = (int)batch.size();
+        cudaStream_t st = L <= kSmallL ? sl->stream_hi : sl->stream;
         const long N = (long)L * L;
         const bool created = plan == nullptr;
         int rc = FC_OK;
@@ -262,9 +282,9 @@ void worker(cg_server* sv, Slot* sl) {
             for (int k = 0; k < nb && rc == FC_OK; ++k) {
                 sl->rtols[k] = batch[k]->rq.rtol;
                 if (cudaMemcpyAsync(sl->ds + (size_t)k * N, batch[k]->sp(), sizeof(double) * N,
-                                    cudaMemcpyHostToDevice, sl->stream) != cudaSuccess ||
+                                    cudaMemcpyHostToDevice, st) != cudaSuccess ||
                     cudaMemcpyAsync(sl->db + (size_t)k * N, batch[k]->bp(), sizeof(double) * N,
-                                    cudaMemcpyHostToDevice, sl->stream) != cudaSuccess)
+                                    cudaMemcpyHostToDevice, st) != cudaSuccess)
                     rc = FC_ECUDA;
             }
         }
@@ -277,16 +297,16 @@ void worker(cg_server* sv, Slot* sl) {
             o.x0_zero = 1;
             o.precond = r->rq.precond;
             rc = fc_batch_solve_rtols(plan, nb, sl->ds, sl->db, sl->dx, &o, sl->rtols.data(), sl->res.data(),
-                                      sl->stream);
+                                      st);
             t_out = now_s();
             if (rc == FC_OK || rc == FC_ENOCONV || rc == FC_ENANINF) {
                 rc = FC_OK;
                 for (int k = 0; k < nb && rc == FC_OK; ++k)
                     if (batch[k]->rq.x &&
                         cudaMemcpyAsync(batch[k]->rq.x, sl->dx + (size_t)k * N, sizeof(double) * N,
-                                        cudaMemcpyDeviceToHost, sl->stream) != cudaSuccess)
+                                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
                         rc = FC_ECUDA;
-                if (rc == FC_OK && (cudaEventRecord(sl->done, sl->stream) != cudaSuccess ||
+                if (rc == FC_OK && (cudaEventRecord(sl->done, st) != cudaSuccess ||
                                     cudaEventSynchronize(sl->done) != cudaSuccess))
                     rc = FC_ECUDA;
             }
@@ -342,9 +362,13 @@ extern "C" int cg_server_create(cg_server** out, size_t mem_budget_bytes, int ma
     sv->max_slots = max_slots;
     for (int i = 0; i < max_slots; ++i) {
         Slot* sl = new (std::nothrow) Slot();
-        if (!sl || cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (!sl || cudaStreamCreateWithPriority(&sl->stream, cudaStreamNonBlocking, lo) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&sl->stream_hi, cudaStreamNonBlocking, hi) != cudaSuccess ||
             cudaEventCreateWithFlags(&sl->done, cudaEventBlockingSync | cudaEventDisableTiming) != cudaSuccess) {
             if (sl && sl->stream) cudaStreamDestroy(sl->stream);
+            if (sl && sl->stream_hi) cudaStreamDestroy(sl->stream_hi);
             delete sl;
             cg_server_destroy(sv);
             return FC_ECUDA;
@@ -354,6 +378,44 @@ extern "C" int cg_server_create(cg_server** out, size_t mem_budget_bytes, int ma
     for (Slot* sl : sv->slots) sl->th = std::thread(worker, sv, sl);
     *out = sv;
     return FC_OK;
+}
+
+extern "C" int cg_server_reserve(cg_server* sv, int L, int nplans) {
+    if (!sv || L < 1 || L > 4096 || nplans < 1) return FC_EINVAL;
+    const int want = nplans < plans_per_size() ? nplans : plans_per_size();
+    for (;;) {
+        const size_t need = estimate_bytes(L);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (sv->plans_of[L] >= want) return FC_OK;
+            if (sv->used + need > sv->budget) return FC_EBUDGET;
+            sv->plans_of[L] += 1;  // the plan made below
+            sv->used += need;
+            if (sv->used > sv->peak) sv->peak = sv->used;
+        }
+        fftconv_plan* plan = nullptr;
+        int rc = fftconv_plan_create(&plan, L, FC_F32 | FC_F64, nullptr);
+        if (rc == FC_OK) rc = fftconv_plan_sync_mode(plan, 1);
+        size_t nbytes = 0;
+        if (rc == FC_OK) fftconv_plan_info(plan, nullptr, nullptr, nullptr, &nbytes);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->used -= need;
+            if (rc != FC_OK) {
+                sv->plans_of[L] -= 1;
+            } else {
+                sv->plan_bytes[plan] = nbytes;
+                sv->used += nbytes;
+                if (sv->used > sv->peak) sv->peak = sv->used;
+                sv->idle.emplace(L, plan);
+            }
+        }
+        if (rc != FC_OK) {
+            if (plan) fftconv_plan_destroy(plan);
+            return rc;
+        }
+        sv->cv.notify_all();
+    }
 }
 
 extern "C" int cg_batch_submit(cg_server* sv, const cg_request* rq, uint64_t* ticket) {
@@ -435,6 +497,10 @@ extern "C" int cg_server_destroy(cg_server* sv) {
         if (sl->th.joinable()) sl->th.join();
     for (auto& kv : sv->plan_bytes) fftconv_plan_destroy(kv.first);
     for (Slot* sl : sv->slots) {
+        if (sl->stream_hi) {
+            cudaStreamSynchronize(sl->stream_hi);
+            cudaStreamDestroy(sl->stream_hi);
+        }
         if (sl->stream) cudaStreamSynchronize(sl->stream);
         if (sl->stream) {
             fc::dev_free_async(sl->ds, sl->stream);

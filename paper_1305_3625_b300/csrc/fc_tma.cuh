@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
     const int j = threadIdx.x;
     const int L = a.L;
     pdl_enter();
+    if (a.mode == RI_PQ && a.st->idle) return;  // PCG: the z pass ended the run (no copy issued yet)
     const unsigned limit = a.st->dbg_limit ? a.st->dbg_limit : (1u << 20);
     // test hook: no copy for the block's first row pair, its waits run out
     const bool skip_first = a.st->dbg_skip == 2;
@@ -193,16 +194,7 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
             if (pending[b]) mbar_wait_bounded(&bar[b], b ? ph1 : ph0, limit);
     }
     pdl_leave();  // every block still joins the grid reduction below
-    if (a.mode == RI_CG) {
-        const Acc<float> pv[5] = {s0, s1, s2, s3, s4};
-        double tot[5];
-        if (grid_sum_last<5>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0)
-            cg_step_decide(a.st, tot[0], tot[1], tot[2], tot[3], tot[4], a.h_inner);
-    } else if (a.mode == RI_PCG_Z) {
-        const Acc<float> pv[1] = {s0};
-        double tot[1];
-        if (grid_sum_last<1>(pv, a.part, &a.st->cntC, tot) && threadIdx.x == 0) pcg_z_decide(a.st, tot[0]);
-    }
+    rinv_sums(a, a.part, a.st, s0, s1, s2, s3, s4);
 }
 
 }  // namespace fc

@@ -190,6 +190,46 @@ def test_masked_step_ties_and_empty():
     assert int(host(rem)[0]) == -1
 
 
+@pytest.mark.parametrize("case", ["near_ties", "exact_ties", "extreme", "zeros"])
+def test_masked_step_edge_ratios(case):
+    """The removal kernel screens sites by an FP32 estimate of |x|/t before
+    the exact FP64 quotient decides; its pick must still be the oracle's,
+    bit for bit: ratios within 1e-12 of the maximum (where the estimate
+    cannot tell them apart), exact ties at scattered sites (lowest index),
+    ratios and operands beyond FP32's range (1e-40 .. 1e40), and x = 0."""
+    L = 300
+    N = L * L
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(N)
+    t = rng.uniform(0.05, 1.0, N)
+    mask = (rng.random(N) > 0.05).astype(np.uint8)
+    if case == "near_ties":
+        top = np.max(np.abs(x) / t) * 2.0
+        idx = rng.choice(N, 40, replace=False)
+        x[idx] = top * t[idx] * (1.0 + rng.integers(-5, 5, 40) * 1e-13)
+    elif case == "exact_ties":
+        idx = np.sort(rng.choice(N, 12, replace=False))
+        t[idx] = 0.25
+        x[idx] = 1e3  # ratio 4000 exactly at every one of them
+        mask[idx[0]] = 0  # the lowest is masked out: the next one wins
+    elif case == "extreme":
+        idx = rng.choice(N, 30, replace=False)
+        x[idx[:10]] = 1e-40
+        t[idx[10:20]] = 1e-38
+        x[idx[20:]] = 1e40
+        t[idx[25:]] = 1e35
+    else:
+        x[:] = 0.0
+        x[rng.choice(N, 3, replace=False)] = -0.0
+    want, wr = oracle.argmax_ratio(x, t, mask)
+    xd, md = dev(x), dev(mask, torch.uint8)
+    rem = torch.empty(1, device="cuda", dtype=torch.int64)
+    fc.fc_masked_step(plan(L), dev(t), md, xd, rem)
+    got = int(host(rem)[0])
+    print(f"{case}: oracle {want} ({wr:.17g}), kernel {got}")
+    assert got == want
+
+
 @pytest.mark.parametrize("mode,rtol,rel_tie", [(0, 1e-12, 1e-9), (1, 1e-10, 1e-5)])
 def test_masked_loop_against_oracle(mode, rtol, rel_tie):
     """Quasi-static loop: solve, remove argmax |x|/t, warm start.  At each step

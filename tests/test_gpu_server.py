@@ -190,3 +190,27 @@ def test_config4_sizes_against_oracle():
         L, tol, s, b = reqs[k]
         xa, ra = alone(L, s, b, tol, fc.FC_MODE_MIXED, precond=True)
         assert np.array_equal(outs[k], xa) and res[tickets[k]]["iters"] == ra["iters"]
+
+
+def test_reserve_makes_plans_ahead():
+    """cg_server_reserve makes a size's plans before any request (at most the
+    plans per size, within the budget); requests then run on them, and a
+    reservation that cannot fit the budget is refused."""
+    sv = fc.cg_server_create(2 << 30, max_slots=2)
+    fc.cg_server_reserve(sv, 64, 2)
+    fc.cg_server_reserve(sv, 64, 5)  # capped at the plans per size
+    st = fc.cg_server_stats(sv)
+    assert st["plans"] == 2 and st["used"] > 0
+    p = fc_inputs.problem(64, seed=3, b_kind="normal")
+    o = np.zeros(64 * 64)
+    r = wait_all(sv, [fc.cg_batch_submit(sv, 64, p["s"], p["b"], x_out=o, rtol=1e-8)])
+    assert all(v["status"] == fc.FC_OK for v in r.values())
+    assert fc.cg_server_stats(sv)["plans"] == 2
+    xa, _ = alone(64, p["s"], p["b"], 1e-8, fc.FC_MODE_MIXED)
+    assert np.array_equal(o, xa)
+    sv.close()
+    small = fc.cg_server_create(32 << 20, max_slots=1)
+    with pytest.raises(fc.FcError) as ei:
+        fc.cg_server_reserve(small, 1024, 1)  # about 110 MB of plan
+    assert ei.value.code == fc.FC_EBUDGET
+    small.close()

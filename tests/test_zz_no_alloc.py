@@ -30,8 +30,10 @@ def c_static_step(n, t, mask, x, removed):
                                          ctypes.c_void_p(removed.data_ptr()), stream)
 
 
-@pytest.mark.parametrize("L", [3, 64, 1024])
+@pytest.mark.parametrize("L", [3, 64, 1024, 4096])
 def test_static_step_matches_plan_step_twice(L):
+    """L = 4096 is the static scratch's limit (N = 4096^2 sites, every one of
+    its 8192 block slots in use)."""
     N = L * L
     p = fc_inputs.problem(L, seed=21, with_t=True)
     rng = np.random.default_rng(L)
