@@ -26,18 +26,25 @@ struct __align__(2 * sizeof(T)) cpx {
     T x, y;
 };
 
+// Products whose rounding the compiler may not change: every multiply-add
+// of the pass kernels is written as an explicit fma of a rounded product,
+// so that two kernels built from the same arithmetic (a pass and its batched
+// twin, whatever their register pressure) round identically.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 template <typename T>
 __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename T>
 __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.x - b.x, a.y - b.y}; }
 template <typename T>
 __device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> w) {
-    return {a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x};
+    return {fma(a.x, w.x, -mul_rn(a.y, w.y)), fma(a.x, w.y, mul_rn(a.y, w.x))};
 }
 // a * conj(w)
 template <typename T>
 __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> w) {
-    return {a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y};
+    return {fma(a.x, w.x, mul_rn(a.y, w.y)), fma(a.y, w.x, -mul_rn(a.x, w.y))};
 }
 
 // Read-only (L1-cached) load of one complex value.
@@ -52,52 +59,100 @@ __device__ __forceinline__ cpx<T> ldg_c(const cpx<T>* p) {
     }
 }
 
-// cos and sin of 2 pi q / 16, q = 0..7 (exact mathematical constants).
-constexpr double kCos16[8] = {1.0,
-                              0.92387953251128675612818318939678829,
-                              0.70710678118654752440084436210484904,
-                              0.38268343236508977172845998403039887,
-                              0.0,
-                              -0.38268343236508977172845998403039887,
-                              -0.70710678118654752440084436210484904,
-                              -0.92387953251128675612818318939678829};
-constexpr double kSin16[8] = {0.0,
-                              0.38268343236508977172845998403039887,
-                              0.70710678118654752440084436210484904,
-                              0.92387953251128675612818318939678829,
-                              1.0,
-                              0.92387953251128675612818318939678829,
-                              0.70710678118654752440084436210484904,
-                              0.38268343236508977172845998403039887};
+// cos(pi q / 16), q = 0..8 (exact mathematical constants); the angles
+// 2 pi Q / 32 of the radix-32 rotations are multiples of pi / 16.
+constexpr double kCosPi16[9] = {1.0,
+                                0.980785280403230449126182236134239037,
+                                0.923879532511286756128183189396788287,
+                                0.831469612302545237078788377617905757,
+                                0.707106781186547524400844362104849039,
+                                0.555570233019602224742830813948532874,
+                                0.382683432365089771728459984030398867,
+                                0.195090322016128267848284868477022241,
+                                0.0};
+// cos and sin of 2 pi Q / 32 for Q in [0, 16).
+__host__ __device__ constexpr double cos32(int Q) { return Q <= 8 ? kCosPi16[Q] : -kCosPi16[16 - Q]; }
+__host__ __device__ constexpr double sin32(int Q) { return Q <= 8 ? kCosPi16[8 - Q] : kCosPi16[Q - 8]; }
 
-// Multiply by exp(-/+ 2 pi i Q/16) (forward / inverse), Q in [0, 8).
+// Multiply by exp(-/+ 2 pi i Q/32) (forward / inverse), Q in [0, 16).
 template <int Q, bool INV, typename T>
-__device__ __forceinline__ cpx<T> rot16(cpx<T> a) {
+__device__ __forceinline__ cpx<T> rot32(cpx<T> a) {
     if constexpr (Q == 0) {
         return a;
-    } else if constexpr (Q == 4) {
+    } else if constexpr (Q == 8) {
         return INV ? cpx<T>{-a.y, a.x} : cpx<T>{a.y, -a.x};
-    } else if constexpr (Q == 2 || Q == 6) {
-        constexpr T h = (T)kCos16[2];
-        // (1 -/+ i) h  for Q = 2, (-1 -/+ i) h for Q = 6
-        if constexpr (Q == 2)
-            return INV ? cpx<T>{(a.x - a.y) * h, (a.x + a.y) * h} : cpx<T>{(a.x + a.y) * h, (a.y - a.x) * h};
+    } else if constexpr (Q == 4 || Q == 12) {
+        constexpr T h = (T)kCosPi16[4];
+        // (1 -/+ i) h  for Q = 4, (-1 -/+ i) h for Q = 12
+        if constexpr (Q == 4)
+            return INV ? cpx<T>{mul_rn(a.x - a.y, h), mul_rn(a.x + a.y, h)}
+                       : cpx<T>{mul_rn(a.x + a.y, h), mul_rn(a.y - a.x, h)};
         else
-            return INV ? cpx<T>{-(a.x + a.y) * h, (a.x - a.y) * h} : cpx<T>{(a.y - a.x) * h, -(a.x + a.y) * h};
+            return INV ? cpx<T>{-mul_rn(a.x + a.y, h), mul_rn(a.x - a.y, h)}
+                       : cpx<T>{mul_rn(a.y - a.x, h), -mul_rn(a.x + a.y, h)};
     } else {
-        constexpr T c = (T)kCos16[Q];
-        constexpr T s = INV ? (T)kSin16[Q] : -(T)kSin16[Q];
-        return {a.x * c - a.y * s, a.x * s + a.y * c};
+        constexpr T c = (T)cos32(Q);
+        constexpr T s = INV ? (T)sin32(Q) : -(T)sin32(Q);
+        return {fma(a.x, c, -mul_rn(a.y, s)), fma(a.x, s, mul_rn(a.y, c))};
+    }
+}
+
+// The butterfly of a radix-2 level with a constant rotation folded in:
+// lo = a + w b, hi = a - w b, w = exp(-/+ 2 pi i Q/32).  A generic rotation
+// is applied as c (b.x - t b.y, b.y + t b.x) with t = s/c (or its
+// cotangent form when |s| > |c|), so that the scale c enters the two sums
+// as fused multiply-adds: 6 operations per butterfly instead of 8.
+template <int Q, bool INV, typename T>
+__device__ __forceinline__ void bfly(cpx<T> a, cpx<T> b, cpx<T>& lo, cpx<T>& hi) {
+    if constexpr (Q == 0) {
+        lo = a + b;
+        hi = a - b;
+    } else if constexpr (Q == 8) {
+        const cpx<T> wb = INV ? cpx<T>{-b.y, b.x} : cpx<T>{b.y, -b.x};
+        lo = a + wb;
+        hi = a - wb;
+    } else if constexpr (Q == 4 || Q == 12) {
+        // w b = h (u, v) with w = (+/-1 +/- i) h
+        constexpr T h = (T)kCosPi16[4];
+        T u, v;
+        if constexpr (Q == 4) {
+            u = INV ? b.x - b.y : b.x + b.y;
+            v = INV ? b.x + b.y : b.y - b.x;
+        } else {
+            u = INV ? -(b.x + b.y) : b.y - b.x;
+            v = INV ? b.x - b.y : -(b.x + b.y);
+        }
+        lo = cpx<T>{fma(h, u, a.x), fma(h, v, a.y)};
+        hi = cpx<T>{fma(-h, u, a.x), fma(-h, v, a.y)};
+    } else {
+        constexpr double cd = cos32(Q), sd = INV ? sin32(Q) : -sin32(Q);
+        if constexpr (cd * cd >= sd * sd) {  // w b = c (b.x - t b.y, b.y + t b.x)
+            constexpr T c = (T)cd, t = (T)(sd / cd);
+            const T u = fma(-t, b.y, b.x), v = fma(t, b.x, b.y);
+            lo = cpx<T>{fma(c, u, a.x), fma(c, v, a.y)};
+            hi = cpx<T>{fma(-c, u, a.x), fma(-c, v, a.y)};
+        } else {  // w b = s (k b.x - b.y, b.x + k b.y), k = c/s
+            constexpr T sc = (T)sd, k = (T)(cd / sd);
+            const T u = fma(k, b.x, -b.y), v = fma(k, b.y, b.x);
+            lo = cpx<T>{fma(sc, u, a.x), fma(sc, v, a.y)};
+            hi = cpx<T>{fma(-sc, u, a.x), fma(-sc, v, a.y)};
+        }
     }
 }
 
 template <int R, bool INV, typename T, int... K>
-__device__ __forceinline__ void twiddle_consts(cpx<T>* o, std::integer_sequence<int, K...>) {
-    ((o[K] = rot16<K * 16 / R, INV>(o[K])), ...);
+__device__ __forceinline__ void bfly_level(const cpx<T>* e, const cpx<T>* o, cpx<T>* v,
+                                           std::integer_sequence<int, K...>) {
+    (bfly<K * 32 / R, INV>(e[K], o[K], v[K], v[K + R / 2]), ...);
 }
 
-// In-register R-point DFT (R = 1, 2, 4, 8, 16), natural order in and out,
-// by recursive radix-2 decimation in time.
+template <int R, bool INV, typename T, int... K>
+__device__ __forceinline__ void rotate_consts(cpx<T>* o, std::integer_sequence<int, K...>) {
+    ((o[K] = rot32<K * 32 / R, INV>(o[K])), ...);
+}
+
+// In-register R-point DFT (R = 1, 2, 4, 8, 16, 32), natural order in and
+// out, by recursive radix-2 decimation in time.
 template <int R, bool INV, typename T>
 struct Dft {
     static __device__ __forceinline__ void run(cpx<T> (&v)[R]) {
@@ -109,12 +164,7 @@ struct Dft {
         }
         Dft<R / 2, INV, T>::run(e);
         Dft<R / 2, INV, T>::run(o);
-        twiddle_consts<R, INV, T>(o, std::make_integer_sequence<int, R / 2>{});
-#pragma unroll
-        for (int k = 0; k < R / 2; ++k) {
-            v[k] = e[k] + o[k];
-            v[k + R / 2] = e[k] - o[k];
-        }
+        bfly_level<R, INV, T>(e, o, v, std::make_integer_sequence<int, R / 2>{});
     }
 };
 template <bool INV, typename T>
@@ -130,14 +180,43 @@ struct Dft<2, INV, T> {
     }
 };
 
-// Shared-memory index with one padding slot every 16 elements; it spreads the
-// radix-16 "expand" writes (stride 16) over the banks.  For every access
-// pattern of the stages below, spad(base + c) = spad(base) + c + (c >> 4)
-// with c a compile-time multiple of the stride (checked exhaustively for all
-// M <= 8192, E in {2,4,8,16}), so addresses are a base plus immediates.
-__host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >> 4); }
+// R-point DFT of a sequence whose upper half is zero (v[n] = 0 for
+// n >= R/2, the zero padding): X[2m] is the R/2-point DFT of x and
+// X[2m+1] that of x[n] exp(-/+ 2 pi i n/R), so no additions of zeros.
+template <int R, bool INV, typename T>
+struct DftZeroHalf {
+    static __device__ __forceinline__ void run(cpx<T> (&v)[R]) {
+        if constexpr (R == 1) {
+            return;
+        } else {
+            cpx<T> a[R / 2], b[R / 2];
+#pragma unroll
+            for (int n = 0; n < R / 2; ++n) a[n] = b[n] = v[n];
+            rotate_consts<R, INV, T>(b, std::make_integer_sequence<int, R / 2>{});
+            Dft<R / 2, INV, T>::run(a);
+            Dft<R / 2, INV, T>::run(b);
+#pragma unroll
+            for (int m = 0; m < R / 2; ++m) {
+                v[2 * m] = a[m];
+                v[2 * m + 1] = b[m];
+            }
+        }
+    }
+};
+
+// Shared-memory index with one padding slot every 2^P elements (P = 4; 5 in
+// the exchanges of radix-32 stages); it spreads the radix-E "expand" writes
+// (stride E) over the banks.  For every access pattern of the stages below,
+// spad(base + c) = spad(base) + c + (c >> P) with c a compile-time multiple
+// of the stride (checked exhaustively for all M <= 8192, E in {2,4,8,16}
+// with P = 4 and E = 32, M >= 1024 with P = 5), so addresses are a base plus
+// immediates.  seg_len(M) covers both paddings.
+template <int P = 4>
+__host__ __device__ __forceinline__ constexpr int spad(int i) { return i + (i >> P); }
 __host__ __device__ constexpr int seg_len(int M) { return M + (M >> 4) + 2; }
-__host__ __device__ constexpr int pofs(int c) { return c + (c >> 4); }
+template <int P = 4>
+__host__ __device__ constexpr int pofs(int c) { return c + (c >> P); }
+__host__ __device__ constexpr int pad_shift(int E) { return E >= 32 ? 5 : 4; }
 
 // Stage structure of a length-M transform with E values per thread: stages
 // NS = 1, E, E^2, ... of radix E, the last one of radix M/NS if smaller.
@@ -157,6 +236,10 @@ __host__ __device__ constexpr int tw_offset(int M, int E, int NS) {
     return off;
 }
 __host__ __device__ constexpr int tw_len(int M, int E) { return tw_offset(M, E, M); }
+// Slot of E's table among a plan's tables (log2 E for E = 2 .. 32).
+__host__ __device__ constexpr int tw_index(int E) {
+    return E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : E == 32 ? 5 : 0;
+}
 
 // Load the R-1 twiddles e = 1..R-1 of column k of a stage block (entry
 // [e][k] at blk[e*NS + k]): one coalesced load per e across the warp.
@@ -171,9 +254,11 @@ __device__ __forceinline__ void load_twiddles(const cpx<T>* __restrict__ blk, in
 // sm0/sm1: this group's two shared segments (seg_len(M) elements each).
 // With DB the exchanges alternate between them (starting with BUF) and need
 // one barrier each; without DB only sm0 is used and each exchange ends with
-// a second barrier.  tws: the stage twiddle table of (M, E).  All threads of
+// a second barrier.  tws: the stage twiddle table of (M, E).  ZH: the
+// upper half of the sequence is zero (x[n] = 0 for n >= M/2, so v[e] = 0 for
+// e >= E/2: the zero padding), which the first stage skips.  All threads of
 // the block call this together.
-template <typename T, int M, int E, bool INV, bool DB, int BUF = 0, int NS = 1>
+template <typename T, int M, int E, bool INV, bool DB, int BUF = 0, int NS = 1, bool ZH = false>
 __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, cpx<T>* sm1,
                                            const cpx<T>* __restrict__ tws) {
     constexpr int G = M / E;
@@ -185,16 +270,20 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, c
 #pragma unroll
             for (int e = 1; e < E; ++e) v[e] = INV ? cmulc(v[e], w[e]) : cmul(v[e], w[e]);
         }
-        Dft<E, INV, T>::run(v);
+        if constexpr (ZH && NS == 1)
+            DftZeroHalf<E, INV, T>::run(v);
+        else
+            Dft<E, INV, T>::run(v);
         if constexpr (NS * E < M) {
             cpx<T>* sm = (DB && BUF) ? sm1 : sm0;
-            cpx<T>* wp = sm + spad((j / NS) * NS * E + k);
+            constexpr int P = pad_shift(E);
+            cpx<T>* wp = sm + spad<P>((j / NS) * NS * E + k);
 #pragma unroll
-            for (int e = 0; e < E; ++e) wp[pofs(e * NS)] = v[e];
+            for (int e = 0; e < E; ++e) wp[pofs<P>(e * NS)] = v[e];
             __syncthreads();
-            const cpx<T>* rp = sm + spad(j);
+            const cpx<T>* rp = sm + spad<P>(j);
 #pragma unroll
-            for (int e = 0; e < E; ++e) v[e] = rp[pofs(e * G)];
+            for (int e = 0; e < E; ++e) v[e] = rp[pofs<P>(e * G)];
             if constexpr (!DB) __syncthreads();
             fft_stages<T, M, E, INV, DB, DB ? 1 - BUF : 0, NS * E>(v, j, sm0, sm1, tws);
         }

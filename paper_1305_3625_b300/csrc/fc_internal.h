@@ -13,8 +13,9 @@ template <typename T>
 struct cpx;
 
 // Scalars of one solve, resident in device memory.  Each field is written by
-// exactly one pass and read by later passes only, so no kernel reads a field
-// that another block of the same kernel may be writing.
+// one thread of a pass.  A pass whose blocks all evaluate a step decision
+// (the PCG passes A, see pcg_zr_eval) reads only fields that no block of it
+// writes, or whose new value leads every block to the same decision.
 struct CgState {
     double rr;           // r.r of the current inner residual (pass C's direct sum)
     double rp;           // r.p of the current residual and direction (pass C)
@@ -28,6 +29,7 @@ struct CgState {
                          // the outer target (0: never)
     double beta_carry;   // direction kept across a true-residual replacement (0: restart)
     double rz, rz_prev;  // PCG: r.z of the current and of the previous iteration
+    double rz_next;      // PCG: r.z just decided on, moved into rz by the next column pass
     double pshift;       // PCG: shift c of the preconditioner (C_M + c I)^-1
     int iter;            // products spent in inner loops (all cycles)
     int max_iter;
@@ -112,9 +114,11 @@ struct RowFwdArgs {
     const float* d32;            // RF_XUPD: correction from the last inner run (or null)
     const uint8_t* mask;         // RF_XUPD: x is zeroed off the active set (null: all active)
     CgState* st;
-    double* part;                // per-block partial sums
+    double* part;                // per-block partial sums (PCG: those of the last pass C)
     cpx<T>* Z;                   // L x M intermediate
     const cpx<T>* tw;            // exp(-2 pi i m/M), m < M
+    int npart;                   // PCG: blocks of the pass C whose partial sums this pass adds
+    unsigned long long h_inner;  // PCG, RF_PCG_P: the inner loop's conditional handle (0: none)
 };
 
 template <typename T>
@@ -123,8 +127,9 @@ struct ColArgs {
     cpx<T>* Z;
     const T* Gq;                 // (M/2+1)^2 real spectrum quarter, 1/M^2 folded in
     const cpx<T>* tw;
-    const CgState* st;           // with gate: the state whose fields may skip the pass
+    CgState* st;                 // with gate: the state whose fields may skip the pass
     int gate;                    // GATE_* bits (GATE_WARM: the residual was updated, no product)
+    int pcg_commit;              // 1: block 0 moves the PCG r.z just decided on into place
 };
 
 template <typename T>
@@ -166,7 +171,7 @@ __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq
     st->rq = rq;
     st->qq = qq;
     double alpha = rp_now / pq;
-    double rrn = rr - 2.0 * alpha * rq + alpha * alpha * qq;
+    double rrn = fma(__dmul_rn(alpha, alpha), qq, fma(-2.0 * alpha, rq, rr));  // explicit: same bits in every kernel
     if (rrn < 0.0) rrn = 0.0;
     int d = 0;
     if (!(pq > 0.0) || !isfinite(alpha) || !isfinite(rrn)) {
@@ -190,50 +195,91 @@ __device__ __forceinline__ void cg_step_decide(CgState* st, double pq, double rq
 // Preconditioned CG (Listing 2 with the Fourier preconditioner M), one
 // iteration as the inner loop body runs it: x += alpha p and r -= alpha q
 // (pass A; at the start of a run r from the true residual), z = M^-1 r
-// (passes B, C: pcg_zr_decide, which also takes the stopping test), p = z +
-// beta p (pass A), q = A p (passes B, C: pcg_alpha_decide).
+// (passes B, C), p = z + beta p (pass A), q = A p (passes B, C).  The two
+// passes C only publish their blocks' partial sums (r.z and r.r; p.q); the
+// pass A that follows each adds them up in every block, in one fixed order,
+// and takes the step decision there, so no pass C waits for a last block.
+// Every block evaluates the decision from the state as the pass found it
+// (the eval functions below are pure functions of a snapshot of the fields
+// they read); one thread commits it.  The fields a
+// commit changes are either not read by the evaluation (rz moves into place
+// in the next column pass, pcg_rz_commit) or change in a way that leads a
+// block evaluating after the commit to the same decision (inner_done only
+// goes from running to ended).
 
+// The state fields a PCG step decision reads, loaded together at the start
+// of the deciding pass.
+struct PcgView {
+    double rz, tol2;
+    int first, inner_done, tma_err, iter, max_iter, cycle_iter, cycle_max;
+};
+__device__ __forceinline__ PcgView pcg_view(const CgState* st) {
+    return {st->rz,   st->tol2,     st->first,      st->inner_done, st->tma_err,
+            st->iter, st->max_iter, st->cycle_iter, st->cycle_max};
+}
+
+struct PcgAlpha {
+    int d;  // inner_done after this step
+    double alpha;
+};
 // After q = A p: alpha = r.z / p.q (the step of Hestenes and Stiefel with
 // the preconditioner).  A breakdown (p.q not positive, alpha not finite) or
-// the iteration cap ends the run after the next update of x and r: the
-// decision of the z pass that follows then stops the loop.
-__device__ __forceinline__ void pcg_alpha_decide(CgState* st, double pq) {
-    st->pq = pq;
-    double alpha = st->rz / pq;
-    int d = st->inner_done;
+// the iteration cap ends the run after this update of x and r: the z
+// decision that follows then stops the loop.
+__device__ __forceinline__ PcgAlpha pcg_alpha_eval(const PcgView& st, double pq) {
+    double alpha = st.rz / pq;
+    int d = st.inner_done;
     if (!(pq > 0.0) || !isfinite(alpha)) {
         d = 3;
         alpha = 0.0;
     }
+    if (d == 0 && (st.iter + 1 >= st.max_iter || st.cycle_iter + 1 >= st.cycle_max)) d = 2;
+    if (st.tma_err) d = 4;
+    return {d, alpha};
+}
+__device__ __forceinline__ void pcg_alpha_commit(CgState* st, const PcgAlpha& a, double pq) {
+    st->pq = pq;
+    st->alpha = a.alpha;
     st->iter += 1;
     st->cycle_iter += 1;
-    if (d == 0 && (st->iter >= st->max_iter || st->cycle_iter >= st->cycle_max)) d = 2;
-    if (st->tma_err) d = 4;
-    st->alpha = alpha;
-    st->first = 0;
-    st->inner_done = d;
+    st->inner_done = a.d;
 }
 
+struct PcgZr {
+    int d;  // inner_done after this step (0: the run goes on)
+    double beta;
+};
 // After z = M^-1 r of the updated residual: beta = r.z / r_prev.z_prev for
 // the next direction, and the stopping test on r.r itself (summed directly
-// from r, not from the recursion |r - alpha q|^2).  Sets the loop condition;
-// once the run has ended (idle) the rest of the body returns at entry.
-__device__ __forceinline__ void pcg_zr_decide(CgState* st, double rz, double rr, unsigned long long h_inner) {
-    st->rr = rr;
-    int d = st->inner_done;
+// from r, not from the recursion |r - alpha q|^2).
+__device__ __forceinline__ PcgZr pcg_zr_eval(const PcgView& st, double rz, double rr) {
+    int d = st.inner_done;
     if (d == 0) {
         if (!isfinite(rz) || !isfinite(rr))
             d = 3;
-        else if (rr <= st->tol2)
+        else if (rr <= st.tol2)
             d = 1;
     }
-    if (st->tma_err) d = 4;
-    st->beta = (st->first || !(st->rz > 0.0)) ? 0.0 : rz / st->rz;
+    if (st.tma_err) d = 4;
+    const double beta = (st.first || !(st.rz > 0.0)) ? 0.0 : rz / st.rz;
+    return {d, beta};
+}
+// Sets the loop condition; once the run has ended (idle) the rest of the
+// body returns at entry.
+__device__ __forceinline__ void pcg_zr_commit(CgState* st, const PcgZr& z, double rz, double rr,
+                                              unsigned long long h_inner) {
+    st->rr = rr;
+    st->beta = z.beta;
+    st->rz_next = rz;
+    st->inner_done = z.d;
+    st->idle = z.d != 0;
+    if (h_inner) cudaGraphSetConditional(h_inner, z.d == 0 ? 1u : 0u);
+}
+// The column pass after p = z + beta p (no block of it reads these fields).
+__device__ __forceinline__ void pcg_rz_commit(CgState* st) {
     st->rz_prev = st->rz;
-    st->rz = rz;
-    st->inner_done = d;
-    st->idle = d != 0;
-    if (h_inner) cudaGraphSetConditional(h_inner, d == 0 ? 1u : 0u);
+    st->rz = st->rz_next;
+    st->first = 0;
 }
 
 // Decide the outer loop after a true residual r = P (b - A x): stop when

@@ -793,7 +793,7 @@ struct PrecRes {
     int pers_grid = 0;       // its cooperative grid (resident blocks)
     void* Z = nullptr;       // cpx<T>[(M/2) * L], column-major half spectra
     void* tw = nullptr;      // FP64 only: base table exp(-2 pi i m/M), m < M
-    void* twst[5] = {};      // stage twiddle tables for E = 2, 4, 8, 16 (index log2 E)
+    void* twst[6] = {};      // stage twiddle tables for E = 2, 4, 8, 16, 32 (index log2 E)
     void* Gq = nullptr;      // T[(M/2+1)^2]
     CUtensorMap zmap;        // FP32: Zt as floats [M/2][2L] for the TMA pass C
     bool tma_ok = false;     // zmap encoded (L even, M >= 256)
@@ -804,7 +804,7 @@ struct PrecRes {
     const KV& rfwd_cg() const { return v.rfwd[sel_cg[0]]; }
     const KV& colc_cg() const { return v.colc[sel_cg[1]]; }
     const KV& rinv_cg() const { return v.rinv[sel_cg[2]]; }
-    const void* tws(int E) const { return twst[E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : E == 16 ? 4 : 0]; }
+    const void* tws(int E) const { return twst[tw_index(E)]; }
     // every shape this precision may launch has its stage twiddle table
     bool tables_ok(int M) const {
         auto ok = [&](int E) { return E >= M || tws(E) != nullptr; };
@@ -1007,7 +1007,7 @@ int build_stage_tables(fftconv_plan* p, PrecRes& R, const cpx<double>* tw64, cud
     for (int i = 0; i < nE; ++i) {
         const int E = Es[i];
         const int len = tw_len(M, E);
-        const int idx = E == 2 ? 1 : E == 4 ? 2 : E == 8 ? 3 : 4;
+        const int idx = tw_index(E);
         int rc = dalloc(p, &R.twst[idx], sizeof(cpx<T>) * (size_t)(len > 2 ? len : 2));
         if (rc) return rc;
         for (int ns = E; ns < M; ns *= stage_radix(M, E, ns)) {
@@ -1139,15 +1139,18 @@ int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStr
     c.Z = (const cpx<T>*)R.Z;
     c.tw = tw;
     if (cgv) {
-        // the solver's modes: pass A's CG update of x and r (x += a p, r -= a q),
-        // pass C's product q = C p + s p with its five sums
+        // the preconditioned solver's modes: pass A's update of x and r
+        // (x += a p, r -= a q) with its step decision from published sums (one
+        // block's, zero: alpha = 0), pass C's product q = C p + s p with p.q
         a.mode = RF_PCG_R;
         a.cx = cgv[0];
         a.cr = cgv[1];
         a.cp = cgv[2];
         a.cq = cgv[3];
         a.st = p->st;
-        c.mode = RI_CG;
+        a.part = p->part;
+        a.npart = 1;
+        c.mode = RI_PQ;
         c.cr = cgv[1];
         c.cp = cgv[2];
         c.cq = cgv[3];
@@ -1271,6 +1274,11 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
         for (int i = 0; i < 5 && !rc; ++i)
             if (cudaMemsetAsync(cgv[i], 0, sizeof(T) * p->N, s) != cudaSuccess)
                 rc = set_cuda_err(cudaGetLastError(), "autotune set-up");
+        // a fresh state (first = 0: pass A decides) and zero sums; every solve
+        // sets the state anew
+        if (!rc && (cudaMemsetAsync(p->st, 0, sizeof(CgState), s) != cudaSuccess ||
+                    cudaMemsetAsync(p->part, 0, 2 * sizeof(double), s) != cudaSuccess))
+            rc = set_cuda_err(cudaGetLastError(), "autotune set-up");
         float best = 1e30f;
         int bi = 0;
         for (int k = 0; k < n[kind] && !rc; ++k) {
@@ -1371,8 +1379,9 @@ int autotune_batched(fftconv_plan* p, PrecRes& R) {
             const KV& kv = lists[kind][k];
             if (!kv.f) continue;
             const cpx<T>* tw = (const cpx<T>*)R.tws(kv.E);
-            // the modes batched solves run: pass A's CG update of x and r, pass
-            // C's product with its five sums (zeroed vectors, fresh states)
+            // the modes batched solves run: pass A's update of x and r with its
+            // step decision from published sums, pass C's product with p.q
+            // (zeroed vectors and sums, fresh states: alpha = 0)
             RowFwdArgs<T> a{};
             a.L = p->L;
             a.mode = RF_PCG_R;
@@ -1382,12 +1391,13 @@ int autotune_batched(fftconv_plan* p, PrecRes& R) {
             a.cq = cv[3];
             a.st = st;
             a.part = part;
+            a.npart = 1;
             a.Z = Z;
             a.tw = tw;
             ColArgs<T> b{p->L, Z, (const T*)R.Gq, tw, st, 0};
             RowInvArgs<T> c{};
             c.L = p->L;
-            c.mode = RI_CG;
+            c.mode = RI_PQ;
             c.cr = cv[1];
             c.cp = cv[2];
             c.cq = cv[3];
@@ -1707,7 +1717,7 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
         dfree(p, p->p64.tw);
         dfree(p, p->p64.Gq);
         p->p64.tw = p->p64.Gq = nullptr;
-        for (int i = 0; i < 5; ++i)
+        for (int i = 0; i < 6; ++i)
             if (p->p64.twst[i]) {
                 dfree(p, p->p64.twst[i]);
                 p->p64.twst[i] = nullptr;
@@ -1722,7 +1732,14 @@ extern "C" int fftconv_plan_create_green(fftconv_plan** out, int L, int prec, in
         goto fail;
     }
     FC_TRYC(cudaStreamSynchronize(cs));
-    if (prec & FC_F64) FC_TRY(autotune<double>(p, p->p64, tune));
+    if (prec & FC_F64) {
+        FC_TRY(autotune<double>(p, p->p64, tune));
+        // FP64 has no batched tuning: batched solves take the single-problem
+        // shapes (every FP64 shape has a batched twin), so that a problem's
+        // FP64 arithmetic does not depend on the batch it joins
+        for (int k = 0; k < 3; ++k) p->p64.sel_b[k] = p->p64.sel_cg[k];
+        p->p64.tuned_b = true;
+    }
     if (p->p32.on) FC_TRY(autotune<float>(p, p->p32, tune));
     if (prec & FC_F64) {
         const char* env = getenv("FC_AUTOTUNE");
@@ -2275,18 +2292,24 @@ void add_inner_body(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes
     if (V.batched) batch_ctl_node(gb, body, nC, V, 0, h_inner, nullptr);
 }
 
-// The inner loop body of preconditioned CG (pcg_zr_decide, pcg_alpha_decide):
-// A1 (x += alpha p, r -= alpha q, or at the start of a run r from the true
-// residual; transform r) -> B1 with the preconditioner spectrum -> C1
-// (z = M^-1 r, r.z and r.r: beta, the stopping test on r.r, the loop
-// condition) -> A2 (p = z + beta p; transform p) -> B2 with the kernel
-// spectrum -> C2 (q = A p, p.q: alpha).  Once C1 has ended the run, A2, B2
-// and C2 return at entry; x already holds the last update.
+// The inner loop body of preconditioned CG (pcg_zr_eval, pcg_alpha_eval):
+// A1 (alpha from C2's p.q; x += alpha p, r -= alpha q, or at the start of a
+// run r from the true residual; transform r) -> B1 with the preconditioner
+// spectrum -> C1 (z = M^-1 r; publishes r.z and r.r) -> A2 (beta and the
+// stopping test on r.r, the loop condition; p = z + beta p; transform p) ->
+// B2 with the kernel spectrum (moves r.z into place) -> C2 (q = A p;
+// publishes p.q).  Once A2 has ended the run it returns, and so do B2 and
+// C2; x already holds the last update.  Batched: the loop control node
+// follows A2.
 template <typename T>
 void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, const SolveView& V, T* cx,
                         T* cr, T* cp, T* cq, T* cz, const T* s, const T* pq, const double* r64_start,
                         cudaGraphConditionalHandle h_inner) {
     const KV &ka = rfwd_shape(R, V.batched), &kb = colc_shape(R, V.batched), &kc = rinv_shape(R, V.batched);
+    // blocks of pass C, whose partial sums the passes A add up
+    int npart = row_grid(p, kc);
+    if constexpr (sizeof(T) == 4)
+        if (kc.tma) npart = R.tma_grid;
     RowFwdArgs<T> a1{};
     a1.L = p->L;
     a1.mode = RF_PCG_R;
@@ -2297,6 +2320,7 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a1.r64 = r64_start;
     a1.st = V.st;
     a1.part = V.part;
+    a1.npart = npart;
     a1.Z = V.Z<T>();
     a1.tw = (const cpx<T>*)R.tws(ka.E);
     cudaGraphNode_t n1 = pass_node(gb, body, nullptr, ka, V.grid(row_grid(p, ka)), V, a1, V.inner());
@@ -2310,11 +2334,9 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     c1.mask = V.mask;
     c1.st = V.st;
     c1.part = V.part;
-    c1.h_inner = V.batched ? 0 : h_inner;
     c1.Z = V.Z<T>();
     c1.tw = (const cpx<T>*)R.tws(kc.E);
     cudaGraphNode_t n3 = graph_rinv<T>(gb, body, n2, p, R, kc, V, c1, V.inner());
-    if (V.batched) batch_ctl_node(gb, body, n3, V, 0, h_inner, &n3);
     RowFwdArgs<T> a2{};
     a2.L = p->L;
     a2.mode = RF_PCG_P;
@@ -2323,14 +2345,20 @@ void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, Pre
     a2.cz = cz;
     a2.st = V.st;
     a2.part = V.part;
+    a2.npart = npart;
+    a2.h_inner = V.batched ? 0 : h_inner;
     a2.Z = V.Z<T>();
     a2.tw = (const cpx<T>*)R.tws(ka.E);
-    cudaGraphNode_t n4 = V.batched ? gb.kernel(body, &n3, 1, ka.f, V.grid(row_grid(p, ka)), ka.threads, ka.smem, a2,
-                                               V.inner())
-                                   : pass_node(gb, body, n3, ka, V.grid(row_grid(p, ka)), V, a2, V.inner());
+    cudaGraphNode_t n4 = pass_node(gb, body, n3, ka, V.grid(row_grid(p, ka)), V, a2, V.inner());
     // the single-problem column pass returns at entry once the run has ended
-    ColArgs<T> b2{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, V.batched ? 0 : GATE_IDLE};
-    cudaGraphNode_t n5 = pass_node(gb, body, n4, kb, V.grid(col_grid(p, kb)), V, b2, V.inner(true));
+    ColArgs<T> b2{p->L, V.Z<T>(), (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E), V.st, V.batched ? 0 : GATE_IDLE, 1};
+    cudaGraphNode_t n5;
+    if (V.batched) {
+        batch_ctl_node(gb, body, n4, V, 0, h_inner, &n4);
+        n5 = gb.kernel(body, &n4, 1, kb.f, V.grid(col_grid(p, kb)), kb.threads, kb.smem, b2, V.inner(true));
+    } else {
+        n5 = pass_node(gb, body, n4, kb, V.grid(col_grid(p, kb)), V, b2, V.inner(true));
+    }
     RowInvArgs<T> c2{};
     c2.L = p->L;
     c2.mode = RI_PQ;

@@ -104,6 +104,36 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*scratch)[NV]
     }
 }
 
+// The grid's partials are added by one warp alone (strided runs, one warp
+// tree): lane l adds blocks l, l + 32, l + 64, ... in that order, four
+// blocks' values loaded at a time so that their L2 round trips overlap.
+// Totals in lane 0.  FP64 partials (NV doubles per block).
+template <int NV>
+__device__ __forceinline__ void warp_sum_partials(const double* part, unsigned G, double (&tot)[NV]) {
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (unsigned b0 = threadIdx.x & 31; b0 < G; b0 += 128) {
+        double q[4][NV];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                q[u][k] = b0 + 32 * u < G ? __ldcg(part + (size_t)(b0 + 32 * u) * NV + k) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                if (b0 + 32 * u < G) acc[k] += q[u][k];
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+        tot[k] = acc[k];
+    }
+}
+
 // Publish this block's partial sums and, in the last block to finish, add
 // all blocks' partials in block order.  Returns true (in every thread of the
 // last block) with the totals in tot (valid in thread 0).  Deterministic:
@@ -127,29 +157,7 @@ __device__ __forceinline__ bool grid_sum_last(double (&v)[NV], double* part, uns
     // blocks' values loaded at a time so that their L2 round trips overlap
     if (threadIdx.x < 32) {
         __threadfence();
-        double acc[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] = 0.0;
-        const unsigned G = gridDim.x;
-        for (unsigned b0 = threadIdx.x; b0 < G; b0 += 128) {
-            double q[4][NV];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int k = 0; k < NV; ++k)
-                    q[u][k] = b0 + 32 * u < G ? __ldcg(part + (size_t)(b0 + 32 * u) * NV + k) : 0.0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int k = 0; k < NV; ++k)
-                    if (b0 + 32 * u < G) acc[k] += q[u][k];
-        }
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
-            tot[k] = acc[k];
-        }
+        warp_sum_partials<NV>(part, gridDim.x, tot);
         if (threadIdx.x == 0) *cnt = 0u;
     }
     return true;
@@ -192,7 +200,7 @@ __device__ __forceinline__ void ff_add(float& hi, float& lo, float h, float l) {
 template <typename T>
 struct Acc {
     T v = 0;
-    __device__ __forceinline__ void prod(T a, T b) { v += a * b; }
+    __device__ __forceinline__ void prod(T a, T b) { v = fma(a, b, v); }
     __device__ __forceinline__ void set(T x) { v = x; }
     __device__ __forceinline__ double value() const { return (double)v; }
 };
@@ -248,6 +256,41 @@ __device__ __forceinline__ void block_sum_ff(float (&hi)[NV], float (&lo)[NV], f
     }
 }
 
+// warp_sum_partials for two-float partials (NV float2 per block, the room of
+// NV doubles), added in the same order with ff_add; FP64 totals in lane 0.
+template <int NV>
+__device__ __forceinline__ void warp_sum_partials(const float2* pf, unsigned G, double (&tot)[NV]) {
+    float hi[NV], lo[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        hi[k] = 0.f;
+        lo[k] = 0.f;
+    }
+    for (unsigned b0 = threadIdx.x & 31; b0 < G; b0 += 128) {
+        float2 q[4][NV];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                q[u][k] = b0 + 32 * u < G ? __ldcg(pf + (size_t)(b0 + 32 * u) * NV + k) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < NV; ++k)
+                if (b0 + 32 * u < G) ff_add(hi[k], lo[k], q[u][k].x, q[u][k].y);
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float h = __shfl_down_sync(0xffffffffu, hi[k], off);
+            const float l = __shfl_down_sync(0xffffffffu, lo[k], off);
+            ff_add(hi[k], lo[k], h, l);
+        }
+        tot[k] = (double)hi[k] + (double)lo[k];
+    }
+}
+
 // grid_sum_last for FP32 partials (each thread's Dot2 pair): the per-block
 // sums are published as two-float pairs (part holds NV float2 per block, the
 // room of NV doubles) and the last block's warp 0 adds them in block order
@@ -276,41 +319,8 @@ __device__ __forceinline__ bool grid_sum_last(const Acc<float> (&v)[NV], double*
     if (!is_last) return false;
     if (threadIdx.x < 32) {
         __threadfence();
-        // lane l adds blocks l, l + 32, l + 64, ... in that order, four blocks'
-        // pairs loaded at a time so that their L2 round trips overlap
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            hi[k] = 0.f;
-            lo[k] = 0.f;
-        }
-        const unsigned G = gridDim.x;
-        for (unsigned b0 = threadIdx.x; b0 < G; b0 += 128) {
-            float2 q[4][NV];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int k = 0; k < NV; ++k)
-                    q[u][k] = b0 + 32 * u < G ? __ldcg(pf + (size_t)(b0 + 32 * u) * NV + k) : make_float2(0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int k = 0; k < NV; ++k)
-                    if (b0 + 32 * u < G) ff_add(hi[k], lo[k], q[u][k].x, q[u][k].y);
-        }
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const float h = __shfl_down_sync(0xffffffffu, hi[k], off);
-                const float l = __shfl_down_sync(0xffffffffu, lo[k], off);
-                ff_add(hi[k], lo[k], h, l);
-            }
-        }
-        if (threadIdx.x == 0) {
-#pragma unroll
-            for (int k = 0; k < NV; ++k) tot[k] = (double)hi[k] + (double)lo[k];
-            *cnt = 0u;
-        }
+        warp_sum_partials<NV>(pf, gridDim.x, tot);
+        if (threadIdx.x == 0) *cnt = 0u;
     }
     return true;
 }
@@ -323,6 +333,84 @@ __device__ __forceinline__ bool grid_sum_last(const Acc<double> (&a)[NV], double
 #pragma unroll
     for (int k = 0; k < NV; ++k) v[k] = a[k].v;
     return grid_sum_last<NV>(v, part, cnt, tot);
+}
+
+// Publish this block's partial sums only (in the layout of grid_sum_last):
+// the pass that follows adds them up (grid_total), after this grid has
+// completed, so no block waits for the others.
+template <int NV>
+__device__ __forceinline__ void grid_publish(const Acc<float> (&v)[NV], double* part) {
+    __shared__ float2 scratch[32][NV];
+    float hi[NV], lo[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        hi[k] = v[k].hi;
+        lo[k] = v[k].lo;
+    }
+    block_sum_ff<NV>(hi, lo, scratch);
+    float2* pf = reinterpret_cast<float2*>(part);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) pf[(size_t)blockIdx.x * NV + k] = make_float2(hi[k], lo[k]);
+}
+template <int NV>
+__device__ __forceinline__ void grid_publish(const Acc<double> (&a)[NV], double* part) {
+    __shared__ double scratch[32][NV];
+    double v[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = a[k].v;
+    block_sum<NV>(v, scratch);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) part[(size_t)blockIdx.x * NV + k] = v[k];
+}
+
+// The totals of NV sums that G blocks of an earlier pass published, added in
+// the order of grid_sum_last (the same values in every block that adds
+// them).  Called by one warp; totals in lane 0.
+template <typename T, int NV>
+__device__ __forceinline__ void warp_total(const double* part, int G, double (&tot)[NV]) {
+    if constexpr (sizeof(T) == 4)
+        warp_sum_partials<NV>(reinterpret_cast<const float2*>(part), (unsigned)G, tot);
+    else
+        warp_sum_partials<NV>(part, (unsigned)G, tot);
+}
+
+// PCG step decisions in the pass A that consumes pass C's sums: warp 0 adds
+// the published partials, thread 0 evaluates the decision (pcg_zr_eval for
+// RF_PCG_P, pcg_alpha_eval for RF_PCG_R) and, in the committing block,
+// commits it.  Returns the coefficient (beta or alpha) in every thread and
+// false when the inner run has ended (RF_PCG_P: nothing to transform).
+template <typename T>
+__device__ __forceinline__ bool pcg_consume(int mode, CgState* st, const double* part, int G,
+                                            unsigned long long h_inner, bool commit, T& coef) {
+    __shared__ double s_coef;
+    __shared__ int s_go;
+    if (threadIdx.x < 32) {
+        const PcgView sv = pcg_view(st);  // loaded with the partials (no dependency between them)
+        if (mode == RF_PCG_P) {
+            double tot[2];
+            warp_total<T, 2>(part, G, tot);
+            if (threadIdx.x == 0) {
+                const PcgZr z = pcg_zr_eval(sv, tot[0], tot[1]);
+                if (commit) pcg_zr_commit(st, z, tot[0], tot[1], h_inner);
+                s_coef = z.beta;
+                s_go = z.d == 0;
+            }
+        } else {
+            double tot[1];
+            warp_total<T, 1>(part, G, tot);
+            if (threadIdx.x == 0) {
+                const PcgAlpha al = pcg_alpha_eval(sv, tot[0]);
+                if (commit) pcg_alpha_commit(st, al, tot[0]);
+                s_coef = al.alpha;
+                s_go = 1;
+            }
+        }
+    }
+    __syncthreads();
+    coef = (T)s_coef;
+    return s_go != 0;
 }
 
 // --------------------------------------------------- per-element input ---
@@ -387,7 +475,7 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
             for (int e = 0; e < H; ++e)
                 if (ok[e]) {
                     double t = xv[e];
-                    if (d32 && sc.sig != 0.0) t += sc.sig * (double)dv[e];
+                    if (d32 && sc.sig != 0.0) t = fma(sc.sig, (double)dv[e], t);
                     if (!mv[e]) t = 0.0;
                     x64[b + e * G] = t;
                     val[e] = (T)t;
@@ -401,7 +489,7 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
 #pragma unroll
                 for (int e = 0; e < H; ++e)
                     if (ok[e]) {
-                        val[e] = (T)(rv[e] * sc.inv_sigma);
+                        val[e] = (T)mul_rn(rv[e], sc.inv_sigma);
                         cr[b + e * G] = val[e];
                         cx[b + e * G] = 0;
                     }
@@ -418,7 +506,7 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
                         if (ok[e]) pv[e] = cp[b + e * G];
 #pragma unroll
                     for (int e = 0; e < H; ++e)
-                        if (ok[e]) val[e] = val[e] + sc.bcarry * pv[e];
+                        if (ok[e]) val[e] = fma(sc.bcarry, pv[e], val[e]);
                 }
 #pragma unroll
                 for (int e = 0; e < H; ++e)
@@ -435,7 +523,7 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
 #pragma unroll
             for (int e = 0; e < H; ++e)
                 if (ok[e]) {
-                    val[e] = sc.first ? zv[e] : zv[e] + sc.beta * pv[e];
+                    val[e] = sc.first ? zv[e] : fma(sc.beta, pv[e], zv[e]);
                     cp[b + e * G] = val[e];
                 }
         } else {  // RF_CG, RF_PCG_R: x += alpha p, r -= alpha q (and p = r + beta p)
@@ -451,11 +539,11 @@ __device__ __forceinline__ void pass_a_inputs(int mode, const T* __restrict__ xi
 #pragma unroll
             for (int e = 0; e < H; ++e)
                 if (ok[e]) {
-                    const T r = rv[e] - sc.alpha * qv[e];
-                    cx[b + e * G] = xv[e] + sc.alpha * pv[e];
+                    const T r = fma(-sc.alpha, qv[e], rv[e]);
+                    cx[b + e * G] = fma(sc.alpha, pv[e], xv[e]);
                     cr[b + e * G] = r;
                     if (mode == RF_CG) {
-                        val[e] = r + sc.beta * pv[e];
+                        val[e] = fma(sc.beta, pv[e], r);
                         cp[b + e * G] = val[e];
                     } else {
                         val[e] = r;
@@ -489,25 +577,19 @@ __device__ __forceinline__ AScal<T> ascal_from_state(const RowFwdArgs<T>& a, con
     return sc;
 }
 
-// One unit of pass A: RB row pairs starting at pair unit*RB, G = M/E threads
-// per pair.  Leaves shared memory in use: the caller synchronises before the
-// block reuses it.  vo, zo: the problem's offsets in the vectors and the
-// intermediate.
+// The transform half of a pass-A unit: FFT of the packed row pairs v, split
+// into the two rows' half spectra, column-major store at offset zo.
 template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
-__device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm,
-                                          size_t vo = 0, size_t zo = 0) {
+__device__ __forceinline__ void rfwd_transform(const RowFwdArgs<T>& a, cpx<T> (&v)[E], int unit, cpx<T>* sm,
+                                               size_t zo) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, NT = RB * G, SEG = seg_len(M);
     constexpr int GS = (DB ? 2 : 1) * SEG;  // shared elements per pair
     constexpr int NB = next_buf(M, E, DB, 0);
     const int t = threadIdx.x, j = t % G, pl = t / G;
     const int L = a.L;
-    const int r0 = (unit * RB + pl) * 2;
-
-    C v[E];
-    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, L, vo, v);
     C* g0 = sm + pl * GS;
-    fft_stages<T, M, E, false, DB, 0>(v, j, g0, g0 + SEG, a.tw);
+    fft_stages<T, M, E, false, DB, 0, 1, true>(v, j, g0, g0 + SEG, a.tw);
     C* wp = g0 + NB * SEG + spad(j);
 #pragma unroll
     for (int e = 0; e < E; ++e) wp[pofs(e * G)] = v[e];
@@ -533,6 +615,96 @@ __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>
     }
 }
 
+// One unit of pass A: RB row pairs starting at pair unit*RB, G = M/E threads
+// per pair.  Leaves shared memory in use: the caller synchronises before the
+// block reuses it.  vo, zo: the problem's offsets in the vectors and the
+// intermediate.
+template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
+__device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm,
+                                          size_t vo = 0, size_t zo = 0) {
+    constexpr int G = M / E;
+    const int t = threadIdx.x, j = t % G, pl = t / G;
+    const int r0 = (unit * RB + pl) * 2;
+    cpx<T> v[E];
+    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, a.L, vo,
+                           v);
+    rfwd_transform<T, M, E, RB, DB>(a, v, unit, sm, zo);
+}
+
+// Whether a pass A takes a PCG step decision from the last pass C's
+// published sums (a.npart blocks; none: the coefficients as the state holds
+// them): RF_PCG_P always (beta, the stopping test), RF_PCG_R after the first
+// update of a run (alpha).
+template <typename T>
+__device__ __forceinline__ bool pcg_decides(const RowFwdArgs<T>& a, const AScal<T>& sc) {
+    return a.npart > 0 && (a.mode == RF_PCG_P || (a.mode == RF_PCG_R && !sc.first));
+}
+
+// A pass-A unit in a PCG mode that takes the step decision: each thread's
+// operands (both rows) are loaded first, so that their memory round trip
+// overlaps the one of the published sums; then the update with the decided
+// coefficient (RF_PCG_R: x += alpha p, r -= alpha q, transform r; RF_PCG_P:
+// p = z + beta p, transform p) and the transform.  Returns false, having
+// written nothing, when the decision ends the run.
+template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
+__device__ __forceinline__ bool rfwd_unit_pcg(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm,
+                                              CgState* st, const double* part, bool commit,
+                                              unsigned long long h_inner, size_t vo = 0, size_t zo = 0) {
+    constexpr int G = M / E, H = E / 2;
+    const int t = threadIdx.x, j = t % G, pl = t / G;
+    const int L = a.L;
+    const int r0 = (unit * RB + pl) * 2;
+    const bool upd_r = a.mode == RF_PCG_R;
+    T o0[2][H], o1[2][H], o2[2][H], o3[2][H];  // RF_PCG_R: p, x, r, q; RF_PCG_P: z, p
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const size_t b = vo + (size_t)(r0 + h) * L + j;
+#pragma unroll
+        for (int e = 0; e < H; ++e) {
+            o0[h][e] = o1[h][e] = o2[h][e] = o3[h][e] = (T)0;
+            if (r0 + h < L && j + e * G < L) {
+                if (upd_r) {
+                    o0[h][e] = a.cp[b + e * G];
+                    o1[h][e] = a.cx[b + e * G];
+                    o2[h][e] = a.cr[b + e * G];
+                    o3[h][e] = a.cq[b + e * G];
+                } else {
+                    o0[h][e] = a.cz[b + e * G];
+                    if (!sc.first) o1[h][e] = a.cp[b + e * G];
+                }
+            }
+        }
+    }
+    T coef;
+    if (!pcg_consume<T>(a.mode, st, part, a.npart, h_inner, commit, coef)) return false;
+    cpx<T> v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = cpx<T>{0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const size_t b = vo + (size_t)(r0 + h) * L + j;
+#pragma unroll
+        for (int e = 0; e < H; ++e) {
+            if (!(r0 + h < L && j + e * G < L)) continue;
+            T val;
+            if (upd_r) {
+                val = fma(-coef, o3[h][e], o2[h][e]);
+                a.cx[b + e * G] = fma(coef, o0[h][e], o1[h][e]);
+                a.cr[b + e * G] = val;
+            } else {
+                val = sc.first ? o0[h][e] : fma(coef, o1[h][e], o0[h][e]);
+                a.cp[b + e * G] = val;
+            }
+            if (h == 0)
+                v[e].x = val;
+            else
+                v[e].y = val;
+        }
+    }
+    rfwd_transform<T, M, E, RB, DB>(a, v, unit, sm, zo);
+    return true;
+}
+
 // MINB: blocks per SM the register allocation must allow; DB: double-buffered
 // exchanges (default: when they fit, see use_db).
 template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
@@ -541,9 +713,15 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
-    if (a.mode == RF_PCG_P && a.st->idle) return;  // PCG: the z pass ended the run
+    if (a.mode == RF_PCG_P && a.st->idle) return;  // PCG: the run has ended
     const AScal<T> sc = ascal_from_state(a, a.st);
-    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    if (pcg_decides(a, sc)) {
+        if (!rfwd_unit_pcg<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), a.st, a.part,
+                                            blockIdx.x == 0, a.h_inner))
+            return;
+    } else {
+        rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    }
     pdl_leave();
 }
 
@@ -556,7 +734,19 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_b(const RowFwdArgs<T>
     pdl_enter();
     if (bb.gate && gate_closed(st, bb.gate)) return;
     if (a.mode == RF_XUPD && st->warm) return;
-    const AScal<T> sc = ascal_from_state(a, st);
+    AScal<T> sc = ascal_from_state(a, st);
+    // the decision first, then the unit: with many problems' blocks resident
+    // the loads' latency hides behind other blocks, and the registers that
+    // early loads would hold cost resident blocks (the arithmetic is the same)
+    if (pcg_decides(a, sc)) {
+        T coef;
+        if (!pcg_consume<T>(a.mode, st, a.part + (size_t)blockIdx.y * bb.bs.part, a.npart, 0, blockIdx.x == 0, coef))
+            return;
+        if (a.mode == RF_PCG_P)
+            sc.beta = coef;
+        else
+            sc.alpha = coef;
+    }
     rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * bb.bs.n,
                                (size_t)blockIdx.y * bb.bs.z);
     pdl_leave();
@@ -586,7 +776,7 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
         v[e] = (e < E / 2 && n < L) ? ldc_cg(col + n) : C{0, 0};
     }
     C* g0 = sm + c * GS;
-    fft_stages<T, M, E, false, DB, 0>(v, j, g0, g0 + SEG, a.tw);
+    fft_stages<T, M, E, false, DB, 0, 1, true>(v, j, g0, g0 + SEG, a.tw);
     if (unit == 0) {
         // column 0 holds P = F0 + i FN (kx = 0 and kx = M/2, both real along y);
         // with the Hermitian partner P[M - ky]: W = P (g0 + gN)/2 + conj(P[M-ky]) (g0 - gN)/2
@@ -602,7 +792,7 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
                 const C pc = conjc(seg[spad((M - ky) & (M - 1))]);
                 const T g0 = __ldg(Gq + fy), gN = __ldg(Gq + (size_t)H * Q + fy);
                 const T sp = (g0 + gN) * (T)0.5, sd = (g0 - gN) * (T)0.5;
-                v[e] = C{v[e].x * sp + pc.x * sd, v[e].y * sp + pc.y * sd};
+                v[e] = C{fma(v[e].x, sp, mul_rn(pc.x, sd)), fma(v[e].y, sp, mul_rn(pc.y, sd))};
             }
         } else {
             const T* gk = Gq + (size_t)kx * Q;
@@ -638,6 +828,7 @@ __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     if (a.gate && gate_closed(a.st, a.gate)) return;
+    if (a.pcg_commit && blockIdx.x == 0 && threadIdx.x == 0) pcg_rz_commit(a.st);
     colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
     pdl_leave();
 }
@@ -647,6 +838,7 @@ __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc_b(const ColArgs<T> a,
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     if ((a.gate | bb.gate) && gate_closed(a.st + blockIdx.y, a.gate | bb.gate)) return;
+    if (a.pcg_commit && blockIdx.x == 0 && threadIdx.x == 0) pcg_rz_commit(a.st + blockIdx.y);
     colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * bb.bs.z,
                                (size_t)blockIdx.y * bb.bs.q);
     pdl_leave();
@@ -709,7 +901,7 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
 #pragma unroll
             for (int e = 0; e < H; ++e)
                 if (ok[e]) {
-                    const T q = act[e] ? yv[e] + sv[e] * pv[e] : (T)0;
+                    const T q = act[e] ? fma(sv[e], pv[e], yv[e]) : (T)0;
                     cq[b + e * G] = q;
                     s0.prod(pv[e], q);
                     s1.prod(rv[e], q);
@@ -728,7 +920,7 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
 #pragma unroll
             for (int e = 0; e < H; ++e)
                 if (ok[e]) {
-                    const T q = act[e] ? yv[e] + sv[e] * pv[e] : (T)0;
+                    const T q = act[e] ? fma(sv[e], pv[e], yv[e]) : (T)0;
                     cq[b + e * G] = q;
                     s0.prod(pv[e], q);
                 }
@@ -758,7 +950,7 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
             for (int e = 0; e < H; ++e)
                 if (ok[e]) {
                     const double bb = act[e] ? bv[e] : 0.0;
-                    const double r = act[e] ? bb - ((double)yv[e] + sv[e] * xv[e]) : 0.0;
+                    const double r = act[e] ? bb - fma(sv[e], xv[e], (double)yv[e]) : 0.0;
                     r64[b + e * G] = r;
                     s0.prod((T)r, (T)r);
                     s1.prod((T)bb, (T)bb);
@@ -824,7 +1016,8 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
                             v, s0, s1, s2, s3, s4);
 }
 
-// Pass C's grid sums and step decisions (last block).  warm (RI_RESID): the
+// Pass C's grid sums and step decisions (last block; the PCG modes only
+// publish their partials for the next pass A).  warm (RI_RESID): the
 // residual and its sums were updated in place, and block 0 alone hands them on.
 template <typename T>
 __device__ __forceinline__ void rinv_sums(const RowInvArgs<T>& a, double* part, CgState* st, const Acc<T>& s0,
@@ -840,14 +1033,12 @@ __device__ __forceinline__ void rinv_sums(const RowInvArgs<T>& a, double* part, 
             refine_decide(st, tot[0], tot[1], a.h_outer, a.h_inner);
             st->warm = 0;  // every block has read it: later cycles recompute the residual
         }
-    } else if (a.mode == RI_PCG_Z) {
+    } else if (a.mode == RI_PCG_Z) {  // the next pass A decides (pcg_step)
         const Acc<T> pv[2] = {s0, s1};
-        double tot[2];
-        if (grid_sum_last<2>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_zr_decide(st, tot[0], tot[1], a.h_inner);
+        grid_publish<2>(pv, part);
     } else if (a.mode == RI_PQ) {
         const Acc<T> pv[1] = {s0};
-        double tot[1];
-        if (grid_sum_last<1>(pv, part, &st->cntC, tot) && threadIdx.x == 0) pcg_alpha_decide(st, tot[0]);
+        grid_publish<1>(pv, part);
     }
 }
 

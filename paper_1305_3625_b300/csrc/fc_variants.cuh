@@ -96,10 +96,10 @@ void add_pers(Variants& v) {
 }
 
 // Launch shapes compiled for each (precision, M).  FP32 sizes from 256 up
-// carry seven to nine shapes per pass for the autotuner: E = 16, 8 or 4 with
+// carry seven to twelve shapes per pass for the autotuner: E = 32, 16, 8 or 4 with
 // one or more rows or columns per block, single-buffered 64-register shapes
 // (more resident blocks), 1024-thread row blocks, and the TMA-staged pass C.
-// FP64 (ALU-bound on this part) carries one.
+// FP64 (ALU-bound on this part) carries one or two: radix 8 and radix 16.
 template <typename T, int M>
 void make_variants(Variants& v) {
     constexpr int H = M / 2;
@@ -137,6 +137,16 @@ void make_variants(Variants& v) {
             // 1024-thread row blocks: more rows per block make the column-major
             // intermediate's row segments longer (full 32-byte sectors at M = 8192)
             add_row<T, M, 16, clampi(1024 / G16, 1, 64), 1, false>(v);
+            if constexpr (M >= 4096) {
+                // radix-32 stages: one exchange fewer per transform at M = 8192
+                // (32^2 x 8; below M = 4096 they timed no faster than radix 16)
+                constexpr int G32 = M / 32;
+                add_row<T, M, 32, clampi(256 / G32, 1, 64)>(v);
+                add_row<T, M, 32, clampi(512 / G32, 1, 64)>(v);
+                add_col<T, M, 32, clampi(256 / G32, 1, H)>(v);
+                add_col<T, M, 32, clampi(256 / G32, 1, H), 2>(v);
+                add_col<T, M, 32, clampi(512 / G32, 1, H)>(v);
+            }
             add_rinv_tma<M>(v);
         }
         add_pers<T, M, 16, 16, (M * M / 32 < 256 ? M * M / 32 : 256)>(v);
@@ -152,6 +162,12 @@ void make_variants(Variants& v) {
         constexpr int CB = clampi(256 / G, 1, H);
         add_row<T, M, E, RB>(v);
         add_col<T, M, E, CB>(v);
+        if constexpr (M >= 256 && M <= 2048) {
+            // radix 16: one twiddled stage fewer than radix 8 below M = 4096
+            constexpr int G16 = M / 16;
+            add_row<T, M, 16, clampi(256 / G16, 1, 128)>(v);
+            add_col<T, M, 16, clampi(256 / G16, 1, H)>(v);
+        }
         constexpr int CBF = clampi(256 / G, 1, M);
         v.rows_full = KV{(const void*)k_rows_full<M, E, RB>, RB * G, RB, E, (size_t)RB * seg_len(M) * sizeof(cpx<double>)};
         v.cols_full = KV{(const void*)k_cols_full<M, E, CBF>, CBF * G, CBF, E, (size_t)CBF * seg_len(M) * sizeof(cpx<double>)};

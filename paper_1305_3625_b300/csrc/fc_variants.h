@@ -26,7 +26,7 @@ struct KVP {
 };
 
 struct Variants {
-    static constexpr int kMax = 12;  // compiled shapes per pass and size (at most)
+    static constexpr int kMax = 16;  // compiled shapes per pass and size (at most)
     KV rfwd[kMax], colc[kMax], rinv[kMax];
     int n_rfwd = 0, n_colc = 0, n_rinv = 0;
     KVP pers[6];
