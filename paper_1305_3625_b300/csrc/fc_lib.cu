@@ -738,6 +738,8 @@ bool get_variants(int M, Variants* v) {
 int set_smem_attr(const KV& k) {
     if (k.f && k.smem > 48 * 1024)
         FC_CK(cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+    if (k.fp && k.smem > 48 * 1024)
+        FC_CK(cudaFuncSetAttribute(k.fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
     return FC_OK;
 }
 
@@ -1163,7 +1165,7 @@ int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStr
     }
     const int grid = kind == 1 ? col_grid(p, kv) : row_grid(p, kv);
     auto go = [&]() -> int {
-        if (kind == 0) return launch(kv.f, grid, kv.threads, kv.smem, s, a);
+        if (kind == 0) return launch(cgv && kv.fp ? kv.fp : kv.f, grid, kv.threads, kv.smem, s, a);
         if (kind == 1) return launch(kv.f, grid, kv.threads, kv.smem, s, b);
         return launch_rinv<T>(p, R, kv, c, s, false);
     };
@@ -2305,7 +2307,11 @@ template <typename T>
 void add_inner_body_pcg(GraphBuilder& gb, cudaGraph_t body, fftconv_plan* p, PrecRes& R, const SolveView& V, T* cx,
                         T* cr, T* cp, T* cq, T* cz, const T* s, const T* pq, const double* r64_start,
                         cudaGraphConditionalHandle h_inner) {
-    const KV &ka = rfwd_shape(R, V.batched), &kb = colc_shape(R, V.batched), &kc = rinv_shape(R, V.batched);
+    const KV &kb = colc_shape(R, V.batched), &kc = rinv_shape(R, V.batched);
+    // single problem: the pass-A kernel that takes the step decision (the
+    // batched twin takes it itself)
+    KV ka = rfwd_shape(R, V.batched);
+    if (!V.batched && ka.fp) ka.f = ka.fp;
     // blocks of pass C, whose partial sums the passes A add up
     int npart = row_grid(p, kc);
     if constexpr (sizeof(T) == 4)

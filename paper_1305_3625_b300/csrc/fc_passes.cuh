@@ -715,6 +715,22 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd(const RowFwdArgs<T> a
     if (a.mode == RF_XUPD && a.st->warm) return;  // residual already updated: no product
     if (a.mode == RF_PCG_P && a.st->idle) return;  // PCG: the run has ended
     const AScal<T> sc = ascal_from_state(a, a.st);
+    rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    pdl_leave();
+}
+
+// The single-problem pass A of the PCG loop (RF_PCG_R, RF_PCG_P), which
+// takes the step decision from the last pass C's published sums (pcg_decides,
+// rfwd_unit_pcg).  A kernel of its own: the early loads of its operands make
+// its code much larger than k_rfwd's, and k_rfwd in the plain apply then
+// stalled on instruction fetch.
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_pcg(const RowFwdArgs<T> a) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
+    if (a.mode == RF_PCG_P && a.st->idle) return;  // the run has ended
+    const AScal<T> sc = ascal_from_state(a, a.st);
     if (pcg_decides(a, sc)) {
         if (!rfwd_unit_pcg<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), a.st, a.part,
                                             blockIdx.x == 0, a.h_inner))

@@ -48,6 +48,7 @@ template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M,
 void add_row(Variants& v) {
     if constexpr (RB * (M / E) <= 1024 && pass_smem<T, M, RB, DB>() <= 200 * 1024) {
         KV f{(const void*)k_rfwd<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
+        f.fp = (const void*)k_rfwd_pcg<T, M, E, RB, MINB, DB>;
         KV i{(const void*)k_rinv<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
         for (int k = 0; k < v.n_rfwd; ++k)
             if (v.rfwd[k].f == f.f) return;

@@ -15,6 +15,7 @@ struct KV {
     int threads = 0, per = 0, E = 0;
     size_t smem = 0;
     int tma = 0;  // 1: TMA-staged persistent pass C (k_rinv_tma; needs the plan's tensor map)
+    const void* fp = nullptr;  // pass A: the same shape's PCG step-deciding kernel (k_rfwd_pcg)
 };
 
 // One compiled persistent inner-CG kernel: pass A/C shape (EA, RB) and
