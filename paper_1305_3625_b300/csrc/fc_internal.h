@@ -49,6 +49,8 @@ struct CgState {
     int warm_used;       // 1: this solve's first true residual was updated, not recomputed
     int wbad;            // the update does not apply (s or b changed, active set grew)
     unsigned wcount;     // entries of x that changed (the list holds the first kWarmMax)
+    int s_check;         // 1: the warm check compares s with the last solve's (its FP32 copy is kept)
+    int s_diff;          // the warm check found s changed (the FP32 copy is made anew)
     int tma_err;         // 1: a staged TMA copy never arrived (the solve ends with FC_ETIMEOUT)
     int idle;            // 1: no inner run is in progress (batched solves: the inner passes skip
                          // this problem)

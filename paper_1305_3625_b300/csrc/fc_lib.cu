@@ -268,7 +268,11 @@ __global__ void k_cg_final(long N, const CgState* st, T* x, const T* p) {
         x[i] += alpha * p[i];
 }
 
-__global__ void k_f64_to_f32(long N, const double* a, float* b) {
+// FP32 copy of the diagonal.  With a state (single-problem solves): nothing
+// to do when the warm check found s bitwise unchanged since the last solve,
+// whose copy is still in place.
+__global__ void k_f64_to_f32(long N, const double* a, float* b, const CgState* st) {
+    if (st && st->s_check && !st->s_diff) return;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
 }
@@ -282,12 +286,27 @@ __global__ void __launch_bounds__(256) k_active_mean(long N, const double* s, co
     if (mask) mask += blockIdx.y * N;
     part += blockIdx.y * bpart;
     st += blockIdx.y;
-    double v[2] = {0.0, 0.0}, tot[2];
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x)
-        if (!mask || mask[i]) {
-            v[0] += s[i];
-            v[1] += 1.0;
+    // four sites per round, all loaded before use; the count is an integer
+    double sum = 0.0;
+    unsigned cnt = 0;
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += 4 * stride) {
+        double sv[4];
+        uint8_t mv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long i = i0 + u * stride;
+            sv[u] = i < N ? s[i] : 0.0;
+            mv[u] = i < N ? (mask ? mask[i] : (uint8_t)1) : (uint8_t)0;
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (mv[u]) {
+                sum += sv[u];
+                ++cnt;
+            }
+    }
+    double v[2] = {sum, (double)cnt}, tot[2];
     if (grid_sum_last<2>(v, part, &st->cntA, tot) && threadIdx.x == 0) st->pshift = tot[1] > 0 ? tot[0] / tot[1] : 1.0;
 }
 
@@ -301,6 +320,16 @@ __global__ void k_precond_spectrum(long QQ, double MM, const double* gq64, const
     const double c = st->pshift;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < QQ; i += (long)gridDim.x * blockDim.x)
         pq[i] = (T)(1.0 / ((MM * gq64[i] + c) * MM));
+}
+// The FP32 preconditioner spectrum from the FP32 kernel spectrum, in FP32
+// arithmetic (an FP64 division per entry cost tens of microseconds per solve
+// on this part; the preconditioner needs no more than FP32 accuracy).
+__global__ void k_precond_spectrum_f32(long QQ, float MM, const float* gq32, const CgState* st, float* pq) {
+    st += blockIdx.y;
+    pq += blockIdx.y * QQ;
+    const float c = (float)st->pshift;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < QQ; i += (long)gridDim.x * blockDim.x)
+        pq[i] = 1.0f / (fmaf(MM, gq32[i], c) * MM);
 }
 
 // A solve from x = 0 needs no product for its first true residual: it is
@@ -350,7 +379,7 @@ __global__ void __launch_bounds__(256) k_warm_resid_batch(long N, int L, const d
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
         double r = 0.0;
         if (mask[i]) {
-            const int iy = (int)(i / L), ix = (int)(i % L);
+            const int iy = (int)i / L, ix = (int)i - iy * L;  // L <= 4096: N < 2^31
             r = r64[i] + xk * __ldg(gt + (size_t)abs(iy - ky) * L + abs(ix - kxx));
             const double bv = b64[i];
             v[1] += bv * bv;
@@ -410,27 +439,33 @@ __global__ void k_fill_u8(long N, uint8_t* m, uint8_t v) {
 
 // Copies s, b, the masked x and the mask into the plan's buffers (writing
 // only entries that changed) and records: st->wbad when s or b differ bitwise
-// or a site became active, st->wcount changed entries of x with the first
-// kWarmMax of them (flat index, x_new - x_old) in widx, wdx.
-__global__ void __launch_bounds__(256) k_warm_check(long N, const double* s, const double* b, const double* x,
-                                                    const uint8_t* mask_in, double* s64, double* b64, double* x64,
-                                                    uint8_t* mask, CgState* st, long long* widx, double* wdx) {
-    int bad = 0;
+// or a site became active, st->s_diff when s differs, st->wcount changed
+// entries of x with the first kWarmMax of them (flat index, x_new - x_old) in
+// widx, wdx.
+__global__ void __launch_bounds__(256) k_warm_check(long N, const double* __restrict__ s,
+                                                    const double* __restrict__ b, const double* __restrict__ x,
+                                                    const uint8_t* __restrict__ mask_in, double* __restrict__ s64,
+                                                    double* __restrict__ b64, double* __restrict__ x64,
+                                                    uint8_t* __restrict__ mask, CgState* st, long long* widx,
+                                                    double* wdx) {
+    int bad = 0, sdiff = 0;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-        const double sn = s[i], bn = b[i];
+        // every operand of the site loaded before the first test (one round trip)
+        const double sn = s[i], bn = b[i], xi = x[i], so = s64[i], bo = b64[i], xo = x64[i];
         const uint8_t mo = mask[i];
         const uint8_t mn = mask_in ? mask_in[i] : (uint8_t)1;
-        if (__double_as_longlong(sn) != __double_as_longlong(s64[i])) {
+        if (__double_as_longlong(sn) != __double_as_longlong(so)) {
             bad = 1;
+            sdiff = 1;
             s64[i] = sn;
         }
-        if (__double_as_longlong(bn) != __double_as_longlong(b64[i])) {
+        if (__double_as_longlong(bn) != __double_as_longlong(bo)) {
             bad = 1;
             b64[i] = bn;
         }
         if (mn && !mo) bad = 1;
         if (mn != mo) mask[i] = mn;
-        const double xn = mn ? x[i] : 0.0, xo = x64[i];
+        const double xn = mn ? xi : 0.0;
         if (__double_as_longlong(xn) != __double_as_longlong(xo)) {
             x64[i] = xn;
             const unsigned k = atomicAdd(&st->wcount, 1u);
@@ -440,17 +475,22 @@ __global__ void __launch_bounds__(256) k_warm_check(long N, const double* s, con
             }
         }
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->wbad, 1);
+    const int any_bad = __syncthreads_or(bad), any_s = __syncthreads_or(sdiff);
+    if (threadIdx.x == 0) {
+        if (any_bad) atomicOr(&st->wbad, 1);
+        if (any_s) atomicOr(&st->s_diff, 1);
+    }
 }
 
 // r64 <- P' (r64 - A D) with the recorded changes, and its sums rr64 = |r|^2,
 // bb = |P' b|^2; the last block sets st->warm so that the first residual
 // passes hand these to the refinement decision.  Does nothing (the passes
 // then compute the residual) when the check found the update inapplicable.
-__global__ void __launch_bounds__(256) k_warm_resid(long N, int L, const double* gt, const uint8_t* mask,
-                                                    const double* s64, const double* b64, double* r64,
-                                                    double* part, CgState* st, const long long* widx,
-                                                    const double* wdx) {
+__global__ void __launch_bounds__(256) k_warm_resid(long N, int L, const double* __restrict__ gt,
+                                                    const uint8_t* __restrict__ mask,
+                                                    const double* __restrict__ s64, const double* __restrict__ b64,
+                                                    double* __restrict__ r64, double* part, CgState* st,
+                                                    const long long* widx, const double* wdx) {
     __shared__ long long ki[kWarmMax];
     __shared__ int ky[kWarmMax], kx[kWarmMax];
     __shared__ double kd[kWarmMax];
@@ -466,20 +506,21 @@ __global__ void __launch_bounds__(256) k_warm_resid(long N, int L, const double*
     __syncthreads();
     double v[2] = {0.0, 0.0}, tot[2];
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const uint8_t m = mask[i];
+        const double r0 = r64[i], bv = b64[i];
         double r = 0.0;
-        if (mask[i]) {
-            const int iy = (int)(i / L), ix = (int)(i % L);
-            r = r64[i];
+        if (m) {
+            const int iy = (int)i / L, ix = (int)i - iy * L;  // L <= 4096: N < 2^31
+            r = r0;
             for (unsigned k = 0; k < K; ++k) {
-                double a = __ldg(gt + (size_t)abs(iy - ky[k]) * L + abs(ix - kx[k]));
+                double a = gt[(size_t)abs(iy - ky[k]) * L + abs(ix - kx[k])];
                 if (i == ki[k]) a += s64[i];
-                r -= kd[k] * a;
+                r = fma(-kd[k], a, r);
             }
-            const double bv = b64[i];
-            v[1] += bv * bv;
+            v[1] = fma(bv, bv, v[1]);
         }
         r64[i] = r;
-        v[0] += r * r;
+        v[0] = fma(r, r, v[0]);
     }
     if (grid_sum_last<2>(v, part, &st->cntC, tot) && threadIdx.x == 0) {
         st->rr64 = tot[0];
@@ -853,6 +894,7 @@ struct fftconv_plan {
     long long* widx = nullptr;
     double* wdx = nullptr;
     bool warm_ok = false;
+    bool s32_ok = false;  // s32 holds the FP32 copy of s64 (made by the last mixed solve)
     int64_t* rm_host = nullptr;  // pinned: last removed index of a fracture run
     bool blocking = false;       // waits block the host thread (event with blocking sync)
     cudaEvent_t ev_wait = nullptr;
@@ -2396,7 +2438,8 @@ int add_solve_nodes(fftconv_plan* p, const SolveView& V, int mode, bool precond,
         const double* sa = V.s64;
         float* sb = V.s32;
         const long NA = N * V.nb;
-        nPro = gb.kernel(g, nullptr, 0, (const void*)k_f64_to_f32, dim3(grid_1d(NA, 256)), 256, 0, NA, sa, sb);
+        const CgState* sst = V.batched ? nullptr : V.st;  // batches always convert
+        nPro = gb.kernel(g, nullptr, 0, (const void*)k_f64_to_f32, dim3(grid_1d(NA, 256)), 256, 0, NA, sa, sb, sst);
         ndeps = 1;
     }
     if (precond) {
@@ -2417,8 +2460,10 @@ int add_solve_nodes(fftconv_plan* p, const SolveView& V, int mode, bool precond,
         const CgState* ccst = V.st;
         if (mixed) {
             float* pq = V.pq32;
-            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<float>, V.grid(grid_1d(QQ, 256)), 256, 0,
-                             QQ, MM, g64, ccst, pq);
+            const float MMf = (float)MM;  // M^2 <= 2^26: exact
+            const float* g32 = (const float*)p->p32.Gq;
+            nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum_f32, V.grid(grid_1d(QQ, 256)), 256, 0, QQ,
+                             MMf, g32, ccst, pq);
         } else {
             double* pq = V.pq64;
             nPro = gb.kernel(g, &nm, 1, (const void*)k_precond_spectrum<double>, V.grid(grid_1d(QQ, 256)), 256, 0,
@@ -2689,12 +2734,17 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     init_state(o, &h);
     h.dbg_skip = p->dbg_skip;
     h.dbg_limit = p->dbg_limit;
-    *p->st_host = h;
-    FC_CK(cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st));
     // inputs into the plan's buffers (the graph is built on them); after a
     // finished solve, through the check that may replace the first FP64
-    // residual product by the update from the last residual
+    // residual product by the update from the last residual (and that finds
+    // whether the FP32 copy of s is still valid)
     const bool try_warm = p->warm_ok && !o->x0_zero && o->warm_resid == 0;
+    // the FP32 copy of s may be kept only if the last solve made it (a mixed
+    // one) and the check finds s unchanged
+    h.s_check = try_warm && p->s32_ok ? 1 : 0;
+    p->s32_ok = false;
+    *p->st_host = h;
+    FC_CK(cudaMemcpyAsync(p->st, p->st_host, sizeof(CgState), cudaMemcpyHostToDevice, st));
     p->warm_ok = false;  // the buffers change from here on
     if (try_warm) {
         k_warm_check<<<grid_1d(N, 256), 256, 0, st>>>(N, s, b, x, mask, p->s64, p->b64, p->x64, p->mask, p->st,
@@ -2728,7 +2778,7 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
         // runs the whole inner CG run; one status read per cycle.
         FC_CK(cudaMemsetAsync(p->pctl, 0, sizeof(PersistCtl), st));
         if (mixed) {
-            k_f64_to_f32<<<grid_1d(N, 256), 256, 0, st>>>(N, p->s64, p->s32);
+            k_f64_to_f32<<<grid_1d(N, 256), 256, 0, st>>>(N, p->s64, p->s32, p->st);
             FC_CK(cudaGetLastError());
         }
         for (int cyc = 0; cyc <= h.max_cycles + 1; ++cyc) {
@@ -2749,6 +2799,7 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
     // r64 is the true residual of the final x64 whenever the refinement
     // decision finished the solve
     p->warm_ok = f.finished && (f.status == FC_OK || f.status == FC_ENOCONV);
+    p->s32_ok = mixed;  // every mixed solve converts s (or keeps a valid copy)
     if (r) {
         fill_result(f, r);
         r->latency_s = r->run_s =

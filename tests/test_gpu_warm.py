@@ -209,3 +209,29 @@ def test_blocking_wait_mode_gives_the_same_solve():
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1:] == out[1][1:]
     with pytest.raises(fc.FcError):
         fc.fftconv_plan_sync_mode(fresh(8), 2)
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_fp32_diagonal_copy_follows_s(precond):
+    """A mixed solve keeps the FP32 copy of s from the previous solve only
+    when that solve was a mixed one and the warm check finds s bitwise
+    unchanged.  After an FP64-mode solve on the same plan, and after s
+    changes between warm-started mixed solves, the copy is made anew: each
+    solve meets its tolerance by the oracle's FP64 residual."""
+    L, rtol = 48, 1e-10
+    p = fc_inputs.problem(L, seed=5, with_t=True)
+    sv = Solver(L, p, precond=precond)
+    m = np.ones(L * L)
+    # FP64 solve first (the FP32 copy is not made), then a warm mixed solve
+    assert sv.solve(rtol, mode=fc.FC_MODE_F64)["status"] == fc.FC_OK
+    r = sv.solve(rtol, mode=fc.FC_MODE_MIXED)
+    assert r["status"] == fc.FC_OK
+    assert oracle_rel_resid(L, p["s"], p["b"], host(sv.x), m) <= 1.01 * rtol
+    # warm mixed solve with the same s (the copy is kept), then with a new s
+    r = sv.solve(rtol, mode=fc.FC_MODE_MIXED)
+    assert r["status"] == fc.FC_OK
+    s2 = p["s"] * 1.25
+    sv.s = dev(s2)
+    r = sv.solve(rtol, mode=fc.FC_MODE_MIXED)
+    assert r["status"] == fc.FC_OK
+    assert oracle_rel_resid(L, s2, p["b"], host(sv.x), m) <= 1.01 * rtol
