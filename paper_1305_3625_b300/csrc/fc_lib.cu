@@ -310,6 +310,37 @@ __global__ void __launch_bounds__(256) k_active_mean(long N, const double* s, co
     if (grid_sum_last<2>(v, part, &st->cntA, tot) && threadIdx.x == 0) st->pshift = tot[1] > 0 ? tot[0] / tot[1] : 1.0;
 }
 
+// The same shift from the FP32 copy of s (mixed solves): two-float sums on
+// the FP32 pipe instead of FP64 adds, which run at a small fraction of the
+// FP32 rate on this part (the shift only sets the preconditioner).
+__global__ void __launch_bounds__(256) k_active_mean_f32(long N, const float* s, const uint8_t* mask, double* part,
+                                                         CgState* st, long bpart) {
+    s += blockIdx.y * N;
+    if (mask) mask += blockIdx.y * N;
+    part += blockIdx.y * bpart;
+    st += blockIdx.y;
+    Acc<float> a[2];
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += 4 * stride) {
+        float sv[4];
+        uint8_t mv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long i = i0 + u * stride;
+            sv[u] = i < N ? s[i] : 0.f;
+            mv[u] = i < N ? (mask ? mask[i] : (uint8_t)1) : (uint8_t)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (mv[u]) {
+                a[0].prod(sv[u], 1.f);
+                a[1].prod(1.f, 1.f);
+            }
+    }
+    double tot[2];
+    if (grid_sum_last<2>(a, part, &st->cntA, tot) && threadIdx.x == 0) st->pshift = tot[1] > 0 ? tot[0] / tot[1] : 1.0;
+}
+
 // Spectrum quarter of the preconditioner (C_M + c I)^-1 in the scaling of
 // the stored kernel spectrum: Gq = eig(C_M)/M^2, so Pq = 1/((M^2 Gq + c) M^2).
 // Problem blockIdx.y of a batch writes its own spectrum (stride QQ).
@@ -2452,8 +2483,15 @@ int add_solve_nodes(fftconv_plan* p, const SolveView& V, int mode, bool precond,
         int gm = grid_1d(N, 256);
         if (gm > 512) gm = 512;
         if (gm > 3 * (p->L + 1) / 2) gm = 3 * (p->L + 1) / 2;  // the partial-sum buffer holds 3 (L+1) doubles
-        cudaGraphNode_t nm = gb.kernel(g, ndeps ? &nPro : nullptr, ndeps, (const void*)k_active_mean, V.grid(gm), 256,
-                                       0, N, sa, mk, pt, cst, bpart);
+        cudaGraphNode_t nm;
+        if (mixed) {  // from the FP32 copy of s the prologue has just made
+            const float* s32 = V.s32;
+            nm = gb.kernel(g, &nPro, 1, (const void*)k_active_mean_f32, V.grid(gm), 256, 0, N, s32, mk, pt, cst,
+                           bpart);
+        } else {
+            nm = gb.kernel(g, ndeps ? &nPro : nullptr, ndeps, (const void*)k_active_mean, V.grid(gm), 256, 0, N, sa,
+                           mk, pt, cst, bpart);
+        }
         const long QQ = (long)(p->M / 2 + 1) * (p->M / 2 + 1);
         const double MM = (double)p->M * (double)p->M;
         const double* g64 = (const double*)p->p64.Gq;
