@@ -89,7 +89,7 @@ typedef struct cg_opts {
     int refine_every;  /* cap on inner iterations between two true residuals
                           (0: 100000)                                           */
     int max_refine;    /* cap on true-residual evaluations (0: 60)              */
-    double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 1e-5 with
+    double inner_rtol; /* mixed: inner FP32 CG reduction per cycle (0: 3e-6 with
                           the preconditioner, 3e-3 without)                     */
     int x0_zero;       /* 1: start from x = 0 and ignore the input x; the first
                           true residual is then P b, taken without a product */

@@ -2720,8 +2720,10 @@ int init_state(const cg_opts* o, CgState* h) {
     *h = CgState{};
     h->rtol2 = o->rtol * o->rtol;
     // default inner reduction per refinement cycle: the preconditioned FP32
-    // solve stays accurate to 1e-5, plain FP32 CG drifts beyond about 3e-3
-    const double irt = o->inner_rtol > 0 ? o->inner_rtol : (o->precond ? 1e-5 : 3e-3);
+    // solve stays accurate to a few 1e-6 (3e-6 spent one FP64 product per
+    // breaking step where 1e-5 spent 1.08, at the same iteration count), plain
+    // FP32 CG drifts beyond about 3e-3
+    const double irt = o->inner_rtol > 0 ? o->inner_rtol : (o->precond ? 3e-6 : 3e-3);
     h->inner_rtol2 = irt * irt;
     {
         // the fraction of the outer target at which an inner run may stop
