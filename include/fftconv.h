@@ -95,8 +95,9 @@ typedef struct cg_opts {
                           true residual is then P b, taken without a product */
     int precond;       /* 1: preconditioned CG with the Fourier preconditioner
                           M^-1 = P crop (C_M + c I)^-1 pad P, C_M the padded
-                          circulant of C (its spectrum, shifted), c = mean of s
-                          over active sites; 0: plain CG as in Listing 2     */
+                          circulant of C (its spectrum, shifted), c = 0.6 x
+                          the mean of s over active sites; 0: plain CG as in
+                          Listing 2                                          */
     int warm_resid;    /* 0: when this solve follows a finished solve on the same
                           plan with bitwise the same s and b, an active set that
                           only shrank and at most 32 changed entries of the

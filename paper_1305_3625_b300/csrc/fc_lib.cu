@@ -277,8 +277,15 @@ __global__ void k_f64_to_f32(long N, const double* a, float* b, const CgState* s
         b[i] = (float)a[i];
 }
 
-// Shift of the Fourier preconditioner: c = mean of s over active sites
-// (last block writes it).  Problem blockIdx.y of a batch (vectors at stride
+// The preconditioner's shift c as a fraction of the mean of s over the active
+// sites.  Measured on breaking loops (60 steps, mixed PCG to 1e-10): 0.6 took
+// the iterations per solve from 9.95 to 9.32 at L = 1024, 10.35 to 9.8 at
+// L = 512 and 11.1 to 10.3 at L = 128 against the plain mean (1.0); 0.2 and
+// 2.0 both took more than 1.0.
+constexpr double kPrecondShiftScale = 0.6;
+
+// Shift of the Fourier preconditioner: c = kPrecondShiftScale x the mean of
+// s over active sites (last block writes it).  Problem blockIdx.y of a batch (vectors at stride
 // N, partial sums at stride bpart).
 __global__ void __launch_bounds__(256) k_active_mean(long N, const double* s, const uint8_t* mask, double* part,
                                                      CgState* st, long bpart) {
@@ -307,7 +314,8 @@ __global__ void __launch_bounds__(256) k_active_mean(long N, const double* s, co
             }
     }
     double v[2] = {sum, (double)cnt}, tot[2];
-    if (grid_sum_last<2>(v, part, &st->cntA, tot) && threadIdx.x == 0) st->pshift = tot[1] > 0 ? tot[0] / tot[1] : 1.0;
+    if (grid_sum_last<2>(v, part, &st->cntA, tot) && threadIdx.x == 0)
+        st->pshift = tot[1] > 0 ? kPrecondShiftScale * tot[0] / tot[1] : 1.0;
 }
 
 // The same shift from the FP32 copy of s (mixed solves): two-float sums on
@@ -338,7 +346,8 @@ __global__ void __launch_bounds__(256) k_active_mean_f32(long N, const float* s,
             }
     }
     double tot[2];
-    if (grid_sum_last<2>(a, part, &st->cntA, tot) && threadIdx.x == 0) st->pshift = tot[1] > 0 ? tot[0] / tot[1] : 1.0;
+    if (grid_sum_last<2>(a, part, &st->cntA, tot) && threadIdx.x == 0)
+        st->pshift = tot[1] > 0 ? kPrecondShiftScale * tot[0] / tot[1] : 1.0;
 }
 
 // Spectrum quarter of the preconditioner (C_M + c I)^-1 in the scaling of
@@ -2474,7 +2483,7 @@ int add_solve_nodes(fftconv_plan* p, const SolveView& V, int mode, bool precond,
         ndeps = 1;
     }
     if (precond) {
-        // preconditioner shift c = mean active s, then its spectrum quarter
+        // preconditioner shift c = 0.6 x mean active s, then its spectrum quarter
         const double* sa = V.s64;
         const uint8_t* mk = V.mask;
         double* pt = V.part;
