@@ -896,7 +896,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--f64-steps", type=int, default=6, dest="f64_steps")
-    ap.add_argument("--e2e-steps", type=int, default=30, dest="e2e_steps")
+    ap.add_argument("--e2e-steps", type=int, default=100, dest="e2e_steps")
     ap.add_argument("--cpu-budget", type=float, default=12.0, dest="cpu_budget",
                     help="seconds of timed warm oracle steps in the cpu_baseline leg (at least one step)")
     ap.add_argument("--big", type=int, default=1)

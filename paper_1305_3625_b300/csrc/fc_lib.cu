@@ -821,6 +821,8 @@ int set_smem_attr(const KV& k) {
         FC_CK(cudaFuncSetAttribute(k.f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
     if (k.fp && k.smem > 48 * 1024)
         FC_CK(cudaFuncSetAttribute(k.fp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
+    if (k.fplain && k.smem > 48 * 1024)
+        FC_CK(cudaFuncSetAttribute(k.fplain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem));
     return FC_OK;
 }
 
@@ -1110,10 +1112,11 @@ int build_stage_tables(fftconv_plan* p, PrecRes& R, const cpx<double>* tw64, cud
 //
 // Each pass has a few compiled launch shapes (values per thread E, rows or
 // columns per block).  At plan creation the tuner times every shape of each
-// pass on the plan's own size (median-free: the mean of 5 launches after 2
-// warm-ups, on a private stream) and keeps the fastest; choices are cached
-// per (precision, M, L, pass) in a text file (FC_TUNE_CACHE, default
-// $HOME/.cache/fftconv/tune_sm103.txt).  FC_AUTOTUNE=0 skips the timing.
+// pass on the plan's own size (the mean of 20 programmatic launches back to
+// back after 3 warm-ups, on a private stream) and keeps the fastest; choices
+// are cached per (precision, M, L, pass) in a text file (FC_TUNE_CACHE,
+// default $HOME/.cache/fftconv/tune_sm103.txt; keys carry the timing's
+// version, "t2").  FC_AUTOTUNE=0 skips the timing.
 
 namespace {
 
@@ -1247,20 +1250,28 @@ int time_shape(fftconv_plan* p, PrecRes& R, int kind, int k, T* x, T* y, cudaStr
     }
     const int grid = kind == 1 ? col_grid(p, kv) : row_grid(p, kv);
     auto go = [&]() -> int {
-        if (kind == 0) return launch(cgv && kv.fp ? kv.fp : kv.f, grid, kv.threads, kv.smem, s, a);
-        if (kind == 1) return launch(kv.f, grid, kv.threads, kv.smem, s, b);
-        return launch_rinv<T>(p, R, kv, c, s, false);
+        // programmatic launches back to back, as the passes run in an apply
+        // or a solve (a shape that keeps more blocks resident overlaps the
+        // next launch's start better)
+        if (kind == 0)
+            return launch_dep(cgv ? (kv.fp ? kv.fp : kv.f) : (kv.fplain ? kv.fplain : kv.f), grid, kv.threads,
+                              kv.smem, s, a);
+        if (kind == 1) return launch_dep(kv.f, grid, kv.threads, kv.smem, s, b);
+        KV kc = kv;
+        if (!cgv && kc.fplain) kc.f = kc.fplain;  // the apply's plain form
+        return launch_rinv<T>(p, R, kc, c, s, true);
     };
+    constexpr int kTimed = 20;
     int rc = FC_OK;
-    for (int w = 0; w < 2 && !rc; ++w) rc = go();
+    for (int w = 0; w < 3 && !rc; ++w) rc = go();
     if (rc) return rc;
     FC_CK(cudaEventRecord(e0, s));
-    for (int w = 0; w < 5 && !rc; ++w) rc = go();
+    for (int w = 0; w < kTimed && !rc; ++w) rc = go();
     if (rc) return rc;
     FC_CK(cudaEventRecord(e1, s));
     FC_CK(cudaEventSynchronize(e1));
     FC_CK(cudaEventElapsedTime(ms, e0, e1));
-    *ms /= 5.0f;
+    *ms /= (float)kTimed;
     return FC_OK;
 }
 
@@ -1293,7 +1304,7 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
         R.sel[kind] = 0;
         R.sel_cg[kind] = 0;
         if (n[kind] <= 1) continue;
-        snprintf(keys[kind], sizeof(keys[kind]), "%s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M,
+        snprintf(keys[kind], sizeof(keys[kind]), "t2 %s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M,
                  p->L, names[kind], n[kind]);
         int idx = 0;
         if (tune_lookup(keys[kind], &idx) && idx >= 0 && idx < n[kind] && !(kind == 2 && R.v.rinv[idx].tma && !R.tma_ok))
@@ -1302,7 +1313,8 @@ int autotune(fftconv_plan* p, PrecRes& R, const cg_tune* tune) {
             need[kind] = timing;
         R.sel_cg[kind] = R.sel[kind];  // the column pass is the same in every mode
         if (kind == 1 || sizeof(T) != 4 || !(p->prec & FC_F64)) continue;  // solves: FP32 passes of mixed plans
-        snprintf(keys_cg[kind], sizeof(keys_cg[kind]), "f32 M=%d L=%d %s_cg n=%d ", p->M, p->L, names[kind], n[kind]);
+        snprintf(keys_cg[kind], sizeof(keys_cg[kind]), "t2 f32 M=%d L=%d %s_cg n=%d ", p->M, p->L, names[kind],
+                 n[kind]);
         if (tune_lookup(keys_cg[kind], &idx) && idx >= 0 && idx < n[kind] &&
             !(kind == 2 && R.v.rinv[idx].tma && !R.tma_ok))
             R.sel_cg[kind] = idx;
@@ -1419,7 +1431,7 @@ int autotune_batched(fftconv_plan* p, PrecRes& R) {
     bool need[3] = {false, false, false};
     for (int kind = 0; kind < 3; ++kind) {
         if (n[kind] <= 1) continue;
-        snprintf(keys[kind], sizeof(keys[kind]), "%s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M, p->L,
+        snprintf(keys[kind], sizeof(keys[kind]), "t2 %s M=%d L=%d %s n=%d ", sizeof(T) == 4 ? "f32" : "f64", p->M, p->L,
                  names[kind], n[kind]);
         int idx = 0;
         if (tune_lookup(keys[kind], &idx) && idx >= 0 && idx < n[kind] && lists[kind][idx].f)
@@ -1932,10 +1944,12 @@ int apply_t(fftconv_plan* p, PrecRes& R, const T* x, T* y, cudaStream_t s) {
     a.x = x;
     a.st = p->st;
     a.part = p->part;
-    const KV &ka = R.rfwd(), &kb = R.colc(), &kc = R.rinv();
+    const KV &ka = R.rfwd(), &kb = R.colc();
+    KV kc = R.rinv();
+    if (kc.fplain) kc.f = kc.fplain;  // the plain-apply forms
     a.Z = (cpx<T>*)R.Z;
     a.tw = (const cpx<T>*)R.tws(ka.E);
-    int rc = launch(ka.f, row_grid(p, ka), ka.threads, ka.smem, s, a);
+    int rc = launch(ka.fplain ? ka.fplain : ka.f, row_grid(p, ka), ka.threads, ka.smem, s, a);
     if (rc) return rc;
     ColArgs<T> b{p->L, (cpx<T>*)R.Z, (const T*)R.Gq, (const cpx<T>*)R.tws(kb.E)};
     rc = launch_dep(kb.f, col_grid(p, kb), kb.threads, kb.smem, s, b);

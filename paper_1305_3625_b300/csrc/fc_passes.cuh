@@ -619,15 +619,17 @@ __device__ __forceinline__ void rfwd_transform(const RowFwdArgs<T>& a, cpx<T> (&
 // per pair.  Leaves shared memory in use: the caller synchronises before the
 // block reuses it.  vo, zo: the problem's offsets in the vectors and the
 // intermediate.
-template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
+// MODE >= 0: the mode fixed at compile time (the other modes' code is not
+// emitted).
+template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>(), int MODE = -1>
 __device__ __forceinline__ void rfwd_unit(const RowFwdArgs<T>& a, const AScal<T>& sc, int unit, cpx<T>* sm,
                                           size_t vo = 0, size_t zo = 0) {
     constexpr int G = M / E;
     const int t = threadIdx.x, j = t % G, pl = t / G;
     const int r0 = (unit * RB + pl) * 2;
     cpx<T> v[E];
-    pass_a_inputs<T, M, E>(a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask, sc, j, r0, a.L, vo,
-                           v);
+    pass_a_inputs<T, M, E>(MODE >= 0 ? MODE : a.mode, a.x, a.cx, a.cr, a.cp, a.cq, a.cz, a.r64, a.x64, a.d32, a.mask,
+                           sc, j, r0, a.L, vo, v);
     rfwd_transform<T, M, E, RB, DB>(a, v, unit, sm, zo);
 }
 
@@ -738,6 +740,19 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_pcg(const RowFwdArgs<
     } else {
         rfwd_unit<T, M, E, RB, DB>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
     }
+    pdl_leave();
+}
+
+// Pass A of the plain apply y = C x (RF_PLAIN only: a kernel of its own with
+// none of the other modes' code, which made the general kernel's
+// instruction footprint larger).
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_plain(const RowFwdArgs<T> a) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
+    const AScal<T> sc{0, 0, 0, 0, 1.0, 0.0};
+    rfwd_unit<T, M, E, RB, DB, RF_PLAIN>(a, sc, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
     pdl_leave();
 }
 
@@ -977,7 +992,7 @@ __device__ __forceinline__ void pass_c_outputs(int mode, T* __restrict__ y, cons
 
 // One unit of pass C: RB row pairs starting at pair unit*RB.  Adds this
 // thread's partial sums to s0 .. s4.  vo, zo: the problem's offsets.
-template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>()>
+template <typename T, int M, int E, int RB, bool DB = use_db<T, M, RB>(), int MODE = -1>
 __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<T>* sm, Acc<T>& s0, Acc<T>& s1,
                                           Acc<T>& s2, Acc<T>& s3, Acc<T>& s4, size_t vo = 0, size_t zo = 0) {
     using C = cpx<T>;
@@ -1028,8 +1043,8 @@ __device__ __forceinline__ void rinv_unit(const RowInvArgs<T>& a, int unit, cpx<
     if constexpr (!DB) __syncthreads();
     // with two buffers the first exchange writes buffer 1 while buffer 0 is still being read
     fft_stages<T, M, E, true, DB, DB ? 1 : 0>(v, j, g0, g0 + SEG, a.tw);
-    pass_c_outputs<T, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j, r0, L, vo,
-                            v, s0, s1, s2, s3, s4);
+    pass_c_outputs<T, M, E>(MODE >= 0 ? MODE : a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64,
+                            a.r64, j, r0, L, vo, v, s0, s1, s2, s3, s4);
 }
 
 // Pass C's grid sums and step decisions (last block; the PCG modes only
@@ -1076,6 +1091,17 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv(const RowInvArgs<T> a
     }
     pdl_leave();
     rinv_sums(a, a.part, a.st, s0, s1, s2, s3, s4);
+}
+
+// Pass C of the plain apply (RI_PLAIN only, no sums), as k_rfwd_plain.
+template <typename T, int M, int E, int RB, int MINB = 1, bool DB = use_db<T, M, RB>()>
+__global__ void __launch_bounds__(RB*(M / E), MINB) k_rinv_plain(const RowInvArgs<T> a) {
+    static_assert((RB * (M / E)) % 32 == 0, "the block reductions need whole warps");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    pdl_enter();
+    Acc<T> s0, s1, s2, s3, s4;
+    rinv_unit<T, M, E, RB, DB, RI_PLAIN>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), s0, s1, s2, s3, s4);
+    pdl_leave();
 }
 
 // The batched form: problem blockIdx.y at the strides of bb, gated.

@@ -49,7 +49,9 @@ void add_row(Variants& v) {
     if constexpr (RB * (M / E) <= 1024 && pass_smem<T, M, RB, DB>() <= 200 * 1024) {
         KV f{(const void*)k_rfwd<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
         f.fp = (const void*)k_rfwd_pcg<T, M, E, RB, MINB, DB>;
+        f.fplain = (const void*)k_rfwd_plain<T, M, E, RB, MINB, DB>;
         KV i{(const void*)k_rinv<T, M, E, RB, MINB, DB>, RB * (M / E), RB, E, pass_smem<T, M, RB, DB>()};
+        i.fplain = (const void*)k_rinv_plain<T, M, E, RB, MINB, DB>;
         for (int k = 0; k < v.n_rfwd; ++k)
             if (v.rfwd[k].f == f.f) return;
         if (v.n_rfwd >= Variants::kMax || v.n_rinv >= Variants::kMax) return;

@@ -16,6 +16,7 @@ struct KV {
     size_t smem = 0;
     int tma = 0;  // 1: TMA-staged persistent pass C (k_rinv_tma; needs the plan's tensor map)
     const void* fp = nullptr;  // pass A: the same shape's PCG step-deciding kernel (k_rfwd_pcg)
+    const void* fplain = nullptr;  // passes A, C: the same shape's plain-apply kernel (k_rfwd_plain, k_rinv_plain)
 };
 
 // One compiled persistent inner-CG kernel: pass A/C shape (EA, RB) and
