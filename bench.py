@@ -43,7 +43,7 @@ L_BENCH = 1024
 RTOL = 1e-10
 # DRAM bytes (read + write) of the three FP32 passes of one L = 1024 apply, summed over the
 # passes of one ncu capture (cold cache per launch; the writes stay in L2)
-MATVEC_TRAFFIC_L1024 = 25.39e6
+MATVEC_TRAFFIC_L1024 = 25.2e6
 FRAC_GRADIENT = 2.0  # thresholds xi + 2 (iy + 1/2)/L in the fracture-run section
 METRIC = "CG matvec GB/s vs HBM peak; solves/sec + p50/p99 latency, mixed vs FP64 plain"
 WORKLOAD = ("quasi-static breaking loop, L=1024 (padded 2048^2 FFT): warm-started (preconditioned) CG to "
