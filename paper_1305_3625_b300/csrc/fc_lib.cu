@@ -545,22 +545,37 @@ __global__ void __launch_bounds__(256) k_warm_resid(long N, int L, const double*
     }
     __syncthreads();
     double v[2] = {0.0, 0.0}, tot[2];
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
-        const uint8_t m = mask[i];
-        const double r0 = r64[i], bv = b64[i];
-        double r = 0.0;
-        if (m) {
-            const int iy = (int)i / L, ix = (int)i - iy * L;  // L <= 4096: N < 2^31
-            r = r0;
-            for (unsigned k = 0; k < K; ++k) {
-                double a = gt[(size_t)abs(iy - ky[k]) * L + abs(ix - kx[k])];
-                if (i == ki[k]) a += s64[i];
-                r = fma(-kd[k], a, r);
-            }
-            v[1] = fma(bv, bv, v[1]);
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i0 = (long)blockIdx.x * blockDim.x + threadIdx.x; i0 < N; i0 += 4 * stride) {
+        uint8_t m[4];
+        double r0[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {  // every operand of the round loaded first
+            const long i = i0 + u * stride;
+            m[u] = i < N ? mask[i] : (uint8_t)0;
+            r0[u] = i < N ? r64[i] : 0.0;
+            bv[u] = i < N ? b64[i] : 0.0;
         }
-        r64[i] = r;
-        v[0] = fma(r, r, v[0]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long i = i0 + u * stride;
+            if (i >= N) break;
+            double r = 0.0;
+            if (m[u]) {
+                r = r0[u];
+                if (K) {
+                    const int iy = (int)i / L, ix = (int)i - iy * L;  // L <= 4096: N < 2^31
+                    for (unsigned k = 0; k < K; ++k) {
+                        double a = gt[(size_t)abs(iy - ky[k]) * L + abs(ix - kx[k])];
+                        if (i == ki[k]) a += s64[i];
+                        r = fma(-kd[k], a, r);
+                    }
+                }
+                v[1] = fma(bv[u], bv[u], v[1]);
+            }
+            r64[i] = r;
+            v[0] = fma(r, r, v[0]);
+        }
     }
     if (grid_sum_last<2>(v, part, &st->cntC, tot) && threadIdx.x == 0) {
         st->rr64 = tot[0];
@@ -2936,7 +2951,10 @@ extern "C" int cg_solve(fftconv_plan* p, const double* s, const double* b, doubl
         k_warm_check<<<grid_1d(N, 256), 256, 0, st>>>(N, s, b, x, mask, p->s64, p->b64, p->x64, p->mask, p->st,
                                                        p->widx, p->wdx);
         FC_CK(cudaGetLastError());
+        // two blocks per SM, each thread four sites per round: the FP64 block
+        // reductions of many small blocks had cost as much as the update itself
         int g = grid_1d(N, 256);
+        if (g > 2 * 148) g = 2 * 148;
         if (g > p->L + 1) g = p->L + 1;  // the partial-sum buffer holds 3 (L+1) doubles
         k_warm_resid<<<g, 256, 0, st>>>(N, p->L, p->gtab, p->mask, p->s64, p->b64, p->r64, p->part, p->st, p->widx,
                                         p->wdx);

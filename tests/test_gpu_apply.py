@@ -162,3 +162,38 @@ def test_autotune_writes_cache(tmp_path, monkeypatch):
     out2 = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     assert out.stdout == out2.stdout
     assert len(cache.read_text().splitlines()) == len(lines)
+
+
+def test_solver_shapes_chain_tuned_and_cached(tmp_path):
+    """A mixed plan's solver shapes (FC_SHAPES_SOLVE): passes A and C timed in
+    the preconditioned modes, then the close candidates paired as chains of
+    whole PCG iterations; the fastest pairing is the one kept and cached, and
+    a second plan reads it without timing again."""
+    import ast
+    import re
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = ("import paper_1305_3625_b300 as fc; p = fc.fftconv_plan_create(512, fc.FC_F32 | fc.FC_F64); "
+            "print(fc.fftconv_plan_shape_set(p, fc.FC_F32, fc.FC_SHAPES_SOLVE))")
+    env = dict(__import__("os").environ, FC_TUNE_CACHE=str(cache), FC_TUNE_VERBOSE="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    chosen = ast.literal_eval(out.stdout.strip().splitlines()[-1])["chosen"]
+    lines = cache.read_text().splitlines()
+    cached = {}
+    for ln in lines:
+        key, idx = ln.rsplit("|", 1)
+        cached[key.strip()] = int(idx)
+    a_key = [k for k in cached if "rfwd_cg" in k]
+    c_key = [k for k in cached if "rinv_cg" in k]
+    assert a_key and c_key, lines
+    assert cached[a_key[-1]] == chosen[0] and cached[c_key[-1]] == chosen[2]
+    chain = [(int(m.group(1)), int(m.group(2)), float(m.group(3)))
+             for m in re.finditer(r"PCG iteration, pass A (\d+), pass C (\d+): ([0-9.]+) us", out.stderr)]
+    if chain:
+        fastest = min(chain, key=lambda c: c[2])
+        assert (fastest[0], fastest[1]) == (chosen[0], chosen[2]), (chain, chosen)
+    out2 = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    assert out2.stdout == out.stdout
+    assert "PCG iteration" not in out2.stderr
+    assert len(cache.read_text().splitlines()) == len(lines)
