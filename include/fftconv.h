@@ -200,8 +200,10 @@ int fftconv_plan_solver(const fftconv_plan *p, int prec, int *n, int *chosen, in
  * block.
  *   FC_SHAPES_APPLY  fftconv_apply (timed in the plain modes at plan creation)
  *   FC_SHAPES_SOLVE  the passes inside cg_solve's graphs (FP32 passes of a
- *                    mixed plan timed again in the CG modes: the vector
- *                    updates and dot products of Listing 2 fused in)
+ *                    mixed plan timed again in the preconditioned solver's
+ *                    modes, the vector updates and dot products of Listing 2
+ *                    fused in; then the close candidates of passes A and C
+ *                    timed together as chains of whole PCG iterations)
  *   FC_SHAPES_BATCH  cg_solve_batch and the calls built on it: the batched
  *                    twins (blockIdx.y = problem), FP32 ones timed in the CG
  *                    modes on the first batched use of a mixed plan and kept
