@@ -126,10 +126,11 @@ def test_f32_only_plan_applies():
         fc.fftconv_apply_prec(p, fc.FC_F64, dev(x), torch.empty(L * L, device="cuda", dtype=torch.float64))
 
 
-@pytest.mark.parametrize("L", [3, 100, 128, 512, 1024, 2048])
+@pytest.mark.parametrize("L", [3, 100, 128, 512, 1024, 2048, 4096])
 def test_every_compiled_shape_matches(L):
     """Each launch shape the autotuner may pick gives the same operator (the
-    radix-32 shapes from L = 2048, M = 4096, on)."""
+    radix-32 shapes from L = 2048, M = 4096, on; L = 4096 runs the M = 8192
+    shapes the large instance uses)."""
     rng = np.random.default_rng(11)
     x = rng.standard_normal(L * L)
     x32 = dev(x, torch.float32)
