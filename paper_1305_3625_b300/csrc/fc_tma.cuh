@@ -96,7 +96,9 @@ __host__ __device__ constexpr size_t tma_buf_bytes(int M) {
 __host__ __device__ constexpr size_t tma_smem_bytes(int M) { return 2 * tma_buf_bytes(M) + 128; }
 __host__ __device__ constexpr int tma_box_cols(int M) { return M / 2 < 256 ? M / 2 : 256; }
 
-template <int M, int E>
+// MODE >= 0: the pass-C mode fixed at compile time (RI_PLAIN: the plain
+// apply's form, without the other modes' epilogues and sums).
+template <int M, int E, int MODE = -1>
 __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowInvTma P) {
     using C = cpx<float>;
     constexpr int G = M / E, H = M / 2, BK = tma_box_cols(M), NBOX = H / BK;
@@ -181,7 +183,8 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
         }
         __syncthreads();  // staged values consumed: the buffer becomes the exchange buffer
         fft_stages<float, M, E, true, false, 0>(v, j, buf[cur], buf[cur], a.tw);
-        pass_c_outputs<float, M, E>(a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64, a.s64, a.r64, j,
+        pass_c_outputs<float, M, E>(MODE >= 0 ? MODE : a.mode, a.y, a.s, a.cp, a.cr, a.cq, a.cz, a.mask, a.x64, a.b64,
+                                    a.s64, a.r64, j,
                                     2 * u, L, 0, v, s0, s1, s2, s3, s4);
         __syncthreads();  // exchanges done: the buffer may receive the copy issued next
     }
@@ -194,7 +197,7 @@ __global__ void __launch_bounds__(M / E) k_rinv_tma(const __grid_constant__ RowI
             if (pending[b]) mbar_wait_bounded(&bar[b], b ? ph1 : ph0, limit);
     }
     pdl_leave();  // every block still joins the grid reduction below
-    rinv_sums(a, a.part, a.st, s0, s1, s2, s3, s4);
+    if constexpr (MODE != RI_PLAIN) rinv_sums(a, a.part, a.st, s0, s1, s2, s3, s4);
 }
 
 }  // namespace fc

@@ -63,13 +63,17 @@ void add_row(Variants& v) {
     }
 }
 
-// TMA-staged pass C (FP32): one row pair per loop iteration, M/16 threads.
-template <int M>
+// TMA-staged pass C (FP32): one row pair per loop iteration, M/E threads.
+template <int M, int E = 16>
 void add_rinv_tma(Variants& v) {
     // whole warps per block (the block reductions shuffle across full warps)
-    if constexpr (M / 16 >= 32 && tma_smem_bytes(M) <= 200 * 1024) {
+    if constexpr (M / E >= 32 && tma_smem_bytes(M) <= 200 * 1024) {
         // no batched twin: rinv_b at this index stays empty
-        if (v.n_rinv < Variants::kMax) v.rinv[v.n_rinv++] = KV{(const void*)k_rinv_tma<M, 16>, M / 16, 1, 16, tma_smem_bytes(M), 1};
+        if (v.n_rinv < Variants::kMax) {
+            KV k{(const void*)k_rinv_tma<M, E>, M / E, 1, E, tma_smem_bytes(M), 1};
+            k.fplain = (const void*)k_rinv_tma<M, E, RI_PLAIN>;
+            v.rinv[v.n_rinv++] = k;
+        }
     }
 }
 
@@ -151,6 +155,7 @@ void make_variants(Variants& v) {
                 add_col<T, M, 32, clampi(512 / G32, 1, H)>(v);
             }
             add_rinv_tma<M>(v);
+            if constexpr (M >= 4096) add_rinv_tma<M, 32>(v);
         }
         add_pers<T, M, 16, 16, (M * M / 32 < 256 ? M * M / 32 : 256)>(v);
         add_pers<T, M, 16, 8, 256>(v);
