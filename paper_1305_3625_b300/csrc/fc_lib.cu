@@ -912,6 +912,8 @@ struct PrecRes {
             if (!ok(v.rfwd[k].E)) return false;
         for (int k = 0; k < v.n_colc; ++k)
             if (!ok(v.colc[k].E)) return false;
+        for (int k = 0; k < v.n_rinv; ++k)  // pass C shapes of their own (the TMA-staged ones)
+            if (!ok(v.rinv[k].E)) return false;
         for (int k = 0; k < v.n_pers; ++k)
             if (!ok(v.pers[k].EA) || !ok(v.pers[k].EB)) return false;
         return true;
@@ -1098,6 +1100,7 @@ int build_stage_tables(fftconv_plan* p, PrecRes& R, const cpx<double>* tw64, cud
     };
     for (int k = 0; k < R.v.n_rfwd; ++k) addE(R.v.rfwd[k].E);
     for (int k = 0; k < R.v.n_colc; ++k) addE(R.v.colc[k].E);
+    for (int k = 0; k < R.v.n_rinv; ++k) addE(R.v.rinv[k].E);  // the TMA-staged pass C has shapes of its own
     for (int k = 0; k < R.v.n_pers; ++k) {
         addE(R.v.pers[k].EA);
         addE(R.v.pers[k].EB);
