@@ -249,31 +249,16 @@ __device__ __forceinline__ void load_twiddles(const cpx<T>* __restrict__ blk, in
     for (int e = 1; e < R; ++e) w[e] = ldg_c(blk + e * NS + k);
 }
 
-// The barrier of an exchange: a transform held by exactly one warp (G = 32
-// consecutive threads, WG) exchanges within that warp, so the warp alone
-// synchronises; the block's other warps (other transforms) go on.  Larger
-// transforms, or groups whose threads are interleaved with other groups',
-// synchronise the block.
-template <int G, bool WG>
-__device__ __forceinline__ void exchange_barrier() {
-    if constexpr (G == 32 && WG)
-        __syncwarp();
-    else
-        __syncthreads();
-}
-
 // Stockham transform of one length-M sequence held by G = M/E threads as
 // v[e] = x[j + e*G] (thread j of its group); on return v[e] = X[j + e*G].
 // sm0/sm1: this group's two shared segments (seg_len(M) elements each).
 // With DB the exchanges alternate between them (starting with BUF) and need
 // one barrier each; without DB only sm0 is used and each exchange ends with
-// a second barrier (exchange_barrier: the warp's own when G = 32).  tws: the
-// stage twiddle table of (M, E).  ZH: the upper half of the sequence is zero
-// (x[n] = 0 for n >= M/2, so v[e] = 0 for e >= E/2: the zero padding), which
-// the first stage skips.  WG: each group of G threads is consecutive in the
-// block (false: the groups are interleaved).  All threads of the block call
-// this together.
-template <typename T, int M, int E, bool INV, bool DB, int BUF = 0, int NS = 1, bool ZH = false, bool WG = true>
+// a second barrier.  tws: the stage twiddle table of (M, E).  ZH: the
+// upper half of the sequence is zero (x[n] = 0 for n >= M/2, so v[e] = 0 for
+// e >= E/2: the zero padding), which the first stage skips.  All threads of
+// the block call this together.
+template <typename T, int M, int E, bool INV, bool DB, int BUF = 0, int NS = 1, bool ZH = false>
 __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, cpx<T>* sm1,
                                            const cpx<T>* __restrict__ tws) {
     constexpr int G = M / E;
@@ -295,12 +280,12 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, c
             cpx<T>* wp = sm + spad<P>((j / NS) * NS * E + k);
 #pragma unroll
             for (int e = 0; e < E; ++e) wp[pofs<P>(e * NS)] = v[e];
-            exchange_barrier<G, WG>();
+            __syncthreads();
             const cpx<T>* rp = sm + spad<P>(j);
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = rp[pofs<P>(e * G)];
-            if constexpr (!DB) exchange_barrier<G, WG>();
-            fft_stages<T, M, E, INV, DB, DB ? 1 - BUF : 0, NS * E, false, WG>(v, j, sm0, sm1, tws);
+            if constexpr (!DB) __syncthreads();
+            fft_stages<T, M, E, INV, DB, DB ? 1 - BUF : 0, NS * E>(v, j, sm0, sm1, tws);
         }
     } else {
         constexpr int R = M / NS;  // 2 <= R < E, last stage

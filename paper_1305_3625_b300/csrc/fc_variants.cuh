@@ -37,8 +37,7 @@ __global__ void __launch_bounds__(CB*(M / E)) k_cols_full(cpx<double>* K, const 
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = K[(size_t)(j + e * G) * M + col];
-    // the column groups are interleaved (thread c + CB j): block barriers
-    fft_stages<double, M, E, false, false, 0, 1, false, false>(v, j, sm + c * seg_len(M), sm + c * seg_len(M), tw);
+    fft_stages<double, M, E, false, false, 0>(v, j, sm + c * seg_len(M), sm + c * seg_len(M), tw);
 #pragma unroll
     for (int e = 0; e < E; ++e) K[(size_t)(j + e * G) * M + col] = v[e];
 }
