@@ -256,9 +256,23 @@ __device__ __forceinline__ void load_twiddles(const cpx<T>* __restrict__ blk, in
 // one barrier each; without DB only sm0 is used and each exchange ends with
 // a second barrier.  tws: the stage twiddle table of (M, E).  ZH: the
 // upper half of the sequence is zero (x[n] = 0 for n >= M/2, so v[e] = 0 for
-// e >= E/2: the zero padding), which the first stage skips.  All threads of
+// e >= E/2: the zero padding), which the first stage skips.  GB: the
+// exchanges synchronise each group alone (exchange_sync).  All threads of
 // the block call this together.
-template <typename T, int M, int E, bool INV, bool DB, int BUF = 0, int NS = 1, bool ZH = false>
+// The barrier of an exchange.  GB: each group of G threads (whole warps,
+// consecutive in the block: group threadIdx.x / G, at most 15 groups) waits
+// only for itself on its own named barrier, 1 + group; otherwise the block.
+template <int G, bool GB>
+__device__ __forceinline__ void exchange_sync() {
+    if constexpr (GB) {
+        static_assert(G % 32 == 0, "group barriers need whole warps");
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / G)), "n"(G) : "memory");
+    } else {
+        __syncthreads();
+    }
+}
+
+template <typename T, int M, int E, bool INV, bool DB, int BUF = 0, int NS = 1, bool ZH = false, bool GB = false>
 __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, cpx<T>* sm1,
                                            const cpx<T>* __restrict__ tws) {
     constexpr int G = M / E;
@@ -280,12 +294,12 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int j, cpx<T>* sm0, c
             cpx<T>* wp = sm + spad<P>((j / NS) * NS * E + k);
 #pragma unroll
             for (int e = 0; e < E; ++e) wp[pofs<P>(e * NS)] = v[e];
-            __syncthreads();
+            exchange_sync<G, GB>();
             const cpx<T>* rp = sm + spad<P>(j);
 #pragma unroll
             for (int e = 0; e < E; ++e) v[e] = rp[pofs<P>(e * G)];
-            if constexpr (!DB) __syncthreads();
-            fft_stages<T, M, E, INV, DB, DB ? 1 - BUF : 0, NS * E>(v, j, sm0, sm1, tws);
+            if constexpr (!DB) exchange_sync<G, GB>();
+            fft_stages<T, M, E, INV, DB, DB ? 1 - BUF : 0, NS * E, false, GB>(v, j, sm0, sm1, tws);
         }
     } else {
         constexpr int R = M / NS;  // 2 <= R < E, last stage

@@ -788,7 +788,9 @@ __global__ void __launch_bounds__(RB*(M / E), MINB) k_rfwd_b(const RowFwdArgs<T>
 // One unit of pass B: CB columns starting at column unit*CB, G = M/E threads
 // per column (j fastest).  Unit 0 holds the packed column 0.  zo, qo: the
 // problem's offsets in the intermediate and the spectrum.
-template <typename T, int M, int E, int CB, bool DB = use_db<T, M, CB>()>
+// GB: the transforms' exchanges synchronise each column's threads alone
+// (named barriers), so that the block's columns need not keep step.
+template <typename T, int M, int E, int CB, bool DB = use_db<T, M, CB>(), bool GB = false>
 __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>* sm, size_t zo = 0, size_t qo = 0) {
     using C = cpx<T>;
     constexpr int G = M / E, H = M / 2, Q = M / 2 + 1, SEG = seg_len(M);
@@ -807,7 +809,7 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
         v[e] = (e < E / 2 && n < L) ? ldc_cg(col + n) : C{0, 0};
     }
     C* g0 = sm + c * GS;
-    fft_stages<T, M, E, false, DB, 0, 1, true>(v, j, g0, g0 + SEG, a.tw);
+    fft_stages<T, M, E, false, DB, 0, 1, true, GB>(v, j, g0, g0 + SEG, a.tw);
     if (unit == 0) {
         // column 0 holds P = F0 + i FN (kx = 0 and kx = M/2, both real along y);
         // with the Hermitian partner P[M - ky]: W = P (g0 + gN)/2 + conj(P[M-ky]) (g0 - gN)/2
@@ -846,7 +848,7 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
             v[e].y *= g;
         }
     }
-    fft_stages<T, M, E, true, DB, NB>(v, j, g0, g0 + SEG, a.tw);
+    fft_stages<T, M, E, true, DB, NB, 1, false, GB>(v, j, g0, g0 + SEG, a.tw);
 #pragma unroll
     for (int e = 0; e < E / 2; ++e) {
         const int n = j + e * G;
@@ -854,24 +856,24 @@ __device__ __forceinline__ void colc_unit(const ColArgs<T>& a, int unit, cpx<T>*
     }
 }
 
-template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
+template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>(), bool GB = false>
 __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc(const ColArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     if (a.gate && gate_closed(a.st, a.gate)) return;
     if (a.pcg_commit && blockIdx.x == 0 && threadIdx.x == 0) pcg_rz_commit(a.st);
-    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
+    colc_unit<T, M, E, CB, DB, GB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw));
     pdl_leave();
 }
 
-template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
+template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>(), bool GB = false>
 __global__ void __launch_bounds__(CB*(M / E), MINB) k_colc_b(const ColArgs<T> a, const BatchArgs bb) {
     extern __shared__ __align__(16) unsigned char smraw[];
     pdl_enter();
     if ((a.gate | bb.gate) && gate_closed(a.st + blockIdx.y, a.gate | bb.gate)) return;
     if (a.pcg_commit && blockIdx.x == 0 && threadIdx.x == 0) pcg_rz_commit(a.st + blockIdx.y);
-    colc_unit<T, M, E, CB, DB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * bb.bs.z,
-                               (size_t)blockIdx.y * bb.bs.q);
+    colc_unit<T, M, E, CB, DB, GB>(a, blockIdx.x, reinterpret_cast<cpx<T>*>(smraw), (size_t)blockIdx.y * bb.bs.z,
+                                   (size_t)blockIdx.y * bb.bs.q);
     pdl_leave();
 }
 

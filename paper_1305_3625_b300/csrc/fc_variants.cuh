@@ -77,14 +77,15 @@ void add_rinv_tma(Variants& v) {
     }
 }
 
-template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>()>
+template <typename T, int M, int E, int CB, int MINB = 1, bool DB = use_db<T, M, CB>(), bool GB = false>
 void add_col(Variants& v) {
-    if constexpr (CB * (M / E) <= 1024 && pass_smem<T, M, CB, DB>() <= 200 * 1024) {
-        KV c{(const void*)k_colc<T, M, E, CB, MINB, DB>, CB * (M / E), CB, E, pass_smem<T, M, CB, DB>()};
+    if constexpr (CB * (M / E) <= 1024 && pass_smem<T, M, CB, DB>() <= 200 * 1024 &&
+                  (!GB || ((M / E) % 32 == 0 && CB > 1 && CB <= 15))) {
+        KV c{(const void*)k_colc<T, M, E, CB, MINB, DB, GB>, CB * (M / E), CB, E, pass_smem<T, M, CB, DB>()};
         for (int k = 0; k < v.n_colc; ++k)
             if (v.colc[k].f == c.f) return;
         if (v.n_colc >= Variants::kMax) return;
-        v.colc_b[v.n_colc] = KV{(const void*)k_colc_b<T, M, E, CB, MINB, DB>, c.threads, CB, E, c.smem};
+        v.colc_b[v.n_colc] = KV{(const void*)k_colc_b<T, M, E, CB, MINB, DB, GB>, c.threads, CB, E, c.smem};
         v.colc[v.n_colc++] = c;
     }
 }
@@ -153,6 +154,8 @@ void make_variants(Variants& v) {
                 add_col<T, M, 32, clampi(256 / G32, 1, H)>(v);
                 add_col<T, M, 32, clampi(256 / G32, 1, H), 2>(v);
                 add_col<T, M, 32, clampi(512 / G32, 1, H)>(v);
+                // the same with each column's exchanges on its own named barrier
+                add_col<T, M, 32, clampi(512 / G32, 1, H), 1, use_db<T, M, clampi(512 / G32, 1, H)>(), true>(v);
             }
             add_rinv_tma<M>(v);
             if constexpr (M >= 4096) add_rinv_tma<M, 32>(v);
